@@ -1,0 +1,204 @@
+/*
+ * cpcp.h -- C ABI of the GB300 multilevel CPCP library.
+ *
+ * The library solves the compressive principal component pursuit program
+ * (Sec. 2, eq. (cpcp)):
+ *
+ *     min_{L,S}  1/2 || P_Q[L + S - D] ||_F^2 + lambda_L ||L||_* + lambda_S ||S||_1
+ *
+ * with lambda_L = mu and lambda_S = lambda * mu, where lambda is the PCP weight
+ * of eq. (rpca) and mu > 0 the nuclear-norm weight.  Q is a set of observed
+ * entries (P_Q keeps them and zeroes the rest, Sec. 2); with Q = everything the
+ * program is the penalised form of PCP (eq. (rpca)).
+ *
+ * Each iteration is one accelerated proximal-gradient step with the joint step
+ * 1/2 fixed by the 2-Lipschitz gradient (Sec. 2.3, eq. (cpcp-grad-LS)).  Its
+ * L-prox is the multilevel step of Alg. 4: restrict M to the coarse model
+ * M_H = M R (Sec. 3.1), singular value thresholding there (Sec. 3.2, minimiser
+ * of the coarse Lagrangian), and prolongation L = L_H R^T.  Its S-prox is the
+ * soft threshold of Alg. 3.  R = R_n R_{n/2} ... R_{n_H} is the composite
+ * linear-interpolation operator of eq. (Rx), scaled to unit spectral norm
+ * (Assumption 4).  The solver starts on the coarsest level and moves one level
+ * finer when the fine-level residual stalls; it always finishes on the fine
+ * level, so single-level and multilevel runs share the optimum of eq. (cpcp).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major with an explicit leading dimension in elements
+ *     (ld >= number of columns).  "device" pointers are CUDA device pointers
+ *     on the handle's device; "host" pointers are ordinary CPU memory.
+ *   - Observation mask Q: bit-packed, row-major, ldq 32-bit words per row
+ *     (ldq >= ceil(n/32)); bit (j % 32) of word [i * ldq + j / 32] set means
+ *     entry (i, j) is observed.  NULL means every entry is observed (PCP).
+ *     Unobserved entries of D are never used arithmetically (NaN is allowed).
+ *   - dtype selects the storage and arithmetic type of D, L and S:
+ *     CPCP_F64 (fp64 throughout) or CPCP_F32 (fp32 storage and elementwise
+ *     arithmetic; the small dense factorisations and all reductions in fp64).
+ *   - All work is queued on the handle's stream.  Calls return after the
+ *     result is complete unless stated otherwise.
+ *   - No entry point aborts, exits or throws; every failure is a status code
+ *     and a message retrievable with cpcp_last_error().
+ *   - The library owns its workspace (device memory allocated on first use and
+ *     grown as needed); callers own every buffer they pass.
+ */
+#ifndef CPCP_H
+#define CPCP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CPCP_OK = 0,
+    CPCP_ERR_INVALID_ARG = 1,    /* argument out of range, NULL where required */
+    CPCP_ERR_NONFINITE_INPUT = 2,/* NaN/Inf in an observed entry of D */
+    CPCP_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    CPCP_ERR_NOMEM = 4,          /* workspace allocation failed */
+    CPCP_ERR_NOT_CONVERGED = 5,  /* iteration cap reached; best iterate returned */
+    CPCP_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired */
+    CPCP_ERR_NUMERIC = 7         /* unrecoverable numerical breakdown */
+} cpcp_status;
+
+typedef enum { CPCP_F32 = 0, CPCP_F64 = 1 } cpcp_dtype;
+
+typedef struct cpcp_context *cpcp_handle;
+
+/* Solver options.  Zero-initialised fields take the listed defaults. */
+typedef struct {
+    int max_iter;          /* iteration cap (default 5000) */
+    int check_every;       /* c: iterations between fine residual checks (10) */
+    double eta;            /* continuation factor, mu_k = max(mu0 eta^k, mu) (0.9) */
+    double mu0;            /* first weight; <= 0 means ||P_Q D||_2 (estimated) */
+    double switch_ratio;   /* move one level finer when rel-KKT > ratio * last (0.9) */
+    int k_max;             /* cap on the subspace width of the coarse SVD (256) */
+    int oversample;        /* p: extra subspace columns beyond the rank (10) */
+    int power_iters;       /* q: power steps per coarse SVD (1) */
+    int check_power_iters; /* power steps of the fine SVD in the residual check (2) */
+    int start_level;       /* 0 (default): start on the coarsest level; s > 0: start
+                              at min(s, levels) - 1 halvings (s = 1: fine level) */
+    uint64_t seed;         /* seed of the random start block of the subspace (1) */
+    double *trace;         /* optional host array: rel-KKT of each residual check */
+    int trace_cap;         /* capacity of trace (entries written: info.checks) */
+} cpcp_options;
+
+/* Per-solve report. */
+typedef struct {
+    int status;            /* cpcp_status of the solve */
+    int iters;             /* iterations taken */
+    int level_iters[8];    /* iterations spent at each number of halvings */
+    int final_level;       /* halvings when the solve stopped (0 = fine) */
+    int rank;              /* rank of the returned L */
+    int checks;            /* fine residual checks performed */
+    double relkkt;         /* last fine relative gradient-mapping residual */
+    double mu0;            /* first continuation weight used */
+    double pqd_fro;        /* ||P_Q D||_F */
+    double seconds;        /* wall time of the solve (host clock) */
+} cpcp_info;
+
+/* Returns a static description of a status code. */
+const char *cpcp_status_string(cpcp_status s);
+
+/* Last error message recorded on the handle (empty string if none).  The
+ * pointer stays valid until the next call on the same handle. */
+const char *cpcp_last_error(cpcp_handle h);
+
+/*
+ * Create a handle bound to CUDA device `device` and stream `stream` (a
+ * cudaStream_t passed as void*, NULL = the legacy default stream).  opt may be
+ * NULL for defaults; the options are copied.  *h receives the handle.
+ * Errors: INVALID_ARG (h NULL, bad device), CUDA.
+ */
+cpcp_status cpcp_create(cpcp_handle *h, int device, void *stream, const cpcp_options *opt);
+
+/* Release the handle and its workspace.  NULL is accepted and ignored. */
+void cpcp_destroy(cpcp_handle h);
+
+/*
+ * Solve eq. (cpcp) for D (m x n, dtype, leading dimension ldd) with mask Q.
+ *   lambda  > 0   weight ratio (lambda_S = lambda * mu)
+ *   mu      > 0   nuclear-norm weight lambda_L (final continuation value)
+ *   levels  >= 1  number of levels; 1 = single level, levels-1 halvings of n
+ *   tol     > 0   stop when the fine relative residual (below) is <= tol
+ *   L_out, S_out  m x n outputs (ldl, lds), may be NULL to skip
+ * The relative residual is the gradient-mapping norm
+ *   || (L - SVT_{mu/2}(L - G/2), S - shrink_{lambda mu/2}(S - G/2)) ||_F * 2
+ *   / ||P_Q D||_F with G = P_Q[L + S - D]; it is zero iff (L, S) is optimal.
+ * D, Q, L_out, S_out may be all device pointers or all host pointers (host
+ * buffers are staged through device memory inside the call).
+ * Validation (INVALID_ARG): m, n >= 1; lambda, mu, tol > 0; 1 <= levels <= 6;
+ * the coarse width n_H after levels-1 halvings (ceil(n/2) per level) must be
+ * >= 1 and, when levels > 1, n_H <= (m + 1) / 2 (Assumption 2).  If n > m
+ * the transposed problem is solved and the results transposed back, with the
+ * same rules applied to the transposed sizes.
+ * Returns OK, NOT_CONVERGED (outputs hold the last iterate), NONFINITE_INPUT,
+ * NOMEM, CUDA or NUMERIC.  info may be NULL.
+ */
+cpcp_status cpcp_solve(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D, int64_t ldd,
+                       const uint32_t *Q, int64_t ldq, double lambda, double mu, int levels, double tol,
+                       void *L_out, int64_t ldl, void *S_out, int64_t lds, cpcp_info *info);
+
+/*
+ * One accelerated proximal-gradient step of the multilevel method (the hot
+ * path of one iteration), on device buffers:
+ *   Lhat = (1 + beta) A_k B_k^T - beta A_p B_p^T        (momentum on L)
+ *   Shat = S_k + beta (S_k - S_p)                        (momentum on S)
+ *   G    = P_Q[Lhat + Shat - D]                          (eq. (cpcp-grad-LS))
+ *   S_out = shrink_{lambda mu_k / 2}(Shat - G/2)         (Alg. 3 threshold)
+ *   M_H  = (Lhat - G/2) R,   L_H = SVT_{mu_k/2}(M_H),   L_out = L_H R^T
+ *                                                        (Alg. 4, restrict/SVT/prolong)
+ * Factors: A_k (m x r_k, lda), B_k (n x r_k, ldb), A_p (m x r_p, ldap),
+ * B_p (n x r_p, ldbp) (a rank may be 0, its pointers are then unused).  R is the unit-norm composite operator
+ * for `halvings` halvings of n (0 = fine level).
+ * The coarse SVD runs subspace iteration with width k (1 <= k <= n_H) and q
+ * power steps from the start block Omega0 (n_H x k, ldo; NULL = seeded random);
+ * with k = n_H it is an exact SVD.
+ * Outputs: S_out (m x n, lds); the new factors A_out (m x k, ldao) =
+ * U diag(sigma - mu_k/2)_+ and B_out (n x k, ldbo) = R V; *r_out = number of
+ * singular values above mu_k/2 (columns beyond r_out are zero); sigma_out
+ * (k doubles, host or device; may be NULL) the coarse singular values.
+ * Requires n <= m (no internal transpose).  Errors: INVALID_ARG, NOMEM, CUDA.
+ */
+cpcp_status cpcp_step(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D, int64_t ldd, const uint32_t *Q,
+                      int64_t ldq, double lambda, double mu_k, double beta, int halvings, const void *S_k,
+                      const void *S_p, int64_t lds_in, const void *A_k, int64_t lda, const void *B_k, int64_t ldb,
+                      int r_k, const void *A_p, int64_t ldap, const void *B_p, int64_t ldbp, int r_p, int k, int q,
+                      const void *Omega0, int64_t ldo, void *S_out, int64_t lds, void *A_out, int64_t ldao,
+                      void *B_out, int64_t ldbo, int *r_out, double *sigma_out);
+
+/*
+ * Restriction M_H = M R (Sec. 3.1; the coarse matrix of Alg. 4):
+ * M (m x n, ldm) -> M_H (m x n_H, ldh), R the unit-norm composite operator for
+ * `halvings` halvings of n.  Device buffers.  Errors: INVALID_ARG, CUDA.
+ */
+cpcp_status cpcp_restrict(cpcp_handle h, int m, int n, int halvings, cpcp_dtype dt, const void *M, int64_t ldm,
+                          void *MH, int64_t ldh);
+
+/*
+ * Prolongation of right factors B = R V (Sec. 3.2, L = L_H R^T = U (R V)^T):
+ * V (n_H x r, ldv) -> B (n x r, ldb).  Device buffers.
+ */
+cpcp_status cpcp_prolong(cpcp_handle h, int n, int halvings, int r, cpcp_dtype dt, const void *V, int64_t ldv,
+                         void *B, int64_t ldb);
+
+/*
+ * Scale of the composite operator: *scale = 1 / ||R_printed||_2 for
+ * `halvings` halvings of n, and *nh = n_H.  Host only.
+ */
+cpcp_status cpcp_transfer_info(int n, int halvings, double *scale, int *nh);
+
+/*
+ * Truncated SVD of a device matrix M (m x n, ldm, m >= n) by subspace
+ * iteration of width k (1 <= k <= n) with q power steps from Omega0 (n x k,
+ * ldo; NULL = seeded random): M ~ U diag(sigma) V^T, U (m x k, ldu),
+ * V (n x k, ldv), sigma (k doubles, device or host).  Singular values are in
+ * descending order; with k = n the factorisation is exact up to rounding.
+ */
+cpcp_status cpcp_svd(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *M, int64_t ldm, int k, int q,
+                     const void *Omega0, int64_t ldo, void *U, int64_t ldu, void *V, int64_t ldv, double *sigma);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPCP_H */

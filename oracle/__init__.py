@@ -102,6 +102,9 @@ def _load():
                                     C.c_int, C.c_double, _dp, _dp, C.c_void_p, C.POINTER(C.c_double)]
             lib.or_ialm.restype = C.c_int
             lib.or_num_threads.restype = C.c_int
+            lib.or_step.argtypes = [C.c_int, C.c_int, _dp, C.c_void_p, C.c_double, C.c_double, C.c_double,
+                                    C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+            lib.or_step.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -237,6 +240,20 @@ def fista(D, mask, lam, mu, levels=1, tol=1e-10, *, tau=0.5, eta=0.9, mu0=0.0, c
             "status": inf.status, "relkkt": inf.relkkt, "objective": inf.objective,
             "level_iters": list(inf.level_iters), "trace": tr[:min(inf.checks, trace_cap)].copy()}
     return L, S, info
+
+
+def step(D, mask, lam, mu_k, beta, halvings, S_k, S_p, L_k, L_p):
+    """One step of the multilevel proximal-gradient iteration from a dense state
+    (momentum, eq. (cpcp-grad-LS), Alg. 3 shrink, Alg. 4 restrict/SVT/prolong).
+    Returns (S_out, L_out, rank)."""
+    D = _f64(D)
+    m, n = D.shape
+    mk, mp = _mask_ptr(mask, D.shape)
+    S_out = np.zeros((m, n))
+    L_out = np.zeros((m, n))
+    r = _load().or_step(m, n, D, mp, float(lam), float(mu_k), float(beta), int(halvings), _f64(S_k), _f64(S_p),
+                        _f64(L_k), _f64(L_p), S_out, L_out)
+    return S_out, L_out, int(r)
 
 
 def ialm(D, lam, levels=1, mu0=0.0, rho=0.0, max_iter=5000, tol=1e-7):

@@ -25,9 +25,10 @@
  *   * momentum: FISTA extrapolation on both L and S, restarted at level switches;
  *   * continuation: mu_k = max(mu_0 eta^k, mu_bar), eta = 0.9, mu_0 = ||P_Q D||_2;
  *   * residual: relative gradient-mapping norm at mu_bar on the fine level;
- *   * level switching: start coarsest; every c iterations once mu_k = mu_bar,
- *     stop if rel-KKT <= tol, else move one level finer if the residual fell
- *     by less than the switch ratio since the last check;
+ *   * level switching: start coarsest; every c iterations evaluate the fine
+ *     residual at the current weight mu_k; stop if mu_k = mu_bar and
+ *     rel-KKT <= tol, else move one level finer if the residual fell by less
+ *     than the switch ratio since the last check on this level;
  *   * R is scaled to unit spectral norm (Assumption 4);
  *   * odd n: coarse node j sits at fine index 2j-1;
  *   * n > m: the transposed problem is solved.
@@ -580,11 +581,13 @@ static int fista_core(int m, int n, const double *D, const unsigned char *mask, 
             }
             continue;
         }
-        if (mu_k == mu_bar && (k + 1) % c == 0) {
-            rel = relkkt_warm(m, n, D, mask, lam, mu_bar, tau, L, S, Vchk);
+        if ((k + 1) % c == 0) {
+            /* fine residual at the weight of this iteration; the stop test
+               needs the final weight, the switch test uses any weight */
+            rel = relkkt_warm(m, n, D, mask, lam, mu_k, tau, L, S, Vchk);
             if (trace && checks < trace_cap) trace[checks] = rel;
             checks++;
-            if (rel <= tol) {
+            if (mu_k == mu_bar && rel <= tol) {
                 k++;
                 status = OR_OK;
                 break;
@@ -627,6 +630,44 @@ static int fista_core(int m, int n, const double *D, const unsigned char *mask, 
     free(Ln);
     free(Sn);
     return status;
+}
+
+/*
+ * One step of the iteration above from an explicit state, with dense L:
+ *   Lhat = L_k + beta (L_k - L_p), Shat = S_k + beta (S_k - S_p)
+ *   G = P_Q[Lhat + Shat - D]                         eq. (cpcp-grad-LS)
+ *   S_out = shrink_{tau lam mu_k}(Shat - tau G)       Alg. 3 threshold
+ *   L_out = SVT_{tau mu_k}((Lhat - tau G) R) R^T       Alg. 4 (R = I if halvings = 0)
+ * Returns the rank of the coarse SVT.  Requires n <= m.
+ */
+int or_step(int m, int n, const double *D, const unsigned char *mask, double lam, double mu_k, double beta,
+            int halvings, const double *Sk, const double *Sp, const double *Lk, const double *Lp, double *S_out,
+            double *L_out)
+{
+    const double tau = 0.5;
+    size_t len = (size_t)m * n;
+    int nh = or_coarse_dim(n, halvings);
+    double *R = NULL;
+    if (halvings > 0) {
+        R = dalloc((size_t)n * nh);
+        or_restriction_scaled(n, halvings, R, NULL);
+    }
+    double *Lh = dalloc(len), *Sh = dalloc(len), *G = dalloc(len), *X = dalloc(len);
+    for (size_t i = 0; i < len; i++) {
+        Lh[i] = Lk[i] + beta * (Lk[i] - Lp[i]);
+        Sh[i] = Sk[i] + beta * (Sk[i] - Sp[i]);
+    }
+    or_grad(m, n, D, mask, Lh, Sh, G);
+    for (size_t i = 0; i < len; i++) X[i] = Sh[i] - tau * G[i];
+    or_shrink(len, X, tau * lam * mu_k, S_out);
+    for (size_t i = 0; i < len; i++) X[i] = Lh[i] - tau * G[i];
+    int r = ml_prox_L(m, n, nh, R, X, tau * mu_k, L_out, NULL);
+    free(R);
+    free(Lh);
+    free(Sh);
+    free(G);
+    free(X);
+    return r;
 }
 
 /*

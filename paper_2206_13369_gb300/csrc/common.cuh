@@ -1,0 +1,165 @@
+// common.cuh -- shared device helpers and launch declarations of the CUDA
+// library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+
+namespace cpcp {
+
+// Device-resident scalars of one solve.  The per-iteration schedule (momentum
+// weight, continuation weight, thresholds, ranks, subspace width) lives here
+// so that an iteration needs no host round trip and can be graph-captured.
+struct Ctrl {
+    double tau;      // step 1/2 (2-Lipschitz gradient)
+    double lam;      // lambda (lambda_S = lam * mu)
+    double mu_bar;   // final weight mu
+    double mu0;      // first continuation weight
+    double eta;      // continuation factor
+    double t;        // FISTA t_k
+    double beta;     // momentum weight of the current iteration
+    double mu_k;     // weight of the current iteration
+    double theta_L;  // tau * mu_k
+    double theta_S;  // tau * lam * mu_k
+    double t_next;   // FISTA t_{k+1}
+    int iter;        // iterations done
+    int rk;          // rank of L_k factors
+    int rp;          // rank of L_{k-1} factors
+    int r_new;       // rank produced by the current iteration
+    int k;           // active subspace width of the coarse SVD
+    int k_next;      // width for the next iteration
+    int kcap;        // min(n_H, k_max) on the current level
+    int oversample;  // p
+    int flags;       // bit 0: rank reached the width at least once
+    int pad_;
+    uint64_t seed;
+};
+
+// shrink(x) = sign(x) max(|x| - th, 0), with a signed zero inside the band
+template <typename T>
+__device__ __forceinline__ T shrink(T x, T th)
+{
+    T a = fabs(x) - th;
+    return a > T(0) ? copysign(a, x) : copysign(T(0), x);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// splitmix64 (Steele, Lea, Flood 2014) -> uniform in [-1, 1)
+__host__ __device__ __forceinline__ double hash_uniform(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x = x ^ (x >> 31);
+    return (double)(x >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
+// Composite transfer operator of one level on the device: fine column j maps
+// to coarse columns j0[j] (weight w0[j]) and j0[j] + 1 (weight w1[j]);
+// coarse column c draws on the contiguous fine range [clo[c], chi[c]].
+template <typename T>
+struct TransferDev {
+    int n, nh;
+    const int *j0;
+    const T *w0, *w1;
+    const int *clo, *chi;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the .cu files); all asynchronous on `st`
+// ---------------------------------------------------------------------------
+
+// Fused iteration pass (momentum, masked gradient, shrink, restriction).
+template <typename T>
+struct PassArgs {
+    int m, n;
+    const T *D;
+    int64_t ldd;
+    const uint32_t *Q;
+    int64_t ldq;
+    const T *Sk, *Sp;  // S_k, S_{k-1}
+    int64_t lds;
+    T *Sout;           // S_{k+1} (step) or nullptr
+    int64_t ldso;
+    const T *Ak, *Bk, *Ap, *Bp;  // low-rank factors (row-major)
+    int64_t ldfa, ldfb;          // leading dimensions of Ak, Bk
+    int64_t ldfap, ldfbp;        // leading dimensions of Ap, Bp
+    const int *rk, *rp;          // device ranks of (Ak, Bk) and (Ap, Bp); may be null (= 0)
+    const Ctrl *ctrl;
+    T *M;              // fine output (level 0) or nullptr
+    int64_t ldm;
+    T *MH;             // coarse output (level > 0), zero on entry
+    int64_t ldh;
+    TransferDev<T> tr;
+    double *partial;   // per-block fp64 partial sums (check / norm passes)
+};
+
+template <typename T> void launch_step_pass(const PassArgs<T> &a, bool coarse, cudaStream_t st);
+// check pass at (L_k, S_k) with weight mu_bar: writes M = L - tau G and
+// per-block sums of ||S - shrink(S - tau G)||^2 (slot 0), ||P_Q D||^2 (slot 1),
+// count of non-finite observed D (slot 2).
+template <typename T> int launch_check_pass(const PassArgs<T> &a, cudaStream_t st);
+// per-block sums of ||A_k B_k^T - A_p B_p^T||^2 (factors with ranks rk, rp from ctrl)
+template <typename T> int launch_diff_pass(const PassArgs<T> &a, cudaStream_t st);
+// dense L = A_k B_k^T into a.M (rank from a.rk)
+template <typename T> void launch_reconstruct(const PassArgs<T> &a, cudaStream_t st);
+void launch_sum_partials(const double *partial, int nblocks, int nslots, double *out, cudaStream_t st);
+
+// dense GEMMs on row-major tall-skinny operands
+template <typename T>
+void launch_gemm_nn(int rows, int K, const T *A, int64_t lda, const T *B, int64_t ldb, T *C, int64_t ldc,
+                    const int *kdyn_K, const int *kdyn_N, int kmaxN, cudaStream_t st);
+template <typename T>
+void launch_gemm_nn_splitk(int rows, int K, const T *A, int64_t lda, const T *B, int64_t ldb, T *C, int64_t ldc,
+                           T *partial, const int *kdyn_N, int kmaxN, cudaStream_t st);
+template <typename T>
+int launch_gemm_tn_partial(int rows, int K, const T *A, int64_t lda, const T *B, int64_t ldb, T *partial,
+                           const int *kdyn_N, int kmaxN, int kmaxK, cudaStream_t st);
+template <typename T>
+void launch_reduce_partial(const T *partial, int splits, int K, int N, T *C, int64_t ldc, const int *kdyn_K,
+                           const int *kdyn_N, cudaStream_t st);
+template <typename T>
+void launch_restrict(int m, int n, const T *M, int64_t ldm, T *MH, int64_t ldh, const TransferDev<T> &tr,
+                     cudaStream_t st);
+template <typename T>
+void launch_prolong(int n, const T *V, int64_t ldv, T *B, int64_t ldb, const TransferDev<T> &tr, const int *kdyn,
+                    int kmax, cudaStream_t st);
+template <typename T>
+void launch_restrict_rows(const T *B, int64_t ldb, T *Om, int64_t ldo, const TransferDev<T> &tr, const int *kdyn,
+                          int kmax, cudaStream_t st);
+template <typename T>
+void launch_transpose(int rows, int cols, const T *A, int64_t lda, T *B, int64_t ldb, cudaStream_t st);
+void launch_transpose_mask(int rows, int cols, const uint32_t *in, int64_t ldi, uint32_t *out, int64_t ldo,
+                           cudaStream_t st);
+
+// small dense kernels (one CTA)
+template <typename T>
+void launch_chol(const T *partialG, int splits, int kmax, const int *kdyn, T *R, T *Rinv, const T *Rprev,
+                 T *Rtot, int ldr, cudaStream_t st);
+template <typename T>
+void launch_jacobi(const T *Rz, int ldr, const int *kdyn, T *Ut, T *Wt, T *sig, int kmax, cudaStream_t st);
+template <typename T>
+void launch_svt_small(const T *Ut, const T *sig, int ldr, Ctrl *ctrl, T *Us, double *sig64, cudaStream_t st);
+// all_cols = 1: fill columns [0, ctrl->k); else columns [ctrl->k, ctrl->k_next)
+// and the columns whose sig is exactly zero
+template <typename T>
+void launch_fill_random(T *Omega, int64_t ldo, int rows, const Ctrl *ctrl, int all_cols, const T *sig, int kmax,
+                        uint64_t salt, cudaStream_t st);
+int small_kmax_f32();
+int small_kmax_f64();
+
+void launch_ctrl_begin(Ctrl *c, cudaStream_t st);
+void launch_ctrl_end(Ctrl *c, cudaStream_t st);
+void launch_ctrl_take_width(Ctrl *c, cudaStream_t st);  // k = k_next
+void launch_ctrl_set_check(Ctrl *chk, const Ctrl *it, double mu_c, cudaStream_t st);
+
+}  // namespace cpcp

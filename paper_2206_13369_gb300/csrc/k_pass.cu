@@ -1,0 +1,408 @@
+// k_pass.cu -- the m x n passes of one iteration.
+//
+// One kernel template covers four passes that share the same tile shape:
+//   STEP_FINE / STEP_COARSE  the fused iteration pass (momentum extrapolation,
+//       masked gradient eq. (cpcp-grad-LS), S shrink (Alg. 3 threshold), and
+//       M = Lhat - tau G, written dense on the fine level or restricted to
+//       M_H = M R on a coarse level (Sec. 3.1 / Alg. 4 restriction step));
+//   CHECK  the same quantities at (L_k, S_k) with the final weight, plus the
+//       S part of the gradient-mapping residual and ||P_Q D||;
+//   DIFF   ||A_k B_k^T - A_p B_p^T||_F^2 (L part of the residual).
+//
+// L is never stored densely: each 64 x 64 tile of Lhat is rebuilt on chip
+// from the low-rank factors (a K = r_k + r_{k-1} contraction) and consumed in
+// the epilogue, so the pass moves D, S_k, S_{k-1}, the mask bits and S_{k+1}
+// through HBM once.
+#include "common.cuh"
+
+namespace cpcp {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, KC = 16, NT = 256;
+constexpr int NSLOT = 3;
+
+enum Mode { STEP_FINE = 0, STEP_COARSE = 1, CHECK = 2, DIFF = 3, RECON = 4 };
+
+template <typename T>
+struct Smem {
+    union {
+        struct {
+            T As[KC][BM + 4];
+            T Bs[KC][BN + 4];
+        } g;
+        T Ms[BM][BN + 1];
+    } u;
+    int j0[BN];
+    T w0[BN], w1[BN];
+    double red[NT / 32][NSLOT];
+};
+
+template <typename T>
+__device__ __forceinline__ bool is_finite_val(T x)
+{
+    return isfinite(x);
+}
+
+// Accumulate coef * A[rows, 0:r] B[cols, 0:r]^T into acc.  With COMP the sum
+// is compensated (Ogita-Rump-Oishi Dot2: exact products by FMA, TwoSum on the
+// running sum, errors gathered in lo), so acc + lo carries about twice the
+// working precision; the residual check needs this because it subtracts two
+// reconstructions of nearly equal matrices.
+template <typename T, bool COMP>
+__device__ __forceinline__ void accumulate_factor(Smem<T> &sm, T acc[4][4], T lo[4][4], const T *A, int64_t lda,
+                                                  const T *B, int64_t ldb, int r, T coef, int m, int n, int rb,
+                                                  int cb)
+{
+    const int t = threadIdx.x;
+    const int tx = t & 15, ty = t >> 4;
+    for (int c0 = 0; c0 < r; c0 += KC) {
+        // load: 64 rows x 16 columns of A and of B, 4 values per thread
+        {
+            int row = t >> 2, kk = (t & 3) * 4;
+            int gr = rb + row, gc = cb + row;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                int c = c0 + kk + u;
+                T av = (gr < m && c < r) ? A[(int64_t)gr * lda + c] : T(0);
+                T bv = (gc < n && c < r) ? B[(int64_t)gc * ldb + c] : T(0);
+                sm.u.g.As[kk + u][row] = av * coef;
+                sm.u.g.Bs[kk + u][row] = bv;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < KC; kk++) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = sm.u.g.As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) b[j] = sm.u.g.Bs[kk][4 * tx + j];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    if constexpr (COMP) {
+                        T p = a[i] * b[j];
+                        T e = fma(a[i], b[j], -p);
+                        T s = acc[i][j] + p;
+                        T z = s - acc[i][j];
+                        T q = (acc[i][j] - (s - z)) + (p - z);
+                        acc[i][j] = s;
+                        lo[i][j] += q + e;
+                    } else {
+                        acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                    }
+                }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void load4(const T *p, int64_t off, int col, int n, bool vec, T v[4])
+{
+    if (vec && col + 3 < n) {
+        if constexpr (sizeof(T) == 4) {
+            float4 q = *reinterpret_cast<const float4 *>(p + off);
+            v[0] = q.x;
+            v[1] = q.y;
+            v[2] = q.z;
+            v[3] = q.w;
+        } else {
+            double2 q0 = *reinterpret_cast<const double2 *>(p + off);
+            double2 q1 = *reinterpret_cast<const double2 *>(p + off + 2);
+            v[0] = q0.x;
+            v[1] = q0.y;
+            v[2] = q1.x;
+            v[3] = q1.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++) v[j] = (col + j < n) ? p[off + j] : T(0);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store4(T *p, int64_t off, int col, int n, bool vec, const T v[4])
+{
+    if (vec && col + 3 < n) {
+        if constexpr (sizeof(T) == 4) {
+            *reinterpret_cast<float4 *>(p + off) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+            *reinterpret_cast<double2 *>(p + off) = make_double2(v[0], v[1]);
+            *reinterpret_cast<double2 *>(p + off + 2) = make_double2(v[2], v[3]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (col + j < n) p[off + j] = v[j];
+    }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(NT) pass_kernel(PassArgs<T> a, int vec_flags)
+{
+    const int *rk_ptr = a.rk, *rp_ptr = a.rp;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Smem<T> &sm = *reinterpret_cast<Smem<T> *>(smraw);
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const int cb = blockIdx.x * BN, rb = blockIdx.y * BM;
+    const int m = a.m, n = a.n;
+    const Ctrl &C = *a.ctrl;
+
+    T coef_k, coef_p;
+    if (MODE == STEP_FINE || MODE == STEP_COARSE) {
+        coef_k = T(1.0 + C.beta);
+        coef_p = T(-C.beta);
+    } else if (MODE == CHECK) {
+        coef_k = T(1);
+        coef_p = T(0);
+    } else if (MODE == DIFF) {
+        coef_k = T(1);
+        coef_p = T(-1);
+    } else {
+        coef_k = T(1);
+        coef_p = T(0);
+    }
+    const int rk = rk_ptr ? *rk_ptr : 0;
+    const int rp = (rp_ptr && coef_p != T(0)) ? *rp_ptr : 0;
+
+    // fp32 residual passes use compensated sums (see accumulate_factor)
+    constexpr bool COMP = (MODE == CHECK || MODE == DIFF) && sizeof(T) == 4;
+    T acc[4][4], lo[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = lo[i][j] = T(0);
+    if (rk > 0) accumulate_factor<T, COMP>(sm, acc, lo, a.Ak, a.ldfa, a.Bk, a.ldfb, rk, coef_k, m, n, rb, cb);
+    if (rp > 0) accumulate_factor<T, COMP>(sm, acc, lo, a.Ap, a.ldfap, a.Bp, a.ldfbp, rp, coef_p, m, n, rb, cb);
+
+    const int col = cb + 4 * tx;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+
+    if (MODE == RECON) {
+        const bool vM = vec_flags & 8;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            int row = rb + ty + 16 * i;
+            if (row < m) store4(a.M, (int64_t)row * a.ldm + col, col, n, vM, acc[i]);
+        }
+        return;
+    }
+    if (MODE == DIFF) {
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            int row = rb + ty + 16 * i;
+            if (row >= m) continue;
+            T part = T(0);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                T dv = acc[i][j] + lo[i][j];
+                if (col + j < n) part += dv * dv;
+            }
+            s0 += (double)part;
+        }
+    } else {
+        const bool vD = vec_flags & 1, vS = vec_flags & 2, vO = vec_flags & 4, vM = vec_flags & 8;
+        const T tau = T(C.tau);
+        const T beta = (MODE == CHECK) ? T(0) : T(C.beta);
+        const T thS = (MODE == CHECK) ? T(C.tau * C.lam * C.mu_bar) : T(C.theta_S);
+        if (MODE == STEP_COARSE) __syncthreads();  // smem tile reused below
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            int lr = ty + 16 * i, row = rb + lr;
+            if (row >= m) continue;
+            T d[4], sk[4], sp[4];
+            load4(a.D, (int64_t)row * a.ldd + col, col, n, vD, d);
+            if (a.Sk) {
+                load4(a.Sk, (int64_t)row * a.lds + col, col, n, vS, sk);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; j++) sk[j] = T(0);
+            }
+            if (MODE != CHECK && a.Sp && beta != T(0)) {
+                load4(a.Sp, (int64_t)row * a.lds + col, col, n, vS, sp);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; j++) sp[j] = sk[j];
+            }
+            uint32_t bits = 0xffffffffu;
+            if (a.Q && col < n) bits = a.Q[(int64_t)row * a.ldq + (col >> 5)] >> (col & 31);
+            T so[4], mo[4];
+            T ps = T(0), pd = T(0);
+            int nf = 0;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                bool obs = (bits >> j) & 1u;
+                bool inb = col + j < n;
+                T sh = sk[j] + beta * (sk[j] - sp[j]);
+                // L + S - D with the large terms cancelled first (lo = 0
+                // unless the sum is compensated)
+                T g = obs ? (((acc[i][j] - d[j]) + sh) + lo[i][j]) : T(0);
+                T sn = shrink(sh - tau * g, thS);
+                so[j] = sn;
+                mo[j] = (acc[i][j] + lo[i][j]) - tau * g;
+                if (MODE == CHECK && inb) {
+                    T e = sk[j] - sn;
+                    ps += e * e;
+                    if (obs) {
+                        if (is_finite_val(d[j]))
+                            pd += d[j] * d[j];
+                        else
+                            nf++;
+                    }
+                }
+            }
+            if (MODE == STEP_FINE || MODE == STEP_COARSE)
+                store4(a.Sout, (int64_t)row * a.ldso + col, col, n, vO, so);
+            if (MODE == STEP_FINE || MODE == CHECK) {
+                store4(a.M, (int64_t)row * a.ldm + col, col, n, vM, mo);
+            } else if (MODE == STEP_COARSE) {
+#pragma unroll
+                for (int j = 0; j < 4; j++) sm.u.Ms[lr][4 * tx + j] = mo[j];
+            }
+            if (MODE == CHECK) {
+                s0 += (double)ps;
+                s1 += (double)pd;
+                s2 += (double)nf;
+            }
+        }
+    }
+
+    if (MODE == STEP_COARSE) {
+        // restriction of the tile: M_H[row, c] += sum_j M[row, j] R[j, c]
+        if (t < BN) {
+            int j = cb + t;
+            if (j < n) {
+                sm.j0[t] = a.tr.j0[j];
+                sm.w0[t] = a.tr.w0[j];
+                sm.w1[t] = a.tr.w1[j];
+            } else {
+                sm.j0[t] = -4;
+                sm.w0[t] = T(0);
+                sm.w1[t] = T(0);
+            }
+        }
+        __syncthreads();
+        const int jlast = min(cb + BN, n) - 1;
+        const int c_lo = a.tr.j0[cb];
+        const int c_hi = min(a.tr.j0[jlast] + 1, a.tr.nh - 1);
+        const int ncol = c_hi - c_lo + 1;
+        const int rows = min(BM, m - rb);
+        for (int p = t; p < rows * ncol; p += NT) {
+            int lr = p / ncol, c = c_lo + p % ncol;
+            int jlo = max(a.tr.clo[c], cb), jhi = min(a.tr.chi[c], jlast);
+            T s = T(0);
+            for (int j = jlo; j <= jhi; j++) {
+                int lj = j - cb;
+                T w = (sm.j0[lj] == c) ? sm.w0[lj] : ((sm.j0[lj] + 1 == c) ? sm.w1[lj] : T(0));
+                s = fma(sm.u.Ms[lr][lj], w, s);
+            }
+            if (jlo <= jhi) atomicAdd(&a.MH[(int64_t)(rb + lr) * a.ldh + c], s);
+        }
+    }
+
+    if (MODE == CHECK || MODE == DIFF) {
+        s0 = warp_sum(s0);
+        s1 = warp_sum(s1);
+        s2 = warp_sum(s2);
+        if ((t & 31) == 0) {
+            sm.red[t >> 5][0] = s0;
+            sm.red[t >> 5][1] = s1;
+            sm.red[t >> 5][2] = s2;
+        }
+        __syncthreads();
+        if (t < NSLOT) {
+            double v = 0.0;
+            for (int w = 0; w < NT / 32; w++) v += sm.red[w][t];
+            a.partial[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * NSLOT + t] = v;
+        }
+    }
+}
+
+template <typename T>
+int vec_flags_for(const PassArgs<T> &a)
+{
+    auto al = [](const void *p, int64_t ld) {
+        return p == nullptr || ((reinterpret_cast<uintptr_t>(p) % 16 == 0) && (ld % (16 / (int64_t)sizeof(T)) == 0));
+    };
+    int f = 0;
+    if (al(a.D, a.ldd)) f |= 1;
+    if (al(a.Sk, a.lds) && al(a.Sp, a.lds)) f |= 2;
+    if (al(a.Sout, a.ldso)) f |= 4;
+    if (al(a.M, a.ldm)) f |= 8;
+    return f;
+}
+
+template <typename T, int MODE>
+int launch_mode(const PassArgs<T> &a, cudaStream_t st)
+{
+    static_assert(sizeof(Smem<T>) <= 48 * 1024, "pass tile exceeds default shared memory");
+    dim3 grid((a.n + BN - 1) / BN, (a.m + BM - 1) / BM);
+    pass_kernel<T, MODE><<<grid, NT, sizeof(Smem<T>), st>>>(a, vec_flags_for(a));
+    return grid.x * grid.y;
+}
+
+__global__ void sum_partials_kernel(const double *partial, int nblocks, int nslots, double *out)
+{
+    __shared__ double red[32];
+    for (int s = 0; s < nslots; s++) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partial[(int64_t)b * nslots + s];
+        v = warp_sum(v);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += red[w];
+            out[s] = tot;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_step_pass(const PassArgs<T> &a, bool coarse, cudaStream_t st)
+{
+    if (coarse)
+        launch_mode<T, STEP_COARSE>(a, st);
+    else
+        launch_mode<T, STEP_FINE>(a, st);
+}
+
+template <typename T>
+int launch_check_pass(const PassArgs<T> &a, cudaStream_t st)
+{
+    return launch_mode<T, CHECK>(a, st);
+}
+
+template <typename T>
+int launch_diff_pass(const PassArgs<T> &a, cudaStream_t st)
+{
+    return launch_mode<T, DIFF>(a, st);
+}
+
+template <typename T>
+void launch_reconstruct(const PassArgs<T> &a, cudaStream_t st)
+{
+    launch_mode<T, RECON>(a, st);
+}
+
+void launch_sum_partials(const double *partial, int nblocks, int nslots, double *out, cudaStream_t st)
+{
+    sum_partials_kernel<<<1, 256, 0, st>>>(partial, nblocks, nslots, out);
+}
+
+template void launch_step_pass<float>(const PassArgs<float> &, bool, cudaStream_t);
+template void launch_step_pass<double>(const PassArgs<double> &, bool, cudaStream_t);
+template int launch_check_pass<float>(const PassArgs<float> &, cudaStream_t);
+template int launch_check_pass<double>(const PassArgs<double> &, cudaStream_t);
+template int launch_diff_pass<float>(const PassArgs<float> &, cudaStream_t);
+template int launch_diff_pass<double>(const PassArgs<double> &, cudaStream_t);
+template void launch_reconstruct<float>(const PassArgs<float> &, cudaStream_t);
+template void launch_reconstruct<double>(const PassArgs<double> &, cudaStream_t);
+
+}  // namespace cpcp

@@ -1,0 +1,1134 @@
+// solver.cu -- host driver of the multilevel accelerated proximal-gradient
+// solver for eq. (cpcp), and the C ABI declared in include/cpcp.h.
+//
+// One iteration (all device work, no host round trip):
+//   ctrl_begin   momentum weight beta_k, continuation weight mu_k, thresholds
+//   step pass    Lhat, Shat, G = P_Q[Lhat + Shat - D] (eq. (cpcp-grad-LS)),
+//                S_{k+1} = shrink(Shat - G/2) (Alg. 3), M = Lhat - G/2 and
+//                its restriction M_H = M R (Sec. 3.1; Alg. 4 restriction)
+//   coarse SVD   subspace iteration on M_H: Y = M_H Omega, CholeskyQR2,
+//                Z = M_H^T Q, CholeskyQR2 (Z = Qz Rz), Jacobi SVD of Rz^T
+//   SVT          sigma > mu_k/2 kept (Sec. 3.2 coarse minimiser):
+//                A = Qy Ut diag(sigma - mu_k/2), V = Qz Wt
+//   prolong      B = R V, so L_{k+1} = A B^T = L_H R^T (Alg. 4 prolongation)
+//   ctrl_end     rotate ranks, t_k, width
+// Every `check_every` iterations once mu_k has reached mu, the fine-level
+// gradient-mapping residual is evaluated (one scalar read back to the host),
+// and the host decides to stop or to move one level finer.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/cpcp.h"
+#include "common.cuh"
+
+using namespace cpcp;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace
+
+struct cpcp_context {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cpcp_options opt{};
+    std::string err;
+    std::map<std::string, DevBuf> bufs;
+    std::map<std::string, std::vector<double>> host_tr_cache;
+};
+
+namespace {
+
+struct CpcpError {
+    cpcp_status st;
+    std::string msg;
+};
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            throw CpcpError{CPCP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};    \
+    } while (0)
+
+void *ws_get(cpcp_context *h, const std::string &name, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    DevBuf &b = h->bufs[name];
+    if (b.cap < bytes) {
+        if (b.p) cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+        cudaError_t e = cudaMalloc(&b.p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw CpcpError{CPCP_ERR_NOMEM, "workspace allocation of " + std::to_string(bytes) + " bytes for " +
+                                                name + " failed: " + cudaGetErrorString(e)};
+        }
+        b.cap = bytes;
+    }
+    return b.p;
+}
+
+template <typename T>
+T *wsT(cpcp_context *h, const std::string &name, size_t elems)
+{
+    return reinterpret_cast<T *>(ws_get(h, name, elems * sizeof(T)));
+}
+
+inline int64_t round4(int64_t x) { return (x + 3) / 4 * 4; }
+
+// ---------------------------------------------------------------------------
+// transfer operator (host construction, fp64)
+// ---------------------------------------------------------------------------
+
+// Largest eigenvalue of the symmetric tridiagonal matrix (d, e) by Sturm
+// bisection (count of eigenvalues below x from the LDL^T pivots).
+double tridiag_max_eig(const std::vector<double> &d, const std::vector<double> &e)
+{
+    const int n = (int)d.size();
+    double lo = -1e300, hi = -1e300;
+    for (int i = 0; i < n; i++) {
+        double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(e[i]) : 0.0);
+        hi = std::max(hi, d[i] + r);
+        lo = std::max(lo, d[i]);  // lambda_max >= max diagonal entry
+    }
+    auto below = [&](double x) {
+        int cnt = 0;
+        double q = d[0] - x;
+        if (q < 0) cnt++;
+        for (int i = 1; i < n; i++) {
+            double qq = q == 0.0 ? 1e-300 : q;
+            q = d[i] - x - e[i - 1] * e[i - 1] / qq;
+            if (q < 0) cnt++;
+        }
+        return cnt;
+    };
+    for (int it = 0; it < 200 && hi - lo > 1e-16 * std::fabs(hi); it++) {
+        double mid = 0.5 * (lo + hi);
+        if (below(mid) == n)
+            hi = mid;
+        else
+            lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+struct HostTransfer {
+    int n = 0, nh = 0, halvings = 0, max_span = 0;
+    double scale = 1.0;
+    std::vector<int> j0, clo, chi;
+    std::vector<double> w0, w1;
+};
+
+// One level of eq. (Rx) in the reading fixed by its worked example (Sec. 3.1):
+// for even size row 1 = e_1, row 2j = e_j, row 2j+1 = (e_j + e_{j+1})/2; for
+// odd size row 2j-1 = e_j, row 2j = (e_j + e_{j+1})/2 (1-based indices).
+// Returns up to two (coarse index, weight) entries of fine row x (0-based).
+int level_row(int size, int x, int *cols, double *ws)
+{
+    const int I = x + 1;
+    if (size % 2 == 0) {
+        if (I == 1) {
+            cols[0] = 0;
+            ws[0] = 1.0;
+            return 1;
+        }
+        if (I % 2 == 0) {
+            cols[0] = I / 2 - 1;
+            ws[0] = 1.0;
+            return 1;
+        }
+        int j = (I - 1) / 2;
+        cols[0] = j - 1;
+        ws[0] = 0.5;
+        cols[1] = j;
+        ws[1] = 0.5;
+        return 2;
+    }
+    if (I % 2 == 1) {
+        cols[0] = (I + 1) / 2 - 1;
+        ws[0] = 1.0;
+        return 1;
+    }
+    int j = I / 2;
+    cols[0] = j - 1;
+    ws[0] = 0.5;
+    cols[1] = j;
+    ws[1] = 0.5;
+    return 2;
+}
+
+HostTransfer build_transfer(int n, int halvings)
+{
+    HostTransfer t;
+    t.n = n;
+    t.halvings = halvings;
+    // sparse rows of the running product, at most 4 entries before merging
+    std::vector<std::vector<std::pair<int, double>>> rows(n);
+    for (int j = 0; j < n; j++) rows[j] = {{j, 1.0}};
+    int cur = n;
+    for (int h = 0; h < halvings; h++) {
+        for (int j = 0; j < n; j++) {
+            std::vector<std::pair<int, double>> out;
+            for (auto &e : rows[j]) {
+                int cols[2];
+                double ws[2];
+                int cnt = level_row(cur, e.first, cols, ws);
+                for (int u = 0; u < cnt; u++) {
+                    bool merged = false;
+                    for (auto &o : out)
+                        if (o.first == cols[u]) {
+                            o.second += e.second * ws[u];
+                            merged = true;
+                        }
+                    if (!merged) out.push_back({cols[u], e.second * ws[u]});
+                }
+            }
+            std::vector<std::pair<int, double>> nz;
+            for (auto &o : out)
+                if (o.second != 0.0) nz.push_back(o);
+            std::sort(nz.begin(), nz.end());
+            rows[j] = nz;
+        }
+        cur = (cur + 1) / 2;
+    }
+    t.nh = cur;
+    t.j0.assign(n, 0);
+    t.w0.assign(n, 0.0);
+    t.w1.assign(n, 0.0);
+    t.clo.assign(cur, n);
+    t.chi.assign(cur, -1);
+    for (int j = 0; j < n; j++) {
+        auto &r = rows[j];
+        if (r.empty() || r.size() > 2 || (r.size() == 2 && r[1].first != r[0].first + 1))
+            throw CpcpError{CPCP_ERR_NUMERIC, "composite transfer operator is not banded"};
+        t.j0[j] = r[0].first;
+        t.w0[j] = r[0].second;
+        if (r.size() == 2) t.w1[j] = r[1].second;
+        for (auto &e : r) {
+            t.clo[e.first] = std::min(t.clo[e.first], j);
+            t.chi[e.first] = std::max(t.chi[e.first], j);
+        }
+    }
+    // R^T R is tridiagonal: diagonal d_c = sum_j R_jc^2, off e_c = sum_j R_jc R_j,c+1
+    std::vector<double> d(cur, 0.0), e(cur > 1 ? cur - 1 : 1, 0.0);
+    for (int j = 0; j < n; j++) {
+        d[t.j0[j]] += t.w0[j] * t.w0[j];
+        if (t.w1[j] != 0.0) {
+            d[t.j0[j] + 1] += t.w1[j] * t.w1[j];
+            e[t.j0[j]] += t.w0[j] * t.w1[j];
+        }
+    }
+    double lmax = tridiag_max_eig(d, e);
+    t.scale = 1.0 / std::sqrt(lmax);
+    for (int j = 0; j < n; j++) {
+        t.w0[j] *= t.scale;
+        t.w1[j] *= t.scale;
+    }
+    for (int c = 0; c < cur; c++) t.max_span = std::max(t.max_span, t.chi[c] - t.clo[c] + 1);
+    return t;
+}
+
+int coarse_dim(int n, int halvings)
+{
+    for (int h = 0; h < halvings; h++) n = (n + 1) / 2;
+    return n;
+}
+
+template <typename T>
+TransferDev<T> upload_transfer(cpcp_context *h, int n, int halvings, const std::string &tag)
+{
+    HostTransfer t;
+    if (halvings == 0) {
+        t.n = n;
+        t.nh = n;
+        t.j0.resize(n);
+        t.w0.assign(n, 1.0);
+        t.w1.assign(n, 0.0);
+        t.clo.resize(n);
+        t.chi.resize(n);
+        for (int j = 0; j < n; j++) t.j0[j] = t.clo[j] = t.chi[j] = j;
+        t.max_span = 1;
+    } else {
+        t = build_transfer(n, halvings);
+    }
+    if (t.max_span > 64)
+        throw CpcpError{CPCP_ERR_INVALID_ARG, "too many levels for the restriction tile (support wider than 64)"};
+    std::string pre = tag + "_tr" + std::to_string(halvings) + "_";
+    int *j0 = wsT<int>(h, pre + "j0", n), *clo = wsT<int>(h, pre + "clo", t.nh), *chi = wsT<int>(h, pre + "chi", t.nh);
+    T *w0 = wsT<T>(h, pre + "w0", n), *w1 = wsT<T>(h, pre + "w1", n);
+    std::vector<T> w0t(t.w0.begin(), t.w0.end()), w1t(t.w1.begin(), t.w1.end());
+    CK(cudaMemcpyAsync(j0, t.j0.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(clo, t.clo.data(), sizeof(int) * t.nh, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(chi, t.chi.data(), sizeof(int) * t.nh, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(w0, w0t.data(), sizeof(T) * n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(w1, w1t.data(), sizeof(T) * n, cudaMemcpyHostToDevice, h->stream));
+    // the host vectors must outlive the asynchronous copies
+    CK(cudaStreamSynchronize(h->stream));
+    TransferDev<T> d;
+    d.n = n;
+    d.nh = t.nh;
+    d.j0 = j0;
+    d.w0 = w0;
+    d.w1 = w1;
+    d.clo = clo;
+    d.chi = chi;
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// subspace-iteration SVD
+// ---------------------------------------------------------------------------
+
+template <typename T>
+struct SvdWork {
+    int KM;     // padded maximum width (leading dimension of k-wide buffers)
+    int kcap;   // maximum live width
+    T *Y, *Q1, *Qy, *Z, *Qz;
+    T *Gpart, *Zpart, *Ypart;
+    T *R1, *R1i, *R2, *R2i, *Rz, *Ut, *Wt, *Us, *sig;
+    double *sig64;
+};
+
+template <typename T>
+SvdWork<T> svd_work(cpcp_context *h, const std::string &tag, int m, int ncols, int kcap)
+{
+    SvdWork<T> w;
+    w.kcap = kcap;
+    w.KM = (int)round4(kcap);
+    size_t KM = w.KM;
+    int rows = std::max(m, ncols);
+    w.Y = wsT<T>(h, tag + "Y", (size_t)m * KM);
+    w.Q1 = wsT<T>(h, tag + "Q1", (size_t)rows * KM);
+    w.Qy = wsT<T>(h, tag + "Qy", (size_t)m * KM);
+    w.Z = wsT<T>(h, tag + "Z", (size_t)ncols * KM);
+    w.Qz = wsT<T>(h, tag + "Qz", (size_t)ncols * KM);
+    w.Gpart = wsT<T>(h, tag + "Gpart", (size_t)64 * KM * KM);
+    w.Zpart = wsT<T>(h, tag + "Zpart", (size_t)64 * ncols * KM);
+    w.Ypart = wsT<T>(h, tag + "Ypart", (size_t)16 * m * KM);
+    w.R1 = wsT<T>(h, tag + "R1", KM * KM);
+    w.R1i = wsT<T>(h, tag + "R1i", KM * KM);
+    w.R2 = wsT<T>(h, tag + "R2", KM * KM);
+    w.R2i = wsT<T>(h, tag + "R2i", KM * KM);
+    w.Rz = wsT<T>(h, tag + "Rz", KM * KM);
+    w.Ut = wsT<T>(h, tag + "Ut", KM * KM);
+    w.Wt = wsT<T>(h, tag + "Wt", KM * KM);
+    w.Us = wsT<T>(h, tag + "Us", KM * KM);
+    w.sig = wsT<T>(h, tag + "sig", KM);
+    w.sig64 = wsT<double>(h, tag + "sig64", KM);
+    return w;
+}
+
+// CholeskyQR2 of X (rows x k): Q = X R^{-1}; if Rout != nullptr it receives R.
+template <typename T>
+void orth(cpcp_context *h, SvdWork<T> &w, int rows, const T *X, T *Q, T *Rout, const int *kdyn)
+{
+    cudaStream_t st = h->stream;
+    const int KM = w.KM;
+    int sp = launch_gemm_tn_partial<T>(rows, -1, X, KM, X, KM, w.Gpart, kdyn, KM, KM, st);
+    launch_chol<T>(w.Gpart, sp, KM, kdyn, w.R1, w.R1i, nullptr, nullptr, KM, st);
+    launch_gemm_nn<T>(rows, 0, X, KM, w.R1i, KM, w.Q1, KM, kdyn, kdyn, KM, st);
+    sp = launch_gemm_tn_partial<T>(rows, -1, w.Q1, KM, w.Q1, KM, w.Gpart, kdyn, KM, KM, st);
+    launch_chol<T>(w.Gpart, sp, KM, kdyn, w.R2, w.R2i, Rout ? w.R1 : nullptr, Rout, KM, st);
+    launch_gemm_nn<T>(rows, 0, w.Q1, KM, w.R2i, KM, Q, KM, kdyn, kdyn, KM, st);
+}
+
+// Rank-k SVD of Mx (m x nc, ld ldx): q range passes from Omega (nc x k).
+// Leaves Qy (m x k), Qz (nc x k), Ut, Wt (k x k), sig (k) with
+// Mx ~ (Qy Ut) diag(sig) (Qz Wt)^T.
+template <typename T>
+void subspace_svd(cpcp_context *h, SvdWork<T> &w, int m, int nc, const T *Mx, int64_t ldx, const T *Omega,
+                  int q, const int *kdyn)
+{
+    cudaStream_t st = h->stream;
+    const int KM = w.KM;
+    const T *Om = Omega;
+    for (int s = 0; s < q; s++) {
+        launch_gemm_nn_splitk<T>(m, nc, Mx, ldx, Om, KM, w.Y, KM, w.Ypart, kdyn, KM, st);
+        orth<T>(h, w, m, w.Y, w.Qy, nullptr, kdyn);
+        int sp = launch_gemm_tn_partial<T>(m, nc, Mx, ldx, w.Qy, KM, w.Zpart, kdyn, KM, nc, st);
+        launch_reduce_partial<T>(w.Zpart, sp, nc, KM, w.Z, KM, nullptr, kdyn, st);
+        orth<T>(h, w, nc, w.Z, w.Qz, w.Rz, kdyn);
+        Om = w.Qz;
+    }
+    launch_jacobi<T>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, st);
+}
+
+template <typename T>
+int kmax_small();
+template <>
+int kmax_small<float>()
+{
+    return small_kmax_f32();
+}
+template <>
+int kmax_small<double>()
+{
+    return small_kmax_f64();
+}
+
+// ---------------------------------------------------------------------------
+// solve
+// ---------------------------------------------------------------------------
+
+struct Opts {
+    int max_iter, check_every, k_max, p, q, qc, start_level;
+    double eta, mu0, ratio;
+    uint64_t seed;
+};
+
+Opts resolve(const cpcp_options &o)
+{
+    Opts r;
+    r.max_iter = o.max_iter > 0 ? o.max_iter : 5000;
+    r.check_every = o.check_every > 0 ? o.check_every : 10;
+    r.eta = o.eta > 0 ? o.eta : 0.9;
+    r.mu0 = o.mu0;
+    r.ratio = o.switch_ratio > 0 ? o.switch_ratio : 0.9;
+    r.k_max = o.k_max > 0 ? o.k_max : 256;
+    r.p = o.oversample > 0 ? o.oversample : 10;
+    r.q = o.power_iters > 0 ? o.power_iters : 1;
+    r.qc = o.check_power_iters > 0 ? o.check_power_iters : 2;
+    r.start_level = o.start_level;
+    r.seed = o.seed ? o.seed : 1;
+    return r;
+}
+
+template <typename T>
+struct SolveState {
+    int m, n, ldS, KM, kcap0;
+    const T *D;
+    int64_t ldd;
+    const uint32_t *Q;
+    int64_t ldq;
+    T *S[2], *A[2], *B[2];
+    T *M, *MH;
+    int64_t ldMH;
+    T *Om, *Omf, *Ac, *Bc;
+    Ctrl *ctrl, *cchk;
+    double *partial, *sums;
+    int partial_blocks;
+    std::vector<TransferDev<T>> tr;
+};
+
+template <typename T>
+PassArgs<T> base_args(SolveState<T> &s)
+{
+    PassArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.m = s.m;
+    a.n = s.n;
+    a.D = s.D;
+    a.ldd = s.ldd;
+    a.Q = s.Q;
+    a.ldq = s.ldq;
+    a.lds = s.ldS;
+    a.ldso = s.ldS;
+    a.ldfa = s.KM;
+    a.ldfb = s.KM;
+    a.ldfap = s.KM;
+    a.ldfbp = s.KM;
+    a.ctrl = s.ctrl;
+    a.ldm = s.ldS;
+    a.M = s.M;
+    a.partial = s.partial;
+    return a;
+}
+
+// Fine-level residual at (L_k, S_k) = (A[cur] B[cur]^T, S[cur]) for the
+// weight mu_c.  Returns rel-KKT (or +inf when the fine SVT width was
+// insufficient).
+template <typename T>
+double fine_check(cpcp_context *h, SolveState<T> &s, SvdWork<T> &wf, int cur, const Opts &o, double pqd,
+                  double mu_c, int *kf, double *s_part_out, int *rank_out)
+{
+    cudaStream_t st = h->stream;
+    launch_ctrl_set_check(s.cchk, s.ctrl, mu_c, st);
+    PassArgs<T> a = base_args(s);
+    a.ctrl = s.cchk;
+    a.Sk = s.S[cur];
+    a.Ak = s.A[cur];
+    a.Bk = s.B[cur];
+    a.rk = &s.ctrl->rk;
+    int nb = launch_check_pass<T>(a, st);
+    launch_sum_partials(s.partial, nb, 3, s.sums, st);
+    // fine SVT of M = L - tau G with width kf, warm-started from the last check
+    launch_fill_random<T>(s.Omf, s.KM, s.n, s.cchk, 0, wf.sig, s.KM, 0xC4ECull, st);
+    launch_ctrl_take_width(s.cchk, st);
+    subspace_svd<T>(h, wf, s.m, s.n, s.M, s.ldS, s.Omf, o.qc, &s.cchk->k);
+    launch_svt_small<T>(wf.Ut, wf.sig, wf.KM, s.cchk, wf.Us, nullptr, st);
+    launch_gemm_nn<T>(s.m, 0, wf.Qy, wf.KM, wf.Us, wf.KM, s.Ac, s.KM, &s.cchk->k, &s.cchk->k, s.KM, st);
+    launch_gemm_nn<T>(s.n, 0, wf.Qz, wf.KM, wf.Wt, wf.KM, s.Omf, s.KM, &s.cchk->k, &s.cchk->k, s.KM, st);
+    launch_prolong<T>(s.n, s.Omf, s.KM, s.Bc, s.KM, s.tr[0], &s.cchk->r_new, s.KM, st);
+    PassArgs<T> b = base_args(s);
+    b.ctrl = s.cchk;
+    b.Ak = s.A[cur];
+    b.Bk = s.B[cur];
+    b.Ap = s.Ac;
+    b.Bp = s.Bc;
+    b.rk = &s.ctrl->rk;
+    b.rp = &s.cchk->r_new;
+    nb = launch_diff_pass<T>(b, st);
+    launch_sum_partials(s.partial, nb, 3, s.sums + 3, st);
+    double sums[6];
+    Ctrl cc;
+    CK(cudaMemcpyAsync(sums, s.sums, sizeof(sums), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&cc, s.cchk, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *s_part_out = sums[0];
+    int kcur = cc.k;
+    int r = cc.r_new;
+    bool saturated = (r >= kcur) && (kcur < s.kcap0);
+    // width for the next check: rank + oversampling, doubled if saturated;
+    // columns [kcur, want) get random vectors before the next check
+    int want = saturated ? std::min(s.kcap0, 2 * kcur) : std::min(s.kcap0, std::max(r + o.p, 1));
+    *kf = want;
+    Ctrl upd = cc;
+    upd.k = kcur;
+    upd.k_next = want;
+    CK(cudaMemcpyAsync(s.cchk, &upd, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    *rank_out = r;
+    if (saturated) return INFINITY;
+    double tau = 0.5;
+    return std::sqrt(std::max(sums[0] + sums[3], 0.0)) / tau / pqd;
+}
+
+template <typename T>
+void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, int cur, const Opts &o)
+{
+    cudaStream_t st = h->stream;
+    const int nxt = cur ^ 1;
+    const TransferDev<T> &tr = s.tr[level];
+    launch_ctrl_begin(s.ctrl, st);
+    PassArgs<T> a = base_args(s);
+    a.Sk = s.S[cur];
+    a.Sp = s.S[nxt];
+    a.Sout = s.S[nxt];
+    a.Ak = s.A[cur];
+    a.Bk = s.B[cur];
+    a.Ap = s.A[nxt];
+    a.Bp = s.B[nxt];
+    a.rk = &s.ctrl->rk;
+    a.rp = &s.ctrl->rp;
+    const T *Mx;
+    int64_t ldx;
+    if (level > 0) {
+        CK(cudaMemsetAsync(s.MH, 0, sizeof(T) * (size_t)s.m * s.ldMH, st));
+        a.M = nullptr;
+        a.MH = s.MH;
+        a.ldh = s.ldMH;
+        a.tr = tr;
+        launch_step_pass<T>(a, true, st);
+        Mx = s.MH;
+        ldx = s.ldMH;
+    } else {
+        launch_step_pass<T>(a, false, st);
+        Mx = s.M;
+        ldx = s.ldS;
+    }
+    subspace_svd<T>(h, w, s.m, tr.nh, Mx, ldx, s.Om, o.q, &s.ctrl->k);
+    launch_svt_small<T>(w.Ut, w.sig, w.KM, s.ctrl, w.Us, nullptr, st);
+    // new factors into the "previous" slot (its old content was consumed above)
+    launch_gemm_nn<T>(s.m, 0, w.Qy, w.KM, w.Us, w.KM, s.A[nxt], s.KM, &s.ctrl->k, &s.ctrl->k, s.KM, st);
+    launch_gemm_nn<T>(tr.nh, 0, w.Qz, w.KM, w.Wt, w.KM, s.Om, s.KM, &s.ctrl->k, &s.ctrl->k, s.KM, st);
+    launch_fill_random<T>(s.Om, s.KM, tr.nh, s.ctrl, 0, w.sig, s.KM, 0x57E9ull, st);
+    launch_prolong<T>(s.n, s.Om, s.KM, s.B[nxt], s.KM, tr, &s.ctrl->r_new, s.KM, st);
+    launch_ctrl_end(s.ctrl, st);
+}
+
+template <typename T>
+cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, const uint32_t *Q, int64_t ldq,
+                       double lam, double mu, int levels, double tol, T *L_out, int64_t ldl, T *S_out, int64_t lds,
+                       cpcp_info *info)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = h->stream;
+    const Opts o = resolve(h->opt);
+    const int H = levels - 1;
+    SolveState<T> s;
+    s.m = m;
+    s.n = n;
+    s.D = D;
+    s.ldd = ldd;
+    s.Q = Q;
+    s.ldq = ldq;
+    s.ldS = round4(n);
+    s.kcap0 = std::min({o.k_max, kmax_small<T>(), n});
+    s.KM = (int)round4(s.kcap0);
+    const size_t mn = (size_t)m * s.ldS;
+    for (int i = 0; i < 2; i++) {
+        s.S[i] = wsT<T>(h, "S" + std::to_string(i), mn);
+        s.A[i] = wsT<T>(h, "A" + std::to_string(i), (size_t)m * s.KM);
+        s.B[i] = wsT<T>(h, "B" + std::to_string(i), (size_t)n * s.KM);
+    }
+    s.M = wsT<T>(h, "M", mn);
+    s.tr.clear();
+    for (int lv = 0; lv <= H; lv++) s.tr.push_back(upload_transfer<T>(h, n, lv, "solve"));
+    int nh1 = H >= 1 ? s.tr[1].nh : 1;
+    s.ldMH = round4(nh1);
+    s.MH = wsT<T>(h, "MH", (size_t)m * s.ldMH);
+    s.Om = wsT<T>(h, "Om", (size_t)n * s.KM);
+    s.Omf = wsT<T>(h, "Omf", (size_t)n * s.KM);
+    s.Ac = wsT<T>(h, "Ac", (size_t)m * s.KM);
+    s.Bc = wsT<T>(h, "Bc", (size_t)n * s.KM);
+    s.ctrl = wsT<Ctrl>(h, "ctrl", 1);
+    s.cchk = wsT<Ctrl>(h, "cchk", 1);
+    s.partial_blocks = ((n + 63) / 64) * ((m + 63) / 64);
+    s.partial = wsT<double>(h, "partial", (size_t)s.partial_blocks * 3);
+    s.sums = wsT<double>(h, "sums", 8);
+    SvdWork<T> w = svd_work<T>(h, "it_", m, n, s.kcap0);
+    SvdWork<T> wf = svd_work<T>(h, "ck_", m, n, s.kcap0);
+
+    // control blocks
+    Ctrl c0;
+    memset(&c0, 0, sizeof(c0));
+    c0.tau = 0.5;
+    c0.lam = lam;
+    c0.mu_bar = mu;
+    c0.eta = o.eta;
+    c0.t = 1.0;
+    c0.oversample = o.p;
+    c0.seed = o.seed;
+    Ctrl cc = c0;
+    cc.theta_L = 0.5 * mu;
+    cc.k = std::min(s.kcap0, 8);
+    cc.k_next = cc.k;
+    cc.kcap = s.kcap0;
+    cc.mu_k = mu;
+    CK(cudaMemcpyAsync(s.cchk, &cc, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+
+    // norms of P_Q D, finiteness, and mu_0 = ||P_Q D||_2 estimate (fine SVD of tau P_Q D)
+    PassArgs<T> a0 = base_args(s);
+    int nb = launch_check_pass<T>(a0, st);
+    launch_sum_partials(s.partial, nb, 3, s.sums, st);
+    double sums0[3];
+    CK(cudaMemcpyAsync(sums0, s.sums, sizeof(sums0), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (sums0[2] > 0) throw CpcpError{CPCP_ERR_NONFINITE_INPUT, "non-finite value in an observed entry of D"};
+    const double pqd = std::sqrt(sums0[1]);
+    if (!(pqd > 0)) throw CpcpError{CPCP_ERR_INVALID_ARG, "P_Q[D] is zero"};
+    double mu0 = o.mu0;
+    if (!(mu0 > 0)) {
+        launch_fill_random<T>(s.Omf, s.KM, n, s.cchk, 1, nullptr, s.KM, 0x30ull, st);
+        subspace_svd<T>(h, wf, m, n, s.M, s.ldS, s.Omf, 4, &s.cchk->k);
+        T sig0;
+        CK(cudaMemcpyAsync(&sig0, wf.sig, sizeof(T), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        mu0 = (double)sig0 / 0.5;
+    }
+    // start state
+    // start_level 0 (default) = coarsest; s > 0 starts at min(s, levels) - 1 halvings
+    int level = o.start_level > 0 ? std::min(o.start_level - 1, H) : H;
+    c0.mu0 = mu0;
+    c0.k = std::min(o.p, std::min(s.kcap0, s.tr[level].nh));
+    c0.k_next = c0.k;
+    c0.kcap = std::min(s.kcap0, s.tr[level].nh);
+    CK(cudaMemcpyAsync(s.ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+    cc.k = std::min(s.kcap0, o.p);
+    cc.k_next = cc.k;
+    CK(cudaMemcpyAsync(s.cchk, &cc, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(s.S[0], 0, sizeof(T) * mn, st));
+    CK(cudaMemsetAsync(s.S[1], 0, sizeof(T) * mn, st));
+    launch_fill_random<T>(s.Om, s.KM, s.tr[level].nh, s.ctrl, 1, nullptr, s.KM, 0x11ull, st);
+    CK(cudaMemsetAsync(s.Omf, 0, sizeof(T) * (size_t)n * s.KM, st));
+    CK(cudaMemsetAsync(wf.sig, 0, sizeof(T) * wf.KM, st));
+    launch_fill_random<T>(s.Omf, s.KM, n, s.cchk, 1, nullptr, s.KM, 0x12ull, st);
+
+    cpcp_info inf;
+    memset(&inf, 0, sizeof(inf));
+    inf.mu0 = mu0;
+    inf.pqd_fro = pqd;
+    int cur = 0, iter = 0, checks = 0, kf = cc.k, rank = 0;
+    double rel = INFINITY, prev = INFINITY;
+    cpcp_status status = CPCP_ERR_NOT_CONVERGED;
+    for (iter = 0; iter < o.max_iter;) {
+        one_iteration<T>(h, s, w, level, cur, o);
+        cur ^= 1;
+        if (level < 8) inf.level_iters[level]++;
+        iter++;
+        if (iter % o.check_every != 0) continue;
+        // weight of the iteration just done: mu_k = max(mu0 eta^k, mu)
+        const double mu_k = std::max(mu0 * std::pow(o.eta, (double)(iter - 1)), mu);
+        const bool at_final = !(mu_k > mu);
+        double spart;
+        rel = fine_check<T>(h, s, wf, cur, o, pqd, at_final ? mu : mu_k, &kf, &spart, &rank);
+        if (h->opt.trace && checks < h->opt.trace_cap) h->opt.trace[checks] = rel;
+        checks++;
+        if (at_final && rel <= tol) {
+            status = CPCP_OK;
+            break;
+        }
+        if (level > 0 && rel > o.ratio * prev) {
+            // move one level finer: restart momentum, warm-start the subspace
+            // from the restriction of the current right factor
+            level--;
+            prev = INFINITY;
+            Ctrl cur_c;
+            CK(cudaMemcpyAsync(&cur_c, s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            cur_c.t = 1.0;
+            cur_c.kcap = std::min(s.kcap0, s.tr[level].nh);
+            cur_c.k = std::min(cur_c.kcap, std::max(cur_c.rk + o.p, 1));
+            cur_c.k_next = cur_c.k;
+            CK(cudaMemcpyAsync(s.ctrl, &cur_c, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+            launch_restrict_rows<T>(s.B[cur], s.KM, s.Om, s.KM, s.tr[level], &s.ctrl->rk, s.KM, st);
+            // columns beyond the rank get random vectors
+            Ctrl tmp = cur_c;
+            tmp.k = std::max(cur_c.rk, 0);
+            tmp.k_next = cur_c.k;
+            Ctrl *ctmp = wsT<Ctrl>(h, "ctmp", 1);
+            CK(cudaMemcpyAsync(ctmp, &tmp, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+            launch_fill_random<T>(s.Om, s.KM, s.tr[level].nh, ctmp, 0, nullptr, s.KM, 0x77ull + level, st);
+            CK(cudaStreamSynchronize(st));
+        } else {
+            prev = rel;
+        }
+    }
+    inf.iters = iter;
+    inf.final_level = level;
+    inf.checks = checks;
+    inf.relkkt = rel;
+    Ctrl fin;
+    CK(cudaMemcpyAsync(&fin, s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    inf.rank = fin.rk;
+    // outputs
+    if (S_out) {
+        CK(cudaMemcpy2DAsync(S_out, sizeof(T) * lds, s.S[cur], sizeof(T) * s.ldS, sizeof(T) * n, m,
+                             cudaMemcpyDeviceToDevice, st));
+    }
+    if (L_out) {
+        PassArgs<T> r = base_args(s);
+        r.Ak = s.A[cur];
+        r.Bk = s.B[cur];
+        r.rk = &s.ctrl->rk;
+        r.M = L_out;
+        r.ldm = ldl;
+        launch_reconstruct<T>(r, st);
+    }
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    inf.status = status;
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    return status;
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return true;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+cpcp_status solve_dispatch(cpcp_context *h, int m, int n, const void *Dv, int64_t ldd, const uint32_t *Q,
+                           int64_t ldq, double lam, double mu, int levels, double tol, void *Lv, int64_t ldl,
+                           void *Sv, int64_t lds, cpcp_info *info)
+{
+    cudaStream_t st = h->stream;
+    const T *D = static_cast<const T *>(Dv);
+    T *L = static_cast<T *>(Lv), *S = static_cast<T *>(Sv);
+    bool host = !is_device_ptr(Dv);
+    if (host) {
+        // stage host buffers through device memory
+        T *Dd = wsT<T>(h, "stage_D", (size_t)m * n);
+        CK(cudaMemcpy2DAsync(Dd, sizeof(T) * n, D, sizeof(T) * ldd, sizeof(T) * n, m, cudaMemcpyHostToDevice, st));
+        const uint32_t *Qd = nullptr;
+        if (Q) {
+            uint32_t *q = wsT<uint32_t>(h, "stage_Q", (size_t)m * ldq);
+            CK(cudaMemcpyAsync(q, Q, sizeof(uint32_t) * m * ldq, cudaMemcpyHostToDevice, st));
+            Qd = q;
+        }
+        T *Ld = L ? wsT<T>(h, "stage_L", (size_t)m * n) : nullptr;
+        T *Sd = S ? wsT<T>(h, "stage_S", (size_t)m * n) : nullptr;
+        cpcp_status r = solve_dispatch<T>(h, m, n, Dd, n, Qd, ldq, lam, mu, levels, tol, Ld, n, Sd, n, info);
+        if (L)
+            CK(cudaMemcpy2DAsync(L, sizeof(T) * ldl, Ld, sizeof(T) * n, sizeof(T) * n, m, cudaMemcpyDeviceToHost,
+                                 st));
+        if (S)
+            CK(cudaMemcpy2DAsync(S, sizeof(T) * lds, Sd, sizeof(T) * n, sizeof(T) * n, m, cudaMemcpyDeviceToHost,
+                                 st));
+        CK(cudaStreamSynchronize(st));
+        return r;
+    }
+    if (n > m) {
+        // solve the transposed problem (PCP/CPCP are transpose invariant)
+        T *Dt = wsT<T>(h, "tr_D", (size_t)n * m);
+        launch_transpose<T>(m, n, D, ldd, Dt, m, st);
+        uint32_t *Qt = nullptr;
+        int64_t ldqt = (m + 31) / 32;
+        if (Q) {
+            Qt = wsT<uint32_t>(h, "tr_Q", (size_t)n * ldqt);
+            launch_transpose_mask(m, n, Q, ldq, Qt, ldqt, st);
+        }
+        T *Lt = L ? wsT<T>(h, "tr_L", (size_t)n * m) : nullptr;
+        T *St = S ? wsT<T>(h, "tr_S", (size_t)n * m) : nullptr;
+        cpcp_status r = solve_core<T>(h, n, m, Dt, m, Qt, ldqt, lam, mu, levels, tol, Lt, m, St, m, info);
+        if (L) launch_transpose<T>(n, m, Lt, m, L, ldl, st);
+        if (S) launch_transpose<T>(n, m, St, m, S, lds, st);
+        CK(cudaStreamSynchronize(st));
+        return r;
+    }
+    return solve_core<T>(h, m, n, D, ldd, Q, ldq, lam, mu, levels, tol, L, ldl, S, lds, info);
+}
+
+// ---------------------------------------------------------------------------
+// single step / standalone operators
+// ---------------------------------------------------------------------------
+
+template <typename T>
+cpcp_status step_impl(cpcp_context *h, int m, int n, const void *Dv, int64_t ldd, const uint32_t *Q, int64_t ldq,
+                      double lam, double mu_k, double beta, int halvings, const void *Skv, const void *Spv,
+                      int64_t lds_in, const void *Akv, int64_t lda, const void *Bkv, int64_t ldb, int r_k,
+                      const void *Apv, int64_t ldap, const void *Bpv, int64_t ldbp, int r_p, int k, int q,
+                      const void *Om0, int64_t ldo,
+                      void *Soutv, int64_t lds, void *Aov, int64_t ldao, void *Bov, int64_t ldbo, int *r_out,
+                      double *sigma_out)
+{
+    cudaStream_t st = h->stream;
+    TransferDev<T> tr = upload_transfer<T>(h, n, halvings, "step");
+    const int nh = tr.nh;
+    if (k < 1 || k > nh || k > kmax_small<T>())
+        throw CpcpError{CPCP_ERR_INVALID_ARG, "k must satisfy 1 <= k <= min(n_H, " +
+                                                  std::to_string(kmax_small<T>()) + ")"};
+    SvdWork<T> w = svd_work<T>(h, "st_", m, n, k);
+    const int KM = w.KM;
+    Ctrl c;
+    memset(&c, 0, sizeof(c));
+    c.tau = 0.5;
+    c.lam = lam;
+    c.mu_bar = mu_k;
+    c.mu_k = mu_k;
+    c.beta = beta;
+    c.theta_L = 0.5 * mu_k;
+    c.theta_S = 0.5 * lam * mu_k;
+    c.rk = r_k;
+    c.rp = r_p;
+    c.k = k;
+    c.k_next = k;
+    c.kcap = k;
+    c.seed = h->opt.seed ? h->opt.seed : 1;
+    Ctrl *cd = wsT<Ctrl>(h, "st_ctrl", 1);
+    CK(cudaMemcpyAsync(cd, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+    PassArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.m = m;
+    a.n = n;
+    a.D = static_cast<const T *>(Dv);
+    a.ldd = ldd;
+    a.Q = Q;
+    a.ldq = ldq;
+    a.Sk = static_cast<const T *>(Skv);
+    a.Sp = static_cast<const T *>(Spv);
+    a.lds = lds_in;
+    a.Sout = static_cast<T *>(Soutv);
+    a.ldso = lds;
+    a.Ak = static_cast<const T *>(Akv);
+    a.Bk = static_cast<const T *>(Bkv);
+    a.Ap = static_cast<const T *>(Apv);
+    a.Bp = static_cast<const T *>(Bpv);
+    a.ldfa = lda;
+    a.ldfb = ldb;
+    a.ldfap = ldap;
+    a.ldfbp = ldbp;
+    a.rk = &cd->rk;
+    a.rp = &cd->rp;
+    a.ctrl = cd;
+    const T *Mx;
+    int64_t ldx;
+    if (halvings > 0) {
+        int64_t ldh = round4(nh);
+        T *MH = wsT<T>(h, "st_MH", (size_t)m * ldh);
+        CK(cudaMemsetAsync(MH, 0, sizeof(T) * (size_t)m * ldh, st));
+        a.MH = MH;
+        a.ldh = ldh;
+        a.tr = tr;
+        launch_step_pass<T>(a, true, st);
+        Mx = MH;
+        ldx = ldh;
+    } else {
+        int64_t ldm = round4(n);
+        T *M = wsT<T>(h, "st_M", (size_t)m * ldm);
+        a.M = M;
+        a.ldm = ldm;
+        launch_step_pass<T>(a, false, st);
+        Mx = M;
+        ldx = ldm;
+    }
+    T *Om = wsT<T>(h, "st_Om", (size_t)nh * KM);
+    if (Om0) {
+        CK(cudaMemcpy2DAsync(Om, sizeof(T) * KM, Om0, sizeof(T) * ldo, sizeof(T) * k, nh, cudaMemcpyDefault, st));
+    } else {
+        launch_fill_random<T>(Om, KM, nh, cd, 1, nullptr, KM, 0x51ull, st);
+    }
+    subspace_svd<T>(h, w, m, nh, Mx, ldx, Om, q, &cd->k);
+    launch_svt_small<T>(w.Ut, w.sig, KM, cd, w.Us, w.sig64, st);
+    launch_gemm_nn<T>(m, 0, w.Qy, KM, w.Us, KM, static_cast<T *>(Aov), ldao, &cd->k, &cd->k, KM, st);
+    T *V = wsT<T>(h, "st_V", (size_t)nh * KM);
+    launch_gemm_nn<T>(nh, 0, w.Qz, KM, w.Wt, KM, V, KM, &cd->k, &cd->k, KM, st);
+    launch_prolong<T>(n, V, KM, static_cast<T *>(Bov), ldbo, tr, &cd->r_new, k, st);
+    Ctrl out;
+    CK(cudaMemcpyAsync(&out, cd, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    if (sigma_out) CK(cudaMemcpyAsync(sigma_out, w.sig64, sizeof(double) * k, cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    if (r_out) *r_out = out.r_new;
+    return CPCP_OK;
+}
+
+template <typename T>
+cpcp_status svd_impl(cpcp_context *h, int m, int n, const void *Mv, int64_t ldm, int k, int q, const void *Om0,
+                     int64_t ldo, void *Uv, int64_t ldu, void *Vv, int64_t ldv, double *sigma)
+{
+    cudaStream_t st = h->stream;
+    if (k < 1 || k > n || k > kmax_small<T>())
+        throw CpcpError{CPCP_ERR_INVALID_ARG, "k must satisfy 1 <= k <= min(n, " +
+                                                  std::to_string(kmax_small<T>()) + ")"};
+    SvdWork<T> w = svd_work<T>(h, "sv_", m, n, k);
+    const int KM = w.KM;
+    Ctrl c;
+    memset(&c, 0, sizeof(c));
+    c.k = k;
+    c.k_next = k;
+    c.kcap = k;
+    c.seed = h->opt.seed ? h->opt.seed : 1;
+    Ctrl *cd = wsT<Ctrl>(h, "sv_ctrl", 1);
+    CK(cudaMemcpyAsync(cd, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+    T *Om = wsT<T>(h, "sv_Om", (size_t)n * KM);
+    if (Om0)
+        CK(cudaMemcpy2DAsync(Om, sizeof(T) * KM, Om0, sizeof(T) * ldo, sizeof(T) * k, n, cudaMemcpyDefault, st));
+    else
+        launch_fill_random<T>(Om, KM, n, cd, 1, nullptr, KM, 0x5Dull, st);
+    subspace_svd<T>(h, w, m, n, static_cast<const T *>(Mv), ldm, Om, q, &cd->k);
+    launch_gemm_nn<T>(m, 0, w.Qy, KM, w.Ut, KM, static_cast<T *>(Uv), ldu, &cd->k, &cd->k, KM, st);
+    launch_gemm_nn<T>(n, 0, w.Qz, KM, w.Wt, KM, static_cast<T *>(Vv), ldv, &cd->k, &cd->k, KM, st);
+    // singular values as doubles
+    std::vector<T> sh(k);
+    CK(cudaMemcpyAsync(sh.data(), w.sig, sizeof(T) * k, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    std::vector<double> sd(sh.begin(), sh.end());
+    CK(cudaMemcpy(sigma, sd.data(), sizeof(double) * k, cudaMemcpyDefault));
+    return CPCP_OK;
+}
+
+template <typename F>
+cpcp_status guarded(cpcp_context *h, F &&f)
+{
+    try {
+        if (h) {
+            h->err.clear();
+            CK(cudaSetDevice(h->device));
+        }
+        return f();
+    } catch (const CpcpError &e) {
+        if (h) h->err = e.msg;
+        return e.st;
+    } catch (const std::exception &e) {
+        if (h) h->err = e.what();
+        return CPCP_ERR_NOMEM;
+    }
+}
+
+bool bad_dtype(cpcp_dtype dt) { return dt != CPCP_F32 && dt != CPCP_F64; }
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+const char *cpcp_status_string(cpcp_status s)
+{
+    switch (s) {
+    case CPCP_OK: return "ok";
+    case CPCP_ERR_INVALID_ARG: return "invalid argument";
+    case CPCP_ERR_NONFINITE_INPUT: return "non-finite observed input";
+    case CPCP_ERR_CUDA: return "CUDA error";
+    case CPCP_ERR_NOMEM: return "out of device memory";
+    case CPCP_ERR_NOT_CONVERGED: return "not converged (iteration cap)";
+    case CPCP_ERR_TIMEOUT: return "bounded device wait expired";
+    case CPCP_ERR_NUMERIC: return "numerical breakdown";
+    }
+    return "unknown status";
+}
+
+const char *cpcp_last_error(cpcp_handle h) { return h ? h->err.c_str() : ""; }
+
+cpcp_status cpcp_create(cpcp_handle *out, int device, void *stream, const cpcp_options *opt)
+{
+    if (!out) return CPCP_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        cudaGetLastError();
+        return CPCP_ERR_CUDA;
+    }
+    if (device < 0 || device >= count) return CPCP_ERR_INVALID_ARG;
+    cpcp_context *h = new (std::nothrow) cpcp_context();
+    if (!h) return CPCP_ERR_NOMEM;
+    h->device = device;
+    h->stream = static_cast<cudaStream_t>(stream);
+    if (opt) h->opt = *opt;
+    *out = h;
+    return CPCP_OK;
+}
+
+void cpcp_destroy(cpcp_handle h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (auto &kv : h->bufs)
+        if (kv.second.p) cudaFree(kv.second.p);
+    delete h;
+}
+
+cpcp_status cpcp_transfer_info(int n, int halvings, double *scale, int *nh)
+{
+    if (n < 1 || halvings < 0 || halvings > 5) return CPCP_ERR_INVALID_ARG;
+    try {
+        if (halvings == 0) {
+            if (scale) *scale = 1.0;
+            if (nh) *nh = n;
+            return CPCP_OK;
+        }
+        HostTransfer t = build_transfer(n, halvings);
+        if (scale) *scale = t.scale;
+        if (nh) *nh = t.nh;
+        return CPCP_OK;
+    } catch (const CpcpError &e) {
+        return e.st;
+    }
+}
+
+cpcp_status cpcp_solve(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D, int64_t ldd, const uint32_t *Q,
+                       int64_t ldq, double lambda, double mu, int levels, double tol, void *L_out, int64_t ldl,
+                       void *S_out, int64_t lds, cpcp_info *info)
+{
+    if (!h) return CPCP_ERR_INVALID_ARG;
+    return guarded(h, [&]() -> cpcp_status {
+        if (m < 1 || n < 1 || !D || bad_dtype(dt)) throw CpcpError{CPCP_ERR_INVALID_ARG, "bad sizes, D or dtype"};
+        if (!(lambda > 0) || !(mu > 0) || !(tol > 0))
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "lambda, mu and tol must be positive"};
+        if (levels < 1 || levels > 6) throw CpcpError{CPCP_ERR_INVALID_ARG, "levels must be in [1, 6]"};
+        if (ldd < n || (L_out && ldl < n) || (S_out && lds < n))
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "leading dimension smaller than n"};
+        if (Q && ldq < (n + 31) / 32) throw CpcpError{CPCP_ERR_INVALID_ARG, "ldq < ceil(n/32)"};
+        int mm = std::max(m, n), nn = std::min(m, n);
+        int nh = coarse_dim(nn, levels - 1);
+        if (nh < 1) throw CpcpError{CPCP_ERR_INVALID_ARG, "coarse width below 1"};
+        if (levels > 1 && 2 * nh > mm + 1)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "coarse width exceeds (m+1)/2 (Assumption 2)"};
+        if (dt == CPCP_F32)
+            return solve_dispatch<float>(h, m, n, D, ldd, Q, ldq, lambda, mu, levels, tol, L_out, ldl, S_out, lds,
+                                         info);
+        return solve_dispatch<double>(h, m, n, D, ldd, Q, ldq, lambda, mu, levels, tol, L_out, ldl, S_out, lds,
+                                      info);
+    });
+}
+
+cpcp_status cpcp_step(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D, int64_t ldd, const uint32_t *Q,
+                      int64_t ldq, double lambda, double mu_k, double beta, int halvings, const void *S_k,
+                      const void *S_p, int64_t lds_in, const void *A_k, int64_t lda, const void *B_k, int64_t ldb,
+                      int r_k, const void *A_p, int64_t ldap, const void *B_p, int64_t ldbp, int r_p, int k, int q,
+                      const void *Omega0, int64_t ldo, void *S_out, int64_t lds, void *A_out, int64_t ldao,
+                      void *B_out, int64_t ldbo, int *r_out, double *sigma_out)
+{
+    if (!h) return CPCP_ERR_INVALID_ARG;
+    return guarded(h, [&]() -> cpcp_status {
+        if (m < 1 || n < 1 || n > m || !D || !S_k || !S_out || !A_out || !B_out || bad_dtype(dt))
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "bad sizes or NULL buffer (cpcp_step needs n <= m)"};
+        if (!(lambda > 0) || !(mu_k > 0) || beta < 0 || halvings < 0 || halvings > 5 || q < 1 || r_k < 0 ||
+            r_p < 0 || (r_k > 0 && (!A_k || !B_k)) || (r_p > 0 && (!A_p || !B_p)) || (beta > 0 && !S_p))
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "bad step parameters"};
+        if (dt == CPCP_F32)
+            return step_impl<float>(h, m, n, D, ldd, Q, ldq, lambda, mu_k, beta, halvings, S_k, S_p, lds_in, A_k,
+                                    lda, B_k, ldb, r_k, A_p, ldap, B_p, ldbp, r_p, k, q, Omega0, ldo, S_out, lds,
+                                    A_out, ldao, B_out, ldbo, r_out, sigma_out);
+        return step_impl<double>(h, m, n, D, ldd, Q, ldq, lambda, mu_k, beta, halvings, S_k, S_p, lds_in, A_k, lda,
+                                 B_k, ldb, r_k, A_p, ldap, B_p, ldbp, r_p, k, q, Omega0, ldo, S_out, lds, A_out,
+                                 ldao, B_out, ldbo, r_out, sigma_out);
+    });
+}
+
+cpcp_status cpcp_restrict(cpcp_handle h, int m, int n, int halvings, cpcp_dtype dt, const void *M, int64_t ldm,
+                          void *MH, int64_t ldh)
+{
+    if (!h) return CPCP_ERR_INVALID_ARG;
+    return guarded(h, [&]() -> cpcp_status {
+        if (m < 1 || n < 1 || halvings < 0 || halvings > 5 || !M || !MH || bad_dtype(dt))
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "bad restrict arguments"};
+        if (dt == CPCP_F32) {
+            TransferDev<float> tr = upload_transfer<float>(h, n, halvings, "op");
+            launch_restrict<float>(m, n, static_cast<const float *>(M), ldm, static_cast<float *>(MH), ldh, tr,
+                                   h->stream);
+        } else {
+            TransferDev<double> tr = upload_transfer<double>(h, n, halvings, "op");
+            launch_restrict<double>(m, n, static_cast<const double *>(M), ldm, static_cast<double *>(MH), ldh, tr,
+                                    h->stream);
+        }
+        CK(cudaStreamSynchronize(h->stream));
+        CK(cudaGetLastError());
+        return CPCP_OK;
+    });
+}
+
+cpcp_status cpcp_prolong(cpcp_handle h, int n, int halvings, int r, cpcp_dtype dt, const void *V, int64_t ldv,
+                         void *B, int64_t ldb)
+{
+    if (!h) return CPCP_ERR_INVALID_ARG;
+    return guarded(h, [&]() -> cpcp_status {
+        if (n < 1 || r < 1 || halvings < 0 || halvings > 5 || !V || !B || bad_dtype(dt) || ldb < r)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "bad prolong arguments"};
+        if (dt == CPCP_F32) {
+            TransferDev<float> tr = upload_transfer<float>(h, n, halvings, "op");
+            launch_prolong<float>(n, static_cast<const float *>(V), ldv, static_cast<float *>(B), ldb, tr, nullptr,
+                                  r, h->stream);
+        } else {
+            TransferDev<double> tr = upload_transfer<double>(h, n, halvings, "op");
+            launch_prolong<double>(n, static_cast<const double *>(V), ldv, static_cast<double *>(B), ldb, tr, nullptr,
+                                   r, h->stream);
+        }
+        CK(cudaStreamSynchronize(h->stream));
+        CK(cudaGetLastError());
+        return CPCP_OK;
+    });
+}
+
+cpcp_status cpcp_svd(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *M, int64_t ldm, int k, int q,
+                     const void *Omega0, int64_t ldo, void *U, int64_t ldu, void *V, int64_t ldv, double *sigma)
+{
+    if (!h) return CPCP_ERR_INVALID_ARG;
+    return guarded(h, [&]() -> cpcp_status {
+        if (m < 1 || n < 1 || n > m || !M || !U || !V || !sigma || q < 1 || bad_dtype(dt))
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "bad svd arguments (needs m >= n)"};
+        if (dt == CPCP_F32) return svd_impl<float>(h, m, n, M, ldm, k, q, Omega0, ldo, U, ldu, V, ldv, sigma);
+        return svd_impl<double>(h, m, n, M, ldm, k, q, Omega0, ldo, U, ldu, V, ldv, sigma);
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+"""C-ABI boundary checks that need no GPU: the CUDA library builds for
+sm_103a, loads, exports every entry point declared in include/cpcp.h, and its
+host-side logic (the composite transfer operator's scale and coarse width,
+Sec. 3.1 / Assumption 4) agrees with the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2206_13369_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "cpcp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cpcp_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ("cpcp_create", "cpcp_destroy", "cpcp_solve", "cpcp_step", "cpcp_restrict", "cpcp_prolong",
+                 "cpcp_svd", "cpcp_status_string", "cpcp_last_error", "cpcp_transfer_info"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_lists_every_symbol(lib):
+    from paper_2206_13369_gb300 import cpcp
+    assert sorted(cpcp.EXPORTED) == declared_functions()
+
+
+def test_status_strings(lib):
+    lib.cpcp_status_string.restype = ctypes.c_char_p
+    assert lib.cpcp_status_string(0) == b"ok"
+    assert lib.cpcp_status_string(1) == b"invalid argument"
+    assert lib.cpcp_status_string(99) == b"unknown status"
+
+
+@pytest.mark.parametrize("n,h", [(200, 1), (96, 2), (75, 3), (301, 2), (16, 3), (1, 0), (7, 0)])
+def test_transfer_scale_matches_oracle(lib, n, h):
+    sc = ctypes.c_double(0)
+    nh = ctypes.c_int(0)
+    lib.cpcp_transfer_info.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int)]
+    assert lib.cpcp_transfer_info(n, h, ctypes.byref(sc), ctypes.byref(nh)) == 0
+    assert nh.value == oracle.coarse_dim(n, h)
+    if h == 0:
+        assert sc.value == 1.0
+    else:
+        _, sc_or = oracle.restriction(n, h, scaled=True)
+        assert abs(sc.value - sc_or) <= 1e-13 * sc_or
+
+
+def test_transfer_rejects_bad_sizes(lib):
+    sc = ctypes.c_double(0)
+    nh = ctypes.c_int(0)
+    assert lib.cpcp_transfer_info(0, 1, ctypes.byref(sc), ctypes.byref(nh)) == 1
+    assert lib.cpcp_transfer_info(100, 6, ctypes.byref(sc), ctypes.byref(nh)) == 1
+
+
+def test_create_without_device_fails_cleanly(lib):
+    # on a machine without a GPU the call returns a status instead of aborting;
+    # on a GPU machine an out-of-range device index is an argument error
+    h = ctypes.c_void_p()
+    lib.cpcp_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    st = lib.cpcp_create(ctypes.byref(h), 9999, None, None)
+    assert st in (1, 3)
+    assert not h.value
+
+
+def test_pack_mask_layout():
+    from paper_2206_13369_gb300 import cpcp
+    rng = np.random.default_rng(0)
+    m = rng.random((7, 70)) < 0.5
+    p = cpcp.pack_mask(m)
+    assert p.shape == (7, 3) and p.dtype == np.uint32
+    for i in range(7):
+        for j in range(70):
+            assert bool((int(p[i, j // 32]) >> (j % 32)) & 1) == bool(m[i, j])

@@ -405,3 +405,47 @@ def test_ml_ialm_is_only_approximate():
     assert fg1[-1] <= 1e-9 and fg2[-1] <= 1e-4
     assert f2 > 1.05 * f1
     assert np.linalg.norm(L1 - p["L0"]) <= 1e-6 * np.linalg.norm(p["L0"])
+
+
+# ----------------------------------------------------------------------------
+# single step (the hot path of one iteration)
+# ----------------------------------------------------------------------------
+
+def test_step_fixed_point_at_optimum(cfg1_solutions):
+    # the optimum of eq. (cpcp) is a fixed point of the fine-level prox step
+    p, sols = cfg1_solutions
+    L, S, _ = sols[1]
+    S1, L1, r = oracle.step(p["D"], None, p["lam"], p["mu"], 0.0, 0, S, S, L, L)
+    assert np.linalg.norm(L1 - L) <= 1e-8 * np.linalg.norm(L)
+    assert np.linalg.norm(S1 - S) <= 1e-8 * np.linalg.norm(S)
+    assert r == sols[1][2]["rank"]
+
+
+def test_step_coarse_prox_optimality():
+    # S_out and L_out solve their prox subproblems: S_out minimises
+    # th_S ||s||_1 + 1/2 ||s - X_S||^2 and L_H minimises
+    # th_L ||L_H||_* + 1/2 ||L_H - M R||^2 with L_out = L_H R^T (Alg. 4).
+    rng = np.random.default_rng(21)
+    m, n, h = 48, 40, 2
+    p = W.planted_cpcp(m, n, 3, 0.1, 0.8, seed=22)
+    D, mask, lam = p["D"], p["mask"], p["lam"]
+    mu_k, beta = 0.3, 0.4
+    Sk, Sp = rng.normal(size=(m, n)) * mask, rng.normal(size=(m, n)) * mask
+    Lk, Lp = rng.normal(size=(m, 3)) @ rng.normal(size=(3, n)), rng.normal(size=(m, 2)) @ rng.normal(size=(2, n))
+    S1, L1, r = oracle.step(D, mask, lam, mu_k, beta, h, Sk, Sp, Lk, Lp)
+    Lh, Sh = Lk + beta * (Lk - Lp), Sk + beta * (Sk - Sp)
+    G = np.where(mask, Lh + Sh - D, 0.0)
+    XS, M = Sh - 0.5 * G, Lh - 0.5 * G
+    thS, thL = 0.5 * lam * mu_k, 0.5 * mu_k
+    on = S1 != 0
+    assert np.allclose((XS - S1)[on], thS * np.sign(S1[on]), atol=1e-12)
+    assert np.all(np.abs(XS[~on]) <= thS + 1e-12)
+    R, _ = oracle.restriction(n, h, scaled=True)
+    LH = L1 @ R @ np.linalg.inv(R.T @ R)
+    assert np.allclose(LH @ R.T, L1, atol=1e-10)  # L_out lies in the prolongation range
+    U, s, Vt = np.linalg.svd(LH, full_matrices=False)
+    rr = int((s > 1e-10).sum())
+    assert rr == r
+    Wm = (M @ R - LH) / thL - U[:, :rr] @ Vt[:rr]
+    assert np.linalg.norm(Wm, 2) <= 1 + 1e-9
+    assert np.max(np.abs(U[:, :rr].T @ Wm)) < 1e-9 and np.max(np.abs(Wm @ Vt[:rr].T)) < 1e-9
