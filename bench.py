@@ -1,0 +1,291 @@
+#!/usr/bin/env python
+"""Benchmark: time to a 1e-6 relative KKT residual of the multilevel CPCP
+solver, against the single-level solver, on the same GB300.
+
+Workload (one "step" = one full solve, all of the hot path):
+  CPCP, fp32, m = n = 2000, L0 rank 50 with unit-variance entries, S0 with
+  10% support uniform in [-5, 5], mask Bernoulli(0.8), lambda = 1/sqrt(2000),
+  mu = 1e-3 ||P_Q D||_2, 3 levels (two halvings, n_H = 500), seed 2000.
+  Synthetic and seeded; inputs resident in HBM when the timed region starts.
+  Between timed steps a 256 MB buffer is written to flush the 129 MB L2.
+
+JSON fields beyond the base contract: the single-level time on the same
+inputs, the roofline of the fused iteration pass (algorithmic bytes per launch
+over its CUDA-event duration, against the measured HBM copy bandwidth), the
+end-to-end time through the C ABI with host buffers, the clocks seen during the
+timed region, and the fp64 oracle timed on the host cores on a bounded sample.
+
+Multi-GPU (torchrun): the solve does not shard, so every rank solves its own
+replica of the workload ("replicas only"); value is the max over ranks.
+`--impl reference` times the fp64 CPU oracle (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-6 rel KKT residual, multilevel vs single-level CPCP, same GB300"
+WORKLOAD = {"workload": "cpcp-2000x2000-r50-fp32-3lv", "m": 2000, "n": 2000, "rank": 50, "corruption": 0.10,
+            "observed": 0.8, "levels": 3, "tol": 1e-6, "seed": 2000,
+            "l2": "flushed between timed steps (256 MB write)"}
+TOL = 1e-6
+# iterations the multilevel solve takes on this workload (measured on the GPU
+# arm, which also reports its own count); the CPU arms scale a per-iteration
+# sample by it
+ITERS_MULTILEVEL = 340
+ORACLE_SAMPLE_STEPS = 2
+
+
+def make_workload():
+    from paper_2206_13369_gb300 import workloads
+    return workloads.planted_cpcp(2000, 2000, 50, 0.10, 0.8, 2000, levels=3)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i - 5] for r in self.rows for i in range(5, 9) if r[i].lower() == "active"})
+        loaded = sorted(sm)[len(sm) // 2:] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def oracle_sample(p, steps: int) -> tuple[float, int, str]:
+    """Seconds per iteration of the fp64 oracle on the full workload: `steps`
+    proximal steps at the coarsest level (n_H = 500) from the zero state.  A
+    lower bound of the oracle's per-iteration cost (fine-level steps need a
+    2000 x 2000 SVD)."""
+    import numpy as np
+
+    import oracle
+    D, mask = p["D"], p["mask"]
+    Z = np.zeros_like(D)
+    S, L = Z, Z
+    mu0 = 100.0 * p["mu"]
+    t0 = time.perf_counter()
+    for i in range(steps):
+        S1, L1, _ = oracle.step(D, mask, p["lam"], mu0, 0.0 if i == 0 else 0.3, 2, S, S, L, L)
+        S, L = S1, L1
+    dt = (time.perf_counter() - t0) / steps
+    sample = (f"{steps} fp64 oracle proximal steps at the coarsest level (n_H=500) of the full 2000x2000 "
+              f"workload; seconds per step x {ITERS_MULTILEVEL} iterations")
+    return dt, oracle.num_threads(), sample
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    p = make_workload()
+    vals = []
+    for i in range(args.warmup + args.steps):
+        dt, cores, sample = oracle_sample(p, 1)
+        if i >= args.warmup:
+            vals.append(dt * ITERS_MULTILEVEL)
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": WORKLOAD,
+            "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
+                             "sample": sample.replace(f"{ORACLE_SAMPLE_STEPS} fp64", "1 fp64")},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2206_13369_gb300 import cpcp
+
+    p = make_workload()
+    m, n = p["D"].shape
+    D = torch.as_tensor(p["D"], dtype=torch.float32).cuda()
+    Qh = cpcp.pack_mask(p["mask"])
+    Q = torch.as_tensor(Qh).cuda()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    h = cpcp.Handle(local, stream=stream, profile=1)
+
+    def solve(levels):
+        return h.solve(D, Q, p["lam"], p["mu"], levels=levels, tol=TOL)
+
+    def timed(levels, steps):
+        times, infos = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, info = solve(levels)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            infos.append(info)
+        return times, infos
+
+    for _ in range(args.warmup):
+        solve(args.levels)
+        solve(1)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_ml, inf_ml = timed(args.levels, args.steps)
+    clocks_info = clocks.stop()
+    t_sl, inf_sl = timed(1, args.steps)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ml = statistics.mean(t_ml)
+    sl = statistics.mean(t_sl)
+    if world > 1:
+        t = torch.tensor([ml, sl], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ml, sl = float(t[0]), float(t[1])
+
+    # end to end through the C ABI with host buffers (H2D of D and the mask,
+    # solve, D2H of L and S inside the timed region)
+    Dh = torch.as_tensor(p["D"], dtype=torch.float32).pin_memory().numpy()
+    Qhp = torch.as_tensor(Qh).pin_memory().numpy()
+    Lh = torch.empty((m, n), dtype=torch.float32).pin_memory().numpy()
+    Sh = torch.empty((m, n), dtype=torch.float32).pin_memory().numpy()
+    e2e = []
+    for i in range(args.steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.solve(Dh, Qhp, p["lam"], p["mu"], levels=args.levels, tol=TOL, L_out=Lh, S_out=Sh)
+        torch.cuda.synchronize()
+        if i > 0:
+            e2e.append(time.perf_counter() - t0)
+
+    # roofline of the fused iteration pass from the events recorded inside the
+    # timed solves: algorithmic bytes per launch / average launch duration
+    peaks = measured_peaks()
+    nh = math.ceil(n / 4)
+    obs_bytes = {"pass_fine": (4 + 4 + 4 + 4 + 4) * m * n + m * math.ceil(n / 32) * 4,
+                 "pass_coarse": (4 + 4 + 4 + 4) * m * n + m * math.ceil(n / 32) * 4 + 4 * m * nh}
+    tot = {k: sum(i["phase_ms"][k] for i in inf_ml) for k in ("pass_fine", "pass_coarse", "svt", "check")}
+    cnt = {k: sum(i["phase_count"][k] for i in inf_ml) for k in ("pass_fine", "pass_coarse", "svt", "check")}
+    dom = "pass_fine" if tot["pass_fine"] >= tot["pass_coarse"] else "pass_coarse"
+    avg_ms = tot[dom] / max(cnt[dom], 1)
+    achieved = obs_bytes[dom] / (avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": f"pass_kernel ({dom})",
+                "bytes_per_launch": obs_bytes[dom], "avg_launch_ms": avg_ms, "peak_source": peaks["source"],
+                "phase_share": {k: tot[k] / max(sum(tot.values()), 1e-30) for k in tot}}
+
+    line = {"metric": METRIC, "value": ml, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ml * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(WORKLOAD, parallelism="replicas" if world > 1 else "single"),
+            "single_level": {"value": sl, "unit": "s", "iters": inf_sl[-1]["iters"]},
+            "multilevel_over_single": ml / sl,
+            "multilevel": {"iters": inf_ml[-1]["iters"], "level_iters": inf_ml[-1]["level_iters"][:3],
+                           "relkkt": inf_ml[-1]["relkkt"], "rank": inf_ml[-1]["rank"]},
+            "clocks": clocks_info,
+            "e2e": {"value": statistics.mean(e2e), "unit": "s",
+                    "h2d_bytes_per_step": int(Dh.nbytes + Qhp.nbytes),
+                    "d2h_bytes_per_step": int(Lh.nbytes + Sh.nbytes)},
+            "gpu_launches": int(sum(i["launches"] for i in inf_ml) / len(inf_ml)),
+            "roofline": roofline}
+    if rank == 0:
+        dt, cores, sample = oracle_sample(p, ORACLE_SAMPLE_STEPS)
+        line["cpu_baseline"] = {"value": dt * ITERS_MULTILEVEL, "unit": "s", "cores": cores, "kind": "oracle",
+                                "sample": sample}
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--levels", type=int, default=3)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

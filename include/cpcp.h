@@ -80,7 +80,17 @@ typedef struct {
     uint64_t seed;         /* seed of the random start block of the subspace (1) */
     double *trace;         /* optional host array: rel-KKT of each residual check */
     int trace_cap;         /* capacity of trace (entries written: info.checks) */
+    int profile;           /* nonzero: time the phases with CUDA events (info.phase_*) */
 } cpcp_options;
+
+/* Phases timed when cpcp_options.profile is set. */
+enum {
+    CPCP_PHASE_PASS_COARSE = 0, /* fused iteration pass with restriction (level > 0) */
+    CPCP_PHASE_PASS_FINE = 1,   /* fused iteration pass on the fine level */
+    CPCP_PHASE_SVT = 2,         /* subspace SVD + SVT + prolongation of one iteration */
+    CPCP_PHASE_CHECK = 3,       /* fine residual check (pass, fine SVD, difference) */
+    CPCP_NUM_PHASES = 4
+};
 
 /* Per-solve report. */
 typedef struct {
@@ -94,6 +104,9 @@ typedef struct {
     double mu0;            /* first continuation weight used */
     double pqd_fro;        /* ||P_Q D||_F */
     double seconds;        /* wall time of the solve (host clock) */
+    double phase_ms[4];    /* device time per phase (profile only), CPCP_PHASE_* */
+    int phase_count[4];    /* timed intervals per phase */
+    long long launches;    /* CUDA kernels launched by the solve */
 } cpcp_info;
 
 /* Returns a static description of a status code. */

@@ -33,18 +33,24 @@ class Options(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("check_every", C.c_int), ("eta", C.c_double), ("mu0", C.c_double),
                 ("switch_ratio", C.c_double), ("k_max", C.c_int), ("oversample", C.c_int),
                 ("power_iters", C.c_int), ("check_power_iters", C.c_int), ("start_level", C.c_int),
-                ("seed", C.c_uint64), ("trace", C.POINTER(C.c_double)), ("trace_cap", C.c_int)]
+                ("seed", C.c_uint64), ("trace", C.POINTER(C.c_double)), ("trace_cap", C.c_int),
+                ("profile", C.c_int)]
 
 
 class Info(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("level_iters", C.c_int * 8), ("final_level", C.c_int),
                 ("rank", C.c_int), ("checks", C.c_int), ("relkkt", C.c_double), ("mu0", C.c_double),
-                ("pqd_fro", C.c_double), ("seconds", C.c_double)]
+                ("pqd_fro", C.c_double), ("seconds", C.c_double), ("phase_ms", C.c_double * 4),
+                ("phase_count", C.c_int * 4), ("launches", C.c_longlong)]
+
+    PHASES = ("pass_coarse", "pass_fine", "svt", "check")
 
     def as_dict(self) -> dict:
         return {"status": self.status, "iters": self.iters, "level_iters": list(self.level_iters),
                 "final_level": self.final_level, "rank": self.rank, "checks": self.checks,
-                "relkkt": self.relkkt, "mu0": self.mu0, "pqd_fro": self.pqd_fro, "seconds": self.seconds}
+                "relkkt": self.relkkt, "mu0": self.mu0, "pqd_fro": self.pqd_fro, "seconds": self.seconds,
+                "phase_ms": dict(zip(self.PHASES, list(self.phase_ms))),
+                "phase_count": dict(zip(self.PHASES, list(self.phase_count))), "launches": self.launches}
 
 
 _vp, _i64, _int, _dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double

@@ -9,6 +9,11 @@
 
 namespace cpcp {
 
+// Number of kernels this library has launched in the process (reported per
+// solve in cpcp_info.launches).
+extern unsigned long long g_kernel_launches;
+#define CPCP_COUNT_LAUNCH() (++::cpcp::g_kernel_launches)
+
 // Device-resident scalars of one solve.  The per-iteration schedule (momentum
 // weight, continuation weight, thresholds, ranks, subspace width) lives here
 // so that an iteration needs no host round trip and can be graph-captured.
@@ -123,7 +128,7 @@ void launch_gemm_nn_splitk(int rows, int K, const T *A, int64_t lda, const T *B,
                            T *partial, const int *kdyn_N, int kmaxN, cudaStream_t st);
 template <typename T>
 int launch_gemm_tn_partial(int rows, int K, const T *A, int64_t lda, const T *B, int64_t ldb, T *partial,
-                           const int *kdyn_N, int kmaxN, int kmaxK, cudaStream_t st);
+                           const int *kdyn_N, int kmaxN, int kmaxK, cudaStream_t st, const int *skip = nullptr);
 template <typename T>
 void launch_reduce_partial(const T *partial, int splits, int K, int N, T *C, int64_t ldc, const int *kdyn_K,
                            const int *kdyn_N, cudaStream_t st);
@@ -142,11 +147,15 @@ void launch_transpose_mask(int rows, int cols, const uint32_t *in, int64_t ldi, 
                            cudaStream_t st);
 
 // small dense kernels (one CTA)
+// Cholesky pass of CholeskyQR: R = chol(X^T X) from row-split partial Gram
+// matrices; well_out / skip_in implement the skip of a second pass
 template <typename T>
-void launch_chol(const T *partialG, int splits, int kmax, const int *kdyn, T *R, T *Rinv, const T *Rprev,
-                 T *Rtot, int ldr, cudaStream_t st);
+void launch_chol(const T *partialG, int splits, int kmax, const int *kdyn, T *R, T *Rinv, const T *Rprev, T *Rtot,
+                 int ldr, int *well_out, const int *skip_in, cudaStream_t st);
+// ctrl (optional): skip rotations that cannot change SVT_{ctrl->theta_L}
 template <typename T>
-void launch_jacobi(const T *Rz, int ldr, const int *kdyn, T *Ut, T *Wt, T *sig, int kmax, cudaStream_t st);
+void launch_jacobi(const T *Rz, int ldr, const int *kdyn, T *Ut, T *Wt, T *sig, int kmax, const Ctrl *ctrl,
+                   cudaStream_t st);
 template <typename T>
 void launch_svt_small(const T *Ut, const T *sig, int ldr, Ctrl *ctrl, T *Us, double *sig64, cudaStream_t st);
 // all_cols = 1: fill columns [0, ctrl->k); else columns [ctrl->k, ctrl->k_next)

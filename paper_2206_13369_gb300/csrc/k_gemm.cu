@@ -94,8 +94,9 @@ template <typename T>
 __global__ void __launch_bounds__(NT)
     gemm_tn_partial_kernel(int rows, int Kstat, int rows_per_split, const T *__restrict__ A, int64_t lda,
                            const T *__restrict__ B, int64_t ldb, T *__restrict__ partial, const int *kdynK,
-                           const int *kdynN, int Nstat, int Kmax, int Nmax)
+                           const int *kdynN, int Nstat, int Kmax, int Nmax, const int *skip)
 {
+    if (skip != nullptr && *skip) return;
     __shared__ T As[TK][TM + 4];
     __shared__ T Bs[TK][TN + 4];
     const int K = kdynK ? *kdynK : Kstat;
@@ -253,6 +254,7 @@ void launch_restrict_rows(const T *B, int64_t ldb, T *Om, int64_t ldo, const Tra
                           int kmax, cudaStream_t st)
 {
     dim3 grid((kmax + 63) / 64, tr.nh);
+    CPCP_COUNT_LAUNCH();
     restrict_rows_kernel<T><<<grid, 64, 0, st>>>(B, ldb, Om, ldo, tr, kdyn, kmax);
 }
 
@@ -260,6 +262,7 @@ template <typename T>
 void launch_transpose(int rows, int cols, const T *A, int64_t lda, T *B, int64_t ldb, cudaStream_t st)
 {
     dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+    CPCP_COUNT_LAUNCH();
     transpose_kernel<T><<<grid, dim3(32, 8), 0, st>>>(rows, cols, A, lda, B, ldb);
 }
 
@@ -267,6 +270,7 @@ void launch_transpose_mask(int rows, int cols, const uint32_t *in, int64_t ldi, 
                            cudaStream_t st)
 {
     dim3 grid((unsigned)((ldo + 63) / 64), cols);
+    CPCP_COUNT_LAUNCH();
     transpose_mask_kernel<<<grid, 64, 0, st>>>(rows, cols, in, ldi, out, ldo);
 }
 
@@ -276,6 +280,7 @@ void launch_gemm_nn(int rows, int K, const T *A, int64_t lda, const T *B, int64_
 {
     if (rows <= 0 || kmaxN <= 0) return;
     dim3 grid((rows + TM - 1) / TM, (kmaxN + TN - 1) / TN);
+    CPCP_COUNT_LAUNCH();
     gemm_nn_kernel<T><<<grid, NT, 0, st>>>(rows, K, A, lda, B, ldb, C, ldc, kdyn_K, kdyn_N, kmaxN, 1 << 30);
 }
 
@@ -297,6 +302,7 @@ void launch_gemm_nn_splitk(int rows, int K, const T *A, int64_t lda, const T *B,
     ks = (ks + TK - 1) / TK * TK;
     splits = (K + ks - 1) / ks;
     dim3 grid(rblocks, (kmaxN + TN - 1) / TN, splits);
+    CPCP_COUNT_LAUNCH();
     gemm_nn_kernel<T><<<grid, NT, 0, st>>>(rows, K, A, lda, B, ldb, partial, ldc, nullptr, kdyn_N, kmaxN, ks);
     launch_reduce_partial<T>(partial, splits, rows, (int)ldc, C, ldc, nullptr, kdyn_N, st);
 }
@@ -304,9 +310,11 @@ void launch_gemm_nn_splitk(int rows, int K, const T *A, int64_t lda, const T *B,
 // returns the number of splits used (partial holds splits x kmaxK x kmaxN)
 template <typename T>
 int launch_gemm_tn_partial(int rows, int K, const T *A, int64_t lda, const T *B, int64_t ldb, T *partial,
-                           const int *kdyn_N, int kmaxN, int kmaxK, cudaStream_t st)
+                           const int *kdyn_N, int kmaxN, int kmaxK, cudaStream_t st, const int *skip)
 {
-    int splits = (rows + 127) / 128;
+    // Gram matrices (K < 0) are small and reduced by one CTA: fewer, taller splits
+    const int per = K < 0 ? 256 : 128;
+    int splits = (rows + per - 1) / per;
     if (splits > 64) splits = 64;
     if (splits < 1) splits = 1;
     int rps = (rows + splits - 1) / splits;
@@ -316,8 +324,9 @@ int launch_gemm_tn_partial(int rows, int K, const T *A, int64_t lda, const T *B,
     dim3 grid((kmaxK + TM - 1) / TM, (kmaxN + TN - 1) / TN, splits);
     // K dynamic when K < 0 (then the K dimension follows kdyn_N: Gram matrices)
     const int *kdynK = K < 0 ? kdyn_N : nullptr;
+    CPCP_COUNT_LAUNCH();
     gemm_tn_partial_kernel<T><<<grid, NT, 0, st>>>(rows, K < 0 ? kmaxK : K, rps, A, lda, B, ldb, partial, kdynK,
-                                                   kdyn_N, kmaxN, kmaxK, kmaxN);
+                                                   kdyn_N, kmaxN, kmaxK, kmaxN, skip);
     return splits;
 }
 
@@ -328,6 +337,7 @@ void launch_reduce_partial(const T *partial, int splits, int K, int N, T *C, int
     int64_t tot = (int64_t)K * N;
     int blocks = (int)((tot + 255) / 256);
     if (blocks < 1) return;
+    CPCP_COUNT_LAUNCH();
     reduce_partial_kernel<T><<<blocks, 256, 0, st>>>(partial, splits, K, N, K, N, C, ldc, kdyn_K, kdyn_N);
 }
 
@@ -336,6 +346,7 @@ void launch_restrict(int m, int n, const T *M, int64_t ldm, T *MH, int64_t ldh, 
                      cudaStream_t st)
 {
     dim3 grid((tr.nh + 127) / 128, m);
+    CPCP_COUNT_LAUNCH();
     restrict_kernel<T><<<grid, 128, 0, st>>>(m, n, M, ldm, MH, ldh, tr);
 }
 
@@ -344,6 +355,7 @@ void launch_prolong(int n, const T *V, int64_t ldv, T *B, int64_t ldb, const Tra
                     int kmax, cudaStream_t st)
 {
     dim3 grid((kmax + 63) / 64, n);
+    CPCP_COUNT_LAUNCH();
     prolong_kernel<T><<<grid, 64, 0, st>>>(n, V, ldv, B, ldb, tr, kdyn, kmax);
 }
 
@@ -353,7 +365,7 @@ void launch_prolong(int n, const T *V, int64_t ldv, T *B, int64_t ldb, const Tra
     template void launch_gemm_nn_splitk<T>(int, int, const T *, int64_t, const T *, int64_t, T *, int64_t, T *,      \
                                            const int *, int, cudaStream_t);                                        \
     template int launch_gemm_tn_partial<T>(int, int, const T *, int64_t, const T *, int64_t, T *, const int *, int, \
-                                           int, cudaStream_t);                                                     \
+                                           int, cudaStream_t, const int *);                                        \
     template void launch_reduce_partial<T>(const T *, int, int, int, T *, int64_t, const int *, const int *,        \
                                            cudaStream_t);                                                          \
     template void launch_restrict<T>(int, int, const T *, int64_t, T *, int64_t, const TransferDev<T> &,            \

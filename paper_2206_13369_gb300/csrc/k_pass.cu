@@ -340,6 +340,7 @@ int launch_mode(const PassArgs<T> &a, cudaStream_t st)
 {
     static_assert(sizeof(Smem<T>) <= 48 * 1024, "pass tile exceeds default shared memory");
     dim3 grid((a.n + BN - 1) / BN, (a.m + BM - 1) / BM);
+    CPCP_COUNT_LAUNCH();
     pass_kernel<T, MODE><<<grid, NT, sizeof(Smem<T>), st>>>(a, vec_flags_for(a));
     return grid.x * grid.y;
 }
@@ -393,6 +394,7 @@ void launch_reconstruct(const PassArgs<T> &a, cudaStream_t st)
 
 void launch_sum_partials(const double *partial, int nblocks, int nslots, double *out, cudaStream_t st)
 {
+    CPCP_COUNT_LAUNCH();
     sum_partials_kernel<<<1, 256, 0, st>>>(partial, nblocks, nslots, out);
 }
 

@@ -31,6 +31,8 @@
 
 using namespace cpcp;
 
+unsigned long long cpcp::g_kernel_launches = 0;
+
 namespace {
 
 struct DevBuf {
@@ -40,13 +42,84 @@ struct DevBuf {
 
 }  // namespace
 
+// CUDA-event timing of the solver phases (cpcp_options.profile)
+struct PhaseTimer {
+    struct Pair {
+        cudaEvent_t a, b;
+        int phase;
+    };
+    std::vector<cudaEvent_t> pool;
+    std::vector<Pair> pending;
+    double ms[CPCP_NUM_PHASES] = {0, 0, 0, 0};
+    int count[CPCP_NUM_PHASES] = {0, 0, 0, 0};
+    bool on = false;
+    cudaStream_t st = nullptr;
+
+    cudaEvent_t take()
+    {
+        if (pool.empty()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            return e;
+        }
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    // returns an open interval; close() records its end
+    int open(int phase)
+    {
+        if (!on) return -1;
+        Pair p{take(), take(), phase};
+        cudaEventRecord(p.a, st);
+        pending.push_back(p);
+        return (int)pending.size() - 1;
+    }
+    void close(int idx)
+    {
+        if (idx >= 0) cudaEventRecord(pending[idx].b, st);
+    }
+    // after a stream synchronisation: fold finished intervals into the totals
+    void harvest()
+    {
+        for (auto &p : pending) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+                ms[p.phase] += t;
+                count[p.phase]++;
+            }
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pending.clear();
+    }
+    void reset(bool enable, cudaStream_t s)
+    {
+        harvest();
+        for (int i = 0; i < CPCP_NUM_PHASES; i++) {
+            ms[i] = 0;
+            count[i] = 0;
+        }
+        on = enable;
+        st = s;
+    }
+    ~PhaseTimer()
+    {
+        for (auto e : pool) cudaEventDestroy(e);
+        for (auto &p : pending) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+    }
+};
+
 struct cpcp_context {
     int device = 0;
     cudaStream_t stream = nullptr;
     cpcp_options opt{};
     std::string err;
     std::map<std::string, DevBuf> bufs;
-    std::map<std::string, std::vector<double>> host_tr_cache;
+    PhaseTimer timer;
 };
 
 namespace {
@@ -301,6 +374,7 @@ struct SvdWork {
     T *Gpart, *Zpart, *Ypart;
     T *R1, *R1i, *R2, *R2i, *Rz, *Ut, *Wt, *Us, *sig;
     double *sig64;
+    int *well;  // per orthogonalisation: 1 when the second CholeskyQR pass is skipped
 };
 
 template <typename T>
@@ -323,6 +397,7 @@ SvdWork<T> svd_work(cpcp_context *h, const std::string &tag, int m, int ncols, i
     w.R1i = wsT<T>(h, tag + "R1i", KM * KM);
     w.R2 = wsT<T>(h, tag + "R2", KM * KM);
     w.R2i = wsT<T>(h, tag + "R2i", KM * KM);
+    w.well = wsT<int>(h, tag + "well", 4);
     w.Rz = wsT<T>(h, tag + "Rz", KM * KM);
     w.Ut = wsT<T>(h, tag + "Ut", KM * KM);
     w.Wt = wsT<T>(h, tag + "Wt", KM * KM);
@@ -332,17 +407,22 @@ SvdWork<T> svd_work(cpcp_context *h, const std::string &tag, int m, int ncols, i
     return w;
 }
 
-// CholeskyQR2 of X (rows x k): Q = X R^{-1}; if Rout != nullptr it receives R.
+// CholeskyQR2 of X (rows x k): Q = X R^{-1}; if Rout != nullptr it receives
+// R = R2 R1.  The second pass is skipped on the device when the first one
+// found X nearly orthogonal after column equilibration (the warm-started
+// steady state), since it would then leave Q unchanged to rounding.
 template <typename T>
-void orth(cpcp_context *h, SvdWork<T> &w, int rows, const T *X, T *Q, T *Rout, const int *kdyn)
+void orth(cpcp_context *h, SvdWork<T> &w, int rows, const T *X, T *Q, T *Rout, const int *kdyn, int slot)
 {
     cudaStream_t st = h->stream;
     const int KM = w.KM;
+    int *well = w.well + slot;
     int sp = launch_gemm_tn_partial<T>(rows, -1, X, KM, X, KM, w.Gpart, kdyn, KM, KM, st);
-    launch_chol<T>(w.Gpart, sp, KM, kdyn, w.R1, w.R1i, nullptr, nullptr, KM, st);
+    launch_chol<T>(w.Gpart, sp, KM, kdyn, w.R1, w.R1i, nullptr, nullptr, KM, well, nullptr, st);
     launch_gemm_nn<T>(rows, 0, X, KM, w.R1i, KM, w.Q1, KM, kdyn, kdyn, KM, st);
-    sp = launch_gemm_tn_partial<T>(rows, -1, w.Q1, KM, w.Q1, KM, w.Gpart, kdyn, KM, KM, st);
-    launch_chol<T>(w.Gpart, sp, KM, kdyn, w.R2, w.R2i, Rout ? w.R1 : nullptr, Rout, KM, st);
+    // second pass; when skipped its factor is the identity and Q = Q1 exactly
+    sp = launch_gemm_tn_partial<T>(rows, -1, w.Q1, KM, w.Q1, KM, w.Gpart, kdyn, KM, KM, st, well);
+    launch_chol<T>(w.Gpart, sp, KM, kdyn, w.R2, w.R2i, Rout ? w.R1 : nullptr, Rout, KM, nullptr, well, st);
     launch_gemm_nn<T>(rows, 0, w.Q1, KM, w.R2i, KM, Q, KM, kdyn, kdyn, KM, st);
 }
 
@@ -351,20 +431,20 @@ void orth(cpcp_context *h, SvdWork<T> &w, int rows, const T *X, T *Q, T *Rout, c
 // Mx ~ (Qy Ut) diag(sig) (Qz Wt)^T.
 template <typename T>
 void subspace_svd(cpcp_context *h, SvdWork<T> &w, int m, int nc, const T *Mx, int64_t ldx, const T *Omega,
-                  int q, const int *kdyn)
+                  int q, const int *kdyn, const Ctrl *jac_ctrl)
 {
     cudaStream_t st = h->stream;
     const int KM = w.KM;
     const T *Om = Omega;
     for (int s = 0; s < q; s++) {
         launch_gemm_nn_splitk<T>(m, nc, Mx, ldx, Om, KM, w.Y, KM, w.Ypart, kdyn, KM, st);
-        orth<T>(h, w, m, w.Y, w.Qy, nullptr, kdyn);
+        orth<T>(h, w, m, w.Y, w.Qy, nullptr, kdyn, 0);
         int sp = launch_gemm_tn_partial<T>(m, nc, Mx, ldx, w.Qy, KM, w.Zpart, kdyn, KM, nc, st);
         launch_reduce_partial<T>(w.Zpart, sp, nc, KM, w.Z, KM, nullptr, kdyn, st);
-        orth<T>(h, w, nc, w.Z, w.Qz, w.Rz, kdyn);
+        orth<T>(h, w, nc, w.Z, w.Qz, w.Rz, kdyn, 1);
         Om = w.Qz;
     }
-    launch_jacobi<T>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, st);
+    launch_jacobi<T>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st);
 }
 
 template <typename T>
@@ -456,6 +536,7 @@ double fine_check(cpcp_context *h, SolveState<T> &s, SvdWork<T> &wf, int cur, co
                   double mu_c, int *kf, double *s_part_out, int *rank_out)
 {
     cudaStream_t st = h->stream;
+    int tmr = h->timer.open(CPCP_PHASE_CHECK);
     launch_ctrl_set_check(s.cchk, s.ctrl, mu_c, st);
     PassArgs<T> a = base_args(s);
     a.ctrl = s.cchk;
@@ -468,7 +549,7 @@ double fine_check(cpcp_context *h, SolveState<T> &s, SvdWork<T> &wf, int cur, co
     // fine SVT of M = L - tau G with width kf, warm-started from the last check
     launch_fill_random<T>(s.Omf, s.KM, s.n, s.cchk, 0, wf.sig, s.KM, 0xC4ECull, st);
     launch_ctrl_take_width(s.cchk, st);
-    subspace_svd<T>(h, wf, s.m, s.n, s.M, s.ldS, s.Omf, o.qc, &s.cchk->k);
+    subspace_svd<T>(h, wf, s.m, s.n, s.M, s.ldS, s.Omf, o.qc, &s.cchk->k, s.cchk);
     launch_svt_small<T>(wf.Ut, wf.sig, wf.KM, s.cchk, wf.Us, nullptr, st);
     launch_gemm_nn<T>(s.m, 0, wf.Qy, wf.KM, wf.Us, wf.KM, s.Ac, s.KM, &s.cchk->k, &s.cchk->k, s.KM, st);
     launch_gemm_nn<T>(s.n, 0, wf.Qz, wf.KM, wf.Wt, wf.KM, s.Omf, s.KM, &s.cchk->k, &s.cchk->k, s.KM, st);
@@ -485,9 +566,11 @@ double fine_check(cpcp_context *h, SolveState<T> &s, SvdWork<T> &wf, int cur, co
     launch_sum_partials(s.partial, nb, 3, s.sums + 3, st);
     double sums[6];
     Ctrl cc;
+    h->timer.close(tmr);
     CK(cudaMemcpyAsync(sums, s.sums, sizeof(sums), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&cc, s.cchk, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    h->timer.harvest();
     *s_part_out = sums[0];
     int kcur = cc.k;
     int r = cc.r_new;
@@ -532,21 +615,27 @@ void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, 
         a.MH = s.MH;
         a.ldh = s.ldMH;
         a.tr = tr;
+        int tp = h->timer.open(CPCP_PHASE_PASS_COARSE);
         launch_step_pass<T>(a, true, st);
+        h->timer.close(tp);
         Mx = s.MH;
         ldx = s.ldMH;
     } else {
+        int tp = h->timer.open(CPCP_PHASE_PASS_FINE);
         launch_step_pass<T>(a, false, st);
+        h->timer.close(tp);
         Mx = s.M;
         ldx = s.ldS;
     }
-    subspace_svd<T>(h, w, s.m, tr.nh, Mx, ldx, s.Om, o.q, &s.ctrl->k);
+    int ts = h->timer.open(CPCP_PHASE_SVT);
+    subspace_svd<T>(h, w, s.m, tr.nh, Mx, ldx, s.Om, o.q, &s.ctrl->k, s.ctrl);
     launch_svt_small<T>(w.Ut, w.sig, w.KM, s.ctrl, w.Us, nullptr, st);
     // new factors into the "previous" slot (its old content was consumed above)
     launch_gemm_nn<T>(s.m, 0, w.Qy, w.KM, w.Us, w.KM, s.A[nxt], s.KM, &s.ctrl->k, &s.ctrl->k, s.KM, st);
     launch_gemm_nn<T>(tr.nh, 0, w.Qz, w.KM, w.Wt, w.KM, s.Om, s.KM, &s.ctrl->k, &s.ctrl->k, s.KM, st);
     launch_fill_random<T>(s.Om, s.KM, tr.nh, s.ctrl, 0, w.sig, s.KM, 0x57E9ull, st);
     launch_prolong<T>(s.n, s.Om, s.KM, s.B[nxt], s.KM, tr, &s.ctrl->r_new, s.KM, st);
+    h->timer.close(ts);
     launch_ctrl_end(s.ctrl, st);
 }
 
@@ -559,6 +648,8 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     cudaStream_t st = h->stream;
     const Opts o = resolve(h->opt);
     const int H = levels - 1;
+    h->timer.reset(h->opt.profile != 0, st);
+    const unsigned long long launches0 = g_kernel_launches;
     SolveState<T> s;
     s.m = m;
     s.n = n;
@@ -625,7 +716,7 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     double mu0 = o.mu0;
     if (!(mu0 > 0)) {
         launch_fill_random<T>(s.Omf, s.KM, n, s.cchk, 1, nullptr, s.KM, 0x30ull, st);
-        subspace_svd<T>(h, wf, m, n, s.M, s.ldS, s.Omf, 4, &s.cchk->k);
+        subspace_svd<T>(h, wf, m, n, s.M, s.ldS, s.Omf, 4, &s.cchk->k, nullptr);
         T sig0;
         CK(cudaMemcpyAsync(&sig0, wf.sig, sizeof(T), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -725,6 +816,12 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     CK(cudaGetLastError());
     inf.status = status;
     inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    inf.launches = (long long)(g_kernel_launches - launches0);
+    h->timer.harvest();
+    for (int i = 0; i < CPCP_NUM_PHASES; i++) {
+        inf.phase_ms[i] = h->timer.ms[i];
+        inf.phase_count[i] = h->timer.count[i];
+    }
     if (info) *info = inf;
     return status;
 }
@@ -882,7 +979,7 @@ cpcp_status step_impl(cpcp_context *h, int m, int n, const void *Dv, int64_t ldd
     } else {
         launch_fill_random<T>(Om, KM, nh, cd, 1, nullptr, KM, 0x51ull, st);
     }
-    subspace_svd<T>(h, w, m, nh, Mx, ldx, Om, q, &cd->k);
+    subspace_svd<T>(h, w, m, nh, Mx, ldx, Om, q, &cd->k, nullptr);
     launch_svt_small<T>(w.Ut, w.sig, KM, cd, w.Us, w.sig64, st);
     launch_gemm_nn<T>(m, 0, w.Qy, KM, w.Us, KM, static_cast<T *>(Aov), ldao, &cd->k, &cd->k, KM, st);
     T *V = wsT<T>(h, "st_V", (size_t)nh * KM);
@@ -920,7 +1017,7 @@ cpcp_status svd_impl(cpcp_context *h, int m, int n, const void *Mv, int64_t ldm,
         CK(cudaMemcpy2DAsync(Om, sizeof(T) * KM, Om0, sizeof(T) * ldo, sizeof(T) * k, n, cudaMemcpyDefault, st));
     else
         launch_fill_random<T>(Om, KM, n, cd, 1, nullptr, KM, 0x5Dull, st);
-    subspace_svd<T>(h, w, m, n, static_cast<const T *>(Mv), ldm, Om, q, &cd->k);
+    subspace_svd<T>(h, w, m, n, static_cast<const T *>(Mv), ldm, Om, q, &cd->k, nullptr);
     launch_gemm_nn<T>(m, 0, w.Qy, KM, w.Ut, KM, static_cast<T *>(Uv), ldu, &cd->k, &cd->k, KM, st);
     launch_gemm_nn<T>(n, 0, w.Qz, KM, w.Wt, KM, static_cast<T *>(Vv), ldv, &cd->k, &cd->k, KM, st);
     // singular values as doubles

@@ -202,7 +202,7 @@ def small_cpcp():
 def test_solve_fp32_cpcp_matches_oracle(cp, h, small_cpcp, levels):
     p, Lr, Sr = small_cpcp
     Qb = torch.as_tensor(cp.pack_mask(p["mask"])).cuda()
-    L, S, info = h.solve(dev(p["D"], torch.float32), Qb, p["lam"], p["mu"], levels=levels, tol=2e-7)
+    L, S, info = h.solve(dev(p["D"], torch.float32), Qb, p["lam"], p["mu"], levels=levels, tol=5e-7)
     assert info["status"] == 0, info
     L, S = host(L), host(S)
     eL, eS = rel(L, Lr), rel(S, Sr)
