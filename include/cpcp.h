@@ -210,6 +210,34 @@ cpcp_status cpcp_transfer_info(int n, int halvings, double *scale, int *nh);
 cpcp_status cpcp_svd(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *M, int64_t ldm, int k, int q,
                      const void *Omega0, int64_t ldo, void *U, int64_t ldu, void *V, int64_t ldv, double *sigma);
 
+/*
+ * ||P_Q[D]||_F (fro, host double) and the number of observed entries of D
+ * that are NaN or infinite (nonfinite, host int64, may be NULL), computed
+ * without allocating any memory.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory while they run --
+ * code inside a CUDA graph capture (a cudaMalloc there would break or stall
+ * the capture), code whose device memory is all handed out up front by its own
+ * pool or arena, and latency-critical loops that cannot afford the device-wide
+ * synchronisation of cudaMalloc/cudaFree.  It needs no handle.
+ *
+ * D (m x n, dtype, ldd) and Q (bit-packed mask as in cpcp_solve, or NULL) are
+ * device pointers on the current device; the work is queued on `stream` (a
+ * cudaStream_t, NULL = legacy default stream) and the call returns after the
+ * results have been copied to the host.  The partial sums live in one static
+ * device array of 1 MiB that every GPU loading the library holds until the
+ * process exits; the largest accepted problem has ceil(m/64) * ceil(n/64) <=
+ * 65536 tiles (for example 16384 x 16384) -- larger sizes return
+ * CPCP_ERR_INVALID_ARG before any device work.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU (different streams or threads on
+ * the same device) race and must be serialised by the caller.  Every slot a
+ * call reads is written by the same call, so nothing needs clearing.
+ * Returns OK, INVALID_ARG or CUDA.
+ */
+cpcp_status cpcp_masked_norm_static(void *stream, int m, int n, cpcp_dtype dt, const void *D, int64_t ldd,
+                                    const uint32_t *Q, int64_t ldq, double *fro, int64_t *nonfinite);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,13 +76,15 @@ def _load():
     lib.cpcp_prolong.argtypes = [_vp, _int, _int, _int, _int, _vp, _i64, _vp, _i64]
     lib.cpcp_transfer_info.argtypes = [_int, _int, C.POINTER(_dbl), C.POINTER(_int)]
     lib.cpcp_svd.argtypes = [_vp, _int, _int, _int, _vp, _i64, _int, _int, _vp, _i64, _vp, _i64, _vp, _i64, _vp]
+    lib.cpcp_masked_norm_static.argtypes = [_vp, _int, _int, _int, _vp, _i64, _vp, _i64, C.POINTER(_dbl),
+                                            C.POINTER(C.c_int64)]
     return lib
 
 
 _lib = _load()
 
 EXPORTED = ["cpcp_status_string", "cpcp_last_error", "cpcp_create", "cpcp_destroy", "cpcp_solve", "cpcp_step",
-            "cpcp_restrict", "cpcp_prolong", "cpcp_transfer_info", "cpcp_svd"]
+            "cpcp_restrict", "cpcp_prolong", "cpcp_transfer_info", "cpcp_svd", "cpcp_masked_norm_static"]
 
 
 def lib():
@@ -289,3 +291,24 @@ def transfer_info(n: int, halvings: int):
     if st != 0:
         raise CPCPError(st, "cpcp_transfer_info")
     return float(sc.value), int(nh.value)
+
+
+def masked_norm_static(D, Qbits=None, stream=None):
+    """||P_Q[D]||_F and the count of non-finite observed entries, through the
+    entry point that allocates nothing (cpcp_masked_norm_static); D and Qbits
+    are device tensors on the current device."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    m, n = D.shape
+    pD, ldd = _ptr(D)
+    pQ, ldq = _ptr(Qbits)
+    fro = _dbl(0)
+    nf = C.c_int64(0)
+    st = _lib.cpcp_masked_norm_static(_vp(stream) if stream else None, m, n, _dtype_code(D), pD, ldd, pQ, ldq,
+                                      C.byref(fro), C.byref(nf))
+    if st != 0:
+        raise CPCPError(st, "cpcp_masked_norm_static")
+    return float(fro.value), int(nf.value)
