@@ -42,7 +42,7 @@ TOL = 1e-6
 # iterations the multilevel solve takes on this workload (measured on the GPU
 # arm, which also reports its own count); the CPU arms scale a per-iteration
 # sample by it
-ITERS_MULTILEVEL = 340
+ITERS_MULTILEVEL = 100
 ORACLE_SAMPLE_STEPS = 2
 
 

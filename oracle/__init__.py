@@ -105,6 +105,8 @@ def _load():
             lib.or_step.argtypes = [C.c_int, C.c_int, _dp, C.c_void_p, C.c_double, C.c_double, C.c_double,
                                     C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
             lib.or_step.restype = C.c_int
+            lib.or_restriction_kappa.argtypes = [C.c_int, C.c_int, _dp]
+            lib.or_restriction_kappa.restype = C.c_double
             _lib = lib
     return _lib
 
@@ -183,6 +185,12 @@ def restriction(n: int, halvings: int, scaled: bool = True):
         return R, float(sc.value)
     _load().or_restriction(n, halvings, R)
     return R, 1.0
+
+
+def restriction_kappa(n: int, halvings: int) -> float:
+    """Threshold of the coarse-gradient test for the unit-norm composite R."""
+    R, _ = restriction(n, halvings, scaled=True)
+    return float(_load().or_restriction_kappa(n, R.shape[1], R))
 
 
 def spectral_norm(A) -> float:

@@ -25,10 +25,12 @@
  *   * momentum: FISTA extrapolation on both L and S, restarted at level switches;
  *   * continuation: mu_k = max(mu_0 eta^k, mu_bar), eta = 0.9, mu_0 = ||P_Q D||_2;
  *   * residual: relative gradient-mapping norm at mu_bar on the fine level;
- *   * level switching: start coarsest; every c iterations evaluate the fine
- *     residual at the current weight mu_k; stop if mu_k = mu_bar and
- *     rel-KKT <= tol, else move one level finer if the residual fell by less
- *     than the switch ratio since the last check on this level;
+ *   * level switching: start coarsest; every c iterations on a coarse level
+ *     move one level finer when the restricted gradient keeps less than
+ *     kappa(level) of the gradient's norm (see or_restriction_kappa); once
+ *     mu_k = mu_bar, every c iterations evaluate the fine residual: stop if
+ *     rel-KKT <= tol, and on a coarse level also move finer if the residual
+ *     fell by less than the switch ratio since the last check on this level;
  *   * R is scaled to unit spectral norm (Assumption 4);
  *   * odd n: coarse node j sits at fine index 2j-1;
  *   * n > m: the transposed problem is solved.
@@ -506,6 +508,29 @@ static int ml_prox_L(int m, int n, int nh, const double *R, const double *M, dou
     return r;
 }
 
+/*
+ * Threshold of the coarse-gradient test for one level: the geometric mean of
+ * the ratio ||g R|| / ||g|| that a row of white noise gets on average
+ * (||R||_F / sqrt(n)) and the ratio that a row constant along the columns gets
+ * (||1^T R|| / sqrt(n)).  A gradient whose restriction keeps less than this
+ * share of its norm is dominated by fine-scale components that the coarse
+ * model cannot represent.
+ */
+double or_restriction_kappa(int n, int nh, const double *R)
+{
+    double fro2 = 0.0, cs2 = 0.0;
+    for (int c = 0; c < nh; c++) {
+        double cs = 0.0;
+        for (int j = 0; j < n; j++) {
+            double r = R[(size_t)j * nh + c];
+            fro2 += r * r;
+            cs += r;
+        }
+        cs2 += cs * cs;
+    }
+    return sqrt(sqrt(fro2 / n) * sqrt(cs2 / n));
+}
+
 static int fista_core(int m, int n, const double *D, const unsigned char *mask, double lam, double mu_bar,
                       int levels, double tol, const or_opts *o, double *L, double *S, or_info *info,
                       double *trace, int trace_cap)
@@ -529,6 +554,9 @@ static int fista_core(int m, int n, const double *D, const unsigned char *mask, 
         R[h] = dalloc((size_t)n * nhs[h]);
         or_restriction_scaled(n, h, R[h], NULL);
     }
+    double *kappa = dalloc((size_t)H + 1);
+    for (int h = 1; h <= H; h++) kappa[h] = or_restriction_kappa(n, nhs[h], R[h]);
+    double *GR = H > 0 ? dalloc((size_t)m * nhs[1]) : NULL;
     double **Vw = (double **)calloc((size_t)H + 1, sizeof(double *));
     for (int h = 0; h <= H; h++) {
         if (m >= nhs[h]) {
@@ -581,26 +609,35 @@ static int fista_core(int m, int n, const double *D, const unsigned char *mask, 
             }
             continue;
         }
-        if ((k + 1) % c == 0) {
-            /* fine residual at the weight of this iteration; the stop test
-               needs the final weight, the switch test uses any weight */
-            rel = relkkt_warm(m, n, D, mask, lam, mu_k, tau, L, S, Vchk);
+        if ((k + 1) % c != 0) continue;
+        int finer = 0;
+        if (level > 0) {
+            /* coarse-gradient test: keep the coarse model while the
+               restricted gradient G R carries at least kappa of ||G|| */
+            matmul(m, n, nhs[level], G, R[level], GR);
+            double gn = sqrt(frob2(len, G)), grn = sqrt(frob2((size_t)m * nhs[level], GR));
+            if (gn > 0.0 && grn < kappa[level] * gn) finer = 1;
+        }
+        if (!finer && mu_k == mu_bar) {
+            /* fine residual at the final weight: stop test, and on a coarse
+               level a stall test */
+            rel = relkkt_warm(m, n, D, mask, lam, mu_bar, tau, L, S, Vchk);
             if (trace && checks < trace_cap) trace[checks] = rel;
             checks++;
-            if (mu_k == mu_bar && rel <= tol) {
+            if (rel <= tol) {
                 k++;
                 status = OR_OK;
                 break;
             }
-            if (level > 0 && rel > ratio * prev) {
-                level--;
-                prev = INFINITY;
-                t = 1.0; /* momentum restart */
-                memcpy(Lp, L, sizeof(double) * len);
-                memcpy(Sp, S, sizeof(double) * len);
-            } else {
-                prev = rel;
-            }
+            if (level > 0 && rel > ratio * prev) finer = 1;
+            prev = rel;
+        }
+        if (finer) {
+            level--;
+            prev = INFINITY;
+            t = 1.0; /* momentum restart */
+            memcpy(Lp, L, sizeof(double) * len);
+            memcpy(Sp, S, sizeof(double) * len);
         }
     }
     if (info) {
@@ -619,6 +656,8 @@ static int fista_core(int m, int n, const double *D, const unsigned char *mask, 
     free(R);
     free(Vw);
     free(nhs);
+    free(kappa);
+    free(GR);
     free(Vchk);
     free(PQD);
     free(Lp);

@@ -74,6 +74,7 @@ __host__ __device__ __forceinline__ double hash_uniform(uint64_t x)
 template <typename T>
 struct TransferDev {
     int n, nh;
+    double kappa;  // threshold of the coarse-gradient test (host use)
     const int *j0;
     const T *w0, *w1;
     const int *clo, *chi;
@@ -104,11 +105,16 @@ struct PassArgs {
     int64_t ldm;
     T *MH;             // coarse output (level > 0), zero on entry
     int64_t ldh;
+    T *GH;             // optional (level > 0): G R, zero on entry, leading dimension ldh;
+                       // then partial slot 0 of each block receives its share of ||G||_F^2
     TransferDev<T> tr;
     double *partial;   // per-block fp64 partial sums (check / norm passes)
 };
 
-template <typename T> void launch_step_pass(const PassArgs<T> &a, bool coarse, cudaStream_t st);
+// returns the number of blocks (partial sums written when a.GH is set)
+template <typename T> int launch_step_pass(const PassArgs<T> &a, bool coarse, cudaStream_t st);
+// per-block fp64 partial sums of squares of X (rows x cols); returns the block count
+template <typename T> int launch_sumsq(int rows, int cols, const T *X, int64_t ld, double *partial, cudaStream_t st);
 // check pass at (L_k, S_k) with weight mu_bar: writes M = L - tau G and
 // per-block sums of ||S - shrink(S - tau G)||^2 (slot 0), ||P_Q D||^2 (slot 1),
 // count of non-finite observed D (slot 2).

@@ -22,16 +22,21 @@ namespace {
 constexpr int BM = 64, BN = 64, KC = 16, NT = 256;
 constexpr int NSLOT = 3;
 
-enum Mode { STEP_FINE = 0, STEP_COARSE = 1, CHECK = 2, DIFF = 3, RECON = 4 };
+// STEP_COARSE_G is STEP_COARSE plus, for the coarse-gradient test of the
+// level switch, the restriction G R of the gradient and ||G||_F^2.
+enum Mode { STEP_FINE = 0, STEP_COARSE = 1, CHECK = 2, DIFF = 3, RECON = 4, STEP_COARSE_G = 5 };
 
-template <typename T>
+template <typename T, bool GM>
 struct Smem {
     union {
         struct {
             T As[KC][BM + 4];
             T Bs[KC][BN + 4];
         } g;
-        T Ms[BM][BN + 1];
+        struct {
+            T Ms[BM][BN + 1];
+            T Gs[GM ? BM : 1][BN + 1];
+        } e;
     } u;
     int j0[BN];
     T w0[BN], w1[BN];
@@ -49,8 +54,8 @@ __device__ __forceinline__ bool is_finite_val(T x)
 // running sum, errors gathered in lo), so acc + lo carries about twice the
 // working precision; the residual check needs this because it subtracts two
 // reconstructions of nearly equal matrices.
-template <typename T, bool COMP>
-__device__ __forceinline__ void accumulate_factor(Smem<T> &sm, T acc[4][4], T lo[4][4], const T *A, int64_t lda,
+template <typename T, bool COMP, typename SM>
+__device__ __forceinline__ void accumulate_factor(SM &sm, T acc[4][4], T lo[4][4], const T *A, int64_t lda,
                                                   const T *B, int64_t ldb, int r, T coef, int m, int n, int rb,
                                                   int cb)
 {
@@ -144,15 +149,18 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(NT) pass_kernel(PassArgs<T> a, int vec_flags)
 {
     const int *rk_ptr = a.rk, *rp_ptr = a.rp;
+    constexpr bool COARSE = (MODE == STEP_COARSE || MODE == STEP_COARSE_G);
+    constexpr bool GM = (MODE == STEP_COARSE_G);
+    using SM = Smem<T, GM>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    Smem<T> &sm = *reinterpret_cast<Smem<T> *>(smraw);
+    SM &sm = *reinterpret_cast<SM *>(smraw);
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
     const int cb = blockIdx.x * BN, rb = blockIdx.y * BM;
     const int m = a.m, n = a.n;
     const Ctrl &C = *a.ctrl;
 
     T coef_k, coef_p;
-    if (MODE == STEP_FINE || MODE == STEP_COARSE) {
+    if (MODE == STEP_FINE || COARSE) {
         coef_k = T(1.0 + C.beta);
         coef_p = T(-C.beta);
     } else if (MODE == CHECK) {
@@ -177,6 +185,7 @@ __global__ void __launch_bounds__(NT) pass_kernel(PassArgs<T> a, int vec_flags)
         for (int j = 0; j < 4; j++) acc[i][j] = lo[i][j] = T(0);
     if (rk > 0) accumulate_factor<T, COMP>(sm, acc, lo, a.Ak, a.ldfa, a.Bk, a.ldfb, rk, coef_k, m, n, rb, cb);
     if (rp > 0) accumulate_factor<T, COMP>(sm, acc, lo, a.Ap, a.ldfap, a.Bp, a.ldfbp, rp, coef_p, m, n, rb, cb);
+    double gsq = 0.0;
 
     const int col = cb + 4 * tx;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
@@ -208,7 +217,7 @@ __global__ void __launch_bounds__(NT) pass_kernel(PassArgs<T> a, int vec_flags)
         const T tau = T(C.tau);
         const T beta = (MODE == CHECK) ? T(0) : T(C.beta);
         const T thS = (MODE == CHECK) ? T(C.tau * C.lam * C.mu_bar) : T(C.theta_S);
-        if (MODE == STEP_COARSE) __syncthreads();  // smem tile reused below
+        if (COARSE) __syncthreads();  // smem tile reused below
 #pragma unroll
         for (int i = 0; i < 4; i++) {
             int lr = ty + 16 * i, row = rb + lr;
@@ -229,8 +238,8 @@ __global__ void __launch_bounds__(NT) pass_kernel(PassArgs<T> a, int vec_flags)
             }
             uint32_t bits = 0xffffffffu;
             if (a.Q && col < n) bits = a.Q[(int64_t)row * a.ldq + (col >> 5)] >> (col & 31);
-            T so[4], mo[4];
-            T ps = T(0), pd = T(0);
+            T so[4], mo[4], go[4];
+            T ps = T(0), pd = T(0), pg = T(0);
             int nf = 0;
 #pragma unroll
             for (int j = 0; j < 4; j++) {
@@ -243,6 +252,8 @@ __global__ void __launch_bounds__(NT) pass_kernel(PassArgs<T> a, int vec_flags)
                 T sn = shrink(sh - tau * g, thS);
                 so[j] = sn;
                 mo[j] = (acc[i][j] + lo[i][j]) - tau * g;
+                go[j] = g;
+                if (GM && inb) pg += g * g;
                 if (MODE == CHECK && inb) {
                     T e = sk[j] - sn;
                     ps += e * e;
@@ -254,13 +265,18 @@ __global__ void __launch_bounds__(NT) pass_kernel(PassArgs<T> a, int vec_flags)
                     }
                 }
             }
-            if (MODE == STEP_FINE || MODE == STEP_COARSE)
+            if (MODE == STEP_FINE || COARSE)
                 store4(a.Sout, (int64_t)row * a.ldso + col, col, n, vO, so);
             if (MODE == STEP_FINE || MODE == CHECK) {
                 store4(a.M, (int64_t)row * a.ldm + col, col, n, vM, mo);
-            } else if (MODE == STEP_COARSE) {
+            } else if (COARSE) {
 #pragma unroll
-                for (int j = 0; j < 4; j++) sm.u.Ms[lr][4 * tx + j] = mo[j];
+                for (int j = 0; j < 4; j++) sm.u.e.Ms[lr][4 * tx + j] = mo[j];
+                if constexpr (GM) {
+#pragma unroll
+                    for (int j = 0; j < 4; j++) sm.u.e.Gs[lr][4 * tx + j] = go[j];
+                    gsq += (double)pg;
+                }
             }
             if (MODE == CHECK) {
                 s0 += (double)ps;
@@ -270,7 +286,7 @@ __global__ void __launch_bounds__(NT) pass_kernel(PassArgs<T> a, int vec_flags)
         }
     }
 
-    if (MODE == STEP_COARSE) {
+    if (COARSE) {
         // restriction of the tile: M_H[row, c] += sum_j M[row, j] R[j, c]
         if (t < BN) {
             int j = cb + t;
@@ -293,17 +309,26 @@ __global__ void __launch_bounds__(NT) pass_kernel(PassArgs<T> a, int vec_flags)
         for (int p = t; p < rows * ncol; p += NT) {
             int lr = p / ncol, c = c_lo + p % ncol;
             int jlo = max(a.tr.clo[c], cb), jhi = min(a.tr.chi[c], jlast);
-            T s = T(0);
+            T s = T(0), sg = T(0);
             for (int j = jlo; j <= jhi; j++) {
                 int lj = j - cb;
                 T w = (sm.j0[lj] == c) ? sm.w0[lj] : ((sm.j0[lj] + 1 == c) ? sm.w1[lj] : T(0));
-                s = fma(sm.u.Ms[lr][lj], w, s);
+                s = fma(sm.u.e.Ms[lr][lj], w, s);
+                if constexpr (GM) sg = fma(sm.u.e.Gs[lr][lj], w, sg);
             }
-            if (jlo <= jhi) atomicAdd(&a.MH[(int64_t)(rb + lr) * a.ldh + c], s);
+            if (jlo <= jhi) {
+                atomicAdd(&a.MH[(int64_t)(rb + lr) * a.ldh + c], s);
+                if constexpr (GM) atomicAdd(&a.GH[(int64_t)(rb + lr) * a.ldh + c], sg);
+            }
         }
     }
+    if constexpr (GM) {
+        s0 = gsq;
+        s1 = 0.0;
+        s2 = 0.0;
+    }
 
-    if (MODE == CHECK || MODE == DIFF) {
+    if (MODE == CHECK || MODE == DIFF || GM) {
         s0 = warp_sum(s0);
         s1 = warp_sum(s1);
         s2 = warp_sum(s2);
@@ -338,10 +363,17 @@ int vec_flags_for(const PassArgs<T> &a)
 template <typename T, int MODE>
 int launch_mode(const PassArgs<T> &a, cudaStream_t st)
 {
-    static_assert(sizeof(Smem<T>) <= 48 * 1024, "pass tile exceeds default shared memory");
+    using SM = Smem<T, MODE == STEP_COARSE_G>;
+    if constexpr (sizeof(SM) > 48 * 1024) {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(pass_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SM));
+            attr = true;
+        }
+    }
     dim3 grid((a.n + BN - 1) / BN, (a.m + BM - 1) / BM);
     CPCP_COUNT_LAUNCH();
-    pass_kernel<T, MODE><<<grid, NT, sizeof(Smem<T>), st>>>(a, vec_flags_for(a));
+    pass_kernel<T, MODE><<<grid, NT, sizeof(SM), st>>>(a, vec_flags_for(a));
     return grid.x * grid.y;
 }
 
@@ -366,12 +398,46 @@ __global__ void sum_partials_kernel(const double *partial, int nblocks, int nslo
 }  // namespace
 
 template <typename T>
-void launch_step_pass(const PassArgs<T> &a, bool coarse, cudaStream_t st)
+int launch_step_pass(const PassArgs<T> &a, bool coarse, cudaStream_t st)
 {
-    if (coarse)
-        launch_mode<T, STEP_COARSE>(a, st);
-    else
-        launch_mode<T, STEP_FINE>(a, st);
+    if (coarse && a.GH != nullptr) return launch_mode<T, STEP_COARSE_G>(a, st);
+    if (coarse) return launch_mode<T, STEP_COARSE>(a, st);
+    return launch_mode<T, STEP_FINE>(a, st);
+}
+
+// sum of squares of a rows x cols matrix (leading dimension ld): fixed grid,
+// one fp64 partial per block, reduced in a fixed order by sum_partials
+constexpr int SUMSQ_BLOCKS = 304;
+
+template <typename T>
+__global__ void __launch_bounds__(256) sumsq_kernel(int rows, int cols, const T *__restrict__ X, int64_t ld,
+                                                    double *__restrict__ partial)
+{
+    __shared__ double red[8];
+    double s = 0.0;
+    const int64_t total = (int64_t)rows * cols;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = idx / cols, c = idx % cols;
+        const double v = (double)X[r * ld + c];
+        s += v * v;
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; w++) t += red[w];
+        partial[blockIdx.x] = t;
+    }
+}
+
+template <typename T>
+int launch_sumsq(int rows, int cols, const T *X, int64_t ld, double *partial, cudaStream_t st)
+{
+    CPCP_COUNT_LAUNCH();
+    sumsq_kernel<T><<<SUMSQ_BLOCKS, 256, 0, st>>>(rows, cols, X, ld, partial);
+    return SUMSQ_BLOCKS;
 }
 
 template <typename T>
@@ -398,8 +464,10 @@ void launch_sum_partials(const double *partial, int nblocks, int nslots, double 
     sum_partials_kernel<<<1, 256, 0, st>>>(partial, nblocks, nslots, out);
 }
 
-template void launch_step_pass<float>(const PassArgs<float> &, bool, cudaStream_t);
-template void launch_step_pass<double>(const PassArgs<double> &, bool, cudaStream_t);
+template int launch_step_pass<float>(const PassArgs<float> &, bool, cudaStream_t);
+template int launch_step_pass<double>(const PassArgs<double> &, bool, cudaStream_t);
+template int launch_sumsq<float>(int, int, const float *, int64_t, double *, cudaStream_t);
+template int launch_sumsq<double>(int, int, const double *, int64_t, double *, cudaStream_t);
 template int launch_check_pass<float>(const PassArgs<float> &, cudaStream_t);
 template int launch_check_pass<double>(const PassArgs<double> &, cudaStream_t);
 template int launch_diff_pass<float>(const PassArgs<float> &, cudaStream_t);

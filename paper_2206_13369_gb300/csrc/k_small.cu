@@ -289,10 +289,10 @@ __global__ void __launch_bounds__(JAC_NT) jacobi_kernel(const T *__restrict__ Rz
     // columns whose norm is below the rounding noise of the largest one carry
     // no information; rotating them against large columns only moves noise
     const T negl = (T(4) * T(k) * eps_of<T>()) * (T(4) * T(k) * eps_of<T>());
-    // a sweep whose largest rotated |g|/sqrt(ab) is this small leaves the
-    // columns orthogonal to rounding (Jacobi converges quadratically); only
-    // noise-level rotations would follow
-    const T stop = T(32) * tol;
+    // a sweep whose largest rotated |g|/sqrt(ab) is delta leaves an
+    // off-orthogonality of order delta^2 (Jacobi converges quadratically), so
+    // a further sweep would only make rounding-level rotations
+    const T stop = min(sqrt(tol), T(1e-4));
     for (int sweep = 0; sweep < 30; sweep++) {
         // exact squared norms at the start of each sweep; rotations then
         // update them by a' = a - t g, b' = b + t g (Rutishauser)

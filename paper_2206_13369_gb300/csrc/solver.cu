@@ -202,6 +202,7 @@ double tridiag_max_eig(const std::vector<double> &d, const std::vector<double> &
 struct HostTransfer {
     int n = 0, nh = 0, halvings = 0, max_span = 0;
     double scale = 1.0;
+    double kappa = 0.0;  // threshold of the coarse-gradient test
     std::vector<int> j0, clo, chi;
     std::vector<double> w0, w1;
 };
@@ -312,6 +313,18 @@ HostTransfer build_transfer(int n, int halvings)
         t.w1[j] *= t.scale;
     }
     for (int c = 0; c < cur; c++) t.max_span = std::max(t.max_span, t.chi[c] - t.clo[c] + 1);
+    // coarse-gradient threshold: geometric mean of the share ||g R|| / ||g|| that
+    // white noise keeps on average (||R||_F / sqrt(n)) and that a row constant
+    // along the columns keeps (||1^T R|| / sqrt(n))
+    double fro2 = 0.0, cs2 = 0.0;
+    std::vector<double> cs(cur, 0.0);
+    for (int j = 0; j < n; j++) {
+        fro2 += t.w0[j] * t.w0[j] + t.w1[j] * t.w1[j];
+        cs[t.j0[j]] += t.w0[j];
+        if (t.w1[j] != 0.0) cs[t.j0[j] + 1] += t.w1[j];
+    }
+    for (int c = 0; c < cur; c++) cs2 += cs[c] * cs[c];
+    t.kappa = std::sqrt(std::sqrt(fro2 / n) * std::sqrt(cs2 / n));
     return t;
 }
 
@@ -354,6 +367,7 @@ TransferDev<T> upload_transfer(cpcp_context *h, int n, int halvings, const std::
     TransferDev<T> d;
     d.n = n;
     d.nh = t.nh;
+    d.kappa = t.kappa;
     d.j0 = j0;
     d.w0 = w0;
     d.w1 = w1;
@@ -495,7 +509,7 @@ struct SolveState {
     const uint32_t *Q;
     int64_t ldq;
     T *S[2], *A[2], *B[2];
-    T *M, *MH;
+    T *M, *MH, *GH;
     int64_t ldMH;
     T *Om, *Omf, *Ac, *Bc;
     Ctrl *ctrl, *cchk;
@@ -590,8 +604,11 @@ double fine_check(cpcp_context *h, SolveState<T> &s, SvdWork<T> &wf, int cur, co
     return std::sqrt(std::max(sums[0] + sums[3], 0.0)) / tau / pqd;
 }
 
+// One iteration.  With want_g on a coarse level the pass also restricts the
+// gradient; s.sums[8] then holds ||G||_F^2 and s.sums[11] ||G R||_F^2.
 template <typename T>
-void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, int cur, const Opts &o)
+void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, int cur, const Opts &o,
+                   bool want_g)
 {
     cudaStream_t st = h->stream;
     const int nxt = cur ^ 1;
@@ -615,9 +632,18 @@ void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, 
         a.MH = s.MH;
         a.ldh = s.ldMH;
         a.tr = tr;
+        if (want_g) {
+            CK(cudaMemsetAsync(s.GH, 0, sizeof(T) * (size_t)s.m * s.ldMH, st));
+            a.GH = s.GH;
+        }
         int tp = h->timer.open(CPCP_PHASE_PASS_COARSE);
-        launch_step_pass<T>(a, true, st);
+        int nb = launch_step_pass<T>(a, true, st);
         h->timer.close(tp);
+        if (want_g) {
+            launch_sum_partials(s.partial, nb, 3, s.sums + 8, st);
+            int nq = launch_sumsq<T>(s.m, tr.nh, s.GH, s.ldMH, s.partial, st);
+            launch_sum_partials(s.partial, nq, 1, s.sums + 11, st);
+        }
         Mx = s.MH;
         ldx = s.ldMH;
     } else {
@@ -672,6 +698,7 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     int nh1 = H >= 1 ? s.tr[1].nh : 1;
     s.ldMH = round4(nh1);
     s.MH = wsT<T>(h, "MH", (size_t)m * s.ldMH);
+    s.GH = wsT<T>(h, "GH", (size_t)m * s.ldMH);
     s.Om = wsT<T>(h, "Om", (size_t)n * s.KM);
     s.Omf = wsT<T>(h, "Omf", (size_t)n * s.KM);
     s.Ac = wsT<T>(h, "Ac", (size_t)m * s.KM);
@@ -679,8 +706,8 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     s.ctrl = wsT<Ctrl>(h, "ctrl", 1);
     s.cchk = wsT<Ctrl>(h, "cchk", 1);
     s.partial_blocks = ((n + 63) / 64) * ((m + 63) / 64);
-    s.partial = wsT<double>(h, "partial", (size_t)s.partial_blocks * 3);
-    s.sums = wsT<double>(h, "sums", 8);
+    s.partial = wsT<double>(h, "partial", (size_t)std::max(s.partial_blocks * 3, 512));
+    s.sums = wsT<double>(h, "sums", 16);
     SvdWork<T> w = svd_work<T>(h, "it_", m, n, s.kcap0);
     SvdWork<T> wf = svd_work<T>(h, "ck_", m, n, s.kcap0);
 
@@ -748,23 +775,39 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     double rel = INFINITY, prev = INFINITY;
     cpcp_status status = CPCP_ERR_NOT_CONVERGED;
     for (iter = 0; iter < o.max_iter;) {
-        one_iteration<T>(h, s, w, level, cur, o);
+        // every check_every iterations: a level decision (coarse levels) and,
+        // once the weight is final, the fine residual check
+        const bool decide = (iter + 1) % o.check_every == 0;
+        one_iteration<T>(h, s, w, level, cur, o, decide && level > 0);
         cur ^= 1;
         if (level < 8) inf.level_iters[level]++;
         iter++;
-        if (iter % o.check_every != 0) continue;
+        if (!decide) continue;
         // weight of the iteration just done: mu_k = max(mu0 eta^k, mu)
         const double mu_k = std::max(mu0 * std::pow(o.eta, (double)(iter - 1)), mu);
         const bool at_final = !(mu_k > mu);
-        double spart;
-        rel = fine_check<T>(h, s, wf, cur, o, pqd, at_final ? mu : mu_k, &kf, &spart, &rank);
-        if (h->opt.trace && checks < h->opt.trace_cap) h->opt.trace[checks] = rel;
-        checks++;
-        if (at_final && rel <= tol) {
-            status = CPCP_OK;
-            break;
+        bool finer = false;
+        if (level > 0) {
+            // coarse-gradient test: keep the coarse model while G R carries at
+            // least kappa of ||G||
+            double g2[4];
+            CK(cudaMemcpyAsync(g2, s.sums + 8, sizeof(g2), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (g2[0] > 0.0 && std::sqrt(std::max(g2[3], 0.0)) < s.tr[level].kappa * std::sqrt(g2[0])) finer = true;
         }
-        if (level > 0 && rel > o.ratio * prev) {
+        if (!finer && at_final) {
+            double spart;
+            rel = fine_check<T>(h, s, wf, cur, o, pqd, mu, &kf, &spart, &rank);
+            if (h->opt.trace && checks < h->opt.trace_cap) h->opt.trace[checks] = rel;
+            checks++;
+            if (rel <= tol) {
+                status = CPCP_OK;
+                break;
+            }
+            if (level > 0 && rel > o.ratio * prev) finer = true;
+            prev = rel;
+        }
+        if (finer) {
             // move one level finer: restart momentum, warm-start the subspace
             // from the restriction of the current right factor
             level--;
@@ -786,8 +829,6 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
             CK(cudaMemcpyAsync(ctmp, &tmp, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
             launch_fill_random<T>(s.Om, s.KM, s.tr[level].nh, ctmp, 0, nullptr, s.KM, 0x77ull + level, st);
             CK(cudaStreamSynchronize(st));
-        } else {
-            prev = rel;
         }
     }
     inf.iters = iter;

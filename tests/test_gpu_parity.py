@@ -199,11 +199,14 @@ def small_cpcp():
 
 
 @pytest.mark.parametrize("levels", [1, 2])
-def test_solve_fp32_cpcp_matches_oracle(cp, h, small_cpcp, levels):
+def test_solve_fp32_cpcp_matches_oracle(cp, small_cpcp, levels):
+    # the fp32 path has a residual floor near 3.5e-7 on this problem; solve to
+    # (or up to 600 iterations at) 4e-7 and compare with the fp64 optimum
     p, Lr, Sr = small_cpcp
     Qb = torch.as_tensor(cp.pack_mask(p["mask"])).cuda()
-    L, S, info = h.solve(dev(p["D"], torch.float32), Qb, p["lam"], p["mu"], levels=levels, tol=5e-7)
-    assert info["status"] == 0, info
+    with cp.Handle(0, max_iter=600) as hh:
+        L, S, info = hh.solve(dev(p["D"], torch.float32), Qb, p["lam"], p["mu"], levels=levels, tol=4e-7)
+    assert info["status"] in (0, 5) and info["relkkt"] <= 5e-7, info
     L, S = host(L), host(S)
     eL, eS = rel(L, Lr), rel(S, Sr)
     print(f"fp32 levels={levels}: rel err L {eL:.3e} S {eS:.3e} relkkt {info['relkkt']:.3e} iters {info['iters']}")
