@@ -31,8 +31,9 @@
  *     entry (i, j) is observed.  NULL means every entry is observed (PCP).
  *     Unobserved entries of D are never used arithmetically (NaN is allowed).
  *   - dtype selects the storage and arithmetic type of D, L and S:
- *     CPCP_F64 (fp64 throughout) or CPCP_F32 (fp32 storage and elementwise
- *     arithmetic; the small dense factorisations and all reductions in fp64).
+ *     CPCP_F64 (fp64 throughout) or CPCP_F32 (fp32 storage, contractions and
+ *     small k x k factorisations; norms and residual reductions accumulate
+ *     in fp64, the residual-check sums with compensated (Dot2) products).
  *   - All work is queued on the handle's stream.  Calls return after the
  *     result is complete unless stated otherwise.
  *   - No entry point aborts, exits or throws; every failure is a status code
@@ -81,6 +82,14 @@ typedef struct {
     double *trace;         /* optional host array: rel-KKT of each residual check */
     int trace_cap;         /* capacity of trace (entries written: info.checks) */
     int profile;           /* nonzero: time the phases with CUDA events (info.phase_*) */
+    int precision;         /* CPCP_F32 solves only.  0: fp32 contractions.  1 (mixed):
+                              the two passes over the restricted iterate in each
+                              subspace step (M_H Omega and M_H^T Q) run on the tensor
+                              cores with BF16 operands and fp32 accumulation, until the
+                              fine rel-KKT falls to refine_at; then fp32 to the end
+                              (momentum restarts at the switch).  Residual checks and
+                              the small k x k factorisations are never BF16. */
+    double refine_at;      /* rel-KKT at which the mixed path turns to fp32 (1e-3) */
 } cpcp_options;
 
 /* Phases timed when cpcp_options.profile is set. */
@@ -107,6 +116,7 @@ typedef struct {
     double phase_ms[4];    /* device time per phase (profile only), CPCP_PHASE_* */
     int phase_count[4];    /* timed intervals per phase */
     long long launches;    /* CUDA kernels launched by the solve */
+    int bf16_iters;        /* iterations whose contractions ran in BF16 (precision 1) */
 } cpcp_info;
 
 /* Returns a static description of a status code. */
@@ -206,9 +216,27 @@ cpcp_status cpcp_transfer_info(int n, int halvings, double *scale, int *nh);
  * ldo; NULL = seeded random): M ~ U diag(sigma) V^T, U (m x k, ldu),
  * V (n x k, ldv), sigma (k doubles, device or host).  Singular values are in
  * descending order; with k = n the factorisation is exact up to rounding.
+ * With options.precision = 1 (CPCP_F32 only) the two contractions with M of
+ * each power step use BF16 operands on the tensor cores (see cpcp_gemm_bf16).
  */
 cpcp_status cpcp_svd(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *M, int64_t ldm, int k, int q,
                      const void *Omega0, int64_t ldo, void *U, int64_t ldu, void *V, int64_t ldv, double *sigma);
+
+/*
+ * The contraction of the mixed-precision subspace iteration (options.precision
+ * = 1), exposed for testing: C = bf16(A) bf16(B)^T with fp32 accumulation on
+ * the tensor cores (tcgen05, TMEM accumulator).  This is the product form of
+ * both passes over the restricted iterate in a power step (M_H Omega and
+ * M_H^T Q, Sec. 4): the library stores both operands K-major.
+ *   A (rows x K, lda) and B (N x K, ldb): fp32 device matrices, rounded to
+ *   BF16 (nearest even) on the device; C (rows x N, ldc): fp32 device output.
+ *   1 <= N <= 256; rows, K >= 1.  The K sum is split across CTAs and the
+ *   partial sums are added in a fixed order, so the result is deterministic.
+ * Errors: INVALID_ARG, NOMEM, CUDA, TIMEOUT (a bounded wait of the kernel
+ * expired; the context stays usable).
+ */
+cpcp_status cpcp_gemm_bf16(cpcp_handle h, int rows, int K, int N, const float *A, int64_t lda, const float *B,
+                           int64_t ldb, float *C, int64_t ldc);
 
 /*
  * ||P_Q[D]||_F (fro, host double) and the number of observed entries of D

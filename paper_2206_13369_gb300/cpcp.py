@@ -34,14 +34,14 @@ class Options(C.Structure):
                 ("switch_ratio", C.c_double), ("k_max", C.c_int), ("oversample", C.c_int),
                 ("power_iters", C.c_int), ("check_power_iters", C.c_int), ("start_level", C.c_int),
                 ("seed", C.c_uint64), ("trace", C.POINTER(C.c_double)), ("trace_cap", C.c_int),
-                ("profile", C.c_int)]
+                ("profile", C.c_int), ("precision", C.c_int), ("refine_at", C.c_double)]
 
 
 class Info(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("level_iters", C.c_int * 8), ("final_level", C.c_int),
                 ("rank", C.c_int), ("checks", C.c_int), ("relkkt", C.c_double), ("mu0", C.c_double),
                 ("pqd_fro", C.c_double), ("seconds", C.c_double), ("phase_ms", C.c_double * 4),
-                ("phase_count", C.c_int * 4), ("launches", C.c_longlong)]
+                ("phase_count", C.c_int * 4), ("launches", C.c_longlong), ("bf16_iters", C.c_int)]
 
     PHASES = ("pass_coarse", "pass_fine", "svt", "check")
 
@@ -50,7 +50,8 @@ class Info(C.Structure):
                 "final_level": self.final_level, "rank": self.rank, "checks": self.checks,
                 "relkkt": self.relkkt, "mu0": self.mu0, "pqd_fro": self.pqd_fro, "seconds": self.seconds,
                 "phase_ms": dict(zip(self.PHASES, list(self.phase_ms))),
-                "phase_count": dict(zip(self.PHASES, list(self.phase_count))), "launches": self.launches}
+                "phase_count": dict(zip(self.PHASES, list(self.phase_count))), "launches": self.launches,
+                "bf16_iters": self.bf16_iters}
 
 
 _vp, _i64, _int, _dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
@@ -76,6 +77,7 @@ def _load():
     lib.cpcp_prolong.argtypes = [_vp, _int, _int, _int, _int, _vp, _i64, _vp, _i64]
     lib.cpcp_transfer_info.argtypes = [_int, _int, C.POINTER(_dbl), C.POINTER(_int)]
     lib.cpcp_svd.argtypes = [_vp, _int, _int, _int, _vp, _i64, _int, _int, _vp, _i64, _vp, _i64, _vp, _i64, _vp]
+    lib.cpcp_gemm_bf16.argtypes = [_vp, _int, _int, _int, _vp, _i64, _vp, _i64, _vp, _i64]
     lib.cpcp_masked_norm_static.argtypes = [_vp, _int, _int, _int, _vp, _i64, _vp, _i64, C.POINTER(_dbl),
                                             C.POINTER(C.c_int64)]
     return lib
@@ -84,7 +86,8 @@ def _load():
 _lib = _load()
 
 EXPORTED = ["cpcp_status_string", "cpcp_last_error", "cpcp_create", "cpcp_destroy", "cpcp_solve", "cpcp_step",
-            "cpcp_restrict", "cpcp_prolong", "cpcp_transfer_info", "cpcp_svd", "cpcp_masked_norm_static"]
+            "cpcp_restrict", "cpcp_prolong", "cpcp_transfer_info", "cpcp_svd", "cpcp_gemm_bf16",
+            "cpcp_masked_norm_static"]
 
 
 def lib():
@@ -281,6 +284,19 @@ class Handle:
         self._check(_lib.cpcp_svd(self._h, m, n, _dtype_code(M), pM, ldm, int(k), int(q), pO, ldo, pU, ldu, pV,
                                   ldv, sig.ctypes.data), "cpcp_svd")
         return U, sig, V
+
+    def gemm_bf16(self, A, B):
+        """C = bf16(A) bf16(B)^T with fp32 accumulation on the tensor cores;
+        A (rows x K) and B (N x K) fp32 device tensors."""
+        import torch
+        rows, K = A.shape
+        N = B.shape[0]
+        Cm = torch.empty((rows, N), dtype=torch.float32, device=A.device)
+        pA, lda = _ptr(A)
+        pB, ldb = _ptr(B)
+        pC, ldc = _ptr(Cm)
+        self._check(_lib.cpcp_gemm_bf16(self._h, rows, K, N, pA, lda, pB, ldb, pC, ldc), "cpcp_gemm_bf16")
+        return Cm
 
 
 def transfer_info(n: int, halvings: int):

@@ -2,6 +2,7 @@
 // library (not part of the public ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -176,5 +177,19 @@ void launch_ctrl_begin(Ctrl *c, cudaStream_t st);
 void launch_ctrl_end(Ctrl *c, cudaStream_t st);
 void launch_ctrl_take_width(Ctrl *c, cudaStream_t st);  // k = k_next
 void launch_ctrl_set_check(Ctrl *chk, const Ctrl *it, double mu_c, cudaStream_t st);
+
+// tensor-core (tcgen05) BF16 contractions of the mixed-precision path
+int umma_pad_rows(int rows);  // rows rounded up to the 128-row tile
+int umma_pad_k(int k);        // K rounded up to the 64-element stage
+// BF16 copies of fp32 X (rows x cols): Xb (rows_b x ldb, same orientation)
+// and/or Xt (rows_t x ldt, transposed); padding is written with zeros.
+void launch_bf16_pair(int rows, int cols, const float *X, int64_t ldx, __nv_bfloat16 *Xb, int rows_b, int64_t ldb,
+                      __nv_bfloat16 *Xt, int rows_t, int64_t ldt, cudaStream_t st);
+// split-K partials of A B^T (A rows_pad x kpad, B nrows_b x kpad, both BF16
+// K-major, zero padded) for the first *kdyn columns; returns the number of
+// splits (partial: splits x rows x ldp fp32) or -1 if no tensor map could be made
+int launch_umma_tn(int rows, int rows_pad, int kpad, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B,
+                   int nrows_b, int64_t ldb, int nbox, const int *kdyn, float *partial, int ldp, int max_splits,
+                   int *err, cudaStream_t st);
 
 }  // namespace cpcp

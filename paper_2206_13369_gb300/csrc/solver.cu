@@ -24,6 +24,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/cpcp.h"
@@ -162,6 +163,7 @@ T *wsT(cpcp_context *h, const std::string &name, size_t elems)
 }
 
 inline int64_t round4(int64_t x) { return (x + 3) / 4 * 4; }
+inline int round16(int x) { return (x + 15) / 16 * 16; }
 
 // ---------------------------------------------------------------------------
 // transfer operator (host construction, fp64)
@@ -389,6 +391,11 @@ struct SvdWork {
     T *R1, *R1i, *R2, *R2i, *Rz, *Ut, *Wt, *Us, *sig;
     double *sig64;
     int *well;  // per orthogonalisation: 1 when the second CholeskyQR pass is skipped
+    // mixed precision: BF16 copies of M (m x nc) and M^T, and of the thin
+    // operand (Omega^T or Q^T, round16(KM) rows); error flag of the
+    // tensor-core kernels' bounded waits
+    __nv_bfloat16 *Mb = nullptr, *Mt = nullptr, *Bt = nullptr;
+    int *err = nullptr;
 };
 
 template <typename T>
@@ -421,6 +428,17 @@ SvdWork<T> svd_work(cpcp_context *h, const std::string &tag, int m, int ncols, i
     return w;
 }
 
+// BF16 buffers of the mixed-precision contractions for matrices up to m x ncols
+template <typename T>
+void svd_work_bf16(cpcp_context *h, SvdWork<T> &w, const std::string &tag, int m, int ncols)
+{
+    const size_t kpm = umma_pad_k(m), kpn = umma_pad_k(ncols);
+    w.Mb = wsT<__nv_bfloat16>(h, tag + "Mb", (size_t)umma_pad_rows(m) * kpn);
+    w.Mt = wsT<__nv_bfloat16>(h, tag + "Mt", (size_t)umma_pad_rows(ncols) * kpm);
+    w.Bt = wsT<__nv_bfloat16>(h, tag + "Bt", (size_t)round16(w.KM) * std::max(kpm, kpn));
+    w.err = wsT<int>(h, "umma_err", 1);
+}
+
 // CholeskyQR2 of X (rows x k): Q = X R^{-1}; if Rout != nullptr it receives
 // R = R2 R1.  The second pass is skipped on the device when the first one
 // found X nearly orthogonal after column equilibration (the warm-started
@@ -440,13 +458,49 @@ void orth(cpcp_context *h, SvdWork<T> &w, int rows, const T *X, T *Q, T *Rout, c
     launch_gemm_nn<T>(rows, 0, w.Q1, KM, w.R2i, KM, Q, KM, kdyn, kdyn, KM, st);
 }
 
+// The subspace SVD below with both contractions with M on the tensor cores:
+// M is rounded to BF16 once (kept as M and M^T, K-major both), each power
+// step rounds the thin operand (Omega, then Q) and forms Y = M Omega and
+// Z = M^T Q with fp32 accumulation.  Orthogonalisation and the core SVD stay
+// fp32.
+void subspace_svd_bf16(cpcp_context *h, SvdWork<float> &w, int m, int nc, const float *Mx, int64_t ldx,
+                       const float *Omega, int q, const int *kdyn, const Ctrl *jac_ctrl)
+{
+    cudaStream_t st = h->stream;
+    const int KM = w.KM, NB = round16(KM);
+    const int mp = umma_pad_rows(m), ncp = umma_pad_rows(nc), kpm = umma_pad_k(m), kpn = umma_pad_k(nc);
+    launch_bf16_pair(m, nc, Mx, ldx, w.Mb, mp, kpn, w.Mt, ncp, kpm, st);
+    const float *Om = Omega;
+    for (int s = 0; s < q; s++) {
+        launch_bf16_pair(nc, KM, Om, KM, nullptr, 0, 0, w.Bt, NB, kpn, st);
+        int sp = launch_umma_tn(m, mp, kpn, w.Mb, kpn, w.Bt, NB, kpn, NB, kdyn, w.Ypart, KM, 16, w.err, st);
+        if (sp < 0) throw CpcpError{CPCP_ERR_CUDA, "could not encode the TMA tensor maps"};
+        launch_reduce_partial<float>(w.Ypart, sp, m, KM, w.Y, KM, nullptr, kdyn, st);
+        orth<float>(h, w, m, w.Y, w.Qy, nullptr, kdyn, 0);
+        launch_bf16_pair(m, KM, w.Qy, KM, nullptr, 0, 0, w.Bt, NB, kpm, st);
+        sp = launch_umma_tn(nc, ncp, kpm, w.Mt, kpm, w.Bt, NB, kpm, NB, kdyn, w.Zpart, KM, 64, w.err, st);
+        if (sp < 0) throw CpcpError{CPCP_ERR_CUDA, "could not encode the TMA tensor maps"};
+        launch_reduce_partial<float>(w.Zpart, sp, nc, KM, w.Z, KM, nullptr, kdyn, st);
+        orth<float>(h, w, nc, w.Z, w.Qz, w.Rz, kdyn, 1);
+        Om = w.Qz;
+    }
+    launch_jacobi<float>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st);
+}
+
 // Rank-k SVD of Mx (m x nc, ld ldx): q range passes from Omega (nc x k).
 // Leaves Qy (m x k), Qz (nc x k), Ut, Wt (k x k), sig (k) with
-// Mx ~ (Qy Ut) diag(sig) (Qz Wt)^T.
+// Mx ~ (Qy Ut) diag(sig) (Qz Wt)^T.  bf16: the contractions with Mx on the
+// tensor cores (fp32 data only; svd_work_bf16 must have sized the buffers).
 template <typename T>
 void subspace_svd(cpcp_context *h, SvdWork<T> &w, int m, int nc, const T *Mx, int64_t ldx, const T *Omega,
-                  int q, const int *kdyn, const Ctrl *jac_ctrl)
+                  int q, const int *kdyn, const Ctrl *jac_ctrl, bool bf16 = false)
 {
+    if constexpr (std::is_same<T, float>::value) {
+        if (bf16) {
+            subspace_svd_bf16(h, w, m, nc, Mx, ldx, Omega, q, kdyn, jac_ctrl);
+            return;
+        }
+    }
     cudaStream_t st = h->stream;
     const int KM = w.KM;
     const T *Om = Omega;
@@ -479,8 +533,8 @@ int kmax_small<double>()
 // ---------------------------------------------------------------------------
 
 struct Opts {
-    int max_iter, check_every, k_max, p, q, qc, start_level;
-    double eta, mu0, ratio;
+    int max_iter, check_every, k_max, p, q, qc, start_level, precision;
+    double eta, mu0, ratio, refine_at;
     uint64_t seed;
 };
 
@@ -497,6 +551,8 @@ Opts resolve(const cpcp_options &o)
     r.q = o.power_iters > 0 ? o.power_iters : 1;
     r.qc = o.check_power_iters > 0 ? o.check_power_iters : 2;
     r.start_level = o.start_level;
+    r.precision = o.precision;
+    r.refine_at = o.refine_at > 0 ? o.refine_at : 1e-3;
     r.seed = o.seed ? o.seed : 1;
     return r;
 }
@@ -515,6 +571,7 @@ struct SolveState {
     Ctrl *ctrl, *cchk;
     double *partial, *sums;
     int partial_blocks;
+    bool bf16;  // contractions of the iteration's SVD in BF16 (mixed precision, before refinement)
     std::vector<TransferDev<T>> tr;
 };
 
@@ -654,7 +711,7 @@ void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, 
         ldx = s.ldS;
     }
     int ts = h->timer.open(CPCP_PHASE_SVT);
-    subspace_svd<T>(h, w, s.m, tr.nh, Mx, ldx, s.Om, o.q, &s.ctrl->k, s.ctrl);
+    subspace_svd<T>(h, w, s.m, tr.nh, Mx, ldx, s.Om, o.q, &s.ctrl->k, s.ctrl, s.bf16);
     launch_svt_small<T>(w.Ut, w.sig, w.KM, s.ctrl, w.Us, nullptr, st);
     // new factors into the "previous" slot (its old content was consumed above)
     launch_gemm_nn<T>(s.m, 0, w.Qy, w.KM, w.Us, w.KM, s.A[nxt], s.KM, &s.ctrl->k, &s.ctrl->k, s.KM, st);
@@ -710,6 +767,11 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     s.sums = wsT<double>(h, "sums", 16);
     SvdWork<T> w = svd_work<T>(h, "it_", m, n, s.kcap0);
     SvdWork<T> wf = svd_work<T>(h, "ck_", m, n, s.kcap0);
+    s.bf16 = o.precision == 1;
+    if (s.bf16) {
+        svd_work_bf16<T>(h, w, "it_", m, n);
+        CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    }
 
     // control blocks
     Ctrl c0;
@@ -781,6 +843,7 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
         one_iteration<T>(h, s, w, level, cur, o, decide && level > 0);
         cur ^= 1;
         if (level < 8) inf.level_iters[level]++;
+        if (s.bf16) inf.bf16_iters++;
         iter++;
         if (!decide) continue;
         // weight of the iteration just done: mu_k = max(mu0 eta^k, mu)
@@ -806,6 +869,17 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
             }
             if (level > 0 && rel > o.ratio * prev) finer = true;
             prev = rel;
+            if (s.bf16 && rel <= o.refine_at) {
+                // mixed precision: fp32 contractions from here on, momentum restarts
+                s.bf16 = false;
+                if (!finer) {
+                    Ctrl c;
+                    CK(cudaMemcpyAsync(&c, s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+                    CK(cudaStreamSynchronize(st));
+                    c.t = 1.0;
+                    CK(cudaMemcpyAsync(s.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+                }
+            }
         }
         if (finer) {
             // move one level finer: restart momentum, warm-start the subspace
@@ -837,7 +911,10 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     inf.relkkt = rel;
     Ctrl fin;
     CK(cudaMemcpyAsync(&fin, s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    int umma_err = 0;
+    if (w.err) CK(cudaMemcpyAsync(&umma_err, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (umma_err) throw CpcpError{CPCP_ERR_TIMEOUT, "a bounded wait of the tensor-core kernel expired"};
     inf.rank = fin.rk;
     // outputs
     if (S_out) {
@@ -1045,6 +1122,11 @@ cpcp_status svd_impl(cpcp_context *h, int m, int n, const void *Mv, int64_t ldm,
                                                   std::to_string(kmax_small<T>()) + ")"};
     SvdWork<T> w = svd_work<T>(h, "sv_", m, n, k);
     const int KM = w.KM;
+    const bool bf16 = std::is_same<T, float>::value && h->opt.precision == 1;
+    if (bf16) {
+        svd_work_bf16<T>(h, w, "sv_", m, n);
+        CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    }
     Ctrl c;
     memset(&c, 0, sizeof(c));
     c.k = k;
@@ -1058,7 +1140,7 @@ cpcp_status svd_impl(cpcp_context *h, int m, int n, const void *Mv, int64_t ldm,
         CK(cudaMemcpy2DAsync(Om, sizeof(T) * KM, Om0, sizeof(T) * ldo, sizeof(T) * k, n, cudaMemcpyDefault, st));
     else
         launch_fill_random<T>(Om, KM, n, cd, 1, nullptr, KM, 0x5Dull, st);
-    subspace_svd<T>(h, w, m, n, static_cast<const T *>(Mv), ldm, Om, q, &cd->k, nullptr);
+    subspace_svd<T>(h, w, m, n, static_cast<const T *>(Mv), ldm, Om, q, &cd->k, nullptr, bf16);
     launch_gemm_nn<T>(m, 0, w.Qy, KM, w.Ut, KM, static_cast<T *>(Uv), ldu, &cd->k, &cd->k, KM, st);
     launch_gemm_nn<T>(n, 0, w.Qz, KM, w.Wt, KM, static_cast<T *>(Vv), ldv, &cd->k, &cd->k, KM, st);
     // singular values as doubles
@@ -1068,6 +1150,36 @@ cpcp_status svd_impl(cpcp_context *h, int m, int n, const void *Mv, int64_t ldm,
     CK(cudaGetLastError());
     std::vector<double> sd(sh.begin(), sh.end());
     CK(cudaMemcpy(sigma, sd.data(), sizeof(double) * k, cudaMemcpyDefault));
+    if (bf16) {
+        int e = 0;
+        CK(cudaMemcpy(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) throw CpcpError{CPCP_ERR_TIMEOUT, "a bounded wait of the tensor-core kernel expired"};
+    }
+    return CPCP_OK;
+}
+
+cpcp_status gemm_bf16_impl(cpcp_context *h, int rows, int K, int N, const float *A, int64_t lda, const float *B,
+                           int64_t ldb, float *C, int64_t ldc)
+{
+    cudaStream_t st = h->stream;
+    const int rp = umma_pad_rows(rows), kp = umma_pad_k(K), NB = round16(N), ldp = (int)round4(N);
+    __nv_bfloat16 *Ab = wsT<__nv_bfloat16>(h, "gb_A", (size_t)rp * kp);
+    __nv_bfloat16 *Bb = wsT<__nv_bfloat16>(h, "gb_B", (size_t)NB * kp);
+    float *part = wsT<float>(h, "gb_part", (size_t)64 * rows * ldp);
+    int *kd = wsT<int>(h, "gb_k", 1);
+    int *err = wsT<int>(h, "umma_err", 1);
+    CK(cudaMemcpyAsync(kd, &N, sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+    launch_bf16_pair(rows, K, A, lda, Ab, rp, kp, nullptr, 0, 0, st);
+    launch_bf16_pair(N, K, B, ldb, Bb, NB, kp, nullptr, 0, 0, st);
+    int sp = launch_umma_tn(rows, rp, kp, Ab, kp, Bb, NB, kp, NB, kd, part, ldp, 64, err, st);
+    if (sp < 0) throw CpcpError{CPCP_ERR_CUDA, "could not encode the TMA tensor maps"};
+    launch_reduce_partial<float>(part, sp, rows, ldp, C, ldc, nullptr, kd, st);
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    if (e) throw CpcpError{CPCP_ERR_TIMEOUT, "a bounded wait of the tensor-core kernel expired"};
     return CPCP_OK;
 }
 
@@ -1173,6 +1285,8 @@ cpcp_status cpcp_solve(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D
         if (!(lambda > 0) || !(mu > 0) || !(tol > 0))
             throw CpcpError{CPCP_ERR_INVALID_ARG, "lambda, mu and tol must be positive"};
         if (levels < 1 || levels > 6) throw CpcpError{CPCP_ERR_INVALID_ARG, "levels must be in [1, 6]"};
+        if (h->opt.precision < 0 || h->opt.precision > 1 || (h->opt.precision == 1 && dt != CPCP_F32))
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "precision must be 0, or 1 (mixed) with CPCP_F32"};
         if (ldd < n || (L_out && ldl < n) || (S_out && lds < n))
             throw CpcpError{CPCP_ERR_INVALID_ARG, "leading dimension smaller than n"};
         if (Q && ldq < (n + 31) / 32) throw CpcpError{CPCP_ERR_INVALID_ARG, "ldq < ceil(n/32)"};
@@ -1264,8 +1378,21 @@ cpcp_status cpcp_svd(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *M, 
     return guarded(h, [&]() -> cpcp_status {
         if (m < 1 || n < 1 || n > m || !M || !U || !V || !sigma || q < 1 || bad_dtype(dt))
             throw CpcpError{CPCP_ERR_INVALID_ARG, "bad svd arguments (needs m >= n)"};
+        if (h->opt.precision < 0 || h->opt.precision > 1 || (h->opt.precision == 1 && dt != CPCP_F32))
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "precision must be 0, or 1 (mixed) with CPCP_F32"};
         if (dt == CPCP_F32) return svd_impl<float>(h, m, n, M, ldm, k, q, Omega0, ldo, U, ldu, V, ldv, sigma);
         return svd_impl<double>(h, m, n, M, ldm, k, q, Omega0, ldo, U, ldu, V, ldv, sigma);
+    });
+}
+
+cpcp_status cpcp_gemm_bf16(cpcp_handle h, int rows, int K, int N, const float *A, int64_t lda, const float *B,
+                           int64_t ldb, float *C, int64_t ldc)
+{
+    if (!h) return CPCP_ERR_INVALID_ARG;
+    return guarded(h, [&]() -> cpcp_status {
+        if (rows < 1 || K < 1 || N < 1 || N > 256 || !A || !B || !C || lda < K || ldb < K || ldc < N)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "bad gemm_bf16 arguments (1 <= N <= 256)"};
+        return gemm_bf16_impl(h, rows, K, N, A, lda, B, ldb, C, ldc);
     });
 }
 

@@ -4,7 +4,9 @@ the solver report (for profiling a solve under a profiler or by hand).
     python -m paper_2206_13369_gb300.run_solve --m 2000 --n 2000 --rank 50 \\
         --levels 3 --max-iter 200 [--fp64] [--power-iters 1] [--tol 1e-6]
 
-The workload is workloads.planted_cpcp(m, n, rank, corruption, observed, seed).
+The workload is workloads.planted_cpcp(m, n, rank, corruption, observed, seed),
+or with --config N one of the numbered workloads of workloads.config (3 is the
+19200 x 400 video-shaped problem).
 """
 from __future__ import annotations
 
@@ -31,13 +33,17 @@ def main() -> int:
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--fp64", action="store_true")
     ap.add_argument("--profile", action="store_true")
+    ap.add_argument("--config", type=int, default=0, help="use workloads.config(N) instead of planted_cpcp")
     args = ap.parse_args()
 
     import torch
 
     from paper_2206_13369_gb300 import cpcp, workloads
-    p = workloads.planted_cpcp(args.m, args.n, args.rank, args.corruption, args.observed, args.seed,
-                               levels=args.levels)
+    if args.config:
+        p = workloads.config(args.config)
+    else:
+        p = workloads.planted_cpcp(args.m, args.n, args.rank, args.corruption, args.observed, args.seed,
+                                   levels=args.levels)
     dt = torch.float64 if args.fp64 else torch.float32
     D = torch.as_tensor(p["D"], dtype=dt).cuda()
     Q = None if p["mask"] is None else torch.as_tensor(cpcp.pack_mask(p["mask"])).cuda()
