@@ -90,6 +90,10 @@ typedef struct {
                               (momentum restarts at the switch).  Residual checks and
                               the small k x k factorisations are never BF16. */
     double refine_at;      /* rel-KKT at which the mixed path turns to fp32 (1e-3) */
+    int batch_threads;     /* cpcp_solve_batched: threads per CTA, 256 or 512; 0 = the
+                              tuned choice for this batch if one was measured, else 512 */
+    int batch_autotune;    /* cpcp_solve_batched: nonzero = on the first call with a new
+                              batch, time every CTA size and keep the fastest */
 } cpcp_options;
 
 /* Phases timed when cpcp_options.profile is set. */
@@ -118,6 +122,22 @@ typedef struct {
     long long launches;    /* CUDA kernels launched by the solve */
     int bf16_iters;        /* iterations whose contractions ran in BF16 (precision 1) */
 } cpcp_info;
+
+/* One instance of cpcp_solve_batched (fp32, device pointers; conventions as
+ * for cpcp_solve).  L and S may be NULL when not wanted. */
+typedef struct {
+    int m, n;              /* rows and columns of D */
+    const float *D;        /* m x n, leading dimension ldd */
+    int64_t ldd;
+    const uint32_t *Q;     /* bit-packed observation mask (ldq words per row) or NULL */
+    int64_t ldq;
+    double lambda, mu;     /* weights as in cpcp_solve */
+    int levels;            /* 1 .. 4 */
+    float *L;              /* m x n output, leading dimension ldl, or NULL */
+    int64_t ldl;
+    float *S;              /* m x n output, leading dimension lds, or NULL */
+    int64_t lds;
+} cpcp_problem;
 
 /* Returns a static description of a status code. */
 const char *cpcp_status_string(cpcp_status s);
@@ -221,6 +241,25 @@ cpcp_status cpcp_transfer_info(int n, int halvings, double *scale, int *nh);
  */
 cpcp_status cpcp_svd(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *M, int64_t ldm, int k, int q,
                      const void *Omega0, int64_t ldo, void *U, int64_t ldu, void *V, int64_t ldv, double *sigma);
+
+/*
+ * Solve `count` independent instances of eq. (cpcp) (fp32) in one persistent
+ * launch.  Each CTA takes the next instance from a device work queue ordered by
+ * decreasing size and runs the whole multilevel solve of cpcp_solve on it (the
+ * same continuation, level switching, residual checks and tolerance), with the
+ * instance's iterates resident in a device arena owned by the handle; a
+ * problem with n > m is solved transposed.  Limits per instance: levels in
+ * [1, 4]; min(m, n) <= 1024; subspace width at most 64 (rank + oversampling);
+ * n_H <= (m + 1) / 2 when levels > 1 (Assumption 2).  The launch and the
+ * read-back of the per-instance reports are captured in a CUDA graph that a
+ * later call with the same problems, tolerance and options replays.
+ *   infos: host array of `count` reports (may be NULL); infos[i].status is
+ *   instance i's status, the return value the first non-OK status in the order
+ *   INVALID_ARG, NONFINITE_INPUT, NOT_CONVERGED (or OK).  seconds is the
+ *   wall time of the whole batch, launches the kernels of the whole call.
+ * Errors before any device work: INVALID_ARG (bad instance), NOMEM.
+ */
+cpcp_status cpcp_solve_batched(cpcp_handle h, int count, const cpcp_problem *probs, double tol, cpcp_info *infos);
 
 /*
  * The contraction of the mixed-precision subspace iteration (options.precision

@@ -34,7 +34,8 @@ class Options(C.Structure):
                 ("switch_ratio", C.c_double), ("k_max", C.c_int), ("oversample", C.c_int),
                 ("power_iters", C.c_int), ("check_power_iters", C.c_int), ("start_level", C.c_int),
                 ("seed", C.c_uint64), ("trace", C.POINTER(C.c_double)), ("trace_cap", C.c_int),
-                ("profile", C.c_int), ("precision", C.c_int), ("refine_at", C.c_double)]
+                ("profile", C.c_int), ("precision", C.c_int), ("refine_at", C.c_double),
+                ("batch_threads", C.c_int), ("batch_autotune", C.c_int)]
 
 
 class Info(C.Structure):
@@ -55,6 +56,12 @@ class Info(C.Structure):
 
 
 _vp, _i64, _int, _dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+
+
+class Problem(C.Structure):
+    _fields_ = [("m", C.c_int), ("n", C.c_int), ("D", _vp), ("ldd", _i64), ("Q", _vp), ("ldq", _i64),
+                ("lam", C.c_double), ("mu", C.c_double), ("levels", C.c_int), ("L", _vp), ("ldl", _i64),
+                ("S", _vp), ("lds", _i64)]
 
 
 def _load():
@@ -78,6 +85,7 @@ def _load():
     lib.cpcp_transfer_info.argtypes = [_int, _int, C.POINTER(_dbl), C.POINTER(_int)]
     lib.cpcp_svd.argtypes = [_vp, _int, _int, _int, _vp, _i64, _int, _int, _vp, _i64, _vp, _i64, _vp, _i64, _vp]
     lib.cpcp_gemm_bf16.argtypes = [_vp, _int, _int, _int, _vp, _i64, _vp, _i64, _vp, _i64]
+    lib.cpcp_solve_batched.argtypes = [_vp, _int, _vp, _dbl, _vp]
     lib.cpcp_masked_norm_static.argtypes = [_vp, _int, _int, _int, _vp, _i64, _vp, _i64, C.POINTER(_dbl),
                                             C.POINTER(C.c_int64)]
     return lib
@@ -87,7 +95,7 @@ _lib = _load()
 
 EXPORTED = ["cpcp_status_string", "cpcp_last_error", "cpcp_create", "cpcp_destroy", "cpcp_solve", "cpcp_step",
             "cpcp_restrict", "cpcp_prolong", "cpcp_transfer_info", "cpcp_svd", "cpcp_gemm_bf16",
-            "cpcp_masked_norm_static"]
+            "cpcp_solve_batched", "cpcp_masked_norm_static"]
 
 
 def lib():
@@ -284,6 +292,34 @@ class Handle:
         self._check(_lib.cpcp_svd(self._h, m, n, _dtype_code(M), pM, ldm, int(k), int(q), pO, ldo, pU, ldu, pV,
                                   ldv, sig.ctypes.data), "cpcp_svd")
         return U, sig, V
+
+    def solve_batched(self, problems, tol: float = 1e-6, want_L: bool = True, want_S: bool = True):
+        """Solve many fp32 instances in one persistent launch.  problems: list
+        of dicts with D (device fp32 tensor), Q (packed device mask or None),
+        lam, mu, levels.  Returns (list of L, list of S, list of info dicts,
+        overall status)."""
+        import torch
+        arr = (Problem * len(problems))()
+        Ls, Ss, keep = [], [], []
+        for i, pr in enumerate(problems):
+            D = pr["D"]
+            m, n = D.shape
+            L = torch.empty((m, n), dtype=torch.float32, device=D.device) if want_L else None
+            S = torch.empty((m, n), dtype=torch.float32, device=D.device) if want_S else None
+            pD, ldd = _ptr(D)
+            pQ, ldq = _ptr(pr.get("Q"))
+            pL, ldl = _ptr(L)
+            pS, lds = _ptr(S)
+            arr[i] = Problem(m, n, pD, ldd, pQ, ldq, float(pr["lam"]), float(pr["mu"]), int(pr.get("levels", 1)),
+                             pL, ldl, pS, lds)
+            Ls.append(L)
+            Ss.append(S)
+            keep.append(pr)
+        infos = (Info * len(problems))()
+        st = _lib.cpcp_solve_batched(self._h, len(problems), C.cast(arr, _vp), float(tol), C.cast(infos, _vp))
+        if st not in (0, 2, 5):
+            raise CPCPError(st, f"cpcp_solve_batched: {_lib.cpcp_last_error(self._h).decode()}")
+        return Ls, Ss, [f.as_dict() for f in infos], st
 
     def gemm_bf16(self, A, B):
         """C = bf16(A) bf16(B)^T with fp32 accumulation on the tensor cores;

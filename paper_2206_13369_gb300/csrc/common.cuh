@@ -178,6 +178,57 @@ void launch_ctrl_end(Ctrl *c, cudaStream_t st);
 void launch_ctrl_take_width(Ctrl *c, cudaStream_t st);  // k = k_next
 void launch_ctrl_set_check(Ctrl *chk, const Ctrl *it, double mu_c, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// batched solve: one persistent launch, one CTA per instance at a time
+// ---------------------------------------------------------------------------
+constexpr int BATCH_KB = 64;     // widest subspace of a batched instance
+constexpr int BATCH_NMAX = 1024; // widest oriented instance (n <= m)
+constexpr int BATCH_LEVELS = 4;
+
+// Device descriptor of one instance.  Oriented sizes: m >= n; when the user's
+// problem is wider than tall (trans) the CTA solves its transpose, reading
+// the user's D and mask through oriented copies Dw, Qw it makes first.
+struct BatchInst {
+    int m, n, trans, levels;
+    int nh[BATCH_LEVELS];
+    double kappa[BATCH_LEVELS];
+    const float *D;      // user D (user orientation), ldd
+    int64_t ldd;
+    const uint32_t *Q;   // user mask or nullptr, ldq
+    int64_t ldq;
+    float *Lout, *Sout;  // user outputs (user orientation) or nullptr
+    int64_t ldl, lds;
+    double lam, mu;
+    // arena (oriented)
+    float *Dw;           // m x n copy of D^T (trans only), leading dimension ld
+    uint32_t *Qw;        // m x ldqw mask words of Q^T (trans with mask only)
+    int64_t ldqw;
+    float *S[2], *L[2], *M, *MH;
+    int64_t ld, ldh;     // leading dimensions of m x n and m x nh[1] arrays
+    float *A, *B, *Ac, *Bc, *Om, *Omf, *Y, *Qy, *Q1, *Z, *Qz;  // rows x BATCH_KB
+    float *R1, *R1i, *R2, *R2i, *Rz, *Ut, *Wt, *Us, *sig;      // BATCH_KB x BATCH_KB (sig: BATCH_KB)
+    const int *j0[BATCH_LEVELS], *clo[BATCH_LEVELS], *chi[BATCH_LEVELS];
+    const float *w0[BATCH_LEVELS], *w1[BATCH_LEVELS];
+};
+
+struct BatchResult {
+    int status, iters, checks, rank, final_level, level_iters[BATCH_LEVELS];
+    double relkkt, mu0, pqd;
+};
+
+struct BatchOpts {
+    int max_iter, check_every, p, q, qc;
+    double eta, ratio, tol;
+    uint64_t seed;
+};
+
+// Launch the persistent kernel with nt threads per CTA (256 or 512) over
+// `count` instances taken in the order `order`; `next` is a zeroed counter.
+// Returns cudaSuccess or the launch error.
+cudaError_t launch_batched(const BatchInst *inst, BatchResult *res, const int *order, int count, int *next,
+                           const BatchOpts &o, int nt, cudaStream_t st);
+int batched_grid(int nt);  // CTAs of the persistent launch (all resident)
+
 // tensor-core (tcgen05) BF16 contractions of the mixed-precision path
 int umma_pad_rows(int rows);  // rows rounded up to the 128-row tile
 int umma_pad_k(int k);        // K rounded up to the 64-element stage

@@ -41,6 +41,18 @@ struct DevBuf {
     size_t cap = 0;
 };
 
+// Captured graph of the last batched solve (persistent launch + read-back of
+// the per-instance reports), replayed while the call signature is unchanged.
+struct BatchGraph {
+    uint64_t sig = 0;
+    int nt = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cpcp::BatchResult *host_res = nullptr;  // pinned
+    int host_cap = 0;
+    cudaStream_t stream = nullptr;          // private non-blocking stream (capturable)
+};
+
 }  // namespace
 
 // CUDA-event timing of the solver phases (cpcp_options.profile)
@@ -121,6 +133,8 @@ struct cpcp_context {
     std::string err;
     std::map<std::string, DevBuf> bufs;
     PhaseTimer timer;
+    BatchGraph batch;
+    std::map<uint64_t, int> batch_tuned;  // signature -> measured best CTA size
 };
 
 namespace {
@@ -1183,6 +1197,312 @@ cpcp_status gemm_bf16_impl(cpcp_context *h, int rows, int K, int N, const float 
     return CPCP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// batched solve (host side): validation, arena layout, transfer tables,
+// descriptors, the captured graph and the CTA-size autotuner
+// ---------------------------------------------------------------------------
+
+uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull)
+{
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; i++) h = (h ^ b[i]) * 1099511628211ull;
+    return h;
+}
+
+struct BatchLayout {
+    std::vector<BatchInst> inst;
+    std::vector<int> order;
+    size_t arena_floats = 0;
+};
+
+cpcp_status batched_impl(cpcp_context *h, int count, const cpcp_problem *P, double tol, cpcp_info *infos)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const unsigned long long launches0 = g_kernel_launches;
+    const Opts o = resolve(h->opt);
+    const int KB = BATCH_KB;
+    if (count < 1 || !P) throw CpcpError{CPCP_ERR_INVALID_ARG, "count must be >= 1 and probs non-NULL"};
+    if (!(tol > 0)) throw CpcpError{CPCP_ERR_INVALID_ARG, "tol must be positive"};
+
+    // validation and oriented sizes
+    std::vector<BatchInst> inst(count);
+    std::map<std::pair<int, int>, HostTransfer> tables;
+    for (int i = 0; i < count; i++) {
+        const cpcp_problem &q = P[i];
+        const std::string who = "instance " + std::to_string(i) + ": ";
+        if (q.m < 1 || q.n < 1 || !q.D || q.ldd < q.n || (q.L && q.ldl < q.n) || (q.S && q.lds < q.n))
+            throw CpcpError{CPCP_ERR_INVALID_ARG, who + "bad sizes, D or leading dimension"};
+        if (q.Q && q.ldq < (q.n + 31) / 32) throw CpcpError{CPCP_ERR_INVALID_ARG, who + "ldq < ceil(n/32)"};
+        if (!(q.lambda > 0) || !(q.mu > 0)) throw CpcpError{CPCP_ERR_INVALID_ARG, who + "lambda and mu must be positive"};
+        if (q.levels < 1 || q.levels > BATCH_LEVELS)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, who + "levels must be in [1, 4] for the batched solve"};
+        BatchInst &b = inst[i];
+        memset(&b, 0, sizeof(b));
+        b.trans = q.n > q.m ? 1 : 0;
+        b.m = std::max(q.m, q.n);
+        b.n = std::min(q.m, q.n);
+        if (b.n > BATCH_NMAX) throw CpcpError{CPCP_ERR_INVALID_ARG, who + "min(m, n) exceeds 1024"};
+        b.levels = q.levels;
+        for (int lv = 0; lv < BATCH_LEVELS; lv++) b.nh[lv] = coarse_dim(b.n, std::min(lv, q.levels - 1));
+        if (q.levels > 1 && 2 * b.nh[q.levels - 1] > b.m + 1)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, who + "coarse width exceeds (m+1)/2 (Assumption 2)"};
+        for (int lv = 1; lv < q.levels; lv++) {
+            auto key = std::make_pair(b.n, lv);
+            if (!tables.count(key)) tables[key] = build_transfer(b.n, lv);
+            b.kappa[lv] = tables[key].kappa;
+        }
+        b.D = q.D;
+        b.ldd = q.ldd;
+        b.Q = q.Q;
+        b.ldq = q.ldq;
+        b.Lout = q.L;
+        b.ldl = q.ldl;
+        b.Sout = q.S;
+        b.lds = q.lds;
+        b.lam = q.lambda;
+        b.mu = q.mu;
+    }
+    // transfer tables in one device buffer: per (n, h) j0, clo, chi (int) and w0, w1 (float)
+    size_t tab_words = 0;
+    std::map<std::pair<int, int>, size_t> tab_off;
+    for (auto &kv : tables) {
+        tab_off[kv.first] = tab_words;
+        const HostTransfer &t = kv.second;
+        tab_words += (size_t)3 * t.n + 2 * (size_t)t.nh;
+        tab_words = (tab_words + 63) / 64 * 64;
+    }
+    std::vector<uint32_t> tab_host(std::max<size_t>(tab_words, 64), 0u);
+    for (auto &kv : tables) {
+        const HostTransfer &t = kv.second;
+        uint32_t *w = tab_host.data() + tab_off[kv.first];
+        for (int j = 0; j < t.n; j++) {
+            w[j] = (uint32_t)t.j0[j];
+            float f0 = (float)t.w0[j], f1 = (float)t.w1[j];
+            memcpy(&w[t.n + j], &f0, 4);
+            memcpy(&w[2 * t.n + j], &f1, 4);
+        }
+        for (int c = 0; c < t.nh; c++) {
+            w[3 * t.n + c] = (uint32_t)t.clo[c];
+            w[3 * t.n + t.nh + c] = (uint32_t)t.chi[c];
+        }
+    }
+    uint32_t *tab_dev = wsT<uint32_t>(h, "bt_tables", tab_host.size());
+
+    // arena layout (floats, every array 256-byte aligned)
+    size_t off = 0;
+    auto take = [&](size_t floats) {
+        size_t o0 = off;
+        off += (floats + 63) / 64 * 64;
+        return o0;
+    };
+    struct Offs {
+        size_t Dw, Qw, S0, S1, L0, L1, M, MH, A, B, Ac, Bc, Om, Omf, Y, Qy, Q1, Z, Qz, R[8], sig;
+    };
+    std::vector<Offs> offs(count);
+    for (int i = 0; i < count; i++) {
+        BatchInst &b = inst[i];
+        Offs &f = offs[i];
+        b.ld = round4(b.n);
+        b.ldh = b.levels > 1 ? round4(b.nh[1]) : 4;
+        b.ldqw = (b.n + 31) / 32;
+        const size_t mn = (size_t)b.m * b.ld;
+        f.Dw = b.trans ? take(mn) : 0;
+        f.Qw = (b.trans && b.Q) ? take((size_t)b.m * b.ldqw) : 0;
+        f.S0 = take(mn);
+        f.S1 = take(mn);
+        f.L0 = take(mn);
+        f.L1 = take(mn);
+        f.M = take(mn);
+        f.MH = b.levels > 1 ? take((size_t)b.m * b.ldh) : 0;
+        f.A = take((size_t)b.m * KB);
+        f.Ac = take((size_t)b.m * KB);
+        f.Y = take((size_t)b.m * KB);
+        f.Qy = take((size_t)b.m * KB);
+        f.Q1 = take((size_t)b.m * KB);
+        f.B = take((size_t)b.n * KB);
+        f.Bc = take((size_t)b.n * KB);
+        f.Om = take((size_t)b.n * KB);
+        f.Omf = take((size_t)b.n * KB);
+        f.Z = take((size_t)b.n * KB);
+        f.Qz = take((size_t)b.n * KB);
+        for (int r = 0; r < 8; r++) f.R[r] = take((size_t)KB * KB);
+        f.sig = take(KB);
+    }
+    float *arena = wsT<float>(h, "bt_arena", off);
+    for (int i = 0; i < count; i++) {
+        BatchInst &b = inst[i];
+        const Offs &f = offs[i];
+        b.Dw = b.trans ? arena + f.Dw : nullptr;
+        b.Qw = (b.trans && b.Q) ? reinterpret_cast<uint32_t *>(arena + f.Qw) : nullptr;
+        b.S[0] = arena + f.S0;
+        b.S[1] = arena + f.S1;
+        b.L[0] = arena + f.L0;
+        b.L[1] = arena + f.L1;
+        b.M = arena + f.M;
+        b.MH = b.levels > 1 ? arena + f.MH : nullptr;
+        b.A = arena + f.A;
+        b.Ac = arena + f.Ac;
+        b.Y = arena + f.Y;
+        b.Qy = arena + f.Qy;
+        b.Q1 = arena + f.Q1;
+        b.B = arena + f.B;
+        b.Bc = arena + f.Bc;
+        b.Om = arena + f.Om;
+        b.Omf = arena + f.Omf;
+        b.Z = arena + f.Z;
+        b.Qz = arena + f.Qz;
+        float **R[8] = {&b.R1, &b.R1i, &b.R2, &b.R2i, &b.Rz, &b.Ut, &b.Wt, &b.Us};
+        for (int r = 0; r < 8; r++) *R[r] = arena + f.R[r];
+        b.sig = arena + f.sig;
+        for (int lv = 1; lv < b.levels; lv++) {
+            const HostTransfer &t = tables[std::make_pair(b.n, lv)];
+            uint32_t *w = tab_dev + tab_off[std::make_pair(b.n, lv)];
+            b.j0[lv] = reinterpret_cast<const int *>(w);
+            b.w0[lv] = reinterpret_cast<const float *>(w + t.n);
+            b.w1[lv] = reinterpret_cast<const float *>(w + 2 * t.n);
+            b.clo[lv] = reinterpret_cast<const int *>(w + 3 * t.n);
+            b.chi[lv] = reinterpret_cast<const int *>(w + 3 * t.n + t.nh);
+        }
+    }
+    // largest instances first
+    std::vector<int> order(count);
+    for (int i = 0; i < count; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (double)inst[a].m * inst[a].n > (double)inst[b].m * inst[b].n;
+    });
+
+    BatchOpts bo;
+    bo.max_iter = o.max_iter;
+    bo.check_every = o.check_every;
+    bo.p = std::min(o.p, BATCH_KB);
+    bo.q = o.q;
+    bo.qc = o.qc;
+    bo.eta = o.eta;
+    bo.ratio = o.ratio;
+    bo.tol = tol;
+    bo.seed = o.seed;
+
+    BatchInst *inst_dev = wsT<BatchInst>(h, "bt_inst", count);
+    BatchResult *res_dev = wsT<BatchResult>(h, "bt_res", count);
+    int *order_dev = wsT<int>(h, "bt_order", count);
+    int *next_dev = wsT<int>(h, "bt_next", 1);
+
+    BatchGraph &g = h->batch;
+    if (!g.stream) CK(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
+    cudaStream_t bs = g.stream;
+    // inputs were produced on the caller's stream
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemcpyAsync(tab_dev, tab_host.data(), sizeof(uint32_t) * tab_host.size(), cudaMemcpyHostToDevice, bs));
+    CK(cudaMemcpyAsync(inst_dev, inst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, bs));
+    CK(cudaMemcpyAsync(order_dev, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, bs));
+    CK(cudaStreamSynchronize(bs));
+
+    // signature: problems, tolerance, options and the device addresses used
+    uint64_t sig = fnv1a(P, sizeof(cpcp_problem) * count);
+    sig = fnv1a(&tol, sizeof(tol), sig);
+    sig = fnv1a(&bo, sizeof(bo), sig);
+    sig = fnv1a(&arena, sizeof(arena), sig);
+    sig = fnv1a(&inst_dev, sizeof(inst_dev), sig);
+
+    int nt = h->opt.batch_threads;
+    if (nt != 0 && nt != 256 && nt != 512) throw CpcpError{CPCP_ERR_INVALID_ARG, "batch_threads must be 0, 256 or 512"};
+    if (nt == 0) {
+        auto it = h->batch_tuned.find(sig);
+        if (it != h->batch_tuned.end()) {
+            nt = it->second;
+        } else if (h->opt.batch_autotune) {
+            // time every CTA size on this batch and keep the fastest
+            float best = 0.f;
+            for (int cand : {256, 512}) {
+                cudaEvent_t e0, e1;
+                CK(cudaEventCreate(&e0));
+                CK(cudaEventCreate(&e1));
+                CK(cudaMemsetAsync(next_dev, 0, sizeof(int), bs));
+                CK(cudaEventRecord(e0, bs));
+                CK(launch_batched(inst_dev, res_dev, order_dev, count, next_dev, bo, cand, bs));
+                CK(cudaEventRecord(e1, bs));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                if (nt == 0 || ms < best) {
+                    best = ms;
+                    nt = cand;
+                }
+            }
+            h->batch_tuned[sig] = nt;
+        } else {
+            nt = 512;
+        }
+    }
+
+    if (g.host_cap < count) {
+        if (g.host_res) cudaFreeHost(g.host_res);
+        g.host_res = nullptr;
+        g.host_cap = 0;
+        CK(cudaMallocHost(&g.host_res, sizeof(BatchResult) * count));
+        g.host_cap = count;
+        g.sig = 0;  // the captured copy targets the old buffer
+    }
+    if (!(g.exec && g.sig == sig && g.nt == nt)) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+        g.exec = nullptr;
+        g.graph = nullptr;
+        g.sig = 0;
+        CK(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e1 = cudaMemsetAsync(next_dev, 0, sizeof(int), bs);
+        cudaError_t e2 = launch_batched(inst_dev, res_dev, order_dev, count, next_dev, bo, nt, bs);
+        cudaError_t e3 = cudaMemcpyAsync(g.host_res, res_dev, sizeof(BatchResult) * count, cudaMemcpyDeviceToHost, bs);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e4 = cudaStreamEndCapture(bs, &graph);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            throw CpcpError{CPCP_ERR_CUDA, "capture of the batched launch failed"};
+        }
+        g.graph = graph;
+        CK(cudaGraphInstantiate(&g.exec, g.graph, 0));
+        g.sig = sig;
+        g.nt = nt;
+    } else {
+        CPCP_COUNT_LAUNCH();  // the replayed persistent kernel
+    }
+    CK(cudaGraphLaunch(g.exec, bs));
+    CK(cudaStreamSynchronize(bs));
+    CK(cudaGetLastError());
+
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    const long long launches = (long long)(g_kernel_launches - launches0);
+    bool any_nf = false, any_nc = false, any_bad = false;
+    for (int i = 0; i < count; i++) {
+        const BatchResult &r = g.host_res[i];
+        any_bad |= r.status == CPCP_ERR_INVALID_ARG;
+        any_nf |= r.status == CPCP_ERR_NONFINITE_INPUT;
+        any_nc |= r.status == CPCP_ERR_NOT_CONVERGED;
+        if (infos) {
+            cpcp_info &f = infos[i];
+            memset(&f, 0, sizeof(f));
+            f.status = r.status;
+            f.iters = r.iters;
+            for (int lv = 0; lv < BATCH_LEVELS; lv++) f.level_iters[lv] = r.level_iters[lv];
+            f.final_level = r.final_level;
+            f.rank = r.rank;
+            f.checks = r.checks;
+            f.relkkt = r.relkkt;
+            f.mu0 = r.mu0;
+            f.pqd_fro = r.pqd;
+            f.seconds = secs;
+            f.launches = launches;
+        }
+    }
+    if (any_bad) return CPCP_ERR_INVALID_ARG;
+    if (any_nf) return CPCP_ERR_NONFINITE_INPUT;
+    if (any_nc) return CPCP_ERR_NOT_CONVERGED;
+    return CPCP_OK;
+}
+
 template <typename F>
 cpcp_status guarded(cpcp_context *h, F &&f)
 {
@@ -1252,6 +1572,11 @@ void cpcp_destroy(cpcp_handle h)
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->batch.stream) cudaStreamSynchronize(h->batch.stream);
+    if (h->batch.exec) cudaGraphExecDestroy(h->batch.exec);
+    if (h->batch.graph) cudaGraphDestroy(h->batch.graph);
+    if (h->batch.host_res) cudaFreeHost(h->batch.host_res);
+    if (h->batch.stream) cudaStreamDestroy(h->batch.stream);
     for (auto &kv : h->bufs)
         if (kv.second.p) cudaFree(kv.second.p);
     delete h;
@@ -1383,6 +1708,12 @@ cpcp_status cpcp_svd(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *M, 
         if (dt == CPCP_F32) return svd_impl<float>(h, m, n, M, ldm, k, q, Omega0, ldo, U, ldu, V, ldv, sigma);
         return svd_impl<double>(h, m, n, M, ldm, k, q, Omega0, ldo, U, ldu, V, ldv, sigma);
     });
+}
+
+cpcp_status cpcp_solve_batched(cpcp_handle h, int count, const cpcp_problem *probs, double tol, cpcp_info *infos)
+{
+    if (!h) return CPCP_ERR_INVALID_ARG;
+    return guarded(h, [&]() -> cpcp_status { return batched_impl(h, count, probs, tol, infos); });
 }
 
 cpcp_status cpcp_gemm_bf16(cpcp_handle h, int rows, int K, int N, const float *A, int64_t lda, const float *B,
