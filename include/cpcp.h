@@ -121,6 +121,9 @@ typedef struct {
     int phase_count[4];    /* timed intervals per phase */
     long long launches;    /* CUDA kernels launched by the solve */
     int bf16_iters;        /* iterations whose contractions ran in BF16 (precision 1) */
+    double svt_detail_ms[4]; /* cpcp_solve_batched only: the instance's SVT phase split into
+                                the products with M, CholeskyQR, the core Jacobi SVD and the
+                                factor products (SM cycle counter at the nominal clock) */
 } cpcp_info;
 
 /* One instance of cpcp_solve_batched (fp32, device pointers; conventions as
@@ -256,7 +259,9 @@ cpcp_status cpcp_svd(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *M, 
  *   infos: host array of `count` reports (may be NULL); infos[i].status is
  *   instance i's status, the return value the first non-OK status in the order
  *   INVALID_ARG, NONFINITE_INPUT, NOT_CONVERGED (or OK).  seconds is the
- *   wall time of the whole batch, launches the kernels of the whole call.
+ *   wall time of the whole batch, launches the kernels of the whole call;
+ *   phase_ms is the instance's own device time per phase, from the SM cycle
+ *   counter at the nominal clock (phase_count is 0).
  * Errors before any device work: INVALID_ARG (bad instance), NOMEM.
  */
 cpcp_status cpcp_solve_batched(cpcp_handle h, int count, const cpcp_problem *probs, double tol, cpcp_info *infos);

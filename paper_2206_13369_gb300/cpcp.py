@@ -42,7 +42,8 @@ class Info(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("level_iters", C.c_int * 8), ("final_level", C.c_int),
                 ("rank", C.c_int), ("checks", C.c_int), ("relkkt", C.c_double), ("mu0", C.c_double),
                 ("pqd_fro", C.c_double), ("seconds", C.c_double), ("phase_ms", C.c_double * 4),
-                ("phase_count", C.c_int * 4), ("launches", C.c_longlong), ("bf16_iters", C.c_int)]
+                ("phase_count", C.c_int * 4), ("launches", C.c_longlong), ("bf16_iters", C.c_int),
+                ("svt_detail_ms", C.c_double * 4)]
 
     PHASES = ("pass_coarse", "pass_fine", "svt", "check")
 
@@ -52,7 +53,8 @@ class Info(C.Structure):
                 "relkkt": self.relkkt, "mu0": self.mu0, "pqd_fro": self.pqd_fro, "seconds": self.seconds,
                 "phase_ms": dict(zip(self.PHASES, list(self.phase_ms))),
                 "phase_count": dict(zip(self.PHASES, list(self.phase_count))), "launches": self.launches,
-                "bf16_iters": self.bf16_iters}
+                "bf16_iters": self.bf16_iters,
+                "svt_detail_ms": dict(zip(("products", "cholqr", "jacobi", "factors"), list(self.svt_detail_ms)))}
 
 
 _vp, _i64, _int, _dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double

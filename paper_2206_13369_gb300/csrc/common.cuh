@@ -214,6 +214,8 @@ struct BatchInst {
 struct BatchResult {
     int status, iters, checks, rank, final_level, level_iters[BATCH_LEVELS];
     double relkkt, mu0, pqd;
+    long long cycles[4];  // SM clock cycles per phase (CPCP_PHASE_* order)
+    long long svt_cycles[4];  // the SVT phase split: products with M, CholeskyQR, Jacobi, factor products
 };
 
 struct BatchOpts {

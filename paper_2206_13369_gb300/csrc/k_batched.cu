@@ -573,17 +573,27 @@ __device__ __noinline__ void jacobi_b(int k, const float *Rz, float *Ut, float *
 // Mx ~ (Qy Ut) diag(sig) (Qz Wt)^T, left in the instance's arena.
 template <int NT>
 __device__ void svd_b(const BatchInst &I, int rows, int nc, const float *Mx, int64_t ldx, const float *Om, int k,
-                      int q, float th2, const Sm &sm, double *red)
+                      int q, float th2, const Sm &sm, double *red, long long *cyc)
 {
     const float *om = Om;
+    long long c0 = clock64(), c1;
     for (int s = 0; s < q; s++) {
         cta_gemm<NT>(rows, k, nc, Mx, ldx, 1, om, KB, 1, I.Y, KB, sm);
+        c1 = clock64();
+        cyc[0] += c1 - c0;
         orth_b<NT>(I, rows, k, I.Y, I.Qy, nullptr, sm, red);
+        c0 = clock64();
+        cyc[1] += c0 - c1;
         gemm_tn_longk<NT>(nc, k, rows, Mx, ldx, I.Qy, KB, I.Z, KB, sm);
+        c1 = clock64();
+        cyc[0] += c1 - c0;
         orth_b<NT>(I, nc, k, I.Z, I.Qz, I.Rz, sm, red);
+        c0 = clock64();
+        cyc[1] += c0 - c1;
         om = I.Qz;
     }
     jacobi_b<NT>(k, I.Rz, I.Ut, I.Wt, I.sig, th2, sm);
+    cyc[2] += clock64() - c0;
 }
 
 // number of singular values above theta (sig sorted descending)
@@ -636,17 +646,30 @@ __device__ __noinline__ void pass_step(const BatchInst &I, const Oriented &od, i
     double gsq = 0.0, ghsq = 0.0;
     for (int i0 = 0; i0 < m; i0 += RB) {
         for (int j = threadIdx.x; j < n; j += NT) {
+            // every load of the chunk is issued before any store (the stores
+            // could alias them, which would serialise one memory round trip
+            // per row)
+            float lk[RB], lp[RB], sk[RB], sp[RB], dv[RB];
+            bool obs[RB];
+#pragma unroll
+            for (int r = 0; r < RB; r++) {
+                const int i = min(i0 + r, m - 1);
+                const int64_t o = (int64_t)i * ld + j;
+                obs[r] = observed(od, i, j);
+                lk[r] = Lk[o];
+                lp[r] = Lp[o];
+                sk[r] = Sk[o];
+                sp[r] = Sn[o];
+                dv[r] = od.D[(int64_t)i * od.ldd + j];  // used only where observed
+            }
 #pragma unroll
             for (int r = 0; r < RB; r++) {
                 const int i = i0 + r;
                 if (i >= m) break;
                 const int64_t o = (int64_t)i * ld + j;
-                const bool obs = observed(od, i, j);
-                const float lk = Lk[o], lp = Lp[o], sk = Sk[o], sp = Sn[o];
-                const float lh = lk + beta * (lk - lp), sh = sk + beta * (sk - sp);
-                float g = 0.f;
-                if (obs) g = lh + sh - od.D[(int64_t)i * od.ldd + j];
-                Sn[o] = obs ? shrink(sh - TAU * g, thS) : 0.f;
+                const float lh = lk[r] + beta * (lk[r] - lp[r]), sh = sk[r] + beta * (sk[r] - sp[r]);
+                const float g = obs[r] ? lh + sh - dv[r] : 0.f;
+                Sn[o] = obs[r] ? shrink(sh - TAU * g, thS) : 0.f;
                 const float mv = lh - TAU * g;
                 if (level == 0) {
                     I.M[o] = mv;
@@ -736,6 +759,18 @@ __device__ __noinline__ double factor_pass(const BatchInst &I, const Oriented &o
             __syncthreads();
             const int j = jb + jl;
             if (j < n) {
+                float skv[RPT], dvv[RPT];
+                bool obv[RPT];
+                if (MODE == F_CHECK) {
+#pragma unroll
+                    for (int t = 0; t < RPT; t++) {
+                        const int i = min(i0 + rg + G * t, m - 1);
+                        skv[t] = I.S[cur][(int64_t)i * I.ld + j];
+                        dvv[t] = od.D[(int64_t)i * od.ldd + j];  // used only where observed
+                        obv[t] = observed(od, i, j);
+                    }
+                }
+#pragma unroll
                 for (int t = 0; t < RPT; t++) {
                     const int rr = rg + G * t, i = i0 + rr;
                     if (i >= m) break;
@@ -750,12 +785,12 @@ __device__ __noinline__ double factor_pass(const BatchInst &I, const Oriented &o
                         const double dl = ((double)h1 + (double)l1) - ((double)h2 + (double)l2);
                         acc += dl * dl;
                     } else {
-                        const float sk = I.S[cur][o];
+                        const float sk = skv[t];
                         float g = 0.f;
-                        if (observed(od, i, j)) {
+                        if (obv[t]) {
                             float s1, e1, s2, e2;
                             two_sum(h1, sk, s1, e1);
-                            two_sum(s1, -od.D[(int64_t)i * od.ldd + j], s2, e2);
+                            two_sum(s1, -dvv[t], s2, e2);
                             g = s2 + ((e1 + e2) + l1);
                             const float x = sk - TAU * g;
                             // S - shrink(x): sk when x shrinks to zero, else tau g + thS sign(x)
@@ -952,7 +987,8 @@ __device__ void solve_instance(const BatchInst &I, BatchResult *res, const Batch
     // mu_0 = ||P_Q D||_2, from a few power steps on M = tau P_Q D
     const int k0 = min(o.p, kcap0);
     fill_random_cols<NT>(I.Omf, n, 0, k0, nullptr, o.seed, 0x30ull, 0);
-    svd_b<NT>(I, m, n, I.M, I.ld, I.Omf, k0, 4, -1.f, sm, red);
+    long long scratch[4] = {0, 0, 0, 0};
+    svd_b<NT>(I, m, n, I.M, I.ld, I.Omf, k0, 4, -1.f, sm, red, scratch);
     const double mu0 = I.sig[0] > 0.f ? (double)I.sig[0] / TAU : I.mu;
     out.mu0 = mu0;
 
@@ -979,12 +1015,16 @@ __device__ void solve_instance(const BatchInst &I, BatchResult *res, const Batch
         const bool decide = (iter + 1) % o.check_every == 0;
         const bool want_g = decide && level > 0;
         double gg[2];
+        long long c0 = clock64();
         pass_step<NT>(I, od, level, cur, beta, thS, want_g, sm, red, gg);
+        long long c1 = clock64();
+        out.cycles[level > 0 ? 0 : 1] += c1 - c0;
         const int nxt = cur ^ 1;
         const int nh = I.nh[level];
         const float *Mx = level > 0 ? I.MH : I.M;
         const int64_t ldx = level > 0 ? I.ldh : I.ld;
-        svd_b<NT>(I, m, nh, Mx, ldx, I.Om, k, o.q, thL * thL, sm, red);
+        svd_b<NT>(I, m, nh, Mx, ldx, I.Om, k, o.q, thL * thL, sm, red, out.svt_cycles);
+        const long long cf = clock64();
         const int r = count_above(I.sig, k, thL);
         svt_scale<NT>(I, k, r, thL);
         cta_gemm<NT>(m, k, k, I.Qy, KB, 1, I.Us, KB, 1, I.A, KB, sm);   // A = Qy Us
@@ -996,6 +1036,9 @@ __device__ void solve_instance(const BatchInst &I, BatchResult *res, const Batch
         for (int idx = threadIdx.x; idx < nh * k; idx += NT) I.Om[(idx / k) * KB + idx % k] = I.Z[(idx / k) * KB + idx % k];
         __syncthreads();
         fill_random_cols<NT>(I.Om, nh, k, max(k, kn), I.sig, o.seed, 0x57E9ull, iter);
+        const long long ce = clock64();
+        out.cycles[2] += ce - c1;
+        out.svt_cycles[3] += ce - cf;
         k = kn;
         rk = r;
         t = t1;
@@ -1009,11 +1052,12 @@ __device__ void solve_instance(const BatchInst &I, BatchResult *res, const Batch
         if (level > 0 && gg[0] > 0.0 && sqrt(fmax(gg[1], 0.0)) < I.kappa[level] * sqrt(gg[0])) finer = true;
         if (!finer && at_final) {
             // fine residual check at (L_k, S_k)
+            c0 = clock64();
             const float thLb = (float)(0.5 * mu), thSb = (float)(0.5 * lam * mu);
             const double s_part = factor_pass<NT, F_CHECK>(I, od, cur, rk, 0, thSb, sm, red);
             const int kce = min(kcap0, max(kc, rk + o.p));
             fill_random_cols<NT>(I.Omf, n, kc, kce, nullptr, o.seed, 0xC4ECull, iter);
-            svd_b<NT>(I, m, n, I.M, I.ld, I.Omf, kce, o.qc, thLb * thLb, sm, red);
+            svd_b<NT>(I, m, n, I.M, I.ld, I.Omf, kce, o.qc, thLb * thLb, sm, red, scratch);
             const int rc = count_above(I.sig, kce, thLb);
             const bool saturated = rc >= kce && kce < kcap0;
             svt_scale<NT>(I, kce, rc, thLb);
@@ -1030,6 +1074,7 @@ __device__ void solve_instance(const BatchInst &I, BatchResult *res, const Batch
                 rel = sqrt(fmax(s_part + l_part, 0.0)) / (double)TAU / pqd;
             }
             checks++;
+            out.cycles[3] += clock64() - c0;
             if (rel <= o.tol) {
                 status = CPCP_OK;
                 break;

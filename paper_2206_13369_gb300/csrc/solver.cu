@@ -1475,6 +1475,8 @@ cpcp_status batched_impl(cpcp_context *h, int count, const cpcp_problem *P, doub
 
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     const long long launches = (long long)(g_kernel_launches - launches0);
+    int khz = 0;
+    CK(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, h->device));
     bool any_nf = false, any_nc = false, any_bad = false;
     for (int i = 0; i < count; i++) {
         const BatchResult &r = g.host_res[i];
@@ -1495,6 +1497,12 @@ cpcp_status batched_impl(cpcp_context *h, int count, const cpcp_problem *P, doub
             f.pqd_fro = r.pqd;
             f.seconds = secs;
             f.launches = launches;
+            // per-instance device time by phase, from the SM cycle counter at the nominal clock
+            for (int ph = 0; ph < 4; ph++) {
+                f.phase_ms[ph] = khz > 0 ? (double)r.cycles[ph] / khz : 0.0;
+                f.phase_count[ph] = 0;
+                f.svt_detail_ms[ph] = khz > 0 ? (double)r.svt_cycles[ph] / khz : 0.0;
+            }
         }
     }
     if (any_bad) return CPCP_ERR_INVALID_ARG;
