@@ -94,6 +94,11 @@ typedef struct {
                               tuned choice for this batch if one was measured, else 512 */
     int batch_autotune;    /* cpcp_solve_batched: nonzero = on the first call with a new
                               batch, time every CTA size and keep the fastest */
+    int unroll;            /* K > 0: cpcp_solve runs the differentiable program instead
+                              (see cpcp_backward): exactly K steps at the deepest level with
+                              an exact SVT, recording checkpoints for the reverse sweep */
+    int ckpt_every;        /* steps between checkpoints of the unrolled run (10) */
+    double rho;            /* unrolled run: mu_k = mu max(rho eta^k, 1); must be > 0 */
 } cpcp_options;
 
 /* Phases timed when cpcp_options.profile is set. */
@@ -244,6 +249,31 @@ cpcp_status cpcp_transfer_info(int n, int halvings, double *scale, int *nh);
  */
 cpcp_status cpcp_svd(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *M, int64_t ldm, int k, int q,
                      const void *Omega0, int64_t ldo, void *U, int64_t ldu, void *V, int64_t ldv, double *sigma);
+
+/*
+ * Reverse sweep of the last unrolled run on this handle (cpcp_solve with
+ * options.unroll = K > 0, CPCP_F32, n <= m).  That run computes, from
+ * L_0 = L_{-1} = S_0 = S_{-1} = 0, K steps of the proximal iteration at the
+ * deepest level h = levels - 1 (Alg. 4 coarse step with an exact SVT of
+ * M_H = (Lh - tau G) R by one-sided Jacobi, Alg. 3 shrink, FISTA momentum,
+ * tau = 1/2) with weights mu_k = mu max(rho eta^k, 1), and returns L_K, S_K.
+ * rho is a constant of the program; rho = ||P_Q D||_2 / mu reproduces the
+ * continuation of cpcp_solve (for levels = 1 its first step then thresholds
+ * tau P_Q D exactly at the top singular value, a point of non-smoothness).
+ * Differentiation is not in the paper.
+ *
+ * Given the cotangents dL = d loss / d L_K (m x n, device, ldgl) and dS =
+ * d loss / d S_K (device, ldgs, or NULL for zero), writes dD = d loss / d D
+ * (device, m x n, ldgd; zero at unobserved entries) and the host scalars
+ * *dlambda, *dmu.  The forward states are recomputed from the checkpoints
+ * (every options.ckpt_every steps); the SVT is differentiated with the
+ * singular-value-gap formula (the Jacobian of a proximal map is
+ * self-adjoint), the shrink with its active set.  D and Q are copied by the
+ * recording run.  Errors: INVALID_ARG (no recorded run, bad arguments), CUDA,
+ * TIMEOUT (a bounded grid barrier of the SVD expired).
+ */
+cpcp_status cpcp_backward(cpcp_handle h, const float *dL, int64_t ldgl, const float *dS, int64_t ldgs, float *dD,
+                          int64_t ldgd, double *dlambda, double *dmu);
 
 /*
  * Solve `count` independent instances of eq. (cpcp) (fp32) in one persistent

@@ -105,6 +105,35 @@ def forward(D, mask, lam, mu, rho, eta, halvings, K, keep=False):
     return L[-1], S[-1]
 
 
+def shrink_margins(D, mask, lam, mu, rho, eta, halvings, K):
+    """Per entry, the smallest relative distance ||XS| - thS| / thS of the
+    shrink input to its threshold over the K steps, and per step the smallest
+    relative distance |s_i - thL| / thL of a singular value to the SVT
+    threshold.  Entries with a small margin sit next to a kink of the program:
+    a change of the trajectory smaller than the margin moves them across it."""
+    D = np.asarray(D, dtype=np.float64)
+    m, n = D.shape
+    obs = np.ones((m, n), bool) if mask is None else np.asarray(mask, bool)
+    R = _R(n, halvings)
+    betas = momentum(K)
+    mus, _ = weights(mu, rho, eta, K)
+    Ls, Ss = forward(D, mask, lam, mu, rho, eta, halvings, K, keep=True)
+    zero = np.zeros((m, n))
+    ent = np.full((m, n), np.inf)
+    sv = []
+    for k in range(K):
+        b = betas[k]
+        Lh = Ls[k] + b * (Ls[k] - (Ls[k - 1] if k else zero))
+        Sh = Ss[k] + b * (Ss[k] - (Ss[k - 1] if k else zero))
+        G = np.where(obs, Lh + Sh - D, 0.0)
+        thS, thL = TAU * lam * mus[k], TAU * mus[k]
+        ent = np.minimum(ent, np.where(obs, np.abs(np.abs(Sh - TAU * G) - thS) / thS, np.inf))
+        X = Lh - TAU * G
+        s = np.linalg.svd(X if R is None else X @ R, compute_uv=False)
+        sv.append(float(np.min(np.abs(s - thL)) / thL))
+    return ent, sv
+
+
 def svt_adjoint(M, theta, gY):
     """(gM, gtheta) of Y = SVT_theta(M) for the cotangent gY (module docstring)."""
     _, U, s, V = _svt_full(M, theta)

@@ -35,7 +35,8 @@ class Options(C.Structure):
                 ("power_iters", C.c_int), ("check_power_iters", C.c_int), ("start_level", C.c_int),
                 ("seed", C.c_uint64), ("trace", C.POINTER(C.c_double)), ("trace_cap", C.c_int),
                 ("profile", C.c_int), ("precision", C.c_int), ("refine_at", C.c_double),
-                ("batch_threads", C.c_int), ("batch_autotune", C.c_int)]
+                ("batch_threads", C.c_int), ("batch_autotune", C.c_int), ("unroll", C.c_int),
+                ("ckpt_every", C.c_int), ("rho", C.c_double)]
 
 
 class Info(C.Structure):
@@ -88,6 +89,7 @@ def _load():
     lib.cpcp_svd.argtypes = [_vp, _int, _int, _int, _vp, _i64, _int, _int, _vp, _i64, _vp, _i64, _vp, _i64, _vp]
     lib.cpcp_gemm_bf16.argtypes = [_vp, _int, _int, _int, _vp, _i64, _vp, _i64, _vp, _i64]
     lib.cpcp_solve_batched.argtypes = [_vp, _int, _vp, _dbl, _vp]
+    lib.cpcp_backward.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _i64, C.POINTER(_dbl), C.POINTER(_dbl)]
     lib.cpcp_masked_norm_static.argtypes = [_vp, _int, _int, _int, _vp, _i64, _vp, _i64, C.POINTER(_dbl),
                                             C.POINTER(C.c_int64)]
     return lib
@@ -97,7 +99,7 @@ _lib = _load()
 
 EXPORTED = ["cpcp_status_string", "cpcp_last_error", "cpcp_create", "cpcp_destroy", "cpcp_solve", "cpcp_step",
             "cpcp_restrict", "cpcp_prolong", "cpcp_transfer_info", "cpcp_svd", "cpcp_gemm_bf16",
-            "cpcp_solve_batched", "cpcp_masked_norm_static"]
+            "cpcp_solve_batched", "cpcp_backward", "cpcp_masked_norm_static"]
 
 
 def lib():
@@ -323,6 +325,22 @@ class Handle:
             raise CPCPError(st, f"cpcp_solve_batched: {_lib.cpcp_last_error(self._h).decode()}")
         return Ls, Ss, [f.as_dict() for f in infos], st
 
+    def backward(self, dL, dS=None):
+        """Reverse sweep of the last unrolled run on this handle (options
+        unroll = K > 0): returns (dD, dlambda, dmu) for the cotangents dL, dS
+        of (L_K, S_K)."""
+        import torch
+        m, n = dL.shape
+        dD = torch.empty((m, n), dtype=torch.float32, device=dL.device)
+        pL, ldl = _ptr(dL.contiguous())
+        dSc = None if dS is None else dS.contiguous()
+        pS, lds = _ptr(dSc)
+        pD, ldd = _ptr(dD)
+        dlam, dmu = _dbl(0), _dbl(0)
+        self._check(_lib.cpcp_backward(self._h, pL, ldl, pS, lds if pS else 0, pD, ldd, C.byref(dlam), C.byref(dmu)),
+                    "cpcp_backward")
+        return dD, float(dlam.value), float(dmu.value)
+
     def gemm_bf16(self, A, B):
         """C = bf16(A) bf16(B)^T with fp32 accumulation on the tensor cores;
         A (rows x K) and B (N x K) fp32 device tensors."""
@@ -335,6 +353,38 @@ class Handle:
         pC, ldc = _ptr(Cm)
         self._check(_lib.cpcp_gemm_bf16(self._h, rows, K, N, pA, lda, pB, ldb, pC, ldc), "cpcp_gemm_bf16")
         return Cm
+
+
+def unrolled_cpcp(D, lam, mu, rho: float, Qbits=None, levels: int = 3, K: int = 50, ckpt_every: int = 10,
+                  eta: float = 0.9, device: int = 0):
+    """Differentiable unrolled multilevel CPCP: (L_K, S_K) as torch tensors,
+    differentiable with respect to D (fp32 device tensor), lam and mu (0-d
+    tensors or floats).  The forward and the hand-written reverse sweep run in
+    the CUDA library (cpcp_solve with options.unroll, cpcp_backward).  The
+    weights are mu_k = mu max(rho eta^k, 1): rho = ||P_Q D||_2 / mu gives the
+    continuation of cpcp_solve."""
+    import torch
+
+    class _Unrolled(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, D_, lam_, mu_):
+            h = Handle(device, unroll=int(K), ckpt_every=int(ckpt_every), rho=float(rho), eta=float(eta))
+            L, S, _ = h.solve(D_.contiguous(), Qbits, float(lam_), float(mu_), levels=levels, tol=1.0)
+            ctx.h = h
+            ctx.dtype = lam_.dtype
+            return L, S
+
+        @staticmethod
+        def backward(ctx, gL, gS):
+            dD, dlam, dmu = ctx.h.backward(gL.contiguous(), None if gS is None else gS.contiguous())
+            ctx.h.close()
+            dl = torch.tensor(dlam, dtype=ctx.dtype, device=gL.device)
+            dm = torch.tensor(dmu, dtype=ctx.dtype, device=gL.device)
+            return dD, dl, dm
+
+    lam_t = lam if torch.is_tensor(lam) else torch.tensor(float(lam), dtype=torch.float64)
+    mu_t = mu if torch.is_tensor(mu) else torch.tensor(float(mu), dtype=torch.float64)
+    return _Unrolled.apply(D, lam_t, mu_t)
 
 
 def transfer_info(n: int, halvings: int):

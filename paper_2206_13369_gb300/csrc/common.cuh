@@ -231,6 +231,30 @@ cudaError_t launch_batched(const BatchInst *inst, BatchResult *res, const int *o
                            const BatchOpts &o, int nt, cudaStream_t st);
 int batched_grid(int nt);  // CTAs of the persistent launch (all resident)
 
+// unrolled (differentiable) iteration, fp32
+void launch_unroll_step(int m, int n, const float *D, int64_t ldd, const uint32_t *Q, int64_t ldq, const float *Lk,
+                        const float *Lp, const float *Sk, const float *Sp, int64_t ld, float beta, float thS,
+                        float *Sout, float *XL, cudaStream_t st);
+int launch_unroll_adjoint(int m, int n, const float *D, int64_t ldd, const uint32_t *Q, int64_t ldq, const float *Lk,
+                          const float *Lp, const float *Sk, const float *Sp, int64_t ld, double beta, float thS,
+                          const float *gXL, double *gLn, double *gSn, double *gLp, double *gSp, double *dD,
+                          float *gL32, double *part, cudaStream_t st);
+void launch_widen(int m, int n, const float *x, int64_t lx, double *y, int64_t ly, cudaStream_t st);
+void launch_narrow(int m, int n, const double *x, int64_t lx, float *y, int64_t ly, cudaStream_t st);
+void launch_row_prolong(int m, int n, int nh, const float *Y, int64_t ldy, const TransferDev<float> &tr, float *out,
+                        int64_t ldo, cudaStream_t st);
+int launch_full_svd(int m, int q, const float *M, int64_t ldm, float *U, int64_t ldu, float *V, int64_t ldv,
+                    double *sig, float *X, float *Vc, double *nrm, int *pos, void *gs, int *err, cudaStream_t st);
+size_t full_svd_sync_bytes();
+void launch_svt_right(int q, const double *sig, const float *V, int64_t ldv, double theta, float *Bf, int64_t ldb,
+                      cudaStream_t st);
+int launch_svt_adjoint_core(int q, const float *A, int64_t lda, const double *sig, double theta, float *B, int64_t ldb,
+                            double *gth_part, cudaStream_t st);
+void launch_svt_adjoint_combine(int m, int q, const float *T, const float *P, const float *W, int64_t ld,
+                                const double *sig, double theta, float *Z, cudaStream_t st);
+void launch_unroll_scalars(const double *gthL_part, int nL, const double *gthS_part, int nS, double lam, double mu_k,
+                           double dmu_k, double *out, cudaStream_t st);
+
 // tensor-core (tcgen05) BF16 contractions of the mixed-precision path
 int umma_pad_rows(int rows);  // rows rounded up to the 128-row tile
 int umma_pad_k(int k);        // K rounded up to the 64-element stage

@@ -63,6 +63,13 @@ __global__ void __launch_bounds__(NT)
             }
         }
         __syncthreads();
+        // the TK terms of a chunk are summed apart and then added to the total
+        // (rounding ~ (sqrt(TK) + sqrt(K / TK)) eps rather than sqrt(K) eps)
+        T part[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) part[i][j] = T(0);
 #pragma unroll
         for (int kk = 0; kk < TK; kk++) {
             T a[4], b[4];
@@ -73,8 +80,12 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
             for (int i = 0; i < 4; i++)
 #pragma unroll
-                for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 4; j++) part[i][j] = fma(a[i], b[j], part[i][j]);
         }
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc[i][j] += part[i][j];
         __syncthreads();
     }
 #pragma unroll
@@ -121,6 +132,11 @@ __global__ void __launch_bounds__(NT)
             }
         }
         __syncthreads();
+        T part[4][4];  // chunk sum, then added to the total (as in gemm_nn_kernel)
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) part[i][j] = T(0);
 #pragma unroll
         for (int kk = 0; kk < TK; kk++) {
             T a[4], b[4];
@@ -131,8 +147,12 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
             for (int i = 0; i < 4; i++)
 #pragma unroll
-                for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 4; j++) part[i][j] = fma(a[i], b[j], part[i][j]);
         }
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc[i][j] += part[i][j];
         __syncthreads();
     }
 #pragma unroll

@@ -41,6 +41,18 @@ struct DevBuf {
     size_t cap = 0;
 };
 
+// The last unrolled (differentiable) run: its constants and where its
+// checkpoints and inputs live (handle workspace), for cpcp_backward.
+struct UnrollRec {
+    bool valid = false;
+    int m = 0, n = 0, K = 0, T = 0, halvings = 0, q = 0;
+    int64_t ld = 0, ldq = 0;
+    double lam = 0, mu = 0, rho = 0, eta = 0;
+    const float *D = nullptr;     // copy of D (m x ld)
+    const uint32_t *Q = nullptr;  // copy of the mask or nullptr
+    float *ck = nullptr;          // checkpoints: per index 4 arrays m x ld (L_k, L_{k-1}, S_k, S_{k-1})
+};
+
 // Captured graph of the last batched solve (persistent launch + read-back of
 // the per-instance reports), replayed while the call signature is unchanged.
 struct BatchGraph {
@@ -135,6 +147,7 @@ struct cpcp_context {
     PhaseTimer timer;
     BatchGraph batch;
     std::map<uint64_t, int> batch_tuned;  // signature -> measured best CTA size
+    UnrollRec unroll;
 };
 
 namespace {
@@ -1511,6 +1524,275 @@ cpcp_status batched_impl(cpcp_context *h, int count, const cpcp_problem *P, doub
     return CPCP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// unrolled (differentiable) program: recording forward and reverse sweep
+// ---------------------------------------------------------------------------
+
+struct UnrollWork {
+    float *XL, *MH, *Y, *Bf, *X, *Vc, *gMH;
+    double *nrm;
+    int *pos, *err;
+    void *gs;
+};
+
+UnrollWork unroll_work(cpcp_context *h, int m, int64_t ld, int q)
+{
+    UnrollWork w;
+    w.XL = wsT<float>(h, "ur_XL", (size_t)m * ld);
+    w.MH = wsT<float>(h, "ur_MH", (size_t)m * q);
+    w.Y = wsT<float>(h, "ur_Y", (size_t)m * q);
+    w.gMH = wsT<float>(h, "ur_gMH", (size_t)m * q);
+    w.Bf = wsT<float>(h, "ur_Bf", (size_t)q * q);
+    w.X = wsT<float>(h, "ur_X", (size_t)q * m);
+    w.Vc = wsT<float>(h, "ur_Vc", (size_t)q * q);
+    w.nrm = wsT<double>(h, "ur_nrm", q);
+    w.pos = wsT<int>(h, "ur_pos", q);
+    w.err = wsT<int>(h, "ur_err", 1);
+    w.gs = ws_get(h, "ur_gs", full_svd_sync_bytes());
+    return w;
+}
+
+// momentum weights beta_k and continuation weights mu_k (and d mu_k / d mu)
+void unroll_schedule(const UnrollRec &r, std::vector<double> &beta, std::vector<double> &mus, std::vector<double> &dmus)
+{
+    beta.resize(r.K);
+    mus.resize(r.K);
+    dmus.resize(r.K);
+    double t = 1.0;
+    for (int k = 0; k < r.K; k++) {
+        const double t1 = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+        beta[k] = (t - 1.0) / t1;
+        t = t1;
+        dmus[k] = std::max(r.rho * std::pow(r.eta, (double)k), 1.0);
+        mus[k] = r.mu * dmus[k];
+    }
+}
+
+// One step: (L_k, L_p, S_k, S_p) -> (Lout, Sout); leaves the exact SVD of the
+// step's M_H in (U, sig, V).
+void unroll_step(cpcp_context *h, const UnrollRec &r, const TransferDev<float> &tr, UnrollWork &w, double beta,
+                 double mu_k, const float *Lk, const float *Lp, const float *Sk, const float *Sp, float *Lout,
+                 float *Sout, float *U, double *sig, float *V)
+{
+    cudaStream_t st = h->stream;
+    const int m = r.m, n = r.n, q = r.q;
+    const double thL = 0.5 * mu_k;
+    const float thS = (float)(0.5 * r.lam * mu_k);
+    launch_unroll_step(m, n, r.D, r.ld, r.Q, r.ldq, Lk, Lp, Sk, Sp, r.ld, (float)beta, thS, Sout, w.XL, st);
+    const float *M = w.XL;
+    int64_t ldm = r.ld;
+    if (r.halvings > 0) {
+        launch_restrict<float>(m, n, w.XL, r.ld, w.MH, q, tr, st);
+        M = w.MH;
+        ldm = q;
+    }
+    if (launch_full_svd(m, q, M, ldm, U, q, V, q, sig, w.X, w.Vc, w.nrm, w.pos, w.gs, w.err, st) < 0)
+        throw CpcpError{CPCP_ERR_CUDA, std::string("full SVD launch failed: ") + cudaGetErrorString(cudaGetLastError())};
+    launch_svt_right(q, sig, V, q, thL, w.Bf, q, st);
+    if (r.halvings > 0) {
+        launch_gemm_nn<float>(m, q, U, q, w.Bf, q, w.Y, q, nullptr, nullptr, q, st);
+        launch_row_prolong(m, n, q, w.Y, q, tr, Lout, r.ld, st);
+    } else {
+        launch_gemm_nn<float>(m, q, U, q, w.Bf, q, Lout, r.ld, nullptr, nullptr, q, st);
+    }
+}
+
+void check_unroll_err(cpcp_context *h, UnrollWork &w)
+{
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaGetLastError());
+    if (e) throw CpcpError{CPCP_ERR_TIMEOUT, "a bounded grid barrier of the SVD expired"};
+}
+
+cpcp_status unroll_forward(cpcp_context *h, int m, int n, const float *D, int64_t ldd, const uint32_t *Q, int64_t ldq,
+                           double lam, double mu, int levels, float *L_out, int64_t ldl, float *S_out, int64_t lds,
+                           cpcp_info *info)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const unsigned long long launches0 = g_kernel_launches;
+    cudaStream_t st = h->stream;
+    UnrollRec &r = h->unroll;
+    r.valid = false;
+    if (n > m) throw CpcpError{CPCP_ERR_INVALID_ARG, "the unrolled program needs n <= m"};
+    if (!(h->opt.rho > 0)) throw CpcpError{CPCP_ERR_INVALID_ARG, "the unrolled program needs options.rho > 0"};
+    r.m = m;
+    r.n = n;
+    r.K = h->opt.unroll;
+    r.T = h->opt.ckpt_every > 0 ? h->opt.ckpt_every : 10;
+    r.halvings = levels - 1;
+    r.q = coarse_dim(n, r.halvings);
+    r.ld = round4(n);
+    r.lam = lam;
+    r.mu = mu;
+    r.rho = h->opt.rho;
+    r.eta = h->opt.eta > 0 ? h->opt.eta : 0.9;
+    if (r.q > 1024) throw CpcpError{CPCP_ERR_INVALID_ARG, "the unrolled program needs n_H <= 1024"};
+    const size_t mn = (size_t)m * r.ld;
+    float *Dc = wsT<float>(h, "ur_D", mn);
+    CK(cudaMemcpy2DAsync(Dc, sizeof(float) * r.ld, D, sizeof(float) * ldd, sizeof(float) * n, m, cudaMemcpyDefault, st));
+    r.D = Dc;
+    r.Q = nullptr;
+    r.ldq = (n + 31) / 32;
+    if (Q) {
+        uint32_t *Qc = wsT<uint32_t>(h, "ur_Q", (size_t)m * r.ldq);
+        CK(cudaMemcpy2DAsync(Qc, sizeof(uint32_t) * r.ldq, Q, sizeof(uint32_t) * ldq, sizeof(uint32_t) * r.ldq, m,
+                             cudaMemcpyDefault, st));
+        r.Q = Qc;
+    }
+    const int nck = (r.K + r.T - 1) / r.T;
+    r.ck = wsT<float>(h, "ur_ck", (size_t)nck * 4 * mn);
+    TransferDev<float> tr = upload_transfer<float>(h, n, r.halvings, "ur");
+    UnrollWork w = unroll_work(h, m, r.ld, r.q);
+    CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    float *L[2] = {wsT<float>(h, "ur_L0", mn), wsT<float>(h, "ur_L1", mn)};
+    float *S[2] = {wsT<float>(h, "ur_S0", mn), wsT<float>(h, "ur_S1", mn)};
+    float *U = wsT<float>(h, "ur_U", (size_t)m * r.q), *V = wsT<float>(h, "ur_V", (size_t)r.q * r.q);
+    double *sig = wsT<double>(h, "ur_sig", r.q);
+    for (int i = 0; i < 2; i++) {
+        CK(cudaMemsetAsync(L[i], 0, sizeof(float) * mn, st));
+        CK(cudaMemsetAsync(S[i], 0, sizeof(float) * mn, st));
+    }
+    std::vector<double> beta, mus, dmus;
+    unroll_schedule(r, beta, mus, dmus);
+    int cur = 0;  // L[cur] = L_k, L[cur ^ 1] = L_{k-1}
+    for (int k = 0; k < r.K; k++) {
+        if (k % r.T == 0) {
+            float *c = r.ck + (size_t)(k / r.T) * 4 * mn;
+            CK(cudaMemcpyAsync(c, L[cur], sizeof(float) * mn, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(c + mn, L[cur ^ 1], sizeof(float) * mn, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(c + 2 * mn, S[cur], sizeof(float) * mn, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(c + 3 * mn, S[cur ^ 1], sizeof(float) * mn, cudaMemcpyDeviceToDevice, st));
+        }
+        unroll_step(h, r, tr, w, beta[k], mus[k], L[cur], L[cur ^ 1], S[cur], S[cur ^ 1], L[cur ^ 1], S[cur ^ 1], U,
+                    sig, V);
+        cur ^= 1;
+    }
+    if (L_out)
+        CK(cudaMemcpy2DAsync(L_out, sizeof(float) * ldl, L[cur], sizeof(float) * r.ld, sizeof(float) * n, m,
+                             cudaMemcpyDefault, st));
+    if (S_out)
+        CK(cudaMemcpy2DAsync(S_out, sizeof(float) * lds, S[cur], sizeof(float) * r.ld, sizeof(float) * n, m,
+                             cudaMemcpyDefault, st));
+    check_unroll_err(h, w);
+    r.valid = true;
+    if (info) {
+        cpcp_info inf;
+        memset(&inf, 0, sizeof(inf));
+        inf.status = CPCP_OK;
+        inf.iters = r.K;
+        inf.level_iters[std::min(r.halvings, 7)] = r.K;
+        inf.final_level = r.halvings;
+        inf.mu0 = mus.empty() ? mu : mus[0];
+        inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        inf.launches = (long long)(g_kernel_launches - launches0);
+        *info = inf;
+    }
+    return CPCP_OK;
+}
+
+cpcp_status unroll_backward(cpcp_context *h, const float *dL, int64_t ldgl, const float *dS, int64_t ldgs, float *dD,
+                            int64_t ldgd, double *dlambda, double *dmu)
+{
+    cudaStream_t st = h->stream;
+    const UnrollRec &r = h->unroll;
+    if (!r.valid) throw CpcpError{CPCP_ERR_INVALID_ARG, "no unrolled run recorded on this handle"};
+    const int m = r.m, n = r.n, q = r.q, T = r.T;
+    const size_t mn = (size_t)m * r.ld, mq = (size_t)m * q, qq = (size_t)q * q;
+    TransferDev<float> tr = upload_transfer<float>(h, n, r.halvings, "ur");
+    UnrollWork w = unroll_work(h, m, r.ld, q);
+    CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    std::vector<double> beta, mus, dmus;
+    unroll_schedule(r, beta, mus, dmus);
+    // segment states (T + 2 of each) and the segment's SVDs
+    float *Ls = wsT<float>(h, "ub_Ls", (size_t)(T + 2) * mn), *Ss = wsT<float>(h, "ub_Ss", (size_t)(T + 2) * mn);
+    float *Us = wsT<float>(h, "ub_U", (size_t)T * mq), *Vs = wsT<float>(h, "ub_V", (size_t)T * qq);
+    double *sigs = wsT<double>(h, "ub_sig", (size_t)T * q);
+    // adjoint recursion and dD in fp64; gL32 is the fp32 copy of gLn for the contractions
+    double *gLn = wsT<double>(h, "ub_gLn", mn), *gSn = wsT<double>(h, "ub_gSn", mn);
+    double *gLp = wsT<double>(h, "ub_gLp", mn), *gSp = wsT<double>(h, "ub_gSp", mn);
+    double *dD64 = wsT<double>(h, "ub_dD", mn);
+    float *gL32 = wsT<float>(h, "ub_gL32", mn), *gXL = wsT<float>(h, "ub_gXL", mn);
+    float *gY = wsT<float>(h, "ub_gY", mq), *P = wsT<float>(h, "ub_P", mq), *Tm = wsT<float>(h, "ub_T", mq);
+    float *W = wsT<float>(h, "ub_W", mq), *Z = wsT<float>(h, "ub_Z", mq);
+    float *A = wsT<float>(h, "ub_A", qq), *B = wsT<float>(h, "ub_B", qq), *Vt = wsT<float>(h, "ub_Vt", qq);
+    float *part = wsT<float>(h, "ub_part", (size_t)64 * qq);
+    double *gthL = wsT<double>(h, "ub_gthL", 256), *gthS = wsT<double>(h, "ub_gthS", 2048);
+    double *scal = wsT<double>(h, "ub_scal", 2);
+    CK(cudaMemcpy2DAsync(gL32, sizeof(float) * r.ld, dL, sizeof(float) * ldgl, sizeof(float) * n, m,
+                         cudaMemcpyDefault, st));
+    launch_widen(m, n, gL32, r.ld, gLn, r.ld, st);
+    if (dS) {
+        float *tmp = wsT<float>(h, "ub_dS", mn);
+        CK(cudaMemcpy2DAsync(tmp, sizeof(float) * r.ld, dS, sizeof(float) * ldgs, sizeof(float) * n, m,
+                             cudaMemcpyDefault, st));
+        launch_widen(m, n, tmp, r.ld, gSn, r.ld, st);
+    } else {
+        CK(cudaMemsetAsync(gSn, 0, sizeof(double) * mn, st));
+    }
+    CK(cudaMemsetAsync(gLp, 0, sizeof(double) * mn, st));
+    CK(cudaMemsetAsync(gSp, 0, sizeof(double) * mn, st));
+    CK(cudaMemsetAsync(dD64, 0, sizeof(double) * mn, st));
+    CK(cudaMemsetAsync(scal, 0, sizeof(double) * 2, st));
+    const int nck = (r.K + T - 1) / T;
+    for (int c = nck - 1; c >= 0; c--) {
+        const int k0 = c * T, k1 = std::min(r.K, k0 + T);
+        // states of the segment: Ls[j] = L_{k0 - 1 + j}
+        const float *ck = r.ck + (size_t)c * 4 * mn;
+        CK(cudaMemcpyAsync(Ls + mn, ck, sizeof(float) * mn, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(Ls, ck + mn, sizeof(float) * mn, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(Ss + mn, ck + 2 * mn, sizeof(float) * mn, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(Ss, ck + 3 * mn, sizeof(float) * mn, cudaMemcpyDeviceToDevice, st));
+        for (int k = k0; k < k1; k++) {
+            const int j = k - k0;
+            unroll_step(h, r, tr, w, beta[k], mus[k], Ls + (j + 1) * mn, Ls + j * mn, Ss + (j + 1) * mn, Ss + j * mn,
+                        Ls + (j + 2) * mn, Ss + (j + 2) * mn, Us + j * mq, sigs + (size_t)j * q, Vs + j * qq);
+        }
+        for (int k = k1 - 1; k >= k0; k--) {
+            const int j = k - k0;
+            const float *U = Us + j * mq, *V = Vs + j * qq;
+            const double *sg = sigs + (size_t)j * q;
+            const double thL = 0.5 * mus[k];
+            const float thS = (float)(0.5 * r.lam * mus[k]);
+            // gY = gL_{k+1} R
+            const float *gy = gL32;
+            int64_t ldy = r.ld;
+            if (r.halvings > 0) {
+                launch_restrict<float>(m, n, gL32, r.ld, gY, q, tr, st);
+                gy = gY;
+                ldy = q;
+            }
+            // SVT adjoint on the exact SVD: A = U^T gY V, B, gM = [U B + (gY V - U A) diag(f/s)] V^T
+            launch_gemm_nn<float>(m, q, gy, ldy, V, q, P, q, nullptr, nullptr, q, st);
+            const int sp = launch_gemm_tn_partial<float>(m, q, U, q, P, q, part, nullptr, q, q, st, nullptr);
+            launch_reduce_partial<float>(part, sp, q, q, A, q, nullptr, nullptr, st);
+            const int nb = launch_svt_adjoint_core(q, A, q, sg, thL, B, q, gthL, st);
+            launch_gemm_nn<float>(m, q, U, q, B, q, Tm, q, nullptr, nullptr, q, st);
+            launch_gemm_nn<float>(m, q, U, q, A, q, W, q, nullptr, nullptr, q, st);
+            launch_svt_adjoint_combine(m, q, Tm, P, W, q, sg, thL, Z, st);
+            launch_transpose<float>(q, q, V, q, Vt, q, st);
+            if (r.halvings > 0) {
+                launch_gemm_nn<float>(m, q, Z, q, Vt, q, w.gMH, q, nullptr, nullptr, q, st);
+                launch_row_prolong(m, n, q, w.gMH, q, tr, gXL, r.ld, st);
+            } else {
+                launch_gemm_nn<float>(m, q, Z, q, Vt, q, gXL, r.ld, nullptr, nullptr, q, st);
+            }
+            const int ns = launch_unroll_adjoint(m, n, r.D, r.ld, r.Q, r.ldq, Ls + (j + 1) * mn, Ls + j * mn,
+                                                 Ss + (j + 1) * mn, Ss + j * mn, r.ld, beta[k], thS, gXL, gLn, gSn,
+                                                 gLp, gSp, dD64, gL32, gthS, st);
+            launch_unroll_scalars(gthL, nb, gthS, ns, r.lam, mus[k], dmus[k], scal, st);
+        }
+    }
+    launch_narrow(m, n, dD64, r.ld, dD, ldgd, st);
+    double sc[2];
+    CK(cudaMemcpyAsync(sc, scal, sizeof(sc), cudaMemcpyDeviceToHost, st));
+    check_unroll_err(h, w);
+    if (dlambda) *dlambda = sc[0];
+    if (dmu) *dmu = sc[1];
+    return CPCP_OK;
+}
+
 template <typename F>
 cpcp_status guarded(cpcp_context *h, F &&f)
 {
@@ -1628,6 +1910,11 @@ cpcp_status cpcp_solve(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D
         if (nh < 1) throw CpcpError{CPCP_ERR_INVALID_ARG, "coarse width below 1"};
         if (levels > 1 && 2 * nh > mm + 1)
             throw CpcpError{CPCP_ERR_INVALID_ARG, "coarse width exceeds (m+1)/2 (Assumption 2)"};
+        if (h->opt.unroll > 0) {
+            if (dt != CPCP_F32) throw CpcpError{CPCP_ERR_INVALID_ARG, "the unrolled program is fp32"};
+            return unroll_forward(h, m, n, static_cast<const float *>(D), ldd, Q, ldq, lambda, mu, levels,
+                                  static_cast<float *>(L_out), ldl, static_cast<float *>(S_out), lds, info);
+        }
         if (dt == CPCP_F32)
             return solve_dispatch<float>(h, m, n, D, ldd, Q, ldq, lambda, mu, levels, tol, L_out, ldl, S_out, lds,
                                          info);
@@ -1715,6 +2002,17 @@ cpcp_status cpcp_svd(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *M, 
             throw CpcpError{CPCP_ERR_INVALID_ARG, "precision must be 0, or 1 (mixed) with CPCP_F32"};
         if (dt == CPCP_F32) return svd_impl<float>(h, m, n, M, ldm, k, q, Omega0, ldo, U, ldu, V, ldv, sigma);
         return svd_impl<double>(h, m, n, M, ldm, k, q, Omega0, ldo, U, ldu, V, ldv, sigma);
+    });
+}
+
+cpcp_status cpcp_backward(cpcp_handle h, const float *dL, int64_t ldgl, const float *dS, int64_t ldgs, float *dD,
+                          int64_t ldgd, double *dlambda, double *dmu)
+{
+    if (!h) return CPCP_ERR_INVALID_ARG;
+    return guarded(h, [&]() -> cpcp_status {
+        if (!dL || !dD || ldgl < h->unroll.n || ldgd < h->unroll.n || (dS && ldgs < h->unroll.n))
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "bad backward arguments"};
+        return unroll_backward(h, dL, ldgl, dS, ldgs, dD, ldgd, dlambda, dmu);
     });
 }
 

@@ -107,3 +107,15 @@ def test_one_step_diagonal_closed_form():
     assert np.allclose(dD, want, atol=1e-12)
     assert np.isclose(dmu, -0.5 * rho * (actL.sum() + lam * actS.sum()))
     assert np.isclose(dlam, -0.5 * mu0 * actS.sum())
+
+
+def test_shrink_margins_one_step():
+    # one step from zero: the shrink input is tau D, its threshold tau lam mu_0
+    d = np.array([5.0, 3.0, 2.0, 0.7, 0.2])
+    D = np.diag(d)
+    lam, mu, rho = 0.9, 1.0, 1.5
+    ent, sv = U.shrink_margins(D, None, lam, mu, rho, 0.9, 0, 1)
+    th = lam * mu * rho
+    assert np.allclose(np.diag(ent), np.abs(d - th) / th)
+    assert np.all(ent[~np.eye(5, dtype=bool)] == 1.0)  # zero entries: | 0 - th | / th
+    assert np.isclose(sv[0], np.min(np.abs(d - mu * rho)) / (mu * rho))
