@@ -15,6 +15,15 @@ over its CUDA-event duration, against the measured HBM copy bandwidth), the
 end-to-end time through the C ABI with host buffers, the clocks seen during the
 timed region, and the fp64 oracle timed on the host cores on a bounded sample.
 
+Three more measurements go into the same line (skipped with --no-extras):
+  "video_mixed": the 19200 x 400 video-shaped workload (4 levels) solved with
+      BF16 tensor-core contractions plus fp32 refinement, with fp32
+      contractions, and single-level;
+  "batched": 256 uneven planted instances in one persistent launch (the
+      launch graph replayed; CTA size autotuned on the first call);
+  "backward": the 1024 x 1024, 3-level, 50-step unrolled solve and its
+      reverse sweep (checkpoints every 10 steps).
+
 Multi-GPU (torchrun): the solve does not shard, so every rank solves its own
 replica of the workload ("replicas only"); value is the max over ranks.
 `--impl reference` times the fp64 CPU oracle (rank 0 only).
@@ -263,6 +272,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(Lh.nbytes + Sh.nbytes)},
             "gpu_launches": int(sum(i["launches"] for i in inf_ml) / len(inf_ml)),
             "roofline": roofline}
+    if rank == 0 and args.extras:
+        line.update(extras(local, stream, flush))
     if rank == 0:
         dt, cores, sample = oracle_sample(p, ORACLE_SAMPLE_STEPS)
         line["cpu_baseline"] = {"value": dt * ITERS_MULTILEVEL, "unit": "s", "cores": cores, "kind": "oracle",
@@ -274,6 +285,68 @@ def run_ours(args):
     return 0
 
 
+def _events_time(stream, fn, reps, flush):
+    import torch
+    out = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1) / 1e3)
+    return statistics.median(out), r
+
+
+def extras(device, stream, flush) -> dict:
+    """The mixed-precision, batched and backward rows on their own workloads."""
+    import torch
+    from paper_2206_13369_gb300 import cpcp, workloads
+    out = {}
+    # video-shaped CPCP, 19200 x 400, 4 levels
+    v = workloads.config(3)
+    D = torch.as_tensor(v["D"], dtype=torch.float32).cuda()
+    Q = torch.as_tensor(cpcp.pack_mask(v["mask"])).cuda()
+    vm = {}
+    for name, prec, lv in (("mixed_4lv", 1, 4), ("fp32_4lv", 0, 4), ("mixed_1lv", 1, 1), ("fp32_1lv", 0, 1)):
+        with cpcp.Handle(device, stream=stream, precision=prec) as hh:
+            hh.solve(D, Q, v["lam"], v["mu"], levels=lv, tol=TOL)
+            t, (_, _, info) = _events_time(stream, lambda: hh.solve(D, Q, v["lam"], v["mu"], levels=lv, tol=TOL), 3,
+                                           flush)
+        vm[name] = {"s": t, "iters": info["iters"], "bf16_iters": info["bf16_iters"], "relkkt": info["relkkt"]}
+    out["video_mixed"] = {"workload": "video-19200x400-r5-cpcp", "unit": "s", "tol": TOL, **vm}
+    del D, Q
+    # 256 uneven instances in one persistent launch
+    ps = workloads.config(4)
+    probs = []
+    for q in ps:
+        Dq = torch.as_tensor(q["D"], dtype=torch.float32).cuda()
+        Qq = None if q["mask"] is None else torch.as_tensor(cpcp.pack_mask(q["mask"])).cuda()
+        probs.append({"D": Dq, "Q": Qq, "lam": q["lam"], "mu": q["mu"], "levels": q["levels"]})
+    with cpcp.Handle(device, stream=stream, batch_autotune=1) as hb:
+        hb.solve_batched(probs, tol=TOL)
+        t, (_, _, infos, st) = _events_time(stream, lambda: hb.solve_batched(probs, tol=TOL), 3, flush)
+    its = [f["iters"] for f in infos]
+    out["batched"] = {"workload": "batched-256-cpcp-fp32", "unit": "s", "s": t, "instances_per_s": 256 / t,
+                      "status": st, "iters_mean": statistics.mean(its), "iters_max": max(its),
+                      "elements": int(sum(q["D"].size for q in ps)), "gpu_launches": int(infos[0]["launches"])}
+    del probs
+    # unrolled 1024 x 1024, 3 levels, 50 steps, forward and reverse sweep
+    c5 = workloads.config(5)
+    D = torch.as_tensor(c5["D"], dtype=torch.float32).cuda()
+    Q = torch.as_tensor(cpcp.pack_mask(c5["mask"])).cuda()
+    L0 = torch.as_tensor(c5["L0"], dtype=torch.float32).cuda()
+    hu = cpcp.Handle(device, stream=stream, unroll=50, ckpt_every=10, rho=1.1 / 1e-3)
+    tf, (L, _, _) = _events_time(stream, lambda: hu.solve(D, Q, c5["lam"], c5["mu"], levels=3, tol=1.0), 2, flush)
+    gL = 2.0 * (L - L0)
+    tb, _ = _events_time(stream, lambda: hu.backward(gL), 2, flush)
+    hu.close()
+    out["backward"] = {"workload": "unrolled-1024x1024-r20-3lv-50steps", "unit": "s", "forward_s": tf,
+                       "backward_s": tb, "ckpt_every": 10}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -281,6 +354,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--levels", type=int, default=3)
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the mixed-precision, batched and backward measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -285,7 +285,9 @@ cpcp_status cpcp_backward(cpcp_handle h, const float *dL, int64_t ldgl, const fl
  * [1, 4]; min(m, n) <= 1024; subspace width at most 64 (rank + oversampling);
  * n_H <= (m + 1) / 2 when levels > 1 (Assumption 2).  The launch and the
  * read-back of the per-instance reports are captured in a CUDA graph that a
- * later call with the same problems, tolerance and options replays.
+ * later call with the same sizes, levels, tolerance and options replays (the
+ * instance descriptors, with the caller's pointers, are uploaded first on
+ * every call).
  *   infos: host array of `count` reports (may be NULL); infos[i].status is
  *   instance i's status, the return value the first non-OK status in the order
  *   INVALID_ARG, NONFINITE_INPUT, NOT_CONVERGED (or OK).  seconds is the

@@ -1410,12 +1410,20 @@ cpcp_status batched_impl(cpcp_context *h, int count, const cpcp_problem *P, doub
     CK(cudaMemcpyAsync(order_dev, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, bs));
     CK(cudaStreamSynchronize(bs));
 
-    // signature: problems, tolerance, options and the device addresses used
-    uint64_t sig = fnv1a(P, sizeof(cpcp_problem) * count);
+    // Shape signature (sizes, levels, masks present, tolerance, options): the
+    // key of the tuned CTA size.  The graph signature adds the handle's own
+    // device buffers the captured launch reads; user pointers are not part of
+    // either, since the descriptors are uploaded before every launch.
+    uint64_t sig = fnv1a(&count, sizeof(count));
+    for (int i = 0; i < count; i++) {
+        const int key[4] = {P[i].m, P[i].n, P[i].levels, P[i].Q != nullptr};
+        sig = fnv1a(key, sizeof(key), sig);
+    }
     sig = fnv1a(&tol, sizeof(tol), sig);
     sig = fnv1a(&bo, sizeof(bo), sig);
-    sig = fnv1a(&arena, sizeof(arena), sig);
-    sig = fnv1a(&inst_dev, sizeof(inst_dev), sig);
+    uint64_t gsig = fnv1a(&arena, sizeof(arena), sig);
+    const void *bufs[4] = {inst_dev, res_dev, order_dev, next_dev};
+    gsig = fnv1a(bufs, sizeof(bufs), gsig);
 
     int nt = h->opt.batch_threads;
     if (nt != 0 && nt != 256 && nt != 512) throw CpcpError{CPCP_ERR_INVALID_ARG, "batch_threads must be 0, 256 or 512"};
@@ -1458,7 +1466,7 @@ cpcp_status batched_impl(cpcp_context *h, int count, const cpcp_problem *P, doub
         g.host_cap = count;
         g.sig = 0;  // the captured copy targets the old buffer
     }
-    if (!(g.exec && g.sig == sig && g.nt == nt)) {
+    if (!(g.exec && g.sig == gsig && g.nt == nt)) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
         if (g.graph) cudaGraphDestroy(g.graph);
         g.exec = nullptr;
@@ -1477,7 +1485,7 @@ cpcp_status batched_impl(cpcp_context *h, int count, const cpcp_problem *P, doub
         }
         g.graph = graph;
         CK(cudaGraphInstantiate(&g.exec, g.graph, 0));
-        g.sig = sig;
+        g.sig = gsig;
         g.nt = nt;
     } else {
         CPCP_COUNT_LAUNCH();  // the replayed persistent kernel

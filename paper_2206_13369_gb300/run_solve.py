@@ -3,6 +3,7 @@ the solver report (for profiling a solve under a profiler or by hand).
 
     python -m paper_2206_13369_gb300.run_solve --m 2000 --n 2000 --rank 50 \\
         --levels 3 --max-iter 200 [--fp64] [--power-iters 1] [--tol 1e-6]
+        [--precision 1] [--unroll K --rho R]
 
 The workload is workloads.planted_cpcp(m, n, rank, corruption, observed, seed),
 or with --config N one of the numbered workloads of workloads.config (3 is the
@@ -34,11 +35,31 @@ def main() -> int:
     ap.add_argument("--fp64", action="store_true")
     ap.add_argument("--profile", action="store_true")
     ap.add_argument("--config", type=int, default=0, help="use workloads.config(N) instead of planted_cpcp")
+    ap.add_argument("--precision", type=int, default=0, help="1: BF16 tensor-core contractions, then fp32")
+    ap.add_argument("--unroll", type=int, default=0, help="K > 0: the K-step differentiable program and its "
+                    "reverse sweep (loss ||L_K - L0||^2)")
+    ap.add_argument("--rho", type=float, default=1100.0, help="continuation scale of the unrolled program")
+    ap.add_argument("--batched", type=int, default=0, help="N > 0: the first N instances of the 256-instance "
+                    "workload in one cpcp_solve_batched call")
     args = ap.parse_args()
 
     import torch
 
     from paper_2206_13369_gb300 import cpcp, workloads
+    if args.batched > 0:
+        ps = workloads.config(4)[:args.batched]
+        probs = []
+        for q in ps:
+            Dq = torch.as_tensor(q["D"], dtype=torch.float32).cuda()
+            Qq = None if q["mask"] is None else torch.as_tensor(cpcp.pack_mask(q["mask"])).cuda()
+            probs.append({"D": Dq, "Q": Qq, "lam": q["lam"], "mu": q["mu"], "levels": q["levels"]})
+        with cpcp.Handle(0, max_iter=args.max_iter) as h:
+            for _ in range(args.repeat):
+                _, _, infos, st = h.solve_batched(probs, tol=args.tol)
+            torch.cuda.synchronize()
+        print(json.dumps({"status": st, "iters": [f["iters"] for f in infos],
+                          "phase_ms": [f["phase_ms"] for f in infos]}))
+        return 0
     if args.config:
         p = workloads.config(args.config)
     else:
@@ -47,9 +68,16 @@ def main() -> int:
     dt = torch.float64 if args.fp64 else torch.float32
     D = torch.as_tensor(p["D"], dtype=dt).cuda()
     Q = None if p["mask"] is None else torch.as_tensor(cpcp.pack_mask(p["mask"])).cuda()
-    with cpcp.Handle(0, max_iter=args.max_iter, power_iters=args.power_iters, profile=int(args.profile)) as h:
+    opts = dict(max_iter=args.max_iter, power_iters=args.power_iters, profile=int(args.profile),
+                precision=args.precision)
+    if args.unroll > 0:
+        opts.update(unroll=args.unroll, rho=args.rho)
+    with cpcp.Handle(0, **opts) as h:
         for _ in range(args.repeat):
-            _, _, info = h.solve(D, Q, p["lam"], p["mu"], levels=args.levels, tol=args.tol)
+            L, _, info = h.solve(D, Q, p["lam"], p["mu"], levels=args.levels, tol=args.tol)
+            if args.unroll > 0:
+                _, dlam, dmu = h.backward(2.0 * (L - torch.as_tensor(p["L0"], dtype=torch.float32).cuda()))
+                info["dlambda"], info["dmu"] = dlam, dmu
         torch.cuda.synchronize()
     print(json.dumps(info))
     return 0
