@@ -99,6 +99,15 @@ typedef struct {
                               an exact SVT, recording checkpoints for the reverse sweep */
     int ckpt_every;        /* steps between checkpoints of the unrolled run (10) */
     double rho;            /* unrolled run: mu_k = mu max(rho eta^k, 1); must be > 0 */
+    int subspace_mode;     /* cpcp_solve: 0 = power_iters full range passes per iteration;
+                              1 = half steps: each iteration projects once onto the previous
+                              iteration's right or left singular subspace, alternating
+                              (one contraction with M_H, one CholeskyQR2, one core SVD) */
+    int pass_tc;           /* cpcp_solve, fp32: nonzero runs the fused fine pass on the tensor
+                              cores (tcgen05, three TF32 products per fp32 product, 2^-22 relative
+                              per product) wherever D and S meet its alignment rules (16-byte
+                              aligned base, leading dimension a multiple of 4); its rel-KKT floor
+                              is about 2e-6.  0 (default): the SIMT pass */
 } cpcp_options;
 
 /* Phases timed when cpcp_options.profile is set. */
@@ -129,6 +138,10 @@ typedef struct {
     double svt_detail_ms[4]; /* cpcp_solve_batched only: the instance's SVT phase split into
                                 the products with M, CholeskyQR, the core Jacobi SVD and the
                                 factor products (SM cycle counter at the nominal clock) */
+    int jacobi_calls;      /* cpcp_solve: core Jacobi SVDs run (iterations and checks) */
+    int jacobi_sweeps;     /* cpcp_solve: their sweeps, summed */
+    int chol_factors;      /* cpcp_solve: Cholesky factorisations of CholeskyQR run (second
+                              passes skipped on the device are not counted) */
 } cpcp_info;
 
 /* One instance of cpcp_solve_batched (fp32, device pointers; conventions as

@@ -36,7 +36,8 @@ class Options(C.Structure):
                 ("seed", C.c_uint64), ("trace", C.POINTER(C.c_double)), ("trace_cap", C.c_int),
                 ("profile", C.c_int), ("precision", C.c_int), ("refine_at", C.c_double),
                 ("batch_threads", C.c_int), ("batch_autotune", C.c_int), ("unroll", C.c_int),
-                ("ckpt_every", C.c_int), ("rho", C.c_double)]
+                ("ckpt_every", C.c_int), ("rho", C.c_double), ("subspace_mode", C.c_int),
+                ("pass_tc", C.c_int)]
 
 
 class Info(C.Structure):
@@ -44,7 +45,8 @@ class Info(C.Structure):
                 ("rank", C.c_int), ("checks", C.c_int), ("relkkt", C.c_double), ("mu0", C.c_double),
                 ("pqd_fro", C.c_double), ("seconds", C.c_double), ("phase_ms", C.c_double * 4),
                 ("phase_count", C.c_int * 4), ("launches", C.c_longlong), ("bf16_iters", C.c_int),
-                ("svt_detail_ms", C.c_double * 4)]
+                ("svt_detail_ms", C.c_double * 4), ("jacobi_calls", C.c_int), ("jacobi_sweeps", C.c_int),
+                ("chol_factors", C.c_int)]
 
     PHASES = ("pass_coarse", "pass_fine", "svt", "check")
 
@@ -55,7 +57,9 @@ class Info(C.Structure):
                 "phase_ms": dict(zip(self.PHASES, list(self.phase_ms))),
                 "phase_count": dict(zip(self.PHASES, list(self.phase_count))), "launches": self.launches,
                 "bf16_iters": self.bf16_iters,
-                "svt_detail_ms": dict(zip(("products", "cholqr", "jacobi", "factors"), list(self.svt_detail_ms)))}
+                "svt_detail_ms": dict(zip(("products", "cholqr", "jacobi", "factors"), list(self.svt_detail_ms))),
+                "jacobi_calls": self.jacobi_calls, "jacobi_sweeps": self.jacobi_sweeps,
+                "chol_factors": self.chol_factors}
 
 
 _vp, _i64, _int, _dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double

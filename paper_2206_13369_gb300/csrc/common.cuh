@@ -41,6 +41,7 @@ struct Ctrl {
     int flags;       // bit 0: rank reached the width at least once
     int pad_;
     uint64_t seed;
+    double eta_k;    // eta^iter (continuation factor so far; 1 at the start)
 };
 
 // shrink(x) = sign(x) max(|x| - th, 0), with a signed zero inside the band
@@ -114,6 +115,12 @@ struct PassArgs {
 
 // returns the number of blocks (partial sums written when a.GH is set)
 template <typename T> int launch_step_pass(const PassArgs<T> &a, bool coarse, cudaStream_t st);
+// the fine STEP pass on the tensor cores (k_pass_tc.cu); false, launching
+// nothing, when an operand does not meet the TMA rules.  Ah, Al (m rows) and
+// Bh, Bl (n rows) hold pass_tc_split_elems(rows, kmax) floats each.
+size_t pass_tc_split_elems(int rows, int kmax);
+bool launch_pass_tc(const PassArgs<float> &p, int kmax, float *Ah, float *Al, float *Bh, float *Bl, int *err,
+                    cudaStream_t st);
 // per-block fp64 partial sums of squares of X (rows x cols); returns the block count
 template <typename T> int launch_sumsq(int rows, int cols, const T *X, int64_t ld, double *partial, cudaStream_t st);
 // check pass at (L_k, S_k) with weight mu_bar: writes M = L - tau G and
@@ -153,16 +160,36 @@ void launch_transpose(int rows, int cols, const T *A, int64_t lda, T *B, int64_t
 void launch_transpose_mask(int rows, int cols, const uint32_t *in, int64_t ldi, uint32_t *out, int64_t ldo,
                            cudaStream_t st);
 
+// tall-skinny contractions with the split-K sums reduced inside a thread-block
+// cluster (k_tsgemm.cu).  Each returns false (launching nothing) when an
+// operand is not 16-byte aligned with a 16-byte multiple leading dimension.
+// C = A B; K dynamic when kdyn_K is given (then kmaxK bounds it); skip: when
+// *skip is set C = A (B is the identity; only with kdyn_K)
+template <typename T>
+bool launch_ts_nn(int rows, int K, const T *A, int64_t lda, const T *B, int64_t ldb, T *C, int64_t ldc,
+                  const int *kdyn_K, const int *kdyn_N, int kmaxK, int kmaxN, const int *skip, cudaStream_t st);
+// C (P x N) = A^T B with A K x P, B K x N
+template <typename T>
+bool launch_ts_tn(int P, int K, const T *A, int64_t lda, const T *B, int64_t ldb, T *C, int64_t ldc,
+                  const int *kdyn_N, int kmaxN, cudaStream_t st);
+// Gram X^T X (k = *kdyn) as partial slices of kmax x kmax; returns their
+// number (-1: not aligned, nothing launched); skip: nothing when *skip is set
+template <typename T>
+int launch_ts_gram(int rows, const T *X, int64_t ldx, T *partial, const int *kdyn, int kmax, const int *skip,
+                   cudaStream_t st);
+
 // small dense kernels (one CTA)
 // Cholesky pass of CholeskyQR: R = chol(X^T X) from row-split partial Gram
 // matrices; well_out / skip_in implement the skip of a second pass
 template <typename T>
 void launch_chol(const T *partialG, int splits, int kmax, const int *kdyn, T *R, T *Rinv, const T *Rprev, T *Rtot,
-                 int ldr, int *well_out, const int *skip_in, cudaStream_t st);
-// ctrl (optional): skip rotations that cannot change SVT_{ctrl->theta_L}
+                 int ldr, int *well_out, const int *skip_in, cudaStream_t st, int *stats = nullptr);
+// ctrl (optional): skip rotations that cannot change SVT_{ctrl->theta_L};
+// stats (optional): calls and sweeps are added to stats[0], stats[1];
+// Us, svt (optional): the SVT of launch_svt_small fused into the epilogue
 template <typename T>
 void launch_jacobi(const T *Rz, int ldr, const int *kdyn, T *Ut, T *Wt, T *sig, int kmax, const Ctrl *ctrl,
-                   cudaStream_t st);
+                   cudaStream_t st, int *stats = nullptr, T *Us = nullptr, Ctrl *svt = nullptr);
 template <typename T>
 void launch_svt_small(const T *Ut, const T *sig, int ldr, Ctrl *ctrl, T *Us, double *sig64, cudaStream_t st);
 // all_cols = 1: fill columns [0, ctrl->k); else columns [ctrl->k, ctrl->k_next)
@@ -170,6 +197,11 @@ void launch_svt_small(const T *Ut, const T *sig, int ldr, Ctrl *ctrl, T *Us, dou
 template <typename T>
 void launch_fill_random(T *Omega, int64_t ldo, int rows, const Ctrl *ctrl, int all_cols, const T *sig, int kmax,
                         uint64_t salt, cudaStream_t st);
+// launch_fill_random (columns [k, k_next) and zero-sigma columns of Omega) and
+// launch_prolong (B = R Omega for the columns c < r_new) in one launch
+template <typename T>
+void launch_fill_prolong(T *Omega, int64_t ldo, int rows_o, const Ctrl *ctrl, const T *sig, int kmax, uint64_t salt,
+                         int n, T *B, int64_t ldb, const TransferDev<T> &tr, cudaStream_t st);
 int small_kmax_f32();
 int small_kmax_f64();
 

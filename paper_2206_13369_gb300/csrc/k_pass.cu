@@ -395,6 +395,186 @@ __global__ void sum_partials_kernel(const double *partial, int nblocks, int nslo
     }
 }
 
+// ---------------------------------------------------------------------------
+// fine-level step pass, fp32, 128 x 128 tiles
+// ---------------------------------------------------------------------------
+// The fine pass is a K = r_k + r_{k-1} contraction (the Lhat tile from the
+// factors) with an elementwise epilogue.  With 64 x 64 tiles and 4 x 4
+// register tiles the contraction is bound by shared-memory loads; here each
+// thread holds an 8 x 8 tile (four 16-byte shared loads feed 64 FMAs; its
+// columns are 4 tx .. 4 tx + 3 and 64 + 4 tx .. 64 + 4 tx + 3, so neighbouring
+// threads read neighbouring 16-byte chunks, in shared and in global memory), the
+// next K chunk of A and B is fetched into registers (16-byte loads) while the
+// current one is multiplied, and the shared staging rows are padded so the
+// transposed stores do not conflict.  Requires 16-byte aligned operands and
+// leading dimensions that are multiples of 4 (checked by the launcher).
+constexpr int FBM = 128, FBN = 128, FKC = 8, FNT = 256, FPAD = 4;
+
+struct FineSmem {
+    float As[FKC][FBM + FPAD];
+    float Bs[FKC][FBN + FPAD];
+};
+
+__global__ void __launch_bounds__(FNT, 2) pass_fine_f32_kernel(PassArgs<float> a)
+{
+    __shared__ __align__(16) FineSmem sm;
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const int cb = blockIdx.x * FBN, rb = blockIdx.y * FBM;
+    const int m = a.m, n = a.n;
+    const Ctrl &C = *a.ctrl;
+    const float beta = (float)C.beta;
+    const float coef_k = (float)(1.0 + C.beta), coef_p = (float)(-C.beta);
+    const int rk = a.rk ? *a.rk : 0;
+    const int rp = (a.rp && coef_p != 0.f) ? *a.rp : 0;
+    const int ck = (rk + FKC - 1) / FKC, cp = (rp + FKC - 1) / FKC, nchunk = ck + cp;
+
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) acc[i][j] = 0.f;
+
+    // staging: thread t loads 4 consecutive K values of row t/2 of the A and
+    // the B chunk (columns (t%2)*4 .. +3 of the chunk)
+    const int srow = t >> 1, skk = (t & 1) * 4;
+    float4 ra, rb4;
+    auto fetch = [&](int ch) {
+        const bool second = ch >= ck;
+        const float *A = second ? a.Ap : a.Ak;
+        const float *B = second ? a.Bp : a.Bk;
+        const int64_t lda = second ? a.ldfap : a.ldfa, ldb = second ? a.ldfbp : a.ldfb;
+        const int r = second ? rp : rk;
+        const float coef = second ? coef_p : coef_k;
+        const int c0 = (second ? ch - ck : ch) * FKC + skk;
+        const int gr = rb + srow, gc = cb + srow;
+        float av[4] = {0.f, 0.f, 0.f, 0.f}, bv[4] = {0.f, 0.f, 0.f, 0.f};
+        if (c0 + 3 < r) {
+            if (gr < m) {
+                const float4 q = *reinterpret_cast<const float4 *>(A + (int64_t)gr * lda + c0);
+                av[0] = q.x; av[1] = q.y; av[2] = q.z; av[3] = q.w;
+            }
+            if (gc < n) {
+                const float4 q = *reinterpret_cast<const float4 *>(B + (int64_t)gc * ldb + c0);
+                bv[0] = q.x; bv[1] = q.y; bv[2] = q.z; bv[3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (c0 + u < r) {
+                    if (gr < m) av[u] = A[(int64_t)gr * lda + c0 + u];
+                    if (gc < n) bv[u] = B[(int64_t)gc * ldb + c0 + u];
+                }
+            }
+        }
+        ra = make_float4(av[0] * coef, av[1] * coef, av[2] * coef, av[3] * coef);
+        rb4 = make_float4(bv[0], bv[1], bv[2], bv[3]);
+    };
+    auto stage = [&]() {
+        sm.As[skk + 0][srow] = ra.x;
+        sm.As[skk + 1][srow] = ra.y;
+        sm.As[skk + 2][srow] = ra.z;
+        sm.As[skk + 3][srow] = ra.w;
+        sm.Bs[skk + 0][srow] = rb4.x;
+        sm.Bs[skk + 1][srow] = rb4.y;
+        sm.Bs[skk + 2][srow] = rb4.z;
+        sm.Bs[skk + 3][srow] = rb4.w;
+    };
+    if (nchunk > 0) {
+        fetch(0);
+        stage();
+    }
+    __syncthreads();
+    for (int ch = 0; ch < nchunk; ch++) {
+        const bool more = ch + 1 < nchunk;
+        if (more) fetch(ch + 1);
+#pragma unroll
+        for (int kk = 0; kk < FKC; kk++) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&sm.As[kk][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&sm.As[kk][ty * 8 + 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&sm.Bs[kk][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&sm.Bs[kk][64 + tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+#pragma unroll
+                for (int j = 0; j < 8; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+        if (more) stage();
+        __syncthreads();
+    }
+
+    // epilogue: rows rb + ty*8 + i; columns cb + 4 tx .. +3 (h = 0) and
+    // cb + 64 + 4 tx .. +3 (h = 1), each group inside one mask word
+    const float tau = (float)C.tau, thS = (float)C.theta_S;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const int row = rb + ty * 8 + i;
+        if (row >= m) continue;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int c4 = cb + 64 * h + tx * 4;
+            if (c4 >= n) continue;
+            const bool full = c4 + 3 < n;
+            uint32_t bits = 0xffffffffu;
+            if (a.Q) bits = a.Q[(int64_t)row * a.ldq + (c4 >> 5)] >> (c4 & 31);
+            float d[4], sk[4], sp[4], so[4], mo[4];
+            if (full) {
+                const float4 qd = *reinterpret_cast<const float4 *>(a.D + (int64_t)row * a.ldd + c4);
+                const float4 qs = *reinterpret_cast<const float4 *>(a.Sk + (int64_t)row * a.lds + c4);
+                d[0] = qd.x; d[1] = qd.y; d[2] = qd.z; d[3] = qd.w;
+                sk[0] = qs.x; sk[1] = qs.y; sk[2] = qs.z; sk[3] = qs.w;
+                if (a.Sp && beta != 0.f) {
+                    const float4 qp = *reinterpret_cast<const float4 *>(a.Sp + (int64_t)row * a.lds + c4);
+                    sp[0] = qp.x; sp[1] = qp.y; sp[2] = qp.z; sp[3] = qp.w;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; j++) sp[j] = sk[j];
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const bool in = c4 + j < n;
+                    d[j] = in ? a.D[(int64_t)row * a.ldd + c4 + j] : 0.f;
+                    sk[j] = in ? a.Sk[(int64_t)row * a.lds + c4 + j] : 0.f;
+                    sp[j] = (in && a.Sp && beta != 0.f) ? a.Sp[(int64_t)row * a.lds + c4 + j] : sk[j];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const bool obs = (bits >> j) & 1u;
+                const float sh = sk[j] + beta * (sk[j] - sp[j]);
+                const float l = acc[i][4 * h + j];
+                const float g = obs ? ((l - d[j]) + sh) : 0.f;
+                so[j] = shrink(sh - tau * g, thS);
+                mo[j] = l - tau * g;
+            }
+            if (full) {
+                *reinterpret_cast<float4 *>(a.Sout + (int64_t)row * a.ldso + c4) = make_float4(so[0], so[1], so[2], so[3]);
+                *reinterpret_cast<float4 *>(a.M + (int64_t)row * a.ldm + c4) = make_float4(mo[0], mo[1], mo[2], mo[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    if (c4 + j < n) {
+                        a.Sout[(int64_t)row * a.ldso + c4 + j] = so[j];
+                        a.M[(int64_t)row * a.ldm + c4 + j] = mo[j];
+                    }
+                }
+            }
+        }
+    }
+}
+
+bool fine_f32_ok(const PassArgs<float> &a)
+{
+    auto al = [](const void *p, int64_t ld) {
+        return p == nullptr || ((reinterpret_cast<uintptr_t>(p) % 16 == 0) && (ld % 4 == 0));
+    };
+    return a.Sk != nullptr && al(a.D, a.ldd) && al(a.Sk, a.lds) && al(a.Sp, a.lds) && al(a.Sout, a.ldso) &&
+           al(a.M, a.ldm) && al(a.Ak, a.ldfa) && al(a.Bk, a.ldfb) && al(a.Ap, a.ldfap) && al(a.Bp, a.ldfbp);
+}
+
 }  // namespace
 
 template <typename T>
@@ -402,6 +582,14 @@ int launch_step_pass(const PassArgs<T> &a, bool coarse, cudaStream_t st)
 {
     if (coarse && a.GH != nullptr) return launch_mode<T, STEP_COARSE_G>(a, st);
     if (coarse) return launch_mode<T, STEP_COARSE>(a, st);
+    if constexpr (sizeof(T) == 4) {
+        if (fine_f32_ok(a)) {
+            dim3 grid((a.n + FBN - 1) / FBN, (a.m + FBM - 1) / FBM);
+            CPCP_COUNT_LAUNCH();
+            pass_fine_f32_kernel<<<grid, FNT, 0, st>>>(a);
+            return grid.x * grid.y;
+        }
+    }
     return launch_mode<T, STEP_FINE>(a, st);
 }
 

@@ -39,11 +39,25 @@ __device__ __forceinline__ double eps_of<double>()
     return DBL_EPSILON;
 }
 
+// 1/sqrt(x) for a threshold test (a few units of rounding are irrelevant)
+__device__ __forceinline__ float rsqrt_of(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_of(double x) { return rsqrt(x); }
+// 1/sqrt(y) for y in [1, 2]: the hardware estimate and one Newton step
+// c <- c (3 - y c^2) / 2, which brings it to about one unit of rounding
+__device__ __forceinline__ float rsqrt_nr(float y)
+{
+    float c = rsqrtf(y);
+    return c * fmaf(-0.5f * y, c * c, 1.5f);
+}
+__device__ __forceinline__ double rsqrt_nr(double y) { return 1.0 / sqrt(y); }
+// quotient for a rotation angle (denominator of magnitude at least |x|)
+__device__ __forceinline__ float fast_div(float x, float y) { return __fdividef(x, y); }
+__device__ __forceinline__ double fast_div(double x, double y) { return x / y; }
+
 // ---------------------------------------------------------------------------
 // Cholesky pass of CholeskyQR
 // ---------------------------------------------------------------------------
 constexpr int CHOL_NT = 512;
-constexpr int PB = 16;  // panel / block width of the blocked factorisation and inverse
 
 // Gram reduction + equilibrated Cholesky R = chol(X^T X) (upper) and its
 // inverse.  well_out (optional): set to 1 when the equilibrated Gram matrix is
@@ -52,20 +66,209 @@ constexpr int PB = 16;  // panel / block width of the blocked factorisation and 
 // units of rounding and a second pass can be skipped.  skip_in (optional):
 // when *skip_in is set this pass is not needed; R = I, Rinv = I, Rtot = Rprev.
 // Rtot = R Rprev when Rprev is given.  A column whose pivot is not positive is
-// dropped: zero row in R, zero column in Rinv (zero column of Q).
+// dropped: zero row in R, zero column in Rinv (zero column of Q).  stats
+// (optional) counts the factorisations run.
+//
+// The factorisation is right-looking: step j eliminates column j from the
+// trailing upper triangle of G with the column operation E_j = I - e_j u_j^T
+// (u_j = G[j][j+1:] / G[j][j]) and, in the same step, applies E_j to W
+// (W = E_0 E_1 ... E_j).  At the end G = U^T P^2 U with U = W^{-1} unit upper
+// triangular and P the pivots' square roots, so R = P U (row j of R is
+// G[j][j:] / P_j) and R^{-1} = W P^{-1}.
+//
+// G and W live together in registers as one k x k array S: G in the upper
+// triangle (with the pivots on the diagonal) and W^T in the strict lower one
+// (S[x][y] = W[y][x] for x > y).  Thread (tr, tc) = (tid / 32, tid % 32) owns
+// rows tr + 16 a and columns tc + 32 b.  Step j updates the positions (x, y)
+// with x > j and either y <= j (W) or y >= x (G), in both cases by
+// S[x][y] -= S[j][x] S'[j][y] / S[j][j] with S'[j][j] = 1: the step reads the
+// single row j of S, which its owners publish into a double-buffered shared
+// row at the end of step j - 1, so a step costs one barrier.  (A blocked
+// variant with 16-column panels, one warp per diagonal block, measured about
+// twice as slow at k = 60: its serial diagonal-block and triangular-solve
+// chains leave the SM idle behind the barriers.)
+template <typename T>
+__device__ __forceinline__ T chol_gram_entry(const T *__restrict__ partial, int splits, int64_t slice, int kmax, int p,
+                                             int c)
+{
+    // row-split partial sums in a fixed order (four independent chains keep
+    // several loads in flight)
+    const T *src = partial + (int64_t)p * kmax + c;
+    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+    int q = 0;
+    for (; q + 3 < splits; q += 4) {
+        s0 += src[q * slice];
+        s1 += src[(q + 1) * slice];
+        s2 += src[(q + 2) * slice];
+        s3 += src[(q + 3) * slice];
+    }
+    for (; q < splits; q++) s0 += src[q * slice];
+    return (s0 + s1) + (s2 + s3);
+}
+
+template <typename T, int RA, int CB>
+__device__ __forceinline__ void chol_body(const T *__restrict__ partial, int splits, int kmax, int k,
+                                          T *__restrict__ R, T *__restrict__ Rinv, const T *__restrict__ Rprev,
+                                          T *__restrict__ Rtot, int ldr, int *well_out, T *sm, double *red)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tr = warp, tc = lane;  // CHOL_NT / 32 = 16 row groups x 32 columns
+    T *d = sm;              // column scales of the equilibration
+    T *piv = d + k;         // square roots of the pivots (0 = dropped)
+    T *rows2 = piv + k;     // 2 x k: row j of S (double buffered)
+    const int64_t slice = (int64_t)kmax * kmax;
+
+    for (int c = tid; c < k; c += CHOL_NT) {
+        const T g = chol_gram_entry(partial, splits, slice, kmax, c, c);
+        d[c] = (g > T(0) && isfinite(g)) ? sqrt(g) : T(0);
+    }
+    __syncthreads();
+
+    T S[RA][CB];
+    double defect = 0.0;
+#pragma unroll
+    for (int a = 0; a < RA; a++) {
+        const int x = tr + 16 * a;
+#pragma unroll
+        for (int b = 0; b < CB; b++) {
+            const int y = tc + 32 * b;
+            T v = T(0);
+            if (x < k && y < k && x <= y) {
+                const T dx = d[x], dy = d[y];
+                v = (dx > T(0) && dy > T(0)) ? chol_gram_entry(partial, splits, slice, kmax, x, y) / dx / dy : T(0);
+                const T ev = v - (x == y ? T(1) : T(0));
+                defect += (x == y ? 1.0 : 2.0) * (double)(ev * ev);  // both triangles of the symmetric matrix
+                if (x == 0) rows2[y] = v;                            // row 0 of S for step 0
+            }
+            S[a][b] = v;  // lower triangle: W^T = 0 off the diagonal
+        }
+    }
+    defect = warp_sum(defect);
+    if (lane == 0) red[warp] = defect;
+    __syncthreads();
+    if (tid == 0 && well_out != nullptr) {
+        double tot = 0.0;
+        for (int q = 0; q < CHOL_NT / 32; q++) tot += red[q];
+        *well_out = tot <= 0.25 ? 1 : 0;
+    }
+
+    // Only a non-positive (or denormal) pivot drops a column; a tiny positive
+    // pivot gives a noise direction that the next CholeskyQR pass cleans up.
+    const T tol = eps_of<T>() * eps_of<T>();
+    for (int j = 0; j < k; j++) {
+        const T *rw = rows2 + (j & 1) * k;
+        T *rn = rows2 + ((j + 1) & 1) * k;
+        const T pj = rw[j];
+        const bool dj = !(pj > tol);
+        const T inv = dj ? T(0) : T(1) / pj;
+        T rx[RA], cy[CB];
+#pragma unroll
+        for (int a = 0; a < RA; a++) {
+            const int x = tr + 16 * a;
+            rx[a] = (x > j && x < k) ? rw[x] : T(0);  // G[j][x]
+        }
+#pragma unroll
+        for (int b = 0; b < CB; b++) {
+            const int y = tc + 32 * b;
+            cy[b] = y == j ? T(1) : (y < k ? rw[y] : T(0));  // G[j][y] (y > j) or W[y][j] (y < j)
+        }
+#pragma unroll
+        for (int a = 0; a < RA; a++) {
+            const int x = tr + 16 * a;
+            if (x <= j || x >= k) continue;
+            const T gxi = rx[a] * inv;
+#pragma unroll
+            for (int b = 0; b < CB; b++) {
+                const int y = tc + 32 * b;
+                if (y >= k) continue;
+                if (y <= j) {
+                    const T wyj = cy[b] * inv;  // W[y][x] -= (W[y][j] / p_j) G[j][x]
+                    S[a][b] -= wyj * rx[a];
+                } else if (y >= x) {
+                    S[a][b] -= gxi * cy[b];  // G[x][y] -= (G[j][x] / p_j) G[j][y]
+                }
+            }
+            if (x == j + 1) {
+#pragma unroll
+                for (int b = 0; b < CB; b++) {
+                    const int y = tc + 32 * b;
+                    if (y < k) rn[y] = S[a][b];
+                }
+            }
+        }
+        if (tid == 0) piv[j] = dj ? T(0) : sqrt(pj);
+        __syncthreads();
+    }
+
+    // undo the equilibration: R = Rt D with Rt = P U (row i of Rt is
+    // G[i][i:] / P_i), R^{-1} = D^{-1} Rt^{-1} = D^{-1} W P^{-1} (dropped columns
+    // zero); then Rtot = R Rprev
+    T *Rs = rows2 + 2 * k;      // k x (k + 1): R (upper), for Rtot
+    T *Ps = Rs + k * (k + 1);   // k x (k + 1): Rprev
+    const int ld = k + 1;
+#pragma unroll
+    for (int a = 0; a < RA; a++) {
+        const int x = tr + 16 * a;
+        if (x >= k) continue;
+#pragma unroll
+        for (int b = 0; b < CB; b++) {
+            const int y = tc + 32 * b;
+            if (y >= k) continue;
+            if (x < y) {
+                const T p_x = piv[x], rx_ = p_x > T(0) ? T(1) / p_x : T(0);
+                const T rv = S[a][b] * rx_ * d[y];
+                R[(int64_t)x * ldr + y] = rv;
+                R[(int64_t)y * ldr + x] = T(0);
+                Rinv[(int64_t)y * ldr + x] = T(0);
+                if (Rprev != nullptr) {
+                    Rs[x * ld + y] = rv;
+                    Rtot[(int64_t)y * ldr + x] = T(0);
+                }
+            } else if (x == y) {
+                const T p_x = piv[x];
+                const T rv = p_x * d[x];
+                R[(int64_t)x * ldr + x] = rv;
+                Rinv[(int64_t)x * ldr + x] = (p_x > T(0) && d[x] > T(0)) ? T(1) / p_x / d[x] : T(0);
+                if (Rprev != nullptr) Rs[x * ld + x] = rv;
+            } else {
+                // S[x][y] = W[y][x]: entry (y, x) of R^{-1} = W[y][x] / P_x / d_y
+                Rinv[(int64_t)y * ldr + x] = (piv[x] > T(0) && d[y] > T(0)) ? S[a][b] / piv[x] / d[y] : T(0);
+            }
+        }
+    }
+    if (Rprev == nullptr) return;
+    for (int idx = tid; idx < k * k; idx += CHOL_NT) {
+        const int i = idx / k, c = idx - (idx / k) * k;
+        Ps[i * ld + c] = Rprev[(int64_t)i * ldr + c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < RA; a++) {
+        const int x = tr + 16 * a;
+        if (x >= k) continue;
+#pragma unroll
+        for (int b = 0; b < CB; b++) {
+            const int y = tc + 32 * b;
+            if (y >= k || y < x) continue;
+            T s = T(0);
+            for (int p = x; p <= y; p++) s = fma(Rs[x * ld + p], Ps[p * ld + y], s);
+            Rtot[(int64_t)x * ldr + y] = s;
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(CHOL_NT) chol_kernel(const T *__restrict__ partial, int splits, int kmax,
                                                        const int *kdyn, T *__restrict__ R, T *__restrict__ Rinv,
                                                        const T *__restrict__ Rprev, T *__restrict__ Rtot, int ldr,
-                                                       int *well_out, const int *skip_in)
+                                                       int *well_out, const int *skip_in, int *stats)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double red[CHOL_NT / 32];
     const int k = *kdyn;
-    const int kp = (k + PB - 1) / PB * PB;
-    const int ld = kp + 1;
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int tid = threadIdx.x;
     if (skip_in != nullptr && *skip_in) {
-        for (int idx = tid; idx < k * k; idx += nt) {
+        for (int idx = tid; idx < k * k; idx += CHOL_NT) {
             int i = idx / k, c = idx % k;
             R[(int64_t)i * ldr + c] = (i == c) ? T(1) : T(0);
             Rinv[(int64_t)i * ldr + c] = (i == c) ? T(1) : T(0);
@@ -73,208 +276,43 @@ __global__ void __launch_bounds__(CHOL_NT) chol_kernel(const T *__restrict__ par
         }
         return;
     }
-    T *G = reinterpret_cast<T *>(smraw);  // kp x ld: equilibrated Gram -> upper factor
-    T *Ri = G + kp * ld;                  // kp x ld: inverse of the factor
-    T *P = Ri + kp * ld;                  // k x ld: Rprev
-    T *Tb = P + k * ld;                   // temporary blocks of the inverse
-    T *d = Tb + (kp / PB) * PB * PB;      // column scales
-    T *diag = d + kp;                     // diagonal of the factor
-    int *drop = reinterpret_cast<int *>(diag + kp);
-    __shared__ double red[CHOL_NT / 32];
-
-    // Gram matrix from the row-split partial sums, in a fixed order (four
-    // independent chains keep several loads in flight); padding = identity
-    const int64_t slice = (int64_t)kmax * kmax;
-    for (int idx = tid; idx < kp * kp; idx += nt) {
-        int p = idx / kp, c = idx % kp;
-        T v = (p == c) ? T(1) : T(0);
-        if (p < k && c < k) {
-            const T *src = partial + (int64_t)p * kmax + c;
-            T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-            int q = 0;
-            for (; q + 3 < splits; q += 4) {
-                s0 += src[q * slice];
-                s1 += src[(q + 1) * slice];
-                s2 += src[(q + 2) * slice];
-                s3 += src[(q + 3) * slice];
-            }
-            for (; q < splits; q++) s0 += src[q * slice];
-            v = (s0 + s1) + (s2 + s3);
-            if (Rprev != nullptr) P[p * ld + c] = Rprev[(int64_t)p * ldr + c];
-        }
-        G[p * ld + c] = v;
-    }
-    __syncthreads();
-    for (int p = tid; p < kp; p += nt) {
-        T g = G[p * ld + p];
-        d[p] = (p < k && g > T(0) && isfinite(g)) ? sqrt(g) : T(0);
-    }
-    __syncthreads();
-    double defect = 0.0;
-    for (int idx = tid; idx < k * k; idx += nt) {
-        int p = idx / k, c = idx % k;
-        T dp = d[p], dc = d[c];
-        T v = (dp > T(0) && dc > T(0)) ? G[p * ld + c] / dp / dc : T(0);
-        G[p * ld + c] = v;
-        T e = v - (p == c ? T(1) : T(0));
-        defect += (double)(e * e);
-    }
-    defect = warp_sum(defect);
-    if (lane == 0) red[warp] = defect;
-    __syncthreads();
-    if (tid == 0 && well_out != nullptr) {
-        double tot = 0.0;
-        for (int w = 0; w < nw; w++) tot += red[w];
-        *well_out = tot <= 0.25 ? 1 : 0;
-    }
-
-    // blocked right-looking Cholesky (upper): per panel of PB columns, warp 0
-    // factors the diagonal block, the panel rows right of it are solved
-    // (one thread per column), and the trailing matrix gets a rank-PB update.
-    // Only a non-positive (or denormal) pivot drops a column; a tiny positive
-    // pivot gives a noise direction that the next CholeskyQR pass cleans up.
-    const T tol = eps_of<T>() * eps_of<T>();
-    for (int p0 = 0; p0 < kp; p0 += PB) {
-        if (warp == 0) {
-            for (int jj = 0; jj < PB; jj++) {
-                const int j = p0 + jj;
-                const T piv = G[j * ld + j];
-                const bool dj = !(piv > tol);
-                const T sq = dj ? T(0) : sqrt(piv);
-                const T inv = dj ? T(0) : T(1) / sq;
-                __syncwarp();
-                if (lane > jj && lane < PB) G[j * ld + p0 + lane] *= inv;
-                if (lane == 0) {
-                    diag[j] = sq;
-                    drop[j] = dj;
-                }
-                __syncwarp();
-                // rank-1 update of the rest of the diagonal block; lane = column
-                if (lane > jj && lane < PB) {
-                    const int b = p0 + lane;
-                    const T gjb = G[j * ld + b];
-                    for (int a = j + 1; a <= b; a++) G[a * ld + b] -= G[j * ld + a] * gjb;
-                }
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        // panel rows: solve Rd^T Y = G[p0:p0+PB, c] for the columns c right of the block
-        for (int c = p0 + PB + tid; c < kp; c += nt) {
-            for (int i = 0; i < PB; i++) {
-                const int row = p0 + i;
-                T s = G[row * ld + c];
-                for (int l = 0; l < i; l++) s -= G[(p0 + l) * ld + row] * G[(p0 + l) * ld + c];
-                G[row * ld + c] = drop[row] ? T(0) : s / diag[row];
-            }
-        }
-        __syncthreads();
-        // trailing update, upper triangle: warp per row, lanes over columns
-        for (int a = p0 + PB + warp; a < kp; a += nw) {
-            T gl[PB];
-#pragma unroll
-            for (int l = 0; l < PB; l++) gl[l] = G[(p0 + l) * ld + a];
-            for (int b = a + lane; b < kp; b += 32) {
-                T s = T(0);
-#pragma unroll
-                for (int l = 0; l < PB; l++) s = fma(gl[l], G[(p0 + l) * ld + b], s);
-                G[a * ld + b] -= s;
-            }
-        }
-        __syncthreads();
-    }
-
-    // blocked inverse of Rh (the factor with dropped diagonals set to one):
-    // diagonal blocks by back substitution (one thread per column), then the
-    // block superdiagonals d = 1, 2, ...: X_ij = -X_ii (sum_l Rh_il X_lj)
-    const int nb = kp / PB;
-    auto rh = [&](int i, int c) -> T {
-        if (c < i) return T(0);
-        if (c == i) return drop[i] ? T(1) : diag[i];
-        return G[i * ld + c];
-    };
-    for (int t = tid; t < nb * PB; t += nt) {
-        const int b = t / PB, cc = t % PB, base = b * PB;
-        for (int i = PB - 1; i >= 0; i--) {
-            T v = (i == cc) ? T(1) : T(0);
-            if (i < cc) {
-                for (int p = i + 1; p <= cc; p++) v -= rh(base + i, base + p) * Ri[(base + p) * ld + base + cc];
-            }
-            Ri[(base + i) * ld + base + cc] = (i <= cc) ? v / rh(base + i, base + i) : T(0);
-        }
-    }
-    for (int idx = tid; idx < kp * kp; idx += nt) {  // below the block diagonal
-        int i = idx / kp, c = idx % kp;
-        if (i / PB > c / PB) Ri[i * ld + c] = T(0);
-    }
-    __syncthreads();
-    for (int dd = 1; dd < nb; dd++) {
-        const int nblk = nb - dd;
-        for (int e = tid; e < nblk * PB * PB; e += nt) {
-            const int bi = e / (PB * PB), rr = (e / PB) % PB, cc = e % PB;
-            const int i0 = bi * PB, j0 = (bi + dd) * PB;
-            T s = T(0);
-            for (int l = i0 + PB; l < j0 + PB; l++) s = fma(rh(i0 + rr, l), Ri[l * ld + j0 + cc], s);
-            Tb[e] = s;
-        }
-        __syncthreads();
-        for (int e = tid; e < nblk * PB * PB; e += nt) {
-            const int bi = e / (PB * PB), rr = (e / PB) % PB, cc = e % PB;
-            const int i0 = bi * PB, j0 = (bi + dd) * PB;
-            T s = T(0);
-            for (int p = rr; p < PB; p++) s = fma(Ri[(i0 + rr) * ld + i0 + p], Tb[bi * PB * PB + p * PB + cc], s);
-            Ri[(i0 + rr) * ld + j0 + cc] = -s;
-        }
-        __syncthreads();
-    }
-
-    // undo the equilibration: R = Rt D, R^{-1} = D^{-1} Rt^{-1} (dropped
-    // columns zero); Rtot = R Rprev
-    for (int idx = tid; idx < k * k; idx += nt) {
-        int i = idx / k, c = idx % k;
-        T rv = T(0), iv = T(0);
-        if (c >= i && !drop[i]) rv = (c == i ? diag[i] : G[i * ld + c]) * d[c];
-        if (c >= i && !drop[c] && d[i] > T(0)) iv = Ri[i * ld + c] / d[i];
-        R[(int64_t)i * ldr + c] = rv;
-        Rinv[(int64_t)i * ldr + c] = iv;
-        if (Rprev != nullptr) {
-            T s = T(0);
-            if (c >= i && !drop[i])
-                for (int p = i; p <= c; p++) s = fma((p == i ? diag[i] : G[i * ld + p]) * d[p], P[p * ld + c], s);
-            Rtot[(int64_t)i * ldr + c] = s;
-        }
-    }
+    if (stats != nullptr && tid == 0) atomicAdd(stats, 1);
+    T *sm = reinterpret_cast<T *>(smraw);
+    // rows per thread group and columns per lane: 4 x 2 covers k <= 64, 8 x 4 covers k <= 128
+    if (k <= 64)
+        chol_body<T, 4, 2>(partial, splits, kmax, k, R, Rinv, Rprev, Rtot, ldr, well_out, sm, red);
+    else
+        chol_body<T, 8, 4>(partial, splits, kmax, k, R, Rinv, Rprev, Rtot, ldr, well_out, sm, red);
 }
 
 // ---------------------------------------------------------------------------
 // one-sided Jacobi SVD of C = Rz^T (k x k): C = Ut diag(sig) Wt^T
 // ---------------------------------------------------------------------------
-constexpr int JAC_NT = 256, JAC_TPP = 8;
+constexpr int JAC_NT = 512;
 
-// When ctrl is given, pairs whose squared norms sum to at most theta_L^2 are
-// not rotated: rotations preserve a + b, so neither column can end above the
-// SVT threshold and their mixing cannot change the thresholded result.
-template <typename T>
-__global__ void __launch_bounds__(JAC_NT) jacobi_kernel(const T *__restrict__ Rz, int ldr, const int *kdyn,
-                                                        T *__restrict__ Ut, T *__restrict__ Wt, T *__restrict__ sig,
-                                                        const Ctrl *ctrl)
+__host__ __device__ constexpr int jac_ld(int k) { return (k + 31) / 32 * 32 + 8; }
+
+// Eight consecutive lanes share one column pair (64 pairs per round at most,
+// k <= 128); each lane keeps its EL elements of the two columns in registers
+// between the dot product and the rotation.
+template <typename T, int EL>
+__device__ __forceinline__ void jacobi_body(const T *__restrict__ Rz, int ldr, int k, T *__restrict__ Ut,
+                                            T *__restrict__ Wt, T *__restrict__ sig, const Ctrl *ctrl, int *stats,
+                                            T *__restrict__ Us, Ctrl *svt, T *sm, T *wmax, T *amax_p)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const int k = *kdyn;
-    const int ld = k + 1;
+    constexpr int TPP = 8;
+    // columns 8 banks apart (ld = 8 mod 32): the four pairs a warp serves
+    // read 32 distinct banks
+    const int ld = jac_ld(k);
     const int N = k + (k & 1);
-    T *X = reinterpret_cast<T *>(smraw);  // X[c * ld + i]: column c of C
+    T *X = sm;          // X[c * ld + i]: column c of C
     T *V = X + k * ld;
-    T *sv = V + k * ld;                   // squared column norms, then singular values
+    T *sv = V + k * ld; // squared column norms, then singular values
     int *pos = reinterpret_cast<int *>(sv + k);
-    __shared__ int rot_count;
-    __shared__ unsigned long long gmax_bits;  // largest |g|/sqrt(ab) rotated in the sweep
-    __shared__ T amax;
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, nt = JAC_NT, lane = tid & 31, warp = tid >> 5;
     const T th2 = ctrl != nullptr ? T(ctrl->theta_L) * T(ctrl->theta_L) : T(-1);
-    // JAC_TPP consecutive lanes share one column pair
-    const int slot = tid / JAC_TPP, sub = tid % JAC_TPP, nslot = JAC_NT / JAC_TPP;
-    const unsigned gmask = 0xFFu << (lane & ~(JAC_TPP - 1));
+    const int slot = tid / TPP, sub = tid % TPP, nslot = JAC_NT / TPP;
+    const unsigned gmask = 0xFFu << (lane & ~(TPP - 1));
 
     for (int idx = tid; idx < k * k; idx += nt) {
         int c = idx / k, i = idx % k;
@@ -284,8 +322,8 @@ __global__ void __launch_bounds__(JAC_NT) jacobi_kernel(const T *__restrict__ Rz
     __syncthreads();
 
     // a pair is rotated when |x_p . x_q| exceeds the rounding bound of the
-    // group dot product (k/8 sequential terms per lane + a 3-level tree)
-    const T tol = T(2) * T((k + JAC_TPP - 1) / JAC_TPP + 4) * eps_of<T>();
+    // group dot product (k/8 terms per lane in two chains + a 3-level tree)
+    const T tol = T(2) * T((k + TPP - 1) / TPP + 4) * eps_of<T>();
     // columns whose norm is below the rounding noise of the largest one carry
     // no information; rotating them against large columns only moves noise
     const T negl = (T(4) * T(k) * eps_of<T>()) * (T(4) * T(k) * eps_of<T>());
@@ -293,79 +331,129 @@ __global__ void __launch_bounds__(JAC_NT) jacobi_kernel(const T *__restrict__ Rz
     // off-orthogonality of order delta^2 (Jacobi converges quadratically), so
     // a further sweep would only make rounding-level rotations
     const T stop = min(sqrt(tol), T(1e-4));
+    int sweeps = 0;
     for (int sweep = 0; sweep < 30; sweep++) {
+        sweeps++;
         // exact squared norms at the start of each sweep; rotations then
         // update them by a' = a - t g, b' = b + t g (Rutishauser)
         for (int c = slot; c < k; c += nslot) {
             T s = T(0);
-            for (int i = sub; i < k; i += JAC_TPP) s = fma(X[c * ld + i], X[c * ld + i], s);
-            for (int o = JAC_TPP / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
+#pragma unroll
+            for (int e = 0; e < EL; e++) {
+                const int i = sub + TPP * e;
+                if (i < k) s = fma(X[c * ld + i], X[c * ld + i], s);
+            }
+#pragma unroll
+            for (int o = TPP / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
             if (sub == 0) sv[c] = s;
         }
-        if (tid == 0) {
-            rot_count = 0;
-            gmax_bits = 0ull;
-        }
+        T mymax = T(0);  // largest rotated |g|/sqrt(ab) of this thread's pairs in the sweep
         __syncthreads();
         if (warp == 0) {
             T v = T(0);
             for (int c = lane; c < k; c += 32) v = max(v, sv[c]);
             for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-            if (lane == 0) amax = v;
+            if (lane == 0) *amax_p = v;
         }
         __syncthreads();
-        const T small = negl * amax;
-        for (int round = 0; round < N - 1; round++) {
-            // round-robin (circle) schedule: slot 0 holds column 0, slot s > 0
-            // holds column 1 + (s - 1 + round) mod (N - 1); slot t meets N-1-t
-            for (int pr = slot; pr < N / 2; pr += nslot) {
-                const int p = pr == 0 ? 0 : 1 + (pr - 1 + round) % (N - 1);
-                const int q = 1 + (N - 2 - pr + round) % (N - 1);
-                if (p >= k || q >= k) continue;
+        const T small = negl * *amax_p;
+        // round-robin (circle) schedule: slot 0 holds column 0, slot s > 0
+        // holds column 1 + (s - 1 + round) mod (N - 1); slot t meets N-1-t.
+        // Every slot holds at most one pair (N / 2 <= 64); p and q advance by
+        // one place per round.
+        const int pr = slot;
+        const bool has_pair = pr < N / 2;
+        int p = pr == 0 ? 0 : 1 + (pr - 1) % (N - 1);
+        int q = has_pair ? 1 + (N - 2 - pr) % (N - 1) : 0;
+        // only the warps that hold pairs take part in the rounds; they meet
+        // at a named barrier of their own
+        const int act = min(JAC_NT, ((N / 2) * TPP + 31) & ~31);
+        for (int round = 0; round < N - 1 && tid < act; round++) {
+            if (has_pair && p < k && q < k) do {
                 T *xp = X + p * ld, *xq = X + q * ld;
-                T g = T(0);
-                for (int i = sub; i < k; i += JAC_TPP) g = fma(xp[i], xq[i], g);
-                for (int o = JAC_TPP / 2; o > 0; o >>= 1) g += __shfl_xor_sync(gmask, g, o);
                 const T a = sv[p], b = sv[q];
-                if (!(a > small) || !(b > small)) continue;
-                if (a + b <= th2) continue;
-                const T rel = fabs(g) / (sqrt(a) * sqrt(b));
-                if (!(rel > tol)) continue;
-                T zeta = (b - a) / (T(2) * g);
-                // t = sign(z) / (|z| + sqrt(1 + z^2)), or 1/(2 z) where z^2 would overflow
-                T az = fabs(zeta);
-                T tt = az > T(1e15) ? T(0.5) / zeta
-                                    : (zeta >= T(0) ? T(1) : T(-1)) / (az + sqrt(T(1) + zeta * zeta));
-                T cs = T(1) / sqrt(T(1) + tt * tt), sn = cs * tt;
+                T u[EL], w[EL];
+#pragma unroll
+                for (int e = 0; e < EL; e++) {
+                    const int i = sub + TPP * e;
+                    u[e] = i < k ? xp[i] : T(0);
+                    w[e] = i < k ? xq[i] : T(0);
+                }
+                T g0 = T(0), g1 = T(0);
+#pragma unroll
+                for (int e = 0; e < EL; e += 2) {
+                    g0 = fma(u[e], w[e], g0);
+                    if (e + 1 < EL) g1 = fma(u[e + 1], w[e + 1], g1);
+                }
+                T g = g0 + g1;
+#pragma unroll
+                for (int o = TPP / 2; o > 0; o >>= 1) g += __shfl_xor_sync(gmask, g, o);
+                if (!(a > small) || !(b > small)) break;
+                if (a + b <= th2) break;
+                const T rel = fabs(g) * rsqrt_of(a) * rsqrt_of(b);
+                if (!(rel > tol)) break;
+                // t = sign(z) / (|z| + sqrt(1 + z^2)) with z = (b - a) / (2 g),
+                // multiplied through by |2 g|; the root is only a rotation
+                // angle, so a rounding-level error in it costs nothing: the
+                // applied rotation is orthogonal through cs and sn below
+                const T e_ = b - a, f = T(2) * g;
+                const T hyp = sqrt(e_ * e_ + f * f);
+                T tt;
+                if (hyp < T(1e37)) {  // finite, and in the fast quotient's range
+                    tt = fast_div(f, e_ + copysign(hyp, e_));
+                } else {
+                    const T zeta = e_ / f, az = fabs(zeta);
+                    tt = az > T(1e15) ? T(0.5) / zeta
+                                      : (zeta >= T(0) ? T(1) : T(-1)) / (az + sqrt(T(1) + zeta * zeta));
+                }
+                const T cs = rsqrt_nr(T(1) + tt * tt), sn = cs * tt;
                 T *vp = V + p * ld, *vq = V + q * ld;
-                for (int i = sub; i < k; i += JAC_TPP) {
-                    T u = xp[i], v = xq[i];
-                    xp[i] = cs * u - sn * v;
-                    xq[i] = sn * u + cs * v;
-                    u = vp[i];
-                    v = vq[i];
-                    vp[i] = cs * u - sn * v;
-                    vq[i] = sn * u + cs * v;
+#pragma unroll
+                for (int e = 0; e < EL; e++) {
+                    const int i = sub + TPP * e;
+                    if (i < k) {
+                        xp[i] = cs * u[e] - sn * w[e];
+                        xq[i] = sn * u[e] + cs * w[e];
+                        const T vu = vp[i], vw = vq[i];
+                        vp[i] = cs * vu - sn * vw;
+                        vq[i] = sn * vu + cs * vw;
+                    }
                 }
                 __syncwarp(gmask);
                 if (sub == 0) {
                     sv[p] = max(a - tt * g, T(0));
                     sv[q] = b + tt * g;
-                    atomicAdd(&rot_count, 1);
-                    atomicMax(&gmax_bits, (unsigned long long)__double_as_longlong((double)rel));
                 }
-            }
-            __syncthreads();
+                mymax = max(mymax, rel);
+            } while (false);
+            asm volatile("bar.sync 1, %0;" ::"r"(act) : "memory");
+            if (pr != 0) p = p == N - 1 ? 1 : p + 1;
+            q = q == N - 1 ? 1 : q + 1;
         }
-        int done = (rot_count == 0) || (__longlong_as_double((long long)gmax_bits) <= (double)stop);
+        // no rotation (largest 0) or only rotations below the stopping level
+        for (int o = 16; o > 0; o >>= 1) mymax = max(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
+        if (lane == 0) wmax[warp] = mymax;
+        __syncthreads();
+        T gmax = T(0);
+        for (int w = 0; w < JAC_NT / 32; w++) gmax = max(gmax, wmax[w]);
+        const int done = !(gmax > stop);
         __syncthreads();
         if (done) break;
+    }
+    if (stats != nullptr && tid == 0) {
+        atomicAdd(stats, 1);
+        atomicAdd(stats + 1, sweeps);
     }
 
     for (int c = slot; c < k; c += nslot) {
         T s = T(0);
-        for (int i = sub; i < k; i += JAC_TPP) s = fma(X[c * ld + i], X[c * ld + i], s);
-        for (int o = JAC_TPP / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
+#pragma unroll
+        for (int e = 0; e < EL; e++) {
+            const int i = sub + TPP * e;
+            if (i < k) s = fma(X[c * ld + i], X[c * ld + i], s);
+        }
+#pragma unroll
+        for (int o = TPP / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
         if (sub == 0) sv[c] = sqrt(s);
     }
     __syncthreads();
@@ -375,14 +463,51 @@ __global__ void __launch_bounds__(JAC_NT) jacobi_kernel(const T *__restrict__ Rz
         pos[c] = p;
         sig[p] = sv[c];
     }
-    __syncthreads();
+    // fused SVT: r = number of singular values above the threshold (the
+    // first r after sorting)
+    const T thL = Us != nullptr ? T(svt->theta_L) : T(0);
+    const int r = __syncthreads_count(Us != nullptr && tid < k && sv[tid] > thL);
     for (int idx = tid; idx < k * k; idx += nt) {
         int c = idx / k, i = idx % k;
         int p = pos[c];
         T s = sv[c];
-        Ut[(int64_t)i * ldr + p] = s > T(0) ? X[c * ld + i] / s : T(0);
+        const T uu = s > T(0) ? X[c * ld + i] / s : T(0);
+        Ut[(int64_t)i * ldr + p] = uu;
         Wt[(int64_t)i * ldr + p] = V[c * ld + i];
+        if (Us != nullptr) Us[(int64_t)i * ldr + p] = p < r ? uu * (s - thL) : T(0);
     }
+    if (Us != nullptr && tid == 0) {
+        svt->r_new = r;
+        int kn = r + svt->oversample;
+        if (kn < 1) kn = 1;
+        if (kn > svt->kcap) kn = svt->kcap;
+        if (r >= k && k < svt->kcap) svt->flags |= 1;
+        svt->k_next = kn;
+    }
+}
+
+// one-sided Jacobi SVD of C = Rz^T (k x k): C = Ut diag(sig) Wt^T.
+// When ctrl is given, pairs whose squared norms sum to at most theta_L^2 are
+// not rotated: rotations preserve a + b, so neither column can end above the
+// SVT threshold and their mixing cannot change the thresholded result.
+// stats (optional): stats[0] counts the calls, stats[1] their sweeps.
+// Us (optional, with svt): the SVT on the factors fused into the epilogue, as
+// svt_small_kernel computes it for svt->theta_L (same arithmetic).
+template <typename T>
+__global__ void __launch_bounds__(JAC_NT) jacobi_kernel(const T *__restrict__ Rz, int ldr, const int *kdyn,
+                                                        T *__restrict__ Ut, T *__restrict__ Wt, T *__restrict__ sig,
+                                                        const Ctrl *ctrl, int *stats, T *__restrict__ Us,
+                                                        Ctrl *svt)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ T wmax[JAC_NT / 32];  // per-warp largest |g|/sqrt(ab) rotated in the sweep
+    __shared__ T amax;
+    const int k = *kdyn;
+    T *sm = reinterpret_cast<T *>(smraw);
+    if (k <= 64)
+        jacobi_body<T, 8>(Rz, ldr, k, Ut, Wt, sig, ctrl, stats, Us, svt, sm, wmax, &amax);
+    else
+        jacobi_body<T, 16>(Rz, ldr, k, Ut, Wt, sig, ctrl, stats, Us, svt, sm, wmax, &amax);
 }
 
 // ---------------------------------------------------------------------------
@@ -435,9 +560,39 @@ __global__ void fill_random_kernel(T *Omega, int64_t ldo, int rows, const Ctrl *
     Omega[(int64_t)j * ldo + c] = T(hash_uniform(key ^ ((uint64_t)j * 1000003ull + (uint64_t)c * 0x100000001B3ull)));
 }
 
+// fill_random_kernel on Omega (rows_o rows) and prolong_kernel from Omega
+// into B (n rows) in one launch: the prolongation reads the columns c < r_new,
+// whose singular values are above the threshold and so are never refilled
+template <typename T>
+__global__ void fill_prolong_kernel(T *Omega, int64_t ldo, int rows_o, const Ctrl *ctrl, const T *__restrict__ sig,
+                                    int kmax, uint64_t salt, int n, T *__restrict__ B, int64_t ldb, TransferDev<T> tr)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (c >= kmax) return;
+    if (j < n) {
+        const int r = ctrl->r_new;
+        T v = T(0);
+        if (c < r) {
+            const int a = tr.j0[j];
+            v = tr.w0[j] * Omega[(int64_t)a * ldo + c];
+            if (a + 1 < tr.nh && tr.w1[j] != T(0)) v = fma(tr.w1[j], Omega[(int64_t)(a + 1) * ldo + c], v);
+        }
+        B[(int64_t)j * ldb + c] = v;
+    }
+    if (j < rows_o) {
+        const int kc = ctrl->k, kn = ctrl->k_next;
+        if (c >= kn) return;
+        const bool fill = (c >= kc) || (sig != nullptr && sig[c] == T(0));
+        if (!fill) return;
+        uint64_t key = ctrl->seed * 0x9E3779B97F4A7C15ull + salt * 0xD1B54A32D192ED03ull + (uint64_t)ctrl->iter * 7919ull;
+        Omega[(int64_t)j * ldo + c] = T(hash_uniform(key ^ ((uint64_t)j * 1000003ull + (uint64_t)c * 0x100000001B3ull)));
+    }
+}
+
 __global__ void ctrl_begin_kernel(Ctrl *c)
 {
-    double mu = c->mu0 * pow(c->eta, (double)c->iter);
+    double mu = c->mu0 * c->eta_k;  // eta_k = eta^iter, kept by ctrl_end_kernel
     if (mu < c->mu_bar) mu = c->mu_bar;
     double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * c->t * c->t));
     c->mu_k = mu;
@@ -468,20 +623,20 @@ __global__ void ctrl_end_kernel(Ctrl *c)
     c->rk = c->r_new;
     c->k = c->k_next;
     c->iter += 1;
+    c->eta_k *= c->eta;
 }
 
 template <typename T>
 size_t chol_smem(int kmax)
 {
-    const int kp = (kmax + PB - 1) / PB * PB;
-    return (size_t)(2 * kp + kmax) * (kp + 1) * sizeof(T) + (size_t)kp * PB * sizeof(T) + 2 * kp * sizeof(T) +
-           kp * sizeof(int) + 16;
+    // d, piv, two rows of S; R and Rprev for Rtot
+    return (size_t)4 * kmax * sizeof(T) + (size_t)2 * kmax * (kmax + 1) * sizeof(T) + 16;
 }
 
 template <typename T>
 size_t jacobi_smem(int kmax)
 {
-    return (size_t)2 * kmax * (kmax + 1) * sizeof(T) + kmax * sizeof(T) + kmax * sizeof(int) + 16;
+    return (size_t)2 * kmax * jac_ld(kmax) * sizeof(T) + kmax * sizeof(T) + kmax * sizeof(int) + 16;
 }
 
 template <typename T>
@@ -500,21 +655,21 @@ void ensure_small_attrs()
 
 template <typename T>
 void launch_chol(const T *partialG, int splits, int kmax, const int *kdyn, T *R, T *Rinv, const T *Rprev, T *Rtot,
-                 int ldr, int *well_out, const int *skip_in, cudaStream_t st)
+                 int ldr, int *well_out, const int *skip_in, cudaStream_t st, int *stats)
 {
     ensure_small_attrs<T>();
     CPCP_COUNT_LAUNCH();
     chol_kernel<T><<<1, CHOL_NT, chol_smem<T>(kmax), st>>>(partialG, splits, kmax, kdyn, R, Rinv, Rprev, Rtot, ldr,
-                                                          well_out, skip_in);
+                                                          well_out, skip_in, stats);
 }
 
 template <typename T>
 void launch_jacobi(const T *Rz, int ldr, const int *kdyn, T *Ut, T *Wt, T *sig, int kmax, const Ctrl *ctrl,
-                   cudaStream_t st)
+                   cudaStream_t st, int *stats, T *Us, Ctrl *svt)
 {
     ensure_small_attrs<T>();
     CPCP_COUNT_LAUNCH();
-    jacobi_kernel<T><<<1, JAC_NT, jacobi_smem<T>(kmax), st>>>(Rz, ldr, kdyn, Ut, Wt, sig, ctrl);
+    jacobi_kernel<T><<<1, JAC_NT, jacobi_smem<T>(kmax), st>>>(Rz, ldr, kdyn, Ut, Wt, sig, ctrl, stats, Us, svt);
 }
 
 template <typename T>
@@ -533,6 +688,15 @@ void launch_fill_random(T *Omega, int64_t ldo, int rows, const Ctrl *ctrl, int a
     fill_random_kernel<T><<<grid, 64, 0, st>>>(Omega, ldo, rows, ctrl, all_cols, sig, kmax, salt);
 }
 
+template <typename T>
+void launch_fill_prolong(T *Omega, int64_t ldo, int rows_o, const Ctrl *ctrl, const T *sig, int kmax, uint64_t salt,
+                         int n, T *B, int64_t ldb, const TransferDev<T> &tr, cudaStream_t st)
+{
+    dim3 grid((kmax + 63) / 64, std::max(rows_o, n));
+    CPCP_COUNT_LAUNCH();
+    fill_prolong_kernel<T><<<grid, 64, 0, st>>>(Omega, ldo, rows_o, ctrl, sig, kmax, salt, n, B, ldb, tr);
+}
+
 void launch_ctrl_begin(Ctrl *c, cudaStream_t st) { CPCP_COUNT_LAUNCH(); ctrl_begin_kernel<<<1, 1, 0, st>>>(c); }
 void launch_ctrl_end(Ctrl *c, cudaStream_t st) { CPCP_COUNT_LAUNCH(); ctrl_end_kernel<<<1, 1, 0, st>>>(c); }
 void launch_ctrl_take_width(Ctrl *c, cudaStream_t st) { CPCP_COUNT_LAUNCH(); ctrl_take_width_kernel<<<1, 1, 0, st>>>(c); }
@@ -547,10 +711,13 @@ int small_kmax_f64() { return small_kmax<double>(); }
 
 #define INST(T)                                                                                                      \
     template void launch_chol<T>(const T *, int, int, const int *, T *, T *, const T *, T *, int, int *, const int *, \
-                                 cudaStream_t);                                                                      \
-    template void launch_jacobi<T>(const T *, int, const int *, T *, T *, T *, int, const Ctrl *, cudaStream_t);      \
+                                 cudaStream_t, int *);                                                               \
+    template void launch_jacobi<T>(const T *, int, const int *, T *, T *, T *, int, const Ctrl *, cudaStream_t,       \
+                                   int *, T *, Ctrl *);                                                              \
     template void launch_svt_small<T>(const T *, const T *, int, Ctrl *, T *, double *, cudaStream_t);               \
-    template void launch_fill_random<T>(T *, int64_t, int, const Ctrl *, int, const T *, int, uint64_t, cudaStream_t);
+    template void launch_fill_random<T>(T *, int64_t, int, const Ctrl *, int, const T *, int, uint64_t, cudaStream_t); \
+    template void launch_fill_prolong<T>(T *, int64_t, int, const Ctrl *, const T *, int, uint64_t, int, T *, int64_t, \
+                                         const TransferDev<T> &, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -423,6 +423,8 @@ struct SvdWork {
     // tensor-core kernels' bounded waits
     __nv_bfloat16 *Mb = nullptr, *Mt = nullptr, *Bt = nullptr;
     int *err = nullptr;
+    // optional counters: Jacobi calls, Jacobi sweeps, Cholesky factorisations
+    int *stats = nullptr;
 };
 
 template <typename T>
@@ -466,6 +468,44 @@ void svd_work_bf16(cpcp_context *h, SvdWork<T> &w, const std::string &tag, int m
     w.err = wsT<int>(h, "umma_err", 1);
 }
 
+// products of the subspace SVD: the cluster-reduced tall-skinny kernels, or the
+// plain tiled ones when an operand is not 16-byte aligned
+template <typename T>
+void prod_nn_small(int rows, const T *A, int64_t lda, const T *B, int64_t ldb, T *C, int64_t ldc, const int *kdyn,
+                   int kmax, cudaStream_t st, const int *skip = nullptr)
+{
+    // C (rows x k) = A (rows x k) B (k x k); skip: B is the identity
+    if (!launch_ts_nn<T>(rows, 0, A, lda, B, ldb, C, ldc, kdyn, kdyn, kmax, kmax, skip, st))
+        launch_gemm_nn<T>(rows, 0, A, lda, B, ldb, C, ldc, kdyn, kdyn, kmax, st);
+}
+
+template <typename T>
+void prod_y(SvdWork<T> &w, int m, int nc, const T *Mx, int64_t ldx, const T *Om, const int *kdyn, cudaStream_t st)
+{
+    // Y = M Omega (m x k), K = nc long
+    if (!launch_ts_nn<T>(m, nc, Mx, ldx, Om, w.KM, w.Y, w.KM, nullptr, kdyn, nc, w.KM, nullptr, st))
+        launch_gemm_nn_splitk<T>(m, nc, Mx, ldx, Om, w.KM, w.Y, w.KM, w.Ypart, kdyn, w.KM, st);
+}
+
+template <typename T>
+void prod_z(SvdWork<T> &w, int m, int nc, const T *Mx, int64_t ldx, const T *Q, int64_t ldq, const int *kdyn,
+            cudaStream_t st)
+{
+    // Z = M^T Q (nc x k), K = m long
+    if (!launch_ts_tn<T>(nc, m, Mx, ldx, Q, ldq, w.Z, w.KM, kdyn, w.KM, st)) {
+        const int sp = launch_gemm_tn_partial<T>(m, nc, Mx, ldx, Q, ldq, w.Zpart, kdyn, w.KM, nc, st, nullptr);
+        launch_reduce_partial<T>(w.Zpart, sp, nc, w.KM, w.Z, w.KM, nullptr, kdyn, st);
+    }
+}
+
+template <typename T>
+int prod_gram(SvdWork<T> &w, int rows, const T *X, const int *kdyn, const int *skip, cudaStream_t st)
+{
+    const int g = launch_ts_gram<T>(rows, X, w.KM, w.Gpart, kdyn, w.KM, skip, st);
+    if (g >= 0) return g;
+    return launch_gemm_tn_partial<T>(rows, -1, X, w.KM, X, w.KM, w.Gpart, kdyn, w.KM, w.KM, st, skip);
+}
+
 // CholeskyQR2 of X (rows x k): Q = X R^{-1}; if Rout != nullptr it receives
 // R = R2 R1.  The second pass is skipped on the device when the first one
 // found X nearly orthogonal after column equilibration (the warm-started
@@ -476,13 +516,15 @@ void orth(cpcp_context *h, SvdWork<T> &w, int rows, const T *X, T *Q, T *Rout, c
     cudaStream_t st = h->stream;
     const int KM = w.KM;
     int *well = w.well + slot;
-    int sp = launch_gemm_tn_partial<T>(rows, -1, X, KM, X, KM, w.Gpart, kdyn, KM, KM, st);
-    launch_chol<T>(w.Gpart, sp, KM, kdyn, w.R1, w.R1i, nullptr, nullptr, KM, well, nullptr, st);
-    launch_gemm_nn<T>(rows, 0, X, KM, w.R1i, KM, w.Q1, KM, kdyn, kdyn, KM, st);
+    int sp = prod_gram<T>(w, rows, X, kdyn, nullptr, st);
+    launch_chol<T>(w.Gpart, sp, KM, kdyn, w.R1, w.R1i, nullptr, nullptr, KM, well, nullptr, st,
+                   w.stats ? w.stats + 2 : nullptr);
+    prod_nn_small<T>(rows, X, KM, w.R1i, KM, w.Q1, KM, kdyn, KM, st);
     // second pass; when skipped its factor is the identity and Q = Q1 exactly
-    sp = launch_gemm_tn_partial<T>(rows, -1, w.Q1, KM, w.Q1, KM, w.Gpart, kdyn, KM, KM, st, well);
-    launch_chol<T>(w.Gpart, sp, KM, kdyn, w.R2, w.R2i, Rout ? w.R1 : nullptr, Rout, KM, nullptr, well, st);
-    launch_gemm_nn<T>(rows, 0, w.Q1, KM, w.R2i, KM, Q, KM, kdyn, kdyn, KM, st);
+    sp = prod_gram<T>(w, rows, w.Q1, kdyn, well, st);
+    launch_chol<T>(w.Gpart, sp, KM, kdyn, w.R2, w.R2i, Rout ? w.R1 : nullptr, Rout, KM, nullptr, well, st,
+                   w.stats ? w.stats + 2 : nullptr);
+    prod_nn_small<T>(rows, w.Q1, KM, w.R2i, KM, Q, KM, kdyn, KM, st, well);
 }
 
 // The subspace SVD below with both contractions with M on the tensor cores:
@@ -491,7 +533,7 @@ void orth(cpcp_context *h, SvdWork<T> &w, int rows, const T *X, T *Q, T *Rout, c
 // Z = M^T Q with fp32 accumulation.  Orthogonalisation and the core SVD stay
 // fp32.
 void subspace_svd_bf16(cpcp_context *h, SvdWork<float> &w, int m, int nc, const float *Mx, int64_t ldx,
-                       const float *Omega, int q, const int *kdyn, const Ctrl *jac_ctrl)
+                       const float *Omega, int q, const int *kdyn, const Ctrl *jac_ctrl, float *Us, Ctrl *svt)
 {
     cudaStream_t st = h->stream;
     const int KM = w.KM, NB = round16(KM);
@@ -511,20 +553,23 @@ void subspace_svd_bf16(cpcp_context *h, SvdWork<float> &w, int m, int nc, const 
         orth<float>(h, w, nc, w.Z, w.Qz, w.Rz, kdyn, 1);
         Om = w.Qz;
     }
-    launch_jacobi<float>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st);
+    launch_jacobi<float>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st, w.stats, Us, svt);
 }
 
 // Rank-k SVD of Mx (m x nc, ld ldx): q range passes from Omega (nc x k).
 // Leaves Qy (m x k), Qz (nc x k), Ut, Wt (k x k), sig (k) with
 // Mx ~ (Qy Ut) diag(sig) (Qz Wt)^T.  bf16: the contractions with Mx on the
 // tensor cores (fp32 data only; svd_work_bf16 must have sized the buffers).
+// Us, svt (optional): the SVT on the factors (launch_svt_small for svt) fused
+// into the core SVD.
 template <typename T>
 void subspace_svd(cpcp_context *h, SvdWork<T> &w, int m, int nc, const T *Mx, int64_t ldx, const T *Omega,
-                  int q, const int *kdyn, const Ctrl *jac_ctrl, bool bf16 = false)
+                  int q, const int *kdyn, const Ctrl *jac_ctrl, bool bf16 = false, T *Us = nullptr,
+                  Ctrl *svt = nullptr)
 {
     if constexpr (std::is_same<T, float>::value) {
         if (bf16) {
-            subspace_svd_bf16(h, w, m, nc, Mx, ldx, Omega, q, kdyn, jac_ctrl);
+            subspace_svd_bf16(h, w, m, nc, Mx, ldx, Omega, q, kdyn, jac_ctrl, Us, svt);
             return;
         }
     }
@@ -532,14 +577,13 @@ void subspace_svd(cpcp_context *h, SvdWork<T> &w, int m, int nc, const T *Mx, in
     const int KM = w.KM;
     const T *Om = Omega;
     for (int s = 0; s < q; s++) {
-        launch_gemm_nn_splitk<T>(m, nc, Mx, ldx, Om, KM, w.Y, KM, w.Ypart, kdyn, KM, st);
+        prod_y<T>(w, m, nc, Mx, ldx, Om, kdyn, st);
         orth<T>(h, w, m, w.Y, w.Qy, nullptr, kdyn, 0);
-        int sp = launch_gemm_tn_partial<T>(m, nc, Mx, ldx, w.Qy, KM, w.Zpart, kdyn, KM, nc, st);
-        launch_reduce_partial<T>(w.Zpart, sp, nc, KM, w.Z, KM, nullptr, kdyn, st);
+        prod_z<T>(w, m, nc, Mx, ldx, w.Qy, KM, kdyn, st);
         orth<T>(h, w, nc, w.Z, w.Qz, w.Rz, kdyn, 1);
         Om = w.Qz;
     }
-    launch_jacobi<T>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st);
+    launch_jacobi<T>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st, w.stats, Us, svt);
 }
 
 template <typename T>
@@ -560,7 +604,7 @@ int kmax_small<double>()
 // ---------------------------------------------------------------------------
 
 struct Opts {
-    int max_iter, check_every, k_max, p, q, qc, start_level, precision;
+    int max_iter, check_every, k_max, p, q, qc, start_level, precision, half, tc_pass;
     double eta, mu0, ratio, refine_at;
     uint64_t seed;
 };
@@ -579,6 +623,8 @@ Opts resolve(const cpcp_options &o)
     r.qc = o.check_power_iters > 0 ? o.check_power_iters : 2;
     r.start_level = o.start_level;
     r.precision = o.precision;
+    r.half = o.subspace_mode == 1;
+    r.tc_pass = o.pass_tc != 0;
     r.refine_at = o.refine_at > 0 ? o.refine_at : 1e-3;
     r.seed = o.seed ? o.seed : 1;
     return r;
@@ -599,6 +645,10 @@ struct SolveState {
     double *partial, *sums;
     int partial_blocks;
     bool bf16;  // contractions of the iteration's SVD in BF16 (mixed precision, before refinement)
+    // fine pass on the tensor cores: split factors (TF32 high and low parts) and the error flag
+    float *Ah = nullptr, *Al = nullptr, *Bh = nullptr, *Bl = nullptr;
+    int *tc_err = nullptr;
+    int side;   // half-step mode: warm subspace of the next iteration, 0 = right (Om), 1 = left (A[cur])
     std::vector<TransferDev<T>> tr;
 };
 
@@ -647,10 +697,9 @@ double fine_check(cpcp_context *h, SolveState<T> &s, SvdWork<T> &wf, int cur, co
     // fine SVT of M = L - tau G with width kf, warm-started from the last check
     launch_fill_random<T>(s.Omf, s.KM, s.n, s.cchk, 0, wf.sig, s.KM, 0xC4ECull, st);
     launch_ctrl_take_width(s.cchk, st);
-    subspace_svd<T>(h, wf, s.m, s.n, s.M, s.ldS, s.Omf, o.qc, &s.cchk->k, s.cchk);
-    launch_svt_small<T>(wf.Ut, wf.sig, wf.KM, s.cchk, wf.Us, nullptr, st);
-    launch_gemm_nn<T>(s.m, 0, wf.Qy, wf.KM, wf.Us, wf.KM, s.Ac, s.KM, &s.cchk->k, &s.cchk->k, s.KM, st);
-    launch_gemm_nn<T>(s.n, 0, wf.Qz, wf.KM, wf.Wt, wf.KM, s.Omf, s.KM, &s.cchk->k, &s.cchk->k, s.KM, st);
+    subspace_svd<T>(h, wf, s.m, s.n, s.M, s.ldS, s.Omf, o.qc, &s.cchk->k, s.cchk, false, wf.Us, s.cchk);
+    prod_nn_small<T>(s.m, wf.Qy, wf.KM, wf.Us, wf.KM, s.Ac, s.KM, &s.cchk->k, wf.KM, st);
+    prod_nn_small<T>(s.n, wf.Qz, wf.KM, wf.Wt, wf.KM, s.Omf, s.KM, &s.cchk->k, wf.KM, st);
     launch_prolong<T>(s.n, s.Omf, s.KM, s.Bc, s.KM, s.tr[0], &s.cchk->r_new, s.KM, st);
     PassArgs<T> b = base_args(s);
     b.ctrl = s.cchk;
@@ -732,19 +781,58 @@ void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, 
         ldx = s.ldMH;
     } else {
         int tp = h->timer.open(CPCP_PHASE_PASS_FINE);
-        launch_step_pass<T>(a, false, st);
+        bool done = false;
+        if constexpr (std::is_same<T, float>::value) {
+            if (s.Ah != nullptr) done = launch_pass_tc(a, s.KM, s.Ah, s.Al, s.Bh, s.Bl, s.tc_err, st);
+        }
+        if (!done) launch_step_pass<T>(a, false, st);
         h->timer.close(tp);
         Mx = s.M;
         ldx = s.ldS;
     }
     int ts = h->timer.open(CPCP_PHASE_SVT);
-    subspace_svd<T>(h, w, s.m, tr.nh, Mx, ldx, s.Om, o.q, &s.ctrl->k, s.ctrl, s.bf16);
-    launch_svt_small<T>(w.Ut, w.sig, w.KM, s.ctrl, w.Us, nullptr, st);
+    if (o.half && !s.bf16) {
+        // Half-step subspace iteration: one projection per iteration onto the
+        // previous iteration's right (V) or left (U) singular subspace,
+        // alternating; at a fixed point it is the power method on M, so the
+        // SVT it converges to is exact.  Either way L = A B^T keeps only the
+        // singular values above theta.
+        const int *kd = &s.ctrl->k;
+        const int KM = w.KM;
+        if (s.side == 0) {
+            // Y = M V = Qy Rz, Rz^T = Ut diag(sig) Wt^T: M ~ (Qy Wt) diag(sig) (V Ut)^T
+            prod_y<T>(w, s.m, tr.nh, Mx, ldx, s.Om, kd, st);
+            orth<T>(h, w, s.m, w.Y, w.Qy, w.Rz, kd, 0);
+            launch_jacobi<T>(w.Rz, KM, kd, w.Ut, w.Wt, w.sig, w.kcap, s.ctrl, st, w.stats);
+            launch_svt_small<T>(w.Ut, w.sig, KM, s.ctrl, w.Us, nullptr, st);
+            // A = Qy Wt (unscaled: it is also the next warm left subspace), B = R (V Ut diag(sig - theta))
+            prod_nn_small<T>(s.m, w.Qy, KM, w.Wt, KM, s.A[nxt], s.KM, kd, KM, st);
+            prod_nn_small<T>(tr.nh, s.Om, KM, w.Us, KM, w.Z, KM, kd, KM, st);
+            launch_fill_random<T>(s.A[nxt], s.KM, s.m, s.ctrl, 0, w.sig, s.KM, 0x57EAull, st);
+            launch_prolong<T>(s.n, w.Z, KM, s.B[nxt], s.KM, tr, &s.ctrl->r_new, s.KM, st);
+            s.side = 1;
+        } else {
+            // Z = M^T U = Qz Rz, Rz^T = Ut diag(sig) Wt^T: M ~ (U Ut) diag(sig) (Qz Wt)^T
+            prod_z<T>(w, s.m, tr.nh, Mx, ldx, s.A[cur], s.KM, kd, st);
+            orth<T>(h, w, tr.nh, w.Z, w.Qz, w.Rz, kd, 1);
+            launch_jacobi<T>(w.Rz, KM, kd, w.Ut, w.Wt, w.sig, w.kcap, s.ctrl, st, w.stats);
+            launch_svt_small<T>(w.Ut, w.sig, KM, s.ctrl, w.Us, nullptr, st);
+            // A = U Ut diag(sig - theta), V = Qz Wt (unscaled: the next warm right subspace), B = R V
+            prod_nn_small<T>(s.m, s.A[cur], s.KM, w.Us, KM, s.A[nxt], s.KM, kd, KM, st);
+            prod_nn_small<T>(tr.nh, w.Qz, KM, w.Wt, KM, s.Om, s.KM, kd, KM, st);
+            launch_fill_random<T>(s.Om, s.KM, tr.nh, s.ctrl, 0, w.sig, s.KM, 0x57E9ull, st);
+            launch_prolong<T>(s.n, s.Om, s.KM, s.B[nxt], s.KM, tr, &s.ctrl->r_new, s.KM, st);
+            s.side = 0;
+        }
+        h->timer.close(ts);
+        launch_ctrl_end(s.ctrl, st);
+        return;
+    }
+    subspace_svd<T>(h, w, s.m, tr.nh, Mx, ldx, s.Om, o.q, &s.ctrl->k, s.ctrl, s.bf16, w.Us, s.ctrl);
     // new factors into the "previous" slot (its old content was consumed above)
-    launch_gemm_nn<T>(s.m, 0, w.Qy, w.KM, w.Us, w.KM, s.A[nxt], s.KM, &s.ctrl->k, &s.ctrl->k, s.KM, st);
-    launch_gemm_nn<T>(tr.nh, 0, w.Qz, w.KM, w.Wt, w.KM, s.Om, s.KM, &s.ctrl->k, &s.ctrl->k, s.KM, st);
-    launch_fill_random<T>(s.Om, s.KM, tr.nh, s.ctrl, 0, w.sig, s.KM, 0x57E9ull, st);
-    launch_prolong<T>(s.n, s.Om, s.KM, s.B[nxt], s.KM, tr, &s.ctrl->r_new, s.KM, st);
+    prod_nn_small<T>(s.m, w.Qy, w.KM, w.Us, w.KM, s.A[nxt], s.KM, &s.ctrl->k, w.KM, st);
+    prod_nn_small<T>(tr.nh, w.Qz, w.KM, w.Wt, w.KM, s.Om, s.KM, &s.ctrl->k, w.KM, st);
+    launch_fill_prolong<T>(s.Om, s.KM, tr.nh, s.ctrl, w.sig, s.KM, 0x57E9ull, s.n, s.B[nxt], s.KM, tr, st);
     h->timer.close(ts);
     launch_ctrl_end(s.ctrl, st);
 }
@@ -794,15 +882,27 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     s.sums = wsT<double>(h, "sums", 16);
     SvdWork<T> w = svd_work<T>(h, "it_", m, n, s.kcap0);
     SvdWork<T> wf = svd_work<T>(h, "ck_", m, n, s.kcap0);
+    w.stats = wf.stats = wsT<int>(h, "svd_stats", 4);
+    CK(cudaMemsetAsync(w.stats, 0, sizeof(int) * 4, st));
     s.bf16 = o.precision == 1;
+    s.side = 0;
     if (s.bf16) {
         svd_work_bf16<T>(h, w, "it_", m, n);
         CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    }
+    if (std::is_same<T, float>::value && o.tc_pass) {
+        s.Ah = wsT<float>(h, "tc_Ah", pass_tc_split_elems(m, s.KM));
+        s.Al = wsT<float>(h, "tc_Al", pass_tc_split_elems(m, s.KM));
+        s.Bh = wsT<float>(h, "tc_Bh", pass_tc_split_elems(n, s.KM));
+        s.Bl = wsT<float>(h, "tc_Bl", pass_tc_split_elems(n, s.KM));
+        s.tc_err = wsT<int>(h, "tc_err", 1);
+        CK(cudaMemsetAsync(s.tc_err, 0, sizeof(int), st));
     }
 
     // control blocks
     Ctrl c0;
     memset(&c0, 0, sizeof(c0));
+    c0.eta_k = 1.0;
     c0.tau = 0.5;
     c0.lam = lam;
     c0.mu_bar = mu;
@@ -930,6 +1030,7 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
             CK(cudaMemcpyAsync(ctmp, &tmp, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
             launch_fill_random<T>(s.Om, s.KM, s.tr[level].nh, ctmp, 0, nullptr, s.KM, 0x77ull + level, st);
             CK(cudaStreamSynchronize(st));
+            s.side = 0;  // the warm subspace is the restricted right factor
         }
     }
     inf.iters = iter;
@@ -938,11 +1039,17 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     inf.relkkt = rel;
     Ctrl fin;
     CK(cudaMemcpyAsync(&fin, s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-    int umma_err = 0;
+    int stats[4];
+    CK(cudaMemcpyAsync(stats, w.stats, sizeof(stats), cudaMemcpyDeviceToHost, st));
+    int umma_err = 0, tc_err = 0;
     if (w.err) CK(cudaMemcpyAsync(&umma_err, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (s.tc_err) CK(cudaMemcpyAsync(&tc_err, s.tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (umma_err) throw CpcpError{CPCP_ERR_TIMEOUT, "a bounded wait of the tensor-core kernel expired"};
+    if (umma_err || tc_err) throw CpcpError{CPCP_ERR_TIMEOUT, "a bounded wait of the tensor-core kernel expired"};
     inf.rank = fin.rk;
+    inf.jacobi_calls = stats[0];
+    inf.jacobi_sweeps = stats[1];
+    inf.chol_factors = stats[2];
     // outputs
     if (S_out) {
         CK(cudaMemcpy2DAsync(S_out, sizeof(T) * lds, s.S[cur], sizeof(T) * s.ldS, sizeof(T) * n, m,
