@@ -108,6 +108,10 @@ typedef struct {
                               per product) wherever D and S meet its alignment rules (16-byte
                               aligned base, leading dimension a multiple of 4); its rel-KKT floor
                               is about 2e-6.  0 (default): the SIMT pass */
+    int plain_launches;    /* cpcp_solve: nonzero launches every kernel of every iteration from
+                              the host; 0 (default) captures an iteration's kernels in a CUDA
+                              graph the second time the same (level, buffer parity) comes up and
+                              replays the graph for the iterations between residual checks */
 } cpcp_options;
 
 /* Phases timed when cpcp_options.profile is set. */

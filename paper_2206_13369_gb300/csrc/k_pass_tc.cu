@@ -6,13 +6,20 @@
 //     A^ = [(1 + beta) A_k, -beta A_{k-1}],  B^ = [B_k, B_{k-1}],
 //
 // on the 5th-generation tensor cores.  fp32 accuracy from TF32 operands: each
-// factor is split as x = x_hi + x_lo with x_hi, x_lo TF32 (round to nearest),
-// and a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (the dropped a_lo b_lo and the
-// rounding of the low parts are below 2^-22 relative), all three products
-// accumulated in fp32 in tensor memory.
+// factor entry is split as x = x_h + x_m + x_l, three TF32 numbers taken by
+// successive round-to-nearest (11 significant bits each, so the split is exact
+// to 2^-33), and
+//     a b ~ a_m b_m + a_l b_h + a_h b_l + a_m b_h + a_h b_m + a_h b_h
+// (the dropped terms are below 2^-32 relative).  The six products are one
+// TF32 contraction over an extended K: A6 = [a_m, a_l, a_h, a_m, a_h, a_h] and
+// B6 = [b_m, b_h, b_l, b_h, b_m, b_h], blocks of the live K each, smallest
+// terms first, accumulated in fp32 in tensor memory.  (Two-term splitting,
+// a b ~ a_h b_h + a_h b_l + a_l b_h, represents each factor only to 2^-22 and
+// left a rel-KKT floor near 2e-6, because the momentum step cancels most of
+// L-hat.)
 //
 // One persistent CTA per SM walks 128 x 64 output tiles.  Warp roles:
-//   warp 0   TMA producer of the operand stages (A^ hi/lo, B^ hi/lo, 32 K each)
+//   warp 0   TMA producer of the operand stages (A6, B6: 32 K each)
 //   warp 1   MMA issuer: tcgen05.mma kind::tf32, M = 128, N = 64, K = 8
 //   warp 2   TMEM allocator (two 64-column fp32 accumulators, double buffered)
 //   warp 3   TMA producer of the epilogue tiles: D, S_k, S_{k-1} in 32-column
@@ -41,12 +48,12 @@ constexpr int TBM = 128;   // tile rows = TMEM lanes
 constexpr int TBN = 64;    // tile columns = accumulator columns
 constexpr int TBK = 32;    // K per operand stage: 128 bytes of fp32
 constexpr int HALF = 32;   // epilogue half-tile columns (128 bytes of fp32)
-constexpr int OPS = 2;     // operand stages
+constexpr int OPS = 4;     // operand stages
 constexpr int EPS = 2;     // epilogue half-tile buffers
 constexpr int NT = 256;
 constexpr uint32_t A_BYTES = TBM * TBK * 4;             // 16 KB
 constexpr uint32_t B_BYTES = TBN * TBK * 4;             // 8 KB
-constexpr uint32_t OP_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // hi + lo
+constexpr uint32_t OP_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t EP_TILE = TBM * HALF * 4;            // 16 KB per array
 constexpr uint32_t EP_BYTES = 3 * EP_TILE;              // D, S_k, S_{k-1}
 constexpr uint32_t TMEM_COLS = 2 * TBN;
@@ -178,7 +185,7 @@ __device__ __forceinline__ float tf32_rn(float x)
     return __uint_as_float(r);
 }
 
-// live K of the contraction and its K blocks (the same on every role)
+// live K of the contraction (the same on every role); the extended K is 6 K
 __device__ __forceinline__ int live_k(const int *rk, const int *rp, const Ctrl *ctrl)
 {
     const int a = rk ? *rk : 0;
@@ -187,8 +194,8 @@ __device__ __forceinline__ int live_k(const int *rk, const int *rp, const Ctrl *
 }
 
 struct TcMaps {
-    CUtensorMap ah, al, bh, bl;  // split factors (K-major, 128-byte swizzle)
-    CUtensorMap d, sk, sp;       // epilogue inputs (32-column boxes, 128-byte swizzle)
+    CUtensorMap a6, b6;     // extended split factors (K-major, 128-byte swizzle)
+    CUtensorMap d, sk, sp;  // epilogue inputs (32-column boxes, 128-byte swizzle)
 };
 
 struct TcArgs {
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
     const int tiles_n = (a.n + TBN - 1) / TBN;
     const int ntiles = ((a.m + TBM - 1) / TBM) * tiles_n;
     const int K = live_k(a.rk, a.rp, a.ctrl);
-    const int nkb = (K + TBK - 1) / TBK;
+    const int nkb = (6 * K + TBK - 1) / TBK;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < OPS; s++) {
@@ -270,10 +277,8 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
                     if (i >= OPS && !mbar_wait(&op_empty[s], ((i / OPS) & 1) ^ 1, abort_flag)) break;
                     uint8_t *st = sOp + s * OP_BYTES;
                     mbar_expect_tx(&op_full[s], OP_BYTES);
-                    tma_load_2d(st, &maps.ah, &op_full[s], kb * TBK, rb);
-                    tma_load_2d(st + A_BYTES, &maps.al, &op_full[s], kb * TBK, rb);
-                    tma_load_2d(st + 2 * A_BYTES, &maps.bh, &op_full[s], kb * TBK, cb);
-                    tma_load_2d(st + 2 * A_BYTES + B_BYTES, &maps.bl, &op_full[s], kb * TBK, cb);
+                    tma_load_2d(st, &maps.a6, &op_full[s], kb * TBK, rb);
+                    tma_load_2d(st + A_BYTES, &maps.b6, &op_full[s], kb * TBK, cb);
                 }
             }
             // drain: the last phase issued on each stage has landed (time bound
@@ -323,15 +328,10 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
                     }
                     tc_fence_after();
                     const uint8_t *st = sOp + s * OP_BYTES;
-                    const uint64_t ah = smem_desc_sw128(st), al = smem_desc_sw128(st + A_BYTES);
-                    const uint64_t bh = smem_desc_sw128(st + 2 * A_BYTES);
-                    const uint64_t bl = smem_desc_sw128(st + 2 * A_BYTES + B_BYTES);
+                    const uint64_t ad = smem_desc_sw128(st), bd = smem_desc_sw128(st + A_BYTES);
 #pragma unroll
-                    for (int kk = 0; kk < TBK / 8; kk++) {  // 8 TF32 = 32 bytes = 2 descriptor units per step
-                        umma_tf32(d, ah + 2 * kk, bh + 2 * kk, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-                        umma_tf32(d, ah + 2 * kk, bl + 2 * kk, idesc, 1u);
-                        umma_tf32(d, al + 2 * kk, bh + 2 * kk, idesc, 1u);
-                    }
+                    for (int kk = 0; kk < TBK / 8; kk++)  // 8 TF32 = 32 bytes = 2 descriptor units per step
+                        umma_tf32(d, ad + 2 * kk, bd + 2 * kk, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
                     umma_commit(&op_empty[s]);
                 }
                 if (!ok) break;
@@ -431,31 +431,41 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
 }
 
 // A^ = [(1 + beta) A_k, -beta A_{k-1}] and B^ = [B_k, B_{k-1}] split into
-// TF32 high and low parts (K-padded with zeros to the next 32)
+// three TF32 parts each and laid out as the extended operands A6, B6 (block j
+// of K columns pairs the parts of product j; zero padding to the next 32)
 __global__ void tf32_split_kernel(int m, int n, const float *__restrict__ Ak, const float *__restrict__ Ap,
                                   int64_t lda, const float *__restrict__ Bk, const float *__restrict__ Bp,
                                   int64_t ldb, const int *rk_p, const int *rp_p, const Ctrl *ctrl,
-                                  float *__restrict__ Ah, float *__restrict__ Al, float *__restrict__ Bh,
-                                  float *__restrict__ Bl, int64_t ldk)
+                                  float *__restrict__ A6, float *__restrict__ B6, int64_t ldk)
 {
     const int rk = rk_p ? *rk_p : 0;
     const int rp = (rp_p && ctrl->beta != 0.0) ? *rp_p : 0;
-    const int K = rk + rp, Kp = (K + TBK - 1) / TBK * TBK;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int K = rk + rp, K6 = 6 * K, Kp = (K6 + TBK - 1) / TBK * TBK;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;  // column of the live K
     const int row = blockIdx.y;
-    if (c >= Kp) return;
-    const float ck = (float)(1.0 + ctrl->beta), cp = (float)(-ctrl->beta);
-    if (row < m) {
-        const float v = c < rk ? Ak[(int64_t)row * lda + c] * ck : (c < K ? Ap[(int64_t)row * lda + c - rk] * cp : 0.f);
-        const float hi = tf32_rn(v);
-        Ah[(int64_t)row * ldk + c] = hi;
-        Al[(int64_t)row * ldk + c] = tf32_rn(v - hi);
-    }
-    if (row < n) {
-        const float v = c < rk ? Bk[(int64_t)row * ldb + c] : (c < K ? Bp[(int64_t)row * ldb + c - rk] : 0.f);
-        const float hi = tf32_rn(v);
-        Bh[(int64_t)row * ldk + c] = hi;
-        Bl[(int64_t)row * ldk + c] = tf32_rn(v - hi);
+    // parts (0 = h, 1 = m, 2 = l) of product j = 0..5: A6 and B6
+    constexpr int PA[6] = {1, 2, 0, 1, 0, 0}, PB[6] = {1, 0, 2, 0, 1, 0};
+    if (c < K) {
+        const float ck = (float)(1.0 + ctrl->beta), cp = (float)(-ctrl->beta);
+        if (row < m) {
+            const float v = c < rk ? Ak[(int64_t)row * lda + c] * ck : Ap[(int64_t)row * lda + c - rk] * cp;
+            const float h = tf32_rn(v), r1 = v - h, md = tf32_rn(r1), lo = tf32_rn(r1 - md);
+            const float part[3] = {h, md, lo};
+#pragma unroll
+            for (int j = 0; j < 6; j++) A6[(int64_t)row * ldk + j * K + c] = part[PA[j]];
+        }
+        if (row < n) {
+            const float v = c < rk ? Bk[(int64_t)row * ldb + c] : Bp[(int64_t)row * ldb + c - rk];
+            const float h = tf32_rn(v), r1 = v - h, md = tf32_rn(r1), lo = tf32_rn(r1 - md);
+            const float part[3] = {h, md, lo};
+#pragma unroll
+            for (int j = 0; j < 6; j++) B6[(int64_t)row * ldk + j * K + c] = part[PB[j]];
+        }
+    } else if (c < K + (Kp - K6)) {
+        // zero padding of the last K block
+        const int z = K6 + (c - K);
+        if (row < m) A6[(int64_t)row * ldk + z] = 0.f;
+        if (row < n) B6[(int64_t)row * ldk + z] = 0.f;
     }
 }
 
@@ -509,25 +519,21 @@ int sm_count()
 
 }  // namespace
 
-size_t pass_tc_split_elems(int rows, int kmax) { return (size_t)rows * (size_t)((2 * kmax + TBK - 1) / TBK * TBK); }
+size_t pass_tc_split_elems(int rows, int kmax) { return (size_t)rows * (size_t)((12 * kmax + TBK - 1) / TBK * TBK); }
 
 // The fused fine pass on the tensor cores; false (nothing launched) when an
 // operand does not meet the TMA rules (16-byte aligned bases and strides) or
-// the tensor maps cannot be made.  Ah, Al (m rows) and Bh, Bl (n rows) are
-// scratch of pass_tc_split_elems each, leading dimension ldk =
-// round32(2 kmax).
-bool launch_pass_tc(const PassArgs<float> &p, int kmax, float *Ah, float *Al, float *Bh, float *Bl, int *err,
-                    cudaStream_t st)
+// the tensor maps cannot be made.  A6 (m rows) and B6 (n rows) are scratch of
+// pass_tc_split_elems each, leading dimension ldk = round32(12 kmax).
+bool launch_pass_tc(const PassArgs<float> &p, int kmax, float *A6, float *B6, int *err, cudaStream_t st)
 {
     if (p.M == nullptr || p.Sout == nullptr || p.Ak == nullptr || p.Bk == nullptr) return false;
     if (p.ldfa != p.ldfap || p.ldfb != p.ldfbp) return false;
-    const int64_t ldk = (2 * kmax + TBK - 1) / TBK * TBK;
+    const int64_t ldk = (12 * kmax + TBK - 1) / TBK * TBK;
     const bool has_sp = p.Sp != nullptr && p.Sp != p.Sk;
     TcMaps maps;
-    if (!make_map_f32(&maps.ah, Ah, (uint64_t)ldk, (uint64_t)p.m, (uint64_t)ldk, TBM)) return false;
-    if (!make_map_f32(&maps.al, Al, (uint64_t)ldk, (uint64_t)p.m, (uint64_t)ldk, TBM)) return false;
-    if (!make_map_f32(&maps.bh, Bh, (uint64_t)ldk, (uint64_t)p.n, (uint64_t)ldk, TBN)) return false;
-    if (!make_map_f32(&maps.bl, Bl, (uint64_t)ldk, (uint64_t)p.n, (uint64_t)ldk, TBN)) return false;
+    if (!make_map_f32(&maps.a6, A6, (uint64_t)ldk, (uint64_t)p.m, (uint64_t)ldk, TBM)) return false;
+    if (!make_map_f32(&maps.b6, B6, (uint64_t)ldk, (uint64_t)p.n, (uint64_t)ldk, TBN)) return false;
     if (!make_map_f32(&maps.d, p.D, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.ldd, TBM)) return false;
     if (!make_map_f32(&maps.sk, p.Sk, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.lds, TBM)) return false;
     if (!make_map_f32(&maps.sp, has_sp ? p.Sp : p.Sk, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.lds, TBM))
@@ -539,12 +545,13 @@ bool launch_pass_tc(const PassArgs<float> &p, int kmax, float *Ah, float *Al, fl
             return false;
         attr = true;
     }
-    // split factors (one launch), then the persistent pass
+    // split factors (one launch; threads over the live K and the padding),
+    // then the persistent pass
     {
-        dim3 grid((unsigned)((ldk + 127) / 128), (unsigned)std::max(p.m, p.n));
+        dim3 grid((unsigned)((2 * kmax + TBK + 127) / 128), (unsigned)std::max(p.m, p.n));
         CPCP_COUNT_LAUNCH();
         tf32_split_kernel<<<grid, 128, 0, st>>>(p.m, p.n, p.Ak, p.Ap ? p.Ap : p.Ak, p.ldfa, p.Bk, p.Bp ? p.Bp : p.Bk,
-                                                p.ldfb, p.rk, p.Ap ? p.rp : nullptr, p.ctrl, Ah, Al, Bh, Bl, ldk);
+                                                p.ldfb, p.rk, p.Ap ? p.rp : nullptr, p.ctrl, A6, B6, ldk);
     }
     TcArgs a;
     a.m = p.m;

@@ -148,6 +148,11 @@ struct cpcp_context {
     BatchGraph batch;
     std::map<uint64_t, int> batch_tuned;  // signature -> measured best CTA size
     UnrollRec unroll;
+    // private non-blocking stream of the graph-replayed solve (the caller's
+    // stream may be the legacy default stream, which cannot be captured) and
+    // the two events that order it after and before the caller's stream
+    cudaStream_t solve_stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 namespace {
@@ -604,7 +609,7 @@ int kmax_small<double>()
 // ---------------------------------------------------------------------------
 
 struct Opts {
-    int max_iter, check_every, k_max, p, q, qc, start_level, precision, half, tc_pass;
+    int max_iter, check_every, k_max, p, q, qc, start_level, precision, half, tc_pass, graphs;
     double eta, mu0, ratio, refine_at;
     uint64_t seed;
 };
@@ -625,6 +630,7 @@ Opts resolve(const cpcp_options &o)
     r.precision = o.precision;
     r.half = o.subspace_mode == 1;
     r.tc_pass = o.pass_tc != 0;
+    r.graphs = o.plain_launches == 0;
     r.refine_at = o.refine_at > 0 ? o.refine_at : 1e-3;
     r.seed = o.seed ? o.seed : 1;
     return r;
@@ -645,8 +651,8 @@ struct SolveState {
     double *partial, *sums;
     int partial_blocks;
     bool bf16;  // contractions of the iteration's SVD in BF16 (mixed precision, before refinement)
-    // fine pass on the tensor cores: split factors (TF32 high and low parts) and the error flag
-    float *Ah = nullptr, *Al = nullptr, *Bh = nullptr, *Bl = nullptr;
+    // fine pass on the tensor cores: the extended split factors and the error flag
+    float *A6 = nullptr, *B6 = nullptr;
     int *tc_err = nullptr;
     int side;   // half-step mode: warm subspace of the next iteration, 0 = right (Om), 1 = left (A[cur])
     std::vector<TransferDev<T>> tr;
@@ -740,12 +746,18 @@ double fine_check(cpcp_context *h, SolveState<T> &s, SvdWork<T> &wf, int cur, co
 // One iteration.  With want_g on a coarse level the pass also restricts the
 // gradient; s.sums[8] then holds ||G||_F^2 and s.sums[11] ||G R||_F^2.
 template <typename T>
+// part 0: the whole iteration; 1: the schedule update and the fused pass
+// only; 2: the rest (subspace SVD, SVT, new factors, schedule end), which the
+// caller times itself (part 2 is what the solver replays as a CUDA graph).
 void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, int cur, const Opts &o,
-                   bool want_g)
+                   bool want_g, int part = 0)
 {
     cudaStream_t st = h->stream;
     const int nxt = cur ^ 1;
     const TransferDev<T> &tr = s.tr[level];
+    const T *Mx = level > 0 ? s.MH : s.M;
+    const int64_t ldx = level > 0 ? s.ldMH : s.ldS;
+    if (part != 2) {
     launch_ctrl_begin(s.ctrl, st);
     PassArgs<T> a = base_args(s);
     a.Sk = s.S[cur];
@@ -757,8 +769,6 @@ void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, 
     a.Bp = s.B[nxt];
     a.rk = &s.ctrl->rk;
     a.rp = &s.ctrl->rp;
-    const T *Mx;
-    int64_t ldx;
     if (level > 0) {
         CK(cudaMemsetAsync(s.MH, 0, sizeof(T) * (size_t)s.m * s.ldMH, st));
         a.M = nullptr;
@@ -777,20 +787,18 @@ void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, 
             int nq = launch_sumsq<T>(s.m, tr.nh, s.GH, s.ldMH, s.partial, st);
             launch_sum_partials(s.partial, nq, 1, s.sums + 11, st);
         }
-        Mx = s.MH;
-        ldx = s.ldMH;
     } else {
         int tp = h->timer.open(CPCP_PHASE_PASS_FINE);
         bool done = false;
         if constexpr (std::is_same<T, float>::value) {
-            if (s.Ah != nullptr) done = launch_pass_tc(a, s.KM, s.Ah, s.Al, s.Bh, s.Bl, s.tc_err, st);
+            if (s.A6 != nullptr) done = launch_pass_tc(a, s.KM, s.A6, s.B6, s.tc_err, st);
         }
         if (!done) launch_step_pass<T>(a, false, st);
         h->timer.close(tp);
-        Mx = s.M;
-        ldx = s.ldS;
     }
-    int ts = h->timer.open(CPCP_PHASE_SVT);
+    }
+    if (part == 1) return;
+    const int ts = part == 0 ? h->timer.open(CPCP_PHASE_SVT) : -1;
     if (o.half && !s.bf16) {
         // Half-step subspace iteration: one projection per iteration onto the
         // previous iteration's right (V) or left (U) singular subspace,
@@ -837,14 +845,65 @@ void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, 
     launch_ctrl_end(s.ctrl, st);
 }
 
+// Runs the solve on the handle's private stream: ordered after the work the
+// caller queued on its stream, and the caller's stream waits for the solve
+// (on every exit path).
+struct PrivateStream {
+    cpcp_context *h;
+    cudaStream_t user;
+    bool on = false;
+    PrivateStream(cpcp_context *h_, bool use) : h(h_), user(h_->stream)
+    {
+        if (!use) return;
+        if (!h->solve_stream) CK(cudaStreamCreateWithFlags(&h->solve_stream, cudaStreamNonBlocking));
+        if (!h->ev_in) CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+        if (!h->ev_out) CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+        CK(cudaEventRecord(h->ev_in, user));
+        CK(cudaStreamWaitEvent(h->solve_stream, h->ev_in, 0));
+        h->stream = h->solve_stream;
+        on = true;
+    }
+    ~PrivateStream()
+    {
+        if (!on) return;
+        cudaEventRecord(h->ev_out, h->solve_stream);
+        cudaStreamWaitEvent(user, h->ev_out, 0);
+        h->stream = user;
+    }
+};
+
+// One iteration's kernels as an instantiated CUDA graph (per level and buffer
+// parity); destroyed with the solve.
+struct IterGraph {
+    bool seen = false;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long launches = 0;
+};
+
+struct IterGraphs {
+    IterGraph g[8][2];
+    ~IterGraphs()
+    {
+        for (auto &row : g)
+            for (auto &x : row)
+                if (x.exec) cudaGraphExecDestroy(x.exec);
+    }
+};
+
 template <typename T>
 cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, const uint32_t *Q, int64_t ldq,
                        double lam, double mu, int levels, double tol, T *L_out, int64_t ldl, T *S_out, int64_t lds,
                        cpcp_info *info)
 {
     auto t0 = std::chrono::steady_clock::now();
-    cudaStream_t st = h->stream;
     const Opts o = resolve(h->opt);
+    // iterations without a level decision replay a CUDA graph of their kernels
+    // (captured the second time the same level and buffer parity come up,
+    // once every workspace buffer exists); the kernels read the iteration's
+    // scalars (weights, widths, ranks) from the device control block
+    const bool use_graphs = o.graphs && !o.half;
+    PrivateStream ps(h, use_graphs);
+    cudaStream_t st = h->stream;
     const int H = levels - 1;
     h->timer.reset(h->opt.profile != 0, st);
     const unsigned long long launches0 = g_kernel_launches;
@@ -891,10 +950,8 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
         CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
     }
     if (std::is_same<T, float>::value && o.tc_pass) {
-        s.Ah = wsT<float>(h, "tc_Ah", pass_tc_split_elems(m, s.KM));
-        s.Al = wsT<float>(h, "tc_Al", pass_tc_split_elems(m, s.KM));
-        s.Bh = wsT<float>(h, "tc_Bh", pass_tc_split_elems(n, s.KM));
-        s.Bl = wsT<float>(h, "tc_Bl", pass_tc_split_elems(n, s.KM));
+        s.A6 = wsT<float>(h, "tc_A6", pass_tc_split_elems(m, s.KM));
+        s.B6 = wsT<float>(h, "tc_B6", pass_tc_split_elems(n, s.KM));
         s.tc_err = wsT<int>(h, "tc_err", 1);
         CK(cudaMemsetAsync(s.tc_err, 0, sizeof(int), st));
     }
@@ -963,11 +1020,49 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     int cur = 0, iter = 0, checks = 0, kf = cc.k, rank = 0;
     double rel = INFINITY, prev = INFINITY;
     cpcp_status status = CPCP_ERR_NOT_CONVERGED;
+    IterGraphs graphs;
     for (iter = 0; iter < o.max_iter;) {
         // every check_every iterations: a level decision (coarse levels) and,
         // once the weight is final, the fine residual check
         const bool decide = (iter + 1) % o.check_every == 0;
-        one_iteration<T>(h, s, w, level, cur, o, decide && level > 0);
+        const bool want_g = decide && level > 0;
+        if (use_graphs && !want_g && !s.bf16 && level < 8) {
+            // the schedule update and the fused pass are launched directly (the
+            // profile's events bracket the pass); the rest of the iteration is
+            // the graph
+            one_iteration<T>(h, s, w, level, cur, o, false, 1);
+            IterGraph &G = graphs.g[level][cur];
+            if (G.exec == nullptr && G.seen) {
+                const unsigned long long l0 = g_kernel_launches;
+                CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                cudaGraph_t graph = nullptr;
+                try {
+                    one_iteration<T>(h, s, w, level, cur, o, false, 2);
+                } catch (...) {
+                    cudaStreamEndCapture(st, &graph);
+                    if (graph) cudaGraphDestroy(graph);
+                    cudaGetLastError();
+                    throw;
+                }
+                CK(cudaStreamEndCapture(st, &graph));
+                const cudaError_t ie = cudaGraphInstantiate(&G.exec, graph, 0);
+                cudaGraphDestroy(graph);
+                CK(ie);
+                G.launches = g_kernel_launches - l0;
+                g_kernel_launches = l0;
+            }
+            const int ts = h->timer.open(CPCP_PHASE_SVT);
+            if (G.exec != nullptr) {
+                CK(cudaGraphLaunch(G.exec, st));
+                g_kernel_launches += G.launches;
+            } else {
+                G.seen = true;
+                one_iteration<T>(h, s, w, level, cur, o, false, 2);
+            }
+            h->timer.close(ts);
+        } else {
+            one_iteration<T>(h, s, w, level, cur, o, want_g);
+        }
         cur ^= 1;
         if (level < 8) inf.level_iters[level]++;
         if (s.bf16) inf.bf16_iters++;
@@ -1982,6 +2077,12 @@ void cpcp_destroy(cpcp_handle h)
     if (h->batch.graph) cudaGraphDestroy(h->batch.graph);
     if (h->batch.host_res) cudaFreeHost(h->batch.host_res);
     if (h->batch.stream) cudaStreamDestroy(h->batch.stream);
+    if (h->solve_stream) {
+        cudaStreamSynchronize(h->solve_stream);
+        cudaStreamDestroy(h->solve_stream);
+    }
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
     for (auto &kv : h->bufs)
         if (kv.second.p) cudaFree(kv.second.p);
     delete h;
