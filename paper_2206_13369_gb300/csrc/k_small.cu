@@ -106,17 +106,22 @@ __device__ __forceinline__ T chol_gram_entry(const T *__restrict__ partial, int 
     return (s0 + s1) + (s2 + s3);
 }
 
-template <typename T, int RA, int CB>
+template <typename T, int RG, int RA, int CB>
 __device__ __forceinline__ void chol_body(const T *__restrict__ partial, int splits, int kmax, int k,
                                           T *__restrict__ R, T *__restrict__ Rinv, const T *__restrict__ Rprev,
                                           T *__restrict__ Rtot, int ldr, int *well_out, T *sm, double *red)
 {
+    // RG warps take part in the elimination: thread (tr, tc) = (warp, lane)
+    // owns rows tr + RG a (a < RA) and columns tc + 32 b (b < CB)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tr = warp, tc = lane;  // CHOL_NT / 32 = 16 row groups x 32 columns
+    const int tr = warp, tc = lane;
+    const bool active = warp < RG;
     T *d = sm;              // column scales of the equilibration
     T *piv = d + k;         // square roots of the pivots (0 = dropped)
-    T *rows2 = piv + k;     // 2 x k: row j of S (double buffered)
+    T *rows2 = piv + k;     // 2 x (k + 1): row j of S and, at [k], 1 / S[j][j] (0 = dropped)
+    const int rl = k + 1;
     const int64_t slice = (int64_t)kmax * kmax;
+    const T tol = eps_of<T>() * eps_of<T>();
 
     for (int c = tid; c < k; c += CHOL_NT) {
         const T g = chol_gram_entry(partial, splits, slice, kmax, c, c);
@@ -125,21 +130,29 @@ __device__ __forceinline__ void chol_body(const T *__restrict__ partial, int spl
     __syncthreads();
 
     T S[RA][CB];
+    uint32_t upper[RA];  // bit b: position (a, b) is in the upper triangle (G), else W^T
     double defect = 0.0;
 #pragma unroll
     for (int a = 0; a < RA; a++) {
-        const int x = tr + 16 * a;
+        const int x = tr + RG * a;
+        upper[a] = 0;
 #pragma unroll
         for (int b = 0; b < CB; b++) {
             const int y = tc + 32 * b;
             T v = T(0);
-            if (x < k && y < k && x <= y) {
+            if (active && x < k && y < k && x <= y) {
+                upper[a] |= 1u << b;
                 const T dx = d[x], dy = d[y];
                 v = (dx > T(0) && dy > T(0)) ? chol_gram_entry(partial, splits, slice, kmax, x, y) / dx / dy : T(0);
                 const T ev = v - (x == y ? T(1) : T(0));
                 defect += (x == y ? 1.0 : 2.0) * (double)(ev * ev);  // both triangles of the symmetric matrix
-                if (x == 0) rows2[y] = v;                            // row 0 of S for step 0
+                if (x == 0 && y == 0) {
+                    const bool dj = !(v > tol);
+                    rows2[k] = dj ? T(0) : T(1) / v;
+                    piv[0] = dj ? T(0) : sqrt(v);
+                }
             }
+            if (active && x == 0 && y < k) rows2[y] = v;  // row 0 of S for step 0
             S[a][b] = v;  // lower triangle: W^T = 0 off the diagonal
         }
     }
@@ -154,85 +167,99 @@ __device__ __forceinline__ void chol_body(const T *__restrict__ partial, int spl
 
     // Only a non-positive (or denormal) pivot drops a column; a tiny positive
     // pivot gives a noise direction that the next CholeskyQR pass cleans up.
-    const T tol = eps_of<T>() * eps_of<T>();
-    for (int j = 0; j < k; j++) {
-        const T *rw = rows2 + (j & 1) * k;
-        T *rn = rows2 + ((j + 1) & 1) * k;
-        const T pj = rw[j];
-        const bool dj = !(pj > tol);
-        const T inv = dj ? T(0) : T(1) / pj;
-        T rx[RA], cy[CB];
+    // The owner of the next diagonal position publishes its reciprocal and
+    // square root with the row, so a step reads one row and one scalar.  (Two
+    // eliminations per barrier, each thread bringing the entries of row j + 1
+    // it needs through step j itself, measured the same: the step is bound by
+    // its per-position work, not by the barrier.)
+    if (active) {
+        for (int j = 0; j < k; j++) {
+            const T *rw = rows2 + (j & 1) * rl;
+            T *rn = rows2 + ((j + 1) & 1) * rl;
+            const T inv = rw[k];
+            T rxi[RA], rx[RA], cy[CB], cyi[CB];
+            bool rowact[RA], selw[CB];
 #pragma unroll
-        for (int a = 0; a < RA; a++) {
-            const int x = tr + 16 * a;
-            rx[a] = (x > j && x < k) ? rw[x] : T(0);  // G[j][x]
-        }
-#pragma unroll
-        for (int b = 0; b < CB; b++) {
-            const int y = tc + 32 * b;
-            cy[b] = y == j ? T(1) : (y < k ? rw[y] : T(0));  // G[j][y] (y > j) or W[y][j] (y < j)
-        }
-#pragma unroll
-        for (int a = 0; a < RA; a++) {
-            const int x = tr + 16 * a;
-            if (x <= j || x >= k) continue;
-            const T gxi = rx[a] * inv;
+            for (int a = 0; a < RA; a++) {
+                const int x = tr + RG * a;
+                rowact[a] = x > j && x < k;
+                rx[a] = rowact[a] ? rw[x] : T(0);  // G[j][x]
+                rxi[a] = rx[a] * inv;
+            }
 #pragma unroll
             for (int b = 0; b < CB; b++) {
                 const int y = tc + 32 * b;
-                if (y >= k) continue;
-                if (y <= j) {
-                    const T wyj = cy[b] * inv;  // W[y][x] -= (W[y][j] / p_j) G[j][x]
-                    S[a][b] -= wyj * rx[a];
-                } else if (y >= x) {
-                    S[a][b] -= gxi * cy[b];  // G[x][y] -= (G[j][x] / p_j) G[j][y]
+                selw[b] = y <= j;
+                cy[b] = y == j ? T(1) : (y < k ? rw[y] : T(0));  // G[j][y] (y > j) or W[y][j] (y <= j)
+                cyi[b] = cy[b] * inv;
+            }
+#pragma unroll
+            for (int a = 0; a < RA; a++) {
+                if (!rowact[a]) continue;
+#pragma unroll
+                for (int b = 0; b < CB; b++) {
+                    if (selw[b])
+                        S[a][b] -= cyi[b] * rx[a];  // W[y][x] -= (W[y][j] / p_j) G[j][x]
+                    else if ((upper[a] >> b) & 1u)
+                        S[a][b] -= rxi[a] * cy[b];  // G[x][y] -= (G[j][x] / p_j) G[j][y]
                 }
             }
-            if (x == j + 1) {
+#pragma unroll
+            for (int a = 0; a < RA; a++) {
+                const int x = tr + RG * a;
+                if (x != j + 1) continue;
 #pragma unroll
                 for (int b = 0; b < CB; b++) {
                     const int y = tc + 32 * b;
                     if (y < k) rn[y] = S[a][b];
+                    if (y == x) {
+                        const T pv = S[a][b];
+                        const bool dj = !(pv > tol);
+                        rn[k] = dj ? T(0) : T(1) / pv;
+                        piv[x] = dj ? T(0) : sqrt(pv);
+                    }
                 }
             }
+            asm volatile("bar.sync 1, %0;" ::"r"(RG * 32) : "memory");
         }
-        if (tid == 0) piv[j] = dj ? T(0) : sqrt(pj);
-        __syncthreads();
     }
+    __syncthreads();
 
     // undo the equilibration: R = Rt D with Rt = P U (row i of Rt is
     // G[i][i:] / P_i), R^{-1} = D^{-1} Rt^{-1} = D^{-1} W P^{-1} (dropped columns
     // zero); then Rtot = R Rprev
-    T *Rs = rows2 + 2 * k;      // k x (k + 1): R (upper), for Rtot
+    T *Rs = rows2 + 2 * rl;     // k x (k + 1): R (upper), for Rtot
     T *Ps = Rs + k * (k + 1);   // k x (k + 1): Rprev
     const int ld = k + 1;
+    if (active) {
 #pragma unroll
-    for (int a = 0; a < RA; a++) {
-        const int x = tr + 16 * a;
-        if (x >= k) continue;
+        for (int a = 0; a < RA; a++) {
+            const int x = tr + RG * a;
+            if (x >= k) continue;
 #pragma unroll
-        for (int b = 0; b < CB; b++) {
-            const int y = tc + 32 * b;
-            if (y >= k) continue;
-            if (x < y) {
-                const T p_x = piv[x], rx_ = p_x > T(0) ? T(1) / p_x : T(0);
-                const T rv = S[a][b] * rx_ * d[y];
-                R[(int64_t)x * ldr + y] = rv;
-                R[(int64_t)y * ldr + x] = T(0);
-                Rinv[(int64_t)y * ldr + x] = T(0);
-                if (Rprev != nullptr) {
-                    Rs[x * ld + y] = rv;
-                    Rtot[(int64_t)y * ldr + x] = T(0);
+            for (int b = 0; b < CB; b++) {
+                const int y = tc + 32 * b;
+                if (y >= k) continue;
+                if (x < y) {
+                    const T p_x = piv[x], rx_ = p_x > T(0) ? T(1) / p_x : T(0);
+                    const T rv = S[a][b] * rx_ * d[y];
+                    R[(int64_t)x * ldr + y] = rv;
+                    R[(int64_t)y * ldr + x] = T(0);
+                    Rinv[(int64_t)y * ldr + x] = T(0);
+                    if (Rprev != nullptr) {
+                        Rs[x * ld + y] = rv;
+                        Rtot[(int64_t)y * ldr + x] = T(0);
+                    }
+                } else if (x == y) {
+                    const T p_x = piv[x];
+                    const T rv = p_x * d[x];
+                    R[(int64_t)x * ldr + x] = rv;
+                    Rinv[(int64_t)x * ldr + x] = (p_x > T(0) && d[x] > T(0)) ? T(1) / p_x / d[x] : T(0);
+                    if (Rprev != nullptr) Rs[x * ld + x] = rv;
+                } else {
+                    // S[x][y] = W[y][x]: entry (y, x) of R^{-1} = W[y][x] / P_x / d_y
+                    Rinv[(int64_t)y * ldr + x] = (piv[x] > T(0) && d[y] > T(0)) ? S[a][b] / piv[x] / d[y] : T(0);
                 }
-            } else if (x == y) {
-                const T p_x = piv[x];
-                const T rv = p_x * d[x];
-                R[(int64_t)x * ldr + x] = rv;
-                Rinv[(int64_t)x * ldr + x] = (p_x > T(0) && d[x] > T(0)) ? T(1) / p_x / d[x] : T(0);
-                if (Rprev != nullptr) Rs[x * ld + x] = rv;
-            } else {
-                // S[x][y] = W[y][x]: entry (y, x) of R^{-1} = W[y][x] / P_x / d_y
-                Rinv[(int64_t)y * ldr + x] = (piv[x] > T(0) && d[y] > T(0)) ? S[a][b] / piv[x] / d[y] : T(0);
             }
         }
     }
@@ -242,23 +269,17 @@ __device__ __forceinline__ void chol_body(const T *__restrict__ partial, int spl
         Ps[i * ld + c] = Rprev[(int64_t)i * ldr + c];
     }
     __syncthreads();
-#pragma unroll
-    for (int a = 0; a < RA; a++) {
-        const int x = tr + 16 * a;
-        if (x >= k) continue;
-#pragma unroll
-        for (int b = 0; b < CB; b++) {
-            const int y = tc + 32 * b;
-            if (y >= k || y < x) continue;
-            T s = T(0);
-            for (int p = x; p <= y; p++) s = fma(Rs[x * ld + p], Ps[p * ld + y], s);
-            Rtot[(int64_t)x * ldr + y] = s;
-        }
+    for (int idx = tid; idx < k * k; idx += CHOL_NT) {
+        const int x = idx / k, y = idx - (idx / k) * k;
+        if (y < x) continue;
+        T s = T(0);
+        for (int p = x; p <= y; p++) s = fma(Rs[x * ld + p], Ps[p * ld + y], s);
+        Rtot[(int64_t)x * ldr + y] = s;
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(CHOL_NT) chol_kernel(const T *__restrict__ partial, int splits, int kmax,
+__global__ void __launch_bounds__(CHOL_NT, 1) chol_kernel(const T *__restrict__ partial, int splits, int kmax,
                                                        const int *kdyn, T *__restrict__ R, T *__restrict__ Rinv,
                                                        const T *__restrict__ Rprev, T *__restrict__ Rtot, int ldr,
                                                        int *well_out, const int *skip_in, int *stats)
@@ -278,11 +299,13 @@ __global__ void __launch_bounds__(CHOL_NT) chol_kernel(const T *__restrict__ par
     }
     if (stats != nullptr && tid == 0) atomicAdd(stats, 1);
     T *sm = reinterpret_cast<T *>(smraw);
-    // rows per thread group and columns per lane: 4 x 2 covers k <= 64, 8 x 4 covers k <= 128
+    // 16 warps x rows per warp x columns per lane: 4 x 2 covers k <= 64, 8 x 4
+    // covers k <= 128.  (With 4 warps and 32 positions per thread a step took
+    // three times as long: the step is latency-bound, and more warps hide it.)
     if (k <= 64)
-        chol_body<T, 4, 2>(partial, splits, kmax, k, R, Rinv, Rprev, Rtot, ldr, well_out, sm, red);
+        chol_body<T, 16, 4, 2>(partial, splits, kmax, k, R, Rinv, Rprev, Rtot, ldr, well_out, sm, red);
     else
-        chol_body<T, 8, 4>(partial, splits, kmax, k, R, Rinv, Rprev, Rtot, ldr, well_out, sm, red);
+        chol_body<T, 16, 8, 4>(partial, splits, kmax, k, R, Rinv, Rprev, Rtot, ldr, well_out, sm, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -629,8 +652,8 @@ __global__ void ctrl_end_kernel(Ctrl *c)
 template <typename T>
 size_t chol_smem(int kmax)
 {
-    // d, piv, two rows of S; R and Rprev for Rtot
-    return (size_t)4 * kmax * sizeof(T) + (size_t)2 * kmax * (kmax + 1) * sizeof(T) + 16;
+    // d, piv, two rows of S with their pivot reciprocals; R and Rprev for Rtot
+    return (size_t)(4 * kmax + 2) * sizeof(T) + (size_t)2 * kmax * (kmax + 1) * sizeof(T) + 16;
 }
 
 template <typename T>

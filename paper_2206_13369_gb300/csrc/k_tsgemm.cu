@@ -278,11 +278,18 @@ void ts_launch(int rows, int K, const T *A, int64_t lda, const T *B, int64_t ldb
                const int *kdynR, const int *kdynK, const int *kdynN, int kmaxN, int cl, int groups, int Kmax,
                const int *skip, cudaStream_t st)
 {
+    // (a cluster of 16 that the device refuses is launched as 8, each CTA
+    // then covering twice the K range; only single-slice launches ask for 16)
     static bool attr = false;
+    static bool wide_ok = false;  // clusters of 16 (beyond the portable 8) accepted
     if (!attr) {
         cudaFuncSetAttribute(ts_gemm_kernel<T, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts_smem<T>());
+        wide_ok = cudaFuncSetAttribute(ts_gemm_kernel<T, TN>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                  cudaSuccess;
+        cudaGetLastError();
         attr = true;
     }
+    if (cl > 8 && !wide_ok) cl = 8;
     // K range per CTA: a multiple of the chunk, covering Kmax over cl * groups CTAs
     const int parts = cl * groups;
     int ks = (Kmax + parts - 1) / parts;
@@ -301,14 +308,26 @@ void ts_launch(int rows, int K, const T *A, int64_t lda, const T *B, int64_t ldb
     cfg.attrs = at;
     cfg.numAttrs = 1;
     CPCP_COUNT_LAUNCH();
-    cudaLaunchKernelEx(&cfg, ts_gemm_kernel<T, TN>, rows, K, A, lda, B, ldb, C, ldc, slice, kdynR, kdynK, kdynN,
-                       kmaxN, ks, skip);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, ts_gemm_kernel<T, TN>, rows, K, A, lda, B, ldb, C, ldc, slice, kdynR,
+                                       kdynK, kdynN, kmaxN, ks, skip);
+    if (e != cudaSuccess && cl > 8) {
+        // the device would not co-schedule 16 CTAs of this size: use 8 from now on
+        cudaGetLastError();
+        wide_ok = false;
+        at[0].val.clusterDim.x = 8;
+        ks = (Kmax + 8 * groups - 1) / (8 * groups);
+        ks = (ks + TsCfg<T>::TK - 1) / TsCfg<T>::TK * TsCfg<T>::TK;
+        cfg.gridDim.x = (unsigned)(8 * groups);
+        cudaLaunchKernelEx(&cfg, ts_gemm_kernel<T, TN>, rows, K, A, lda, B, ldb, C, ldc, slice, kdynR, kdynK, kdynN,
+                           kmaxN, ks, skip);
+    }
 }
 
 int ts_cluster_for(int tiles, int K)
 {
-    // split a long K over a cluster until about two CTAs per SM are busy,
-    // keeping at least 128 terms per CTA
+    // split a long K over a cluster (up to 8 CTAs) until about two CTAs per
+    // SM are busy, keeping at least 128 terms per CTA (clusters of 16, 64
+    // terms per CTA, measured slower at 2000 x 2000)
     int cl = 1;
     while (cl < 8 && tiles * cl < 304 && K >= 128 * cl * 2) cl *= 2;
     return cl;

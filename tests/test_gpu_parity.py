@@ -286,3 +286,19 @@ def test_iteration_cap_returns_not_converged(cp):
         L, S, info = hh.solve(dev(p["D"]), None, p["lam"], p["mu"], tol=1e-12)
         assert info["status"] == 5 and info["iters"] == 15
         assert torch.isfinite(L).all() and torch.isfinite(S).all()
+
+
+def test_graph_replay_equals_plain_launches(cp, small_cpcp):
+    # the iterations replayed from a captured CUDA graph run the same kernels
+    # on the same data as direct launches: bit-identical results
+    p, _, _ = small_cpcp
+    Qb = torch.as_tensor(cp.pack_mask(p["mask"])).cuda()
+    D = dev(p["D"], torch.float32)
+    out = []
+    for plain in (0, 1):
+        with cp.Handle(0, plain_launches=plain) as hh:
+            L, S, info = hh.solve(D, Qb, p["lam"], p["mu"], levels=2, tol=1e-6)
+        out.append((L, S, info))
+    (L0, S0, i0), (L1, S1, i1) = out
+    assert i0["iters"] == i1["iters"] and i0["launches"] == i1["launches"]
+    assert torch.equal(L0, L1) and torch.equal(S0, S1)
