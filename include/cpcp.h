@@ -103,11 +103,12 @@ typedef struct {
                               1 = half steps: each iteration projects once onto the previous
                               iteration's right or left singular subspace, alternating
                               (one contraction with M_H, one CholeskyQR2, one core SVD) */
-    int pass_tc;           /* cpcp_solve, fp32: nonzero runs the fused fine pass on the tensor
-                              cores (tcgen05, three TF32 products per fp32 product, 2^-22 relative
-                              per product) wherever D and S meet its alignment rules (16-byte
-                              aligned base, leading dimension a multiple of 4); its rel-KKT floor
-                              is about 2e-6.  0 (default): the SIMT pass */
+    int pass_simt;         /* cpcp_solve, fp32: nonzero runs the fused fine pass on the SIMT
+                              cores.  0 (default): the tensor-core pass (tcgen05, each factor
+                              entry split into three TF32 parts, the six products of order
+                              >= 2^-22, small and large terms in separate fp32 accumulators)
+                              wherever D and S meet its alignment rules (16-byte aligned base,
+                              leading dimension a multiple of 4); else the SIMT pass */
     int plain_launches;    /* cpcp_solve: nonzero launches every kernel of every iteration from
                               the host; 0 (default) captures an iteration's kernels in a CUDA
                               graph the second time the same (level, buffer parity) comes up and

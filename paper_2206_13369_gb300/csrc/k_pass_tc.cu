@@ -10,20 +10,27 @@
 // successive round-to-nearest (11 significant bits each, so the split is exact
 // to 2^-33), and
 //     a b ~ a_m b_m + a_l b_h + a_h b_l + a_m b_h + a_h b_m + a_h b_h
-// (the dropped terms are below 2^-32 relative).  The six products are one
-// TF32 contraction over an extended K: A6 = [a_m, a_l, a_h, a_m, a_h, a_h] and
-// B6 = [b_m, b_h, b_l, b_h, b_m, b_h], blocks of the live K each, smallest
-// terms first, accumulated in fp32 in tensor memory.  (Two-term splitting,
-// a b ~ a_h b_h + a_h b_l + a_l b_h, represents each factor only to 2^-22 and
-// left a rel-KKT floor near 2e-6, because the momentum step cancels most of
-// L-hat.)
+// (the dropped terms are below 2^-32 relative).  The five small products
+// accumulate in one fp32 TMEM accumulator and a_h b_h in another; the
+// epilogue adds the two in fp32.  Each operand stage holds the three parts of
+// a 16-wide K slice of A^ and of B^ (64-byte swizzle), and the MMA issuer
+// pairs them: six MMAs per K step of 8.
 //
-// One persistent CTA per SM walks 128 x 64 output tiles.  Warp roles:
-//   warp 0   TMA producer of the operand stages (A6, B6: 32 K each)
-//   warp 1   MMA issuer: tcgen05.mma kind::tf32, M = 128, N = 64, K = 8
-//   warp 2   TMEM allocator (two 64-column fp32 accumulators, double buffered)
+// Measured alternatives, each worse on the 2000 x 2000 rank-50 workload:
+// two-term splitting (a_h b_h + a_h b_l + a_l b_h) represents a factor only
+// to 2^-22, and one accumulator shared by all six products loses the small
+// terms' low bits to the large running sum; both left a rel-KKT floor near
+// 1.7e-6, because the momentum step cancels most of L-hat.  Laying the six
+// products out as one contraction over an extended K = 6 K re-read the
+// operands six times from L2.
+//
+// One persistent CTA per SM walks 128 x 128 output tiles.  Warp roles:
+//   warp 0   TMA producer of the operand stages (A^ and B^, three parts each)
+//   warp 1   MMA issuer: tcgen05.mma kind::tf32, M = 128, N = 128, K = 8
+//   warp 2   TMEM allocator (per buffer a 128-column accumulator for a_h b_h and
+//            one for the small products; two buffers: all 512 columns)
 //   warp 3   TMA producer of the epilogue tiles: D, S_k, S_{k-1} in 32-column
-//            halves (128-byte swizzle), double buffered
+//            quarters (128-byte swizzle), double buffered
 //   warps 4-7 epilogue: tcgen05.ld of the accumulator (one TMEM lane quarter
 //            per warp, one row per thread), the elementwise step, stores.
 // So the HBM stream of the epilogue inputs runs while the tensor cores work
@@ -45,18 +52,18 @@ namespace cpcp {
 namespace {
 
 constexpr int TBM = 128;   // tile rows = TMEM lanes
-constexpr int TBN = 64;    // tile columns = accumulator columns
-constexpr int TBK = 32;    // K per operand stage: 128 bytes of fp32
-constexpr int HALF = 32;   // epilogue half-tile columns (128 bytes of fp32)
-constexpr int OPS = 4;     // operand stages
-constexpr int EPS = 2;     // epilogue half-tile buffers
+constexpr int TBN = 128;   // tile columns = accumulator columns
+constexpr int TBK = 16;    // K per operand stage: 64 bytes of fp32
+constexpr int HALF = 32;   // epilogue sub-tile columns (128 bytes of fp32)
+constexpr int OPS = 2;     // operand stages
+constexpr int EPS = 2;     // epilogue sub-tile buffers
 constexpr int NT = 256;
-constexpr uint32_t A_BYTES = TBM * TBK * 4;             // 16 KB
-constexpr uint32_t B_BYTES = TBN * TBK * 4;             // 8 KB
-constexpr uint32_t OP_BYTES = A_BYTES + B_BYTES;
+constexpr uint32_t A_BYTES = TBM * TBK * 4;             // 8 KB per part
+constexpr uint32_t B_BYTES = TBN * TBK * 4;             // 8 KB per part
+constexpr uint32_t OP_BYTES = 3 * A_BYTES + 3 * B_BYTES;  // three parts of each
 constexpr uint32_t EP_TILE = TBM * HALF * 4;            // 16 KB per array
 constexpr uint32_t EP_BYTES = 3 * EP_TILE;              // D, S_k, S_{k-1}
-constexpr uint32_t TMEM_COLS = 2 * TBN;
+constexpr uint32_t TMEM_COLS = 4 * TBN;  // two buffers x (large, small)
 constexpr size_t SMEM_BYTES = 1024 + OPS * (size_t)OP_BYTES + EPS * (size_t)EP_BYTES + 256;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -126,19 +133,19 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// K-major operand, 128-byte swizzle, 128-byte rows, 8-row atoms 1024 bytes apart
-__device__ __forceinline__ uint64_t smem_desc_sw128(const void *p)
+// K-major operand, 64-byte swizzle, 64-byte rows, 8-row atoms 512 bytes apart
+__device__ __forceinline__ uint64_t smem_desc_sw64(const void *p)
 {
     const uint64_t addr = smem_u32(p);
     uint64_t d = (addr >> 4) & 0x3FFFull;
-    d |= (uint64_t)(16 >> 4) << 16;    // leading dimension byte offset (unused here)
-    d |= (uint64_t)(1024 >> 4) << 32;  // stride dimension byte offset
-    d |= 1ull << 46;                   // descriptor version of tcgen05
-    d |= 2ull << 61;                   // 128-byte swizzle
+    d |= (uint64_t)(16 >> 4) << 16;   // leading dimension byte offset (unused here)
+    d |= (uint64_t)(512 >> 4) << 32;  // stride dimension byte offset
+    d |= 1ull << 46;                  // descriptor version of tcgen05
+    d |= 4ull << 61;                  // 64-byte swizzle
     return d;
 }
 
-// kind::tf32: fp32 accumulator, TF32 A and B (both K-major), M = 128, N = 64
+// kind::tf32: fp32 accumulator, TF32 A and B (both K-major), M = 128, N = 128
 __device__ __forceinline__ uint32_t idesc_tf32()
 {
     return (1u << 4)                        // accumulator format fp32
@@ -194,8 +201,8 @@ __device__ __forceinline__ int live_k(const int *rk, const int *rp, const Ctrl *
 }
 
 struct TcMaps {
-    CUtensorMap a6, b6;     // extended split factors (K-major, 128-byte swizzle)
-    CUtensorMap d, sk, sp;  // epilogue inputs (32-column boxes, 128-byte swizzle)
+    CUtensorMap a[3], b[3];  // split factors: high, middle, low parts (K-major, 64-byte swizzle)
+    CUtensorMap d, sk, sp;   // epilogue inputs (32-column boxes, 128-byte swizzle)
 };
 
 struct TcArgs {
@@ -236,7 +243,7 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
     const int tiles_n = (a.n + TBN - 1) / TBN;
     const int ntiles = ((a.m + TBM - 1) / TBM) * tiles_n;
     const int K = live_k(a.rk, a.rp, a.ctrl);
-    const int nkb = (6 * K + TBK - 1) / TBK;
+    const int nkb = (K + TBK - 1) / TBK;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < OPS; s++) {
@@ -277,8 +284,11 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
                     if (i >= OPS && !mbar_wait(&op_empty[s], ((i / OPS) & 1) ^ 1, abort_flag)) break;
                     uint8_t *st = sOp + s * OP_BYTES;
                     mbar_expect_tx(&op_full[s], OP_BYTES);
-                    tma_load_2d(st, &maps.a6, &op_full[s], kb * TBK, rb);
-                    tma_load_2d(st + A_BYTES, &maps.b6, &op_full[s], kb * TBK, cb);
+#pragma unroll
+                    for (int q = 0; q < 3; q++) {
+                        tma_load_2d(st + q * A_BYTES, &maps.a[q], &op_full[s], kb * TBK, rb);
+                        tma_load_2d(st + 3 * A_BYTES + q * B_BYTES, &maps.b[q], &op_full[s], kb * TBK, cb);
+                    }
                 }
             }
             // drain: the last phase issued on each stage has landed (time bound
@@ -318,7 +328,8 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
                 const int buf = lt & 1;
                 if (lt >= 2 && !mbar_wait(&acc_empty[buf], ((lt >> 1) - 1) & 1, abort_flag)) break;
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(buf * TBN);
+                const uint32_t d = tmem + (uint32_t)(buf * 2 * TBN);  // a_h b_h
+                const uint32_t dsm = d + (uint32_t)TBN;               // the five small products
                 bool ok = true;
                 for (int kb = 0; kb < nkb; kb++, i++) {
                     const int s = i % OPS;
@@ -328,10 +339,22 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
                     }
                     tc_fence_after();
                     const uint8_t *st = sOp + s * OP_BYTES;
-                    const uint64_t ad = smem_desc_sw128(st), bd = smem_desc_sw128(st + A_BYTES);
+                    uint64_t ad[3], bd[3];
 #pragma unroll
-                    for (int kk = 0; kk < TBK / 8; kk++)  // 8 TF32 = 32 bytes = 2 descriptor units per step
-                        umma_tf32(d, ad + 2 * kk, bd + 2 * kk, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                    for (int q = 0; q < 3; q++) {
+                        ad[q] = smem_desc_sw64(st + q * A_BYTES);
+                        bd[q] = smem_desc_sw64(st + 3 * A_BYTES + q * B_BYTES);
+                    }
+                    // parts (0 = h, 1 = m, 2 = l) of the five small products
+                    constexpr int PA[5] = {1, 2, 0, 1, 0}, PB[5] = {1, 0, 2, 0, 1};
+#pragma unroll
+                    for (int kk = 0; kk < TBK / 8; kk++) {  // 8 TF32 = 32 bytes = 2 descriptor units per step
+                        const uint32_t first = (kb > 0 || kk > 0) ? 1u : 0u;
+#pragma unroll
+                        for (int t = 0; t < 5; t++)
+                            umma_tf32(dsm, ad[PA[t]] + 2 * kk, bd[PB[t]] + 2 * kk, idesc, (first || t > 0) ? 1u : 0u);
+                        umma_tf32(d, ad[0] + 2 * kk, bd[0] + 2 * kk, idesc, first);
+                    }
                     umma_commit(&op_empty[s]);
                 }
                 if (!ok) break;
@@ -350,9 +373,18 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
         for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, lt++) {
             const int buf = lt & 1;
             const int rb = (t / tiles_n) * TBM, cb = (t % tiles_n) * TBN;
+            const int row = rb + r;
+            // the row's mask words for this tile, loaded before the wait so that
+            // their latency overlaps it (one word per 32-column sub-tile)
+            uint32_t words[TBN / HALF];
+#pragma unroll
+            for (int w = 0; w < TBN / HALF; w++) {
+                const int c0 = cb + w * HALF;
+                words[w] = (a.Q != nullptr && row < a.m && c0 < a.n) ? a.Q[(int64_t)row * a.ldq + (c0 >> 5)]
+                                                                     : 0xffffffffu;
+            }
             if (!mbar_wait(&acc_full[buf], (lt >> 1) & 1, abort_flag)) break;
             tc_fence_after();
-            const int row = rb + r;
             bool ok = true;
             for (int h = 0; h < TBN / HALF; h++, i++) {
                 const int s = i % EPS;
@@ -362,22 +394,22 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
                 }
                 float acc[HALF];
                 {
-                    float v[16];
-                    const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TBN + h * HALF);
-                    tmem_ld16(ta, v);
+                    float v[16], w[16];
+                    const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * TBN + h * HALF);
 #pragma unroll
-                    for (int j = 0; j < 16; j++) acc[j] = nkb > 0 ? v[j] : 0.f;
-                    tmem_ld16(ta + 16, v);
+                    for (int half = 0; half < 2; half++) {
+                        tmem_ld16(ta + 16 * half, v);
+                        tmem_ld16(ta + TBN + 16 * half, w);
 #pragma unroll
-                    for (int j = 0; j < 16; j++) acc[16 + j] = nkb > 0 ? v[j] : 0.f;
+                        for (int j = 0; j < 16; j++) acc[16 * half + j] = nkb > 0 ? v[j] + w[j] : 0.f;
+                    }
                 }
                 const uint8_t *tD = sEp + s * EP_BYTES;
                 const uint8_t *tS = tD + EP_TILE;
                 const uint8_t *tP = a.has_sp ? tD + 2 * EP_TILE : tS;
                 const int c0 = cb + h * HALF;
                 if (row < a.m) {
-                    const uint32_t *qrow = a.Q ? a.Q + (int64_t)row * a.ldq : nullptr;
-                    const uint32_t word = qrow && c0 < a.n ? qrow[c0 >> 5] : 0xffffffffu;  // 32 columns, one word
+                    const uint32_t word = words[h];  // 32 columns, one word
 #pragma unroll
                     for (int c4 = 0; c4 < HALF / 4; c4++) {
                         const int col = c0 + 4 * c4;
@@ -431,41 +463,37 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
 }
 
 // A^ = [(1 + beta) A_k, -beta A_{k-1}] and B^ = [B_k, B_{k-1}] split into
-// three TF32 parts each and laid out as the extended operands A6, B6 (block j
-// of K columns pairs the parts of product j; zero padding to the next 32)
+// three TF32 parts each (P[0] high, P[1] middle, P[2] low; zero padding of the
+// live K to the next 16)
+struct SplitOut {
+    float *a[3], *b[3];
+};
+
 __global__ void tf32_split_kernel(int m, int n, const float *__restrict__ Ak, const float *__restrict__ Ap,
                                   int64_t lda, const float *__restrict__ Bk, const float *__restrict__ Bp,
-                                  int64_t ldb, const int *rk_p, const int *rp_p, const Ctrl *ctrl,
-                                  float *__restrict__ A6, float *__restrict__ B6, int64_t ldk)
+                                  int64_t ldb, const int *rk_p, const int *rp_p, const Ctrl *ctrl, SplitOut o,
+                                  int64_t ldk)
 {
     const int rk = rk_p ? *rk_p : 0;
     const int rp = (rp_p && ctrl->beta != 0.0) ? *rp_p : 0;
-    const int K = rk + rp, K6 = 6 * K, Kp = (K6 + TBK - 1) / TBK * TBK;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;  // column of the live K
+    const int K = rk + rp, Kp = (K + TBK - 1) / TBK * TBK;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int row = blockIdx.y;
-    // parts (0 = h, 1 = m, 2 = l) of product j = 0..5: A6 and B6
-    constexpr int PA[6] = {1, 2, 0, 1, 0, 0}, PB[6] = {1, 0, 2, 0, 1, 0};
-    if (c < K) {
-        const float ck = (float)(1.0 + ctrl->beta), cp = (float)(-ctrl->beta);
-        if (row < m) {
-            const float v = c < rk ? Ak[(int64_t)row * lda + c] * ck : Ap[(int64_t)row * lda + c - rk] * cp;
-            const float h = tf32_rn(v), r1 = v - h, md = tf32_rn(r1), lo = tf32_rn(r1 - md);
-            const float part[3] = {h, md, lo};
-#pragma unroll
-            for (int j = 0; j < 6; j++) A6[(int64_t)row * ldk + j * K + c] = part[PA[j]];
-        }
-        if (row < n) {
-            const float v = c < rk ? Bk[(int64_t)row * ldb + c] : Bp[(int64_t)row * ldb + c - rk];
-            const float h = tf32_rn(v), r1 = v - h, md = tf32_rn(r1), lo = tf32_rn(r1 - md);
-            const float part[3] = {h, md, lo};
-#pragma unroll
-            for (int j = 0; j < 6; j++) B6[(int64_t)row * ldk + j * K + c] = part[PB[j]];
-        }
-    } else if (c < K + (Kp - K6)) {
-        // zero padding of the last K block
-        const int z = K6 + (c - K);
-        if (row < m) A6[(int64_t)row * ldk + z] = 0.f;
-        if (row < n) B6[(int64_t)row * ldk + z] = 0.f;
+    if (c >= Kp) return;
+    const float ck = (float)(1.0 + ctrl->beta), cp = (float)(-ctrl->beta);
+    if (row < m) {
+        const float v = c < rk ? Ak[(int64_t)row * lda + c] * ck : (c < K ? Ap[(int64_t)row * lda + c - rk] * cp : 0.f);
+        const float h = tf32_rn(v), r1 = v - h, md = tf32_rn(r1);
+        o.a[0][(int64_t)row * ldk + c] = h;
+        o.a[1][(int64_t)row * ldk + c] = md;
+        o.a[2][(int64_t)row * ldk + c] = tf32_rn(r1 - md);
+    }
+    if (row < n) {
+        const float v = c < rk ? Bk[(int64_t)row * ldb + c] : (c < K ? Bp[(int64_t)row * ldb + c - rk] : 0.f);
+        const float h = tf32_rn(v), r1 = v - h, md = tf32_rn(r1);
+        o.b[0][(int64_t)row * ldk + c] = h;
+        o.b[1][(int64_t)row * ldk + c] = md;
+        o.b[2][(int64_t)row * ldk + c] = tf32_rn(r1 - md);
     }
 }
 
@@ -490,18 +518,20 @@ EncodeTiledFn encode_fn()
 }
 
 // fp32 row-major (rows x cols, leading dimension ld) map with boxes of
-// box_rows x 32 columns and 128-byte swizzle
-bool make_map_f32(CUtensorMap *map, const float *base, uint64_t cols, uint64_t rows, uint64_t ld, uint32_t box_rows)
+// box_rows x box_cols (32 columns: 128-byte swizzle; 16 columns: 64-byte)
+bool make_map_f32(CUtensorMap *map, const float *base, uint64_t cols, uint64_t rows, uint64_t ld, uint32_t box_rows,
+                  uint32_t box_cols = 32)
 {
     EncodeTiledFn fn = encode_fn();
     if (fn == nullptr) return false;
     if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld * 4) % 16 != 0) return false;
     cuuint64_t dims[2] = {cols, rows};
     cuuint64_t strides[1] = {ld * 4};
-    cuuint32_t box[2] = {32, box_rows};
+    cuuint32_t box[2] = {box_cols, box_rows};
     cuuint32_t es[2] = {1, 1};
+    const CUtensorMapSwizzle sw = box_cols == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -519,21 +549,28 @@ int sm_count()
 
 }  // namespace
 
-size_t pass_tc_split_elems(int rows, int kmax) { return (size_t)rows * (size_t)((12 * kmax + TBK - 1) / TBK * TBK); }
+// three parts, each rows x round16(2 kmax)
+size_t pass_tc_split_elems(int rows, int kmax) { return 3 * (size_t)rows * (size_t)((2 * kmax + TBK - 1) / TBK * TBK); }
 
 // The fused fine pass on the tensor cores; false (nothing launched) when an
 // operand does not meet the TMA rules (16-byte aligned bases and strides) or
-// the tensor maps cannot be made.  A6 (m rows) and B6 (n rows) are scratch of
-// pass_tc_split_elems each, leading dimension ldk = round32(12 kmax).
-bool launch_pass_tc(const PassArgs<float> &p, int kmax, float *A6, float *B6, int *err, cudaStream_t st)
+// the tensor maps cannot be made.  A3 (m rows) and B3 (n rows) are scratch of
+// pass_tc_split_elems each: three parts of leading dimension ldk =
+// round16(2 kmax).
+bool launch_pass_tc(const PassArgs<float> &p, int kmax, float *A3, float *B3, int *err, cudaStream_t st)
 {
     if (p.M == nullptr || p.Sout == nullptr || p.Ak == nullptr || p.Bk == nullptr) return false;
     if (p.ldfa != p.ldfap || p.ldfb != p.ldfbp) return false;
-    const int64_t ldk = (12 * kmax + TBK - 1) / TBK * TBK;
+    const int64_t ldk = (2 * kmax + TBK - 1) / TBK * TBK;
     const bool has_sp = p.Sp != nullptr && p.Sp != p.Sk;
     TcMaps maps;
-    if (!make_map_f32(&maps.a6, A6, (uint64_t)ldk, (uint64_t)p.m, (uint64_t)ldk, TBM)) return false;
-    if (!make_map_f32(&maps.b6, B6, (uint64_t)ldk, (uint64_t)p.n, (uint64_t)ldk, TBN)) return false;
+    SplitOut so;
+    for (int q = 0; q < 3; q++) {
+        so.a[q] = A3 + (size_t)q * p.m * ldk;
+        so.b[q] = B3 + (size_t)q * p.n * ldk;
+        if (!make_map_f32(&maps.a[q], so.a[q], (uint64_t)ldk, (uint64_t)p.m, (uint64_t)ldk, TBM, TBK)) return false;
+        if (!make_map_f32(&maps.b[q], so.b[q], (uint64_t)ldk, (uint64_t)p.n, (uint64_t)ldk, TBN, TBK)) return false;
+    }
     if (!make_map_f32(&maps.d, p.D, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.ldd, TBM)) return false;
     if (!make_map_f32(&maps.sk, p.Sk, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.lds, TBM)) return false;
     if (!make_map_f32(&maps.sp, has_sp ? p.Sp : p.Sk, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.lds, TBM))
@@ -545,13 +582,13 @@ bool launch_pass_tc(const PassArgs<float> &p, int kmax, float *A6, float *B6, in
             return false;
         attr = true;
     }
-    // split factors (one launch; threads over the live K and the padding),
-    // then the persistent pass
+    // split factors (one launch; threads over the padded live K), then the
+    // persistent pass
     {
-        dim3 grid((unsigned)((2 * kmax + TBK + 127) / 128), (unsigned)std::max(p.m, p.n));
+        dim3 grid((unsigned)((ldk + 127) / 128), (unsigned)std::max(p.m, p.n));
         CPCP_COUNT_LAUNCH();
         tf32_split_kernel<<<grid, 128, 0, st>>>(p.m, p.n, p.Ak, p.Ap ? p.Ap : p.Ak, p.ldfa, p.Bk, p.Bp ? p.Bp : p.Bk,
-                                                p.ldfb, p.rk, p.Ap ? p.rp : nullptr, p.ctrl, A6, B6, ldk);
+                                                p.ldfb, p.rk, p.Ap ? p.rp : nullptr, p.ctrl, so, ldk);
     }
     TcArgs a;
     a.m = p.m;

@@ -420,7 +420,8 @@ __device__ __forceinline__ void jacobi_body(const T *__restrict__ Rz, int ldr, i
                 // angle, so a rounding-level error in it costs nothing: the
                 // applied rotation is orthogonal through cs and sn below
                 const T e_ = b - a, f = T(2) * g;
-                const T hyp = sqrt(e_ * e_ + f * f);
+                const T h2 = e_ * e_ + f * f;  // > 0: f != 0 here
+                const T hyp = h2 * rsqrt_of(h2);
                 T tt;
                 if (hyp < T(1e37)) {  // finite, and in the fast quotient's range
                     tt = fast_div(f, e_ + copysign(hyp, e_));

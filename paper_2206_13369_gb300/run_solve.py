@@ -34,7 +34,7 @@ def main() -> int:
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--fp64", action="store_true")
     ap.add_argument("--profile", action="store_true")
-    ap.add_argument("--pass-tc", action="store_true", help="fused fine pass on the tensor cores")
+    ap.add_argument("--pass-simt", action="store_true", help="fused fine pass on the SIMT cores")
     ap.add_argument("--plain-launches", action="store_true", help="no CUDA graph replay of iterations")
     ap.add_argument("--config", type=int, default=0, help="use workloads.config(N) instead of planted_cpcp")
     ap.add_argument("--precision", type=int, default=0, help="1: BF16 tensor-core contractions, then fp32")
@@ -71,7 +71,7 @@ def main() -> int:
     D = torch.as_tensor(p["D"], dtype=dt).cuda()
     Q = None if p["mask"] is None else torch.as_tensor(cpcp.pack_mask(p["mask"])).cuda()
     opts = dict(max_iter=args.max_iter, power_iters=args.power_iters, profile=int(args.profile),
-                pass_tc=int(args.pass_tc), plain_launches=int(args.plain_launches),
+                pass_simt=int(args.pass_simt), plain_launches=int(args.plain_launches),
                 precision=args.precision)
     if args.unroll > 0:
         opts.update(unroll=args.unroll, rho=args.rho)
