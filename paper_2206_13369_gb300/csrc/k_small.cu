@@ -352,8 +352,13 @@ __device__ __forceinline__ void jacobi_body(const T *__restrict__ Rz, int ldr, i
     const T negl = (T(4) * T(k) * eps_of<T>()) * (T(4) * T(k) * eps_of<T>());
     // a sweep whose largest rotated |g|/sqrt(ab) is delta leaves an
     // off-orthogonality of order delta^2 (Jacobi converges quadratically), so
-    // a further sweep would only make rounding-level rotations
-    const T stop = min(sqrt(tol), T(1e-4));
+    // a further sweep would only make rounding-level rotations.  While the
+    // continuation weight is still above its final value the iterate moves
+    // far more per iteration than an off-orthogonality of 1e-4 (the subspace
+    // step itself is inexact), so the sweeps stop at delta <= 1e-2 there; at
+    // the final weight (and in residual checks) they stop at 1e-4.
+    const bool cont = ctrl != nullptr && ctrl->mu_k > ctrl->mu_bar * (1.0 + 1e-9);
+    const T stop = cont ? T(1e-2) : min(sqrt(tol), T(1e-4));
     int sweeps = 0;
     for (int sweep = 0; sweep < 30; sweep++) {
         sweeps++;
