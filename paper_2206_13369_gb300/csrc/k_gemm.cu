@@ -186,14 +186,15 @@ __global__ void restrict_kernel(int m, int n, const T *__restrict__ M, int64_t l
                                 TransferDev<T> tr)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    int i = blockIdx.y;
-    if (c >= tr.nh || i >= m) return;
-    T s = T(0);
-    for (int j = tr.clo[c]; j <= tr.chi[c]; j++) {
-        T w = (tr.j0[j] == c) ? tr.w0[j] : ((tr.j0[j] + 1 == c) ? tr.w1[j] : T(0));
-        s = fma(M[(int64_t)i * ldm + j], w, s);
+    if (c >= tr.nh) return;
+    for (int i = blockIdx.y; i < m; i += gridDim.y) {  // rows beyond the 65535 grid rows loop
+        T s = T(0);
+        for (int j = tr.clo[c]; j <= tr.chi[c]; j++) {
+            T w = (tr.j0[j] == c) ? tr.w0[j] : ((tr.j0[j] + 1 == c) ? tr.w1[j] : T(0));
+            s = fma(M[(int64_t)i * ldm + j], w, s);
+        }
+        MH[(int64_t)i * ldh + c] = s;
     }
-    MH[(int64_t)i * ldh + c] = s;
 }
 
 // B[j][c] = w0[j] V[j0[j]][c] + w1[j] V[j0[j]+1][c] for c < r; zero for r <= c < kmax
@@ -202,16 +203,17 @@ __global__ void prolong_kernel(int n, const T *__restrict__ V, int64_t ldv, T *_
                                TransferDev<T> tr, const int *kdyn, int kmax)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y;
-    if (c >= kmax || j >= n) return;
+    if (c >= kmax) return;
     int r = kdyn ? *kdyn : kmax;
-    T v = T(0);
-    if (c < r) {
-        int a = tr.j0[j];
-        v = tr.w0[j] * V[(int64_t)a * ldv + c];
-        if (a + 1 < tr.nh && tr.w1[j] != T(0)) v = fma(tr.w1[j], V[(int64_t)(a + 1) * ldv + c], v);
+    for (int j = blockIdx.y; j < n; j += gridDim.y) {
+        T v = T(0);
+        if (c < r) {
+            int a = tr.j0[j];
+            v = tr.w0[j] * V[(int64_t)a * ldv + c];
+            if (a + 1 < tr.nh && tr.w1[j] != T(0)) v = fma(tr.w1[j], V[(int64_t)(a + 1) * ldv + c], v);
+        }
+        B[(int64_t)j * ldb + c] = v;
     }
-    B[(int64_t)j * ldb + c] = v;
 }
 
 // Omega[c][:] = sum_j R[j][c] B[j][:] for the coarse rows c < nh, columns < r;
@@ -221,16 +223,17 @@ __global__ void restrict_rows_kernel(const T *__restrict__ B, int64_t ldb, T *__
                                      TransferDev<T> tr, const int *kdyn, int kmax)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    int row = blockIdx.y;
-    if (c >= kmax || row >= tr.nh) return;
+    if (c >= kmax) return;
     int r = kdyn ? *kdyn : kmax;
     if (c >= r) return;
-    T s = T(0);
-    for (int j = tr.clo[row]; j <= tr.chi[row]; j++) {
-        T w = (tr.j0[j] == row) ? tr.w0[j] : ((tr.j0[j] + 1 == row) ? tr.w1[j] : T(0));
-        s = fma(w, B[(int64_t)j * ldb + c], s);
+    for (int row = blockIdx.y; row < tr.nh; row += gridDim.y) {
+        T s = T(0);
+        for (int j = tr.clo[row]; j <= tr.chi[row]; j++) {
+            T w = (tr.j0[j] == row) ? tr.w0[j] : ((tr.j0[j] + 1 == row) ? tr.w1[j] : T(0));
+            s = fma(w, B[(int64_t)j * ldb + c], s);
+        }
+        Om[(int64_t)row * ldo + c] = s;
     }
-    Om[(int64_t)row * ldo + c] = s;
 }
 
 template <typename T>
@@ -255,16 +258,17 @@ __global__ void transpose_mask_kernel(int rows, int cols, const uint32_t *__rest
                                       uint32_t *__restrict__ out, int64_t ldo)
 {
     int w = blockIdx.x * blockDim.x + threadIdx.x;  // word index along the output row
-    int r = blockIdx.y;                             // output row = input column
-    if (r >= cols || (int64_t)w >= ldo) return;
-    uint32_t word = 0;
-    for (int b = 0; b < 32; b++) {
-        int c = w * 32 + b;  // output column = input row
-        if (c >= rows) break;
-        uint32_t bit = (in[(int64_t)c * ldi + (r >> 5)] >> (r & 31)) & 1u;
-        word |= bit << b;
+    if ((int64_t)w >= ldo) return;
+    for (int r = blockIdx.y; r < cols; r += gridDim.y) {  // output row = input column
+        uint32_t word = 0;
+        for (int b = 0; b < 32; b++) {
+            int c = w * 32 + b;  // output column = input row
+            if (c >= rows) break;
+            uint32_t bit = (in[(int64_t)c * ldi + (r >> 5)] >> (r & 31)) & 1u;
+            word |= bit << b;
+        }
+        out[(int64_t)r * ldo + w] = word;
     }
-    out[(int64_t)r * ldo + w] = word;
 }
 
 }  // namespace
@@ -273,7 +277,7 @@ template <typename T>
 void launch_restrict_rows(const T *B, int64_t ldb, T *Om, int64_t ldo, const TransferDev<T> &tr, const int *kdyn,
                           int kmax, cudaStream_t st)
 {
-    dim3 grid((kmax + 63) / 64, tr.nh);
+    dim3 grid((kmax + 63) / 64, std::min(tr.nh, 65535));
     CPCP_COUNT_LAUNCH();
     restrict_rows_kernel<T><<<grid, 64, 0, st>>>(B, ldb, Om, ldo, tr, kdyn, kmax);
 }
@@ -289,7 +293,7 @@ void launch_transpose(int rows, int cols, const T *A, int64_t lda, T *B, int64_t
 void launch_transpose_mask(int rows, int cols, const uint32_t *in, int64_t ldi, uint32_t *out, int64_t ldo,
                            cudaStream_t st)
 {
-    dim3 grid((unsigned)((ldo + 63) / 64), cols);
+    dim3 grid((unsigned)((ldo + 63) / 64), (unsigned)std::min(cols, 65535));
     CPCP_COUNT_LAUNCH();
     transpose_mask_kernel<<<grid, 64, 0, st>>>(rows, cols, in, ldi, out, ldo);
 }
@@ -365,7 +369,7 @@ template <typename T>
 void launch_restrict(int m, int n, const T *M, int64_t ldm, T *MH, int64_t ldh, const TransferDev<T> &tr,
                      cudaStream_t st)
 {
-    dim3 grid((tr.nh + 127) / 128, m);
+    dim3 grid((tr.nh + 127) / 128, std::min(m, 65535));
     CPCP_COUNT_LAUNCH();
     restrict_kernel<T><<<grid, 128, 0, st>>>(m, n, M, ldm, MH, ldh, tr);
 }
@@ -374,7 +378,7 @@ template <typename T>
 void launch_prolong(int n, const T *V, int64_t ldv, T *B, int64_t ldb, const TransferDev<T> &tr, const int *kdyn,
                     int kmax, cudaStream_t st)
 {
-    dim3 grid((kmax + 63) / 64, n);
+    dim3 grid((kmax + 63) / 64, std::min(n, 65535));
     CPCP_COUNT_LAUNCH();
     prolong_kernel<T><<<grid, 64, 0, st>>>(n, V, ldv, B, ldb, tr, kdyn, kmax);
 }

@@ -478,22 +478,25 @@ __global__ void tf32_split_kernel(int m, int n, const float *__restrict__ Ak, co
     const int rp = (rp_p && ctrl->beta != 0.0) ? *rp_p : 0;
     const int K = rk + rp, Kp = (K + TBK - 1) / TBK * TBK;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int row = blockIdx.y;
     if (c >= Kp) return;
     const float ck = (float)(1.0 + ctrl->beta), cp = (float)(-ctrl->beta);
-    if (row < m) {
-        const float v = c < rk ? Ak[(int64_t)row * lda + c] * ck : (c < K ? Ap[(int64_t)row * lda + c - rk] * cp : 0.f);
-        const float h = tf32_rn(v), r1 = v - h, md = tf32_rn(r1);
-        o.a[0][(int64_t)row * ldk + c] = h;
-        o.a[1][(int64_t)row * ldk + c] = md;
-        o.a[2][(int64_t)row * ldk + c] = tf32_rn(r1 - md);
-    }
-    if (row < n) {
-        const float v = c < rk ? Bk[(int64_t)row * ldb + c] : (c < K ? Bp[(int64_t)row * ldb + c - rk] : 0.f);
-        const float h = tf32_rn(v), r1 = v - h, md = tf32_rn(r1);
-        o.b[0][(int64_t)row * ldk + c] = h;
-        o.b[1][(int64_t)row * ldk + c] = md;
-        o.b[2][(int64_t)row * ldk + c] = tf32_rn(r1 - md);
+    const int rows = max(m, n);
+    for (int row = blockIdx.y; row < rows; row += gridDim.y) {  // rows beyond the 65535 grid rows loop
+        if (row < m) {
+            const float v =
+                c < rk ? Ak[(int64_t)row * lda + c] * ck : (c < K ? Ap[(int64_t)row * lda + c - rk] * cp : 0.f);
+            const float h = tf32_rn(v), r1 = v - h, md = tf32_rn(r1);
+            o.a[0][(int64_t)row * ldk + c] = h;
+            o.a[1][(int64_t)row * ldk + c] = md;
+            o.a[2][(int64_t)row * ldk + c] = tf32_rn(r1 - md);
+        }
+        if (row < n) {
+            const float v = c < rk ? Bk[(int64_t)row * ldb + c] : (c < K ? Bp[(int64_t)row * ldb + c - rk] : 0.f);
+            const float h = tf32_rn(v), r1 = v - h, md = tf32_rn(r1);
+            o.b[0][(int64_t)row * ldk + c] = h;
+            o.b[1][(int64_t)row * ldk + c] = md;
+            o.b[2][(int64_t)row * ldk + c] = tf32_rn(r1 - md);
+        }
     }
 }
 
@@ -585,7 +588,7 @@ bool launch_pass_tc(const PassArgs<float> &p, int kmax, float *A3, float *B3, in
     // split factors (one launch; threads over the padded live K), then the
     // persistent pass
     {
-        dim3 grid((unsigned)((ldk + 127) / 128), (unsigned)std::max(p.m, p.n));
+        dim3 grid((unsigned)((ldk + 127) / 128), (unsigned)std::min(std::max(p.m, p.n), 65535));
         CPCP_COUNT_LAUNCH();
         tf32_split_kernel<<<grid, 128, 0, st>>>(p.m, p.n, p.Ak, p.Ap ? p.Ap : p.Ak, p.ldfa, p.Bk, p.Bp ? p.Bp : p.Bk,
                                                 p.ldfb, p.rk, p.Ap ? p.rp : nullptr, p.ctrl, so, ldk);

@@ -578,15 +578,15 @@ __global__ void fill_random_kernel(T *Omega, int64_t ldo, int rows, const Ctrl *
                                    const T *__restrict__ sig, int kmax, uint64_t salt)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y;
-    if (j >= rows || c >= kmax) return;
+    if (c >= kmax) return;
     int kc = all_cols ? 0 : ctrl->k;
     int kn = all_cols ? ctrl->k : ctrl->k_next;
     if (c >= kn) return;
     bool fill = (c >= kc) || (sig != nullptr && sig[c] == T(0));
     if (!fill) return;
     uint64_t key = ctrl->seed * 0x9E3779B97F4A7C15ull + salt * 0xD1B54A32D192ED03ull + (uint64_t)ctrl->iter * 7919ull;
-    Omega[(int64_t)j * ldo + c] = T(hash_uniform(key ^ ((uint64_t)j * 1000003ull + (uint64_t)c * 0x100000001B3ull)));
+    for (int j = blockIdx.y; j < rows; j += gridDim.y)  // rows beyond the 65535 grid rows loop
+        Omega[(int64_t)j * ldo + c] = T(hash_uniform(key ^ ((uint64_t)j * 1000003ull + (uint64_t)c * 0x100000001B3ull)));
 }
 
 // fill_random_kernel on Omega (rows_o rows) and prolong_kernel from Omega
@@ -597,25 +597,25 @@ __global__ void fill_prolong_kernel(T *Omega, int64_t ldo, int rows_o, const Ctr
                                     int kmax, uint64_t salt, int n, T *__restrict__ B, int64_t ldb, TransferDev<T> tr)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
     if (c >= kmax) return;
-    if (j < n) {
-        const int r = ctrl->r_new;
-        T v = T(0);
-        if (c < r) {
-            const int a = tr.j0[j];
-            v = tr.w0[j] * Omega[(int64_t)a * ldo + c];
-            if (a + 1 < tr.nh && tr.w1[j] != T(0)) v = fma(tr.w1[j], Omega[(int64_t)(a + 1) * ldo + c], v);
+    const int r = ctrl->r_new, kc = ctrl->k, kn = ctrl->k_next;
+    const bool fill = c < kn && ((c >= kc) || (sig != nullptr && sig[c] == T(0)));
+    const uint64_t key =
+        ctrl->seed * 0x9E3779B97F4A7C15ull + salt * 0xD1B54A32D192ED03ull + (uint64_t)ctrl->iter * 7919ull;
+    const int rows = max(n, rows_o);
+    for (int j = blockIdx.y; j < rows; j += gridDim.y) {  // rows beyond the 65535 grid rows loop
+        if (j < n) {
+            T v = T(0);
+            if (c < r) {
+                const int a = tr.j0[j];
+                v = tr.w0[j] * Omega[(int64_t)a * ldo + c];
+                if (a + 1 < tr.nh && tr.w1[j] != T(0)) v = fma(tr.w1[j], Omega[(int64_t)(a + 1) * ldo + c], v);
+            }
+            B[(int64_t)j * ldb + c] = v;
         }
-        B[(int64_t)j * ldb + c] = v;
-    }
-    if (j < rows_o) {
-        const int kc = ctrl->k, kn = ctrl->k_next;
-        if (c >= kn) return;
-        const bool fill = (c >= kc) || (sig != nullptr && sig[c] == T(0));
-        if (!fill) return;
-        uint64_t key = ctrl->seed * 0x9E3779B97F4A7C15ull + salt * 0xD1B54A32D192ED03ull + (uint64_t)ctrl->iter * 7919ull;
-        Omega[(int64_t)j * ldo + c] = T(hash_uniform(key ^ ((uint64_t)j * 1000003ull + (uint64_t)c * 0x100000001B3ull)));
+        if (j < rows_o && fill)
+            Omega[(int64_t)j * ldo + c] =
+                T(hash_uniform(key ^ ((uint64_t)j * 1000003ull + (uint64_t)c * 0x100000001B3ull)));
     }
 }
 
@@ -712,7 +712,7 @@ template <typename T>
 void launch_fill_random(T *Omega, int64_t ldo, int rows, const Ctrl *ctrl, int all_cols, const T *sig, int kmax,
                         uint64_t salt, cudaStream_t st)
 {
-    dim3 grid((kmax + 63) / 64, rows);
+    dim3 grid((kmax + 63) / 64, std::min(rows, 65535));
     CPCP_COUNT_LAUNCH();
     fill_random_kernel<T><<<grid, 64, 0, st>>>(Omega, ldo, rows, ctrl, all_cols, sig, kmax, salt);
 }
@@ -721,7 +721,7 @@ template <typename T>
 void launch_fill_prolong(T *Omega, int64_t ldo, int rows_o, const Ctrl *ctrl, const T *sig, int kmax, uint64_t salt,
                          int n, T *B, int64_t ldb, const TransferDev<T> &tr, cudaStream_t st)
 {
-    dim3 grid((kmax + 63) / 64, std::max(rows_o, n));
+    dim3 grid((kmax + 63) / 64, std::min(std::max(rows_o, n), 65535));
     CPCP_COUNT_LAUNCH();
     fill_prolong_kernel<T><<<grid, 64, 0, st>>>(Omega, ldo, rows_o, ctrl, sig, kmax, salt, n, B, ldb, tr);
 }

@@ -30,6 +30,10 @@ for their shapes and structure):
   rank-5 background of smooth random fields with smooth temporal
   coefficients, 10x10 moving foreground blocks, mask Bernoulli(0.6).
 * batched CPCP: many uneven planted CPCP instances.
+* hyperspectral-shaped CPCP (the hyperspectral motivation of Sec. 1):
+  pixels x bands under a linear mixing model, smooth endmember spectra
+  (so the right singular subspace is smooth in the band index, the setting
+  of Assumption 3), sparse outliers, mask Bernoulli(obs).
 """
 from __future__ import annotations
 
@@ -43,6 +47,7 @@ __all__ = [
     "planted_cpcp",
     "video_cpcp",
     "batched_cpcp",
+    "hyperspectral_cpcp",
     "config",
     "CONFIG_NAMES",
 ]
@@ -174,6 +179,37 @@ def video_cpcp(seed: int, h: int = 120, w: int = 160, frames: int = 400, rank: i
     return _finish(D, mask, L0, S0, 1.0 / math.sqrt(max(m, frames)), levels)
 
 
+def hyperspectral_cpcp(seed: int, h: int = 256, w: int = 256, bands: int = 128, rank: int = 8,
+                       rho: float = 0.05, obs: float = 0.8, levels: int = 3) -> dict:
+    """Hyperspectral-shaped CPCP: pixels x bands, linear mixing of smooth spectra.
+
+    Endmember spectra V (bands x rank): each a sum of three Gaussian bumps in
+    the band index (centres U[0, bands), widths U[6, 20] bands, heights
+    U[0.5, 1]).  Abundances U (pixels x rank): white-noise fields blurred with a
+    Gaussian of 6 px, shifted to be non-negative and normalised to sum to 1 per
+    pixel.  L0 = U V^T.  Outliers S0: Bernoulli(rho) support with values
+    U[-1, 1] * max|L0|.  Mask Bernoulli(obs).
+    """
+    rng = np.random.default_rng(seed)
+    m = h * w
+    b = np.arange(bands, dtype=np.float64)
+    V = np.zeros((bands, rank))
+    for i in range(rank):
+        for _ in range(3):
+            c, wd, ht = rng.uniform(0, bands), rng.uniform(6, 20), rng.uniform(0.5, 1.0)
+            V[:, i] += ht * np.exp(-0.5 * ((b - c) / wd) ** 2)
+    U = np.empty((m, rank))
+    for i in range(rank):
+        f = _gauss_blur(rng.normal(size=(h, w)), 6.0)
+        U[:, i] = (f - f.min()).reshape(-1)
+    U /= np.maximum(U.sum(axis=1, keepdims=True), 1e-30)
+    L0 = U @ V.T
+    support = rng.random((m, bands)) < rho
+    S0 = np.where(support, rng.uniform(-1.0, 1.0, (m, bands)) * np.abs(L0).max(), 0.0)
+    mask = rng.random((m, bands)) < obs
+    return _finish(L0 + S0, mask, L0, S0, 1.0 / math.sqrt(max(m, bands)), levels)
+
+
 def _batched_levels(m: int, n: int, rank: int, max_levels: int = 3) -> int:
     """Deepest level count <= max_levels with n_H >= 2 (rank + 10) and
     n_H <= (m + 1) / 2 (Assumption 2), halving n with ceil per level."""
@@ -209,11 +245,13 @@ CONFIG_NAMES = {
     3: "video-19200x400-r5-mixed-4lv",
     4: "batched-256-cpcp-fp32",
     5: "unrolled-1024x1024-r20-fp32-3lv",
+    6: "hyperspectral-65536x128-r8-fp32-3lv",
 }
 
 
 def config(idx: int):
-    """The five workload configurations (seed 1000 * idx)."""
+    """The workload configurations (seed 1000 * idx); 6 is the hyperspectral
+    shape of the next-steps list."""
     seed = 1000 * idx
     if idx == 1:
         return planted_pcp(200, 200, 10, 0.05, seed, levels=2, factor_var=1.0 / 200)
@@ -225,4 +263,6 @@ def config(idx: int):
         return batched_cpcp(256, seed)
     if idx == 5:
         return planted_cpcp(1024, 1024, 20, 0.10, 0.7, seed, levels=3)
+    if idx == 6:
+        return hyperspectral_cpcp(seed)
     raise ValueError(f"unknown config {idx}")
