@@ -306,7 +306,9 @@ def _events_time(stream, fn, reps, flush):
 
 
 def extras(device, stream, flush) -> dict:
-    """The mixed-precision, batched and backward rows on their own workloads."""
+    """The mixed-precision, batched and backward rows on their own workloads, and the
+    hyperspectral-shaped workload, and IALM / ML-IALM for PCP."""
+    import numpy as np
     import torch
     from paper_2206_13369_gb300 import cpcp, workloads
     out = {}
@@ -350,6 +352,49 @@ def extras(device, stream, flush) -> dict:
     hu.close()
     out["backward"] = {"workload": "unrolled-1024x1024-r20-3lv-50steps", "unit": "s", "forward_s": tf,
                        "backward_s": tb, "ckpt_every": 10}
+    del D, Q, L0, gL
+    # hyperspectral-shaped CPCP, 65536 pixels x 128 bands, rank 8: 3 levels vs single-level
+    c6 = workloads.config(6)
+    D = torch.as_tensor(c6["D"], dtype=torch.float32).cuda()
+    Q = torch.as_tensor(cpcp.pack_mask(c6["mask"])).cuda()
+    hs = {}
+    for name, lv in (("3lv", 3), ("1lv", 1)):
+        with cpcp.Handle(device, stream=stream) as hh:
+            hh.solve(D, Q, c6["lam"], c6["mu"], levels=lv, tol=TOL)
+            t, (_, _, info) = _events_time(stream, lambda: hh.solve(D, Q, c6["lam"], c6["mu"], levels=lv, tol=TOL), 3,
+                                           flush)
+        hs[name] = {"s": t, "iters": info["iters"], "level_iters": info["level_iters"][:lv], "relkkt": info["relkkt"],
+                    "rank": info["rank"]}
+    out["hyperspectral"] = {"workload": "hyperspectral-65536x128-r8-cpcp", "unit": "s", "tol": TOL, **hs,
+                            "multilevel_over_single": hs["3lv"]["s"] / hs["1lv"]["s"]}
+    del D, Q
+    # IALM (Alg. 1) for PCP on a 2000 x 2000 planted problem, fp32, geometric penalty
+    # (rho = 1.5), to a feasibility gap of 1e-5
+    pp = workloads.planted_pcp(2000, 2000, 50, 0.05, seed=2100, levels=1)
+    D = torch.as_tensor(pp["D"], dtype=torch.float32).cuda()
+    with cpcp.Handle(device, stream=stream) as hh:
+        hh.ialm(D, pp["lam"], rho=1.5, tol=1e-5, max_iter=500)
+        t, (L, _, info) = _events_time(stream, lambda: hh.ialm(D, pp["lam"], rho=1.5, tol=1e-5, max_iter=500), 3,
+                                       flush)
+    err = float(np.linalg.norm(L.double().cpu().numpy() - pp["L0"]) / np.linalg.norm(pp["L0"]))
+    out["ialm_pcp"] = {"workload": "pcp-2000x2000-r50-ialm-fp32", "unit": "s", "tol_gap": 1e-5, "s": t,
+                       "iters": info["iters"], "gap": info["relkkt"], "rank": info["rank"], "rel_err_L": err}
+    del D, L
+    # IALM vs ML-IALM (Alg. 4, 3 levels) for the same iteration budget on a fully observed
+    # video-shaped matrix (19200 pixels x 400 frames), as in the fixed-budget comparisons
+    vv = workloads.video_cpcp(3, obs=1.0, levels=3)
+    D = torch.as_tensor(vv["D"], dtype=torch.float32).cuda()
+    nL0 = np.linalg.norm(vv["L0"])
+    ml = {}
+    for name, lv in (("ialm", 1), ("ml_ialm_3lv", 3)):
+        with cpcp.Handle(device, stream=stream) as hh:
+            hh.ialm(D, vv["lam"], levels=lv, rho=1.5, tol=1e-30, max_iter=15)
+            t, (L, _, info) = _events_time(stream, lambda: hh.ialm(D, vv["lam"], levels=lv, rho=1.5, tol=1e-30,
+                                                                   max_iter=15), 3, flush)
+        ml[name] = {"s": t, "iters": info["iters"], "gap": info["relkkt"], "rank": info["rank"],
+                    "rel_err_L": float(np.linalg.norm(L.double().cpu().numpy() - vv["L0"]) / nL0)}
+    out["ml_ialm_video"] = {"workload": "video-19200x400-r5-pcp-15-iterations", "unit": "s", **ml}
+    del D, L
     return out
 
 

@@ -208,6 +208,31 @@ cpcp_status cpcp_solve(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D
                        void *L_out, int64_t ldl, void *S_out, int64_t lds, cpcp_info *info);
 
 /*
+ * Inexact augmented Lagrangian method for PCP, eq. (rpca) (min ||L||_* +
+ * lambda ||S||_1 subject to L + S = D): Alg. 1 (levels == 1) or its
+ * multilevel form Alg. 4 (levels > 1; every iteration takes the low-rank step
+ * on the coarse level, L = SVT_{1/mu_k}(M R) R^T with R the composite
+ * restriction scaled to unit norm), with S_0 = Y_0 = 0 and
+ *   M = D - S + Y / mu_k;  L = SVT_{1/mu_k}(M)  (or the coarse step);
+ *   S = shrink_{lambda/mu_k}(D - L + Y / mu_k);  Y += mu_k (D - L - S).
+ * Penalty schedule: rho > 1 gives mu_{k+1} = rho mu_k, otherwise mu_k =
+ * mu0 (1 + k); mu0 <= 0 means 1.25 / ||D||_2 (estimated on the device).  The
+ * SVT of each iteration uses the subspace-iteration SVD of cpcp_solve (warm
+ * started, options power_iters, oversample, k_max).  Stops at the first
+ * iteration whose feasibility gap ||D - L - S||_F / ||D||_F is <= tol, or
+ * after max_iter iterations (NOT_CONVERGED); fg (optional, host, max_iter
+ * doubles) receives the gap after each iteration.  D, L_out, S_out: m x n
+ * device or host buffers as in cpcp_solve; requires n <= m (the restriction
+ * acts on columns; pass the transpose otherwise).  info->iters, rank,
+ * relkkt (the last gap), seconds and launches are filled.
+ * Validation (INVALID_ARG): 1 <= n <= m; lambda, tol > 0; max_iter >= 1;
+ * 1 <= levels <= 6 with n_H >= 1 and, when levels > 1, n_H <= (m + 1) / 2.
+ */
+cpcp_status cpcp_ialm(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D, int64_t ldd, double lambda,
+                      int levels, double mu0, double rho, int max_iter, double tol, void *L_out, int64_t ldl,
+                      void *S_out, int64_t lds, double *fg, cpcp_info *info);
+
+/*
  * One accelerated proximal-gradient step of the multilevel method (the hot
  * path of one iteration), on device buffers:
  *   Lhat = (1 + beta) A_k B_k^T - beta A_p B_p^T        (momentum on L)

@@ -96,6 +96,8 @@ def _load():
     lib.cpcp_backward.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _i64, C.POINTER(_dbl), C.POINTER(_dbl)]
     lib.cpcp_masked_norm_static.argtypes = [_vp, _int, _int, _int, _vp, _i64, _vp, _i64, C.POINTER(_dbl),
                                             C.POINTER(C.c_int64)]
+    lib.cpcp_ialm.argtypes = [_vp, _int, _int, _int, _vp, _i64, _dbl, _int, _dbl, _dbl, _int, _dbl, _vp, _i64, _vp,
+                              _i64, _vp, _vp]
     return lib
 
 
@@ -103,7 +105,7 @@ _lib = _load()
 
 EXPORTED = ["cpcp_status_string", "cpcp_last_error", "cpcp_create", "cpcp_destroy", "cpcp_solve", "cpcp_step",
             "cpcp_restrict", "cpcp_prolong", "cpcp_transfer_info", "cpcp_svd", "cpcp_gemm_bf16",
-            "cpcp_solve_batched", "cpcp_backward", "cpcp_masked_norm_static"]
+            "cpcp_solve_batched", "cpcp_backward", "cpcp_masked_norm_static", "cpcp_ialm"]
 
 
 def lib():
@@ -237,6 +239,30 @@ class Handle:
         d = info.as_dict()
         if self._trace is not None:
             d["trace"] = self._trace[:min(info.checks, len(self._trace))].copy()
+        return L_out, S_out, d
+
+    def ialm(self, D, lam: float, levels: int = 1, mu0: float = 0.0, rho: float = 0.0, max_iter: int = 1000,
+             tol: float = 1e-7, L_out=None, S_out=None):
+        """IALM (Alg. 1) / ML-IALM (Alg. 4, levels > 1) for eq. (rpca) on D
+        (m x n, n <= m); returns (L, S, info) with info["fg"] the feasibility
+        gap after each iteration."""
+        m, n = D.shape
+        dt = _dtype_code(D)
+        if L_out is None:
+            L_out = _empty_like(D, (m, n))
+        if S_out is None:
+            S_out = _empty_like(D, (m, n))
+        pD, ldd = _ptr(D)
+        pL, ldl = _ptr(L_out)
+        pS, lds = _ptr(S_out)
+        fg = np.zeros(int(max_iter), dtype=np.float64)
+        info = Info()
+        st = _lib.cpcp_ialm(self._h, m, n, dt, pD, ldd, float(lam), int(levels), float(mu0), float(rho),
+                            int(max_iter), float(tol), pL, ldl, pS, lds, fg.ctypes.data_as(_vp), C.byref(info))
+        if st not in (0, 5):
+            self._check(st, "cpcp_ialm")
+        d = info.as_dict()
+        d["fg"] = fg[:info.iters].copy()
         return L_out, S_out, d
 
     def step(self, D, Qbits, lam, mu_k, beta, halvings, S_k, S_p, A_k, B_k, r_k, A_p, B_p, r_p, k, q=1,

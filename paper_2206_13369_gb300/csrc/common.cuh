@@ -177,6 +177,18 @@ template <typename T>
 int launch_ts_gram(int rows, const T *X, int64_t ldx, T *partial, const int *kdyn, int kmax, const int *skip,
                    cudaStream_t st);
 
+// IALM / ML-IALM passes (k_ialm.cu): M = D - S + Y / mu; the S and Y steps
+// with per-block partial sums of ||D - L - S||_F^2 (ialm_blocks() of them)
+int ialm_blocks();
+template <typename T>
+void launch_ialm_m(int m, int n, const T *D, int64_t ldd, const T *S, const T *Y, int64_t lds, double mu, T *M,
+                   int64_t ldm, cudaStream_t st);
+template <typename T>
+void launch_ialm_update(int m, int n, const T *D, int64_t ldd, const T *L, int64_t ldl, T *S, T *Y, int64_t lds,
+                        double lam, double mu, double *partial, cudaStream_t st);
+// end == 0: theta_L = 1 / mu into the control block; 1: width bookkeeping
+void launch_ialm_ctrl(Ctrl *c, double mu, int end, cudaStream_t st);
+
 // small dense kernels (one CTA)
 // Cholesky pass of CholeskyQR: R = chol(X^T X) from row-split partial Gram
 // matrices; well_out / skip_in implement the skip of a second pass

@@ -1185,6 +1185,200 @@ bool is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// IALM (Alg. 1) / ML-IALM (Alg. 4) for PCP on device buffers, n <= m; see
+// cpcp_ialm.  The low-rank step is the CPCP path's: M (or its restriction
+// M R) -> warm-started subspace SVD with the SVT fused into its core SVD ->
+// factors A = U diag(sigma - 1/mu)_+ and B = R V -> L = A B^T.
+template <typename T>
+cpcp_status ialm_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, double lam, int levels, double mu0,
+                      double rho, int max_iter, double tol, T *L_out, int64_t ldl, T *S_out, int64_t lds,
+                      double *fg, cpcp_info *info)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const unsigned long long launches0 = g_kernel_launches;
+    cudaStream_t st = h->stream;
+    const Opts o = resolve(h->opt);
+    const int H = levels - 1;
+    const int64_t ldS = round4(n);
+    const int kcap0 = std::min({o.k_max, kmax_small<T>(), n});
+    const int KM = (int)round4(kcap0);
+    const size_t mn = (size_t)m * ldS;
+    T *S = wsT<T>(h, "ia_S", mn), *Y = wsT<T>(h, "ia_Y", mn), *M = wsT<T>(h, "ia_M", mn), *L = wsT<T>(h, "ia_L", mn);
+    TransferDev<T> tr = upload_transfer<T>(h, n, H, "ialm");
+    const int nh = tr.nh;
+    const int64_t ldh = round4(nh);
+    T *MH = H > 0 ? wsT<T>(h, "ia_MH", (size_t)m * ldh) : nullptr;
+    T *A = wsT<T>(h, "ia_A", (size_t)m * KM), *B = wsT<T>(h, "ia_B", (size_t)n * KM);
+    T *Om = wsT<T>(h, "ia_Om", (size_t)n * KM);
+    Ctrl *ctrl = wsT<Ctrl>(h, "ia_ctrl", 1);
+    const int nblk = ialm_blocks();
+    double *partial = wsT<double>(h, "ia_partial", (size_t)std::max(nblk, 1024));
+    double *sums = wsT<double>(h, "ia_sums", 4);
+    SvdWork<T> w = svd_work<T>(h, "ia_svd_", m, n, kcap0);  // own tags: "ia_Y" is the multiplier
+
+    // ||D||_F, and ||D||_2 for the default mu0 (subspace SVD of D, 4 passes)
+    const int nq = launch_sumsq<T>(m, n, D, ldd, partial, st);
+    launch_sum_partials(partial, nq, 1, sums, st);
+    double d2 = 0.0;
+    CK(cudaMemcpyAsync(&d2, sums, sizeof(double), cudaMemcpyDeviceToHost, st));
+    Ctrl c0;
+    memset(&c0, 0, sizeof(c0));
+    c0.eta_k = 1.0;
+    c0.tau = 1.0;
+    c0.lam = lam;
+    c0.mu_bar = INFINITY;  // the core SVD's sweeps always stop at the strict level
+    c0.seed = o.seed;
+    c0.oversample = o.p;
+    c0.kcap = std::min(kcap0, nh);
+    c0.k = std::min(c0.kcap, 8);
+    c0.k_next = c0.k;
+    CK(cudaStreamSynchronize(st));
+    const double nD = std::sqrt(d2);
+    if (!(nD > 0) || !std::isfinite(nD)) throw CpcpError{CPCP_ERR_INVALID_ARG, "D is zero or not finite"};
+    if (!(mu0 > 0)) {
+        // ||D||_2: block of 16, 8 passes (the top value converges like
+        // (sigma_17 / sigma_1)^16)
+        Ctrl ce = c0;
+        ce.k = std::min(kcap0, 16);
+        ce.k_next = ce.k;
+        CK(cudaMemcpyAsync(ctrl, &ce, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+        launch_fill_random<T>(Om, KM, n, ctrl, 1, nullptr, KM, 0x1A10ull, st);
+        subspace_svd<T>(h, w, m, n, D, ldd, Om, 8, &ctrl->k, nullptr);
+        T s0;
+        CK(cudaMemcpyAsync(&s0, w.sig, sizeof(T), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        mu0 = 1.25 / (double)s0;
+    }
+    c0.k = std::min(c0.kcap, o.p);
+    c0.k_next = c0.k;
+    CK(cudaMemcpyAsync(ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(S, 0, sizeof(T) * mn, st));
+    CK(cudaMemsetAsync(Y, 0, sizeof(T) * mn, st));
+    launch_fill_random<T>(Om, KM, nh, ctrl, 1, nullptr, KM, 0x1A11ull, st);
+
+    PassArgs<T> rc;
+    memset(&rc, 0, sizeof(rc));
+    rc.m = m;
+    rc.n = n;
+    rc.Ak = A;
+    rc.Bk = B;
+    rc.ldfa = KM;
+    rc.ldfb = KM;
+    rc.ldfap = KM;
+    rc.ldfbp = KM;
+    rc.rk = &ctrl->r_new;
+    rc.ctrl = ctrl;
+    rc.M = L;
+    rc.ldm = ldS;
+
+    cpcp_status status = CPCP_ERR_NOT_CONVERGED;
+    double mu = mu0, gap = INFINITY;
+    int k = 0;
+    for (k = 0; k < max_iter;) {
+        launch_ialm_ctrl(ctrl, mu, 0, st);
+        launch_ialm_m<T>(m, n, D, ldd, S, Y, ldS, mu, M, ldS, st);
+        const T *Mx = M;
+        int64_t ldx = ldS;
+        if (H > 0) {
+            launch_restrict<T>(m, n, M, ldS, MH, ldh, tr, st);
+            Mx = MH;
+            ldx = ldh;
+        }
+        // the SVT must be complete: an SVT truncated at the subspace width
+        // leaves D - L - S large, which the multiplier step then amplifies by
+        // the growing mu_k.  While every value of the width is above the
+        // threshold, widen (new random columns) and redo (the r = k rule).
+        for (;;) {
+            subspace_svd<T>(h, w, m, nh, Mx, ldx, Om, std::max(o.q, 2), &ctrl->k, ctrl, false, w.Us, ctrl);
+            Ctrl cw;
+            CK(cudaMemcpyAsync(&cw, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (cw.r_new < cw.k || cw.k >= cw.kcap) break;
+            Ctrl wide = cw;
+            wide.k_next = std::min(cw.kcap, 2 * cw.k);
+            CK(cudaMemcpyAsync(ctrl, &wide, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+            prod_nn_small<T>(nh, w.Qz, KM, w.Wt, KM, Om, KM, &ctrl->k, KM, st);  // the subspace found so far
+            launch_fill_random<T>(Om, KM, nh, ctrl, 0, nullptr, KM, 0x1A13ull + (uint64_t)cw.k, st);
+            wide.k = wide.k_next;
+            CK(cudaMemcpyAsync(ctrl, &wide, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+        }
+        prod_nn_small<T>(m, w.Qy, KM, w.Us, KM, A, KM, &ctrl->k, KM, st);
+        prod_nn_small<T>(nh, w.Qz, KM, w.Wt, KM, Om, KM, &ctrl->k, KM, st);
+        launch_fill_prolong<T>(Om, KM, nh, ctrl, w.sig, KM, 0x1A12ull, n, B, KM, tr, st);
+        launch_reconstruct<T>(rc, st);
+        launch_ialm_update<T>(m, n, D, ldd, L, ldS, S, Y, ldS, lam, mu, partial, st);
+        launch_sum_partials(partial, nblk, 1, sums, st);
+        launch_ialm_ctrl(ctrl, mu, 1, st);
+        double e2 = 0.0;
+        CK(cudaMemcpyAsync(&e2, sums, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        gap = std::sqrt(e2) / nD;
+        if (fg) fg[k] = gap;
+        mu = rho > 1.0 ? mu * rho : mu0 * (double)(k + 2);
+        k++;
+        if (!std::isfinite(gap)) {
+            status = CPCP_ERR_NUMERIC;
+            break;
+        }
+        if (gap <= tol) {
+            status = CPCP_OK;
+            break;
+        }
+    }
+    Ctrl fin;
+    CK(cudaMemcpyAsync(&fin, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    if (S_out)
+        CK(cudaMemcpy2DAsync(S_out, sizeof(T) * lds, S, sizeof(T) * ldS, sizeof(T) * n, m, cudaMemcpyDeviceToDevice,
+                             st));
+    if (L_out)
+        CK(cudaMemcpy2DAsync(L_out, sizeof(T) * ldl, L, sizeof(T) * ldS, sizeof(T) * n, m, cudaMemcpyDeviceToDevice,
+                             st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    if (info) {
+        cpcp_info inf;
+        memset(&inf, 0, sizeof(inf));
+        inf.status = status;
+        inf.iters = k;
+        inf.level_iters[std::min(H, 7)] = k;
+        inf.final_level = H;
+        inf.rank = fin.rk;
+        inf.relkkt = gap;
+        inf.mu0 = mu0;
+        inf.pqd_fro = nD;
+        inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        inf.launches = (long long)(g_kernel_launches - launches0);
+        *info = inf;
+    }
+    return status;
+}
+
+template <typename T>
+cpcp_status ialm_dispatch(cpcp_context *h, int m, int n, const void *Dv, int64_t ldd, double lam, int levels,
+                          double mu0, double rho, int max_iter, double tol, void *Lv, int64_t ldl, void *Sv,
+                          int64_t lds, double *fg, cpcp_info *info)
+{
+    cudaStream_t st = h->stream;
+    const T *D = static_cast<const T *>(Dv);
+    T *L = static_cast<T *>(Lv), *S = static_cast<T *>(Sv);
+    if (!is_device_ptr(Dv)) {
+        T *Dd = wsT<T>(h, "stage_D", (size_t)m * n);
+        CK(cudaMemcpy2DAsync(Dd, sizeof(T) * n, D, sizeof(T) * ldd, sizeof(T) * n, m, cudaMemcpyHostToDevice, st));
+        T *Ld = L ? wsT<T>(h, "stage_L", (size_t)m * n) : nullptr;
+        T *Sd = S ? wsT<T>(h, "stage_S", (size_t)m * n) : nullptr;
+        cpcp_status r = ialm_core<T>(h, m, n, Dd, n, lam, levels, mu0, rho, max_iter, tol, Ld, n, Sd, n, fg, info);
+        if (L)
+            CK(cudaMemcpy2DAsync(L, sizeof(T) * ldl, Ld, sizeof(T) * n, sizeof(T) * n, m, cudaMemcpyDeviceToHost,
+                                 st));
+        if (S)
+            CK(cudaMemcpy2DAsync(S, sizeof(T) * lds, Sd, sizeof(T) * n, sizeof(T) * n, m, cudaMemcpyDeviceToHost,
+                                 st));
+        CK(cudaStreamSynchronize(st));
+        return r;
+    }
+    return ialm_core<T>(h, m, n, D, ldd, lam, levels, mu0, rho, max_iter, tol, L, ldl, S, lds, fg, info);
+}
+
 template <typename T>
 cpcp_status solve_dispatch(cpcp_context *h, int m, int n, const void *Dv, int64_t ldd, const uint32_t *Q,
                            int64_t ldq, double lam, double mu, int levels, double tol, void *Lv, int64_t ldl,
@@ -2136,6 +2330,30 @@ cpcp_status cpcp_solve(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D
                                          info);
         return solve_dispatch<double>(h, m, n, D, ldd, Q, ldq, lambda, mu, levels, tol, L_out, ldl, S_out, lds,
                                       info);
+    });
+}
+
+cpcp_status cpcp_ialm(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D, int64_t ldd, double lambda,
+                      int levels, double mu0, double rho, int max_iter, double tol, void *L_out, int64_t ldl,
+                      void *S_out, int64_t lds, double *fg, cpcp_info *info)
+{
+    if (!h) return CPCP_ERR_INVALID_ARG;
+    return guarded(h, [&]() -> cpcp_status {
+        if (n < 1 || m < n || !D || bad_dtype(dt)) throw CpcpError{CPCP_ERR_INVALID_ARG, "need 1 <= n <= m, D, dtype"};
+        if (!(lambda > 0) || !(tol > 0) || max_iter < 1)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "lambda and tol must be positive, max_iter >= 1"};
+        if (levels < 1 || levels > 6) throw CpcpError{CPCP_ERR_INVALID_ARG, "levels must be in [1, 6]"};
+        if (ldd < n || (L_out && ldl < n) || (S_out && lds < n))
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "leading dimension smaller than n"};
+        const int nh = coarse_dim(n, levels - 1);
+        if (nh < 1) throw CpcpError{CPCP_ERR_INVALID_ARG, "coarse width below 1"};
+        if (levels > 1 && 2 * nh > m + 1)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "coarse width exceeds (m+1)/2 (Assumption 2)"};
+        if (dt == CPCP_F32)
+            return ialm_dispatch<float>(h, m, n, D, ldd, lambda, levels, mu0, rho, max_iter, tol, L_out, ldl, S_out,
+                                        lds, fg, info);
+        return ialm_dispatch<double>(h, m, n, D, ldd, lambda, levels, mu0, rho, max_iter, tol, L_out, ldl, S_out, lds,
+                                     fg, info);
     });
 }
 
