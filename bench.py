@@ -275,7 +275,8 @@ def run_ours(args):
             "clocks": clocks_info,
             "e2e": {"value": statistics.mean(e2e), "unit": "s",
                     "h2d_bytes_per_step": int(Dh.nbytes + Qhp.nbytes),
-                    "d2h_bytes_per_step": int(Lh.nbytes + Sh.nbytes)},
+                    "d2h_bytes_per_step": int(Lh.nbytes + Sh.nbytes),
+                    "steps_ms": [round(x * 1e3, 3) for x in e2e]},
             "gpu_launches": int(sum(i["launches"] for i in inf_ml) / len(inf_ml)),
             "roofline": roofline}
     if rank == 0 and args.extras:
