@@ -116,10 +116,9 @@ struct PassArgs {
 // returns the number of blocks (partial sums written when a.GH is set)
 template <typename T> int launch_step_pass(const PassArgs<T> &a, bool coarse, cudaStream_t st);
 // the fine STEP pass on the tensor cores (k_pass_tc.cu); false, launching
-// nothing, when an operand does not meet the TMA rules.  A3 (m rows) and B3
-// (n rows) hold pass_tc_split_elems(rows, kmax) floats each (three TF32 parts).
-size_t pass_tc_split_elems(int rows, int kmax);
-bool launch_pass_tc(const PassArgs<float> &p, int kmax, float *A3, float *B3, int *err, cudaStream_t st);
+// nothing, when an operand does not meet the TMA rules.  err: device flag set
+// when a bounded wait of the kernel expired.
+bool launch_pass_tc(const PassArgs<float> &p, int *err, cudaStream_t st);
 // per-block fp64 partial sums of squares of X (rows x cols); returns the block count
 template <typename T> int launch_sumsq(int rows, int cols, const T *X, int64_t ld, double *partial, cudaStream_t st);
 // check pass at (L_k, S_k) with weight mu_bar: writes M = L - tau G and

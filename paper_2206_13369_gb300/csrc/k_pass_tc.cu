@@ -12,11 +12,28 @@
 //     a b ~ a_m b_m + a_l b_h + a_h b_l + a_m b_h + a_h b_m + a_h b_h
 // (the dropped terms are below 2^-32 relative).  The five small products
 // accumulate in one fp32 TMEM accumulator and a_h b_h in another; the
-// epilogue adds the two in fp32.  Each operand stage holds the three parts of
-// a 16-wide K slice of A^ and of B^ (64-byte swizzle), and the MMA issuer
-// pairs them: six MMAs per K step of 8.
+// epilogue adds the two in fp32.
+//
+// The split happens in shared memory: TMA brings a 16-wide K slice of the
+// fp32 factors (A_k or A_{k-1}, and B_k or B_{k-1}: the K blocks of A^ walk
+// the columns of A_k first, then those of A_{k-1}) into a raw stage;
+// converter warps scale it by (1 + beta) or -beta, zero the columns beyond
+// the live rank, and write the three parts into an operand stage (the same
+// swizzled offset in each part's slot), then hand that stage to the MMA
+// issuer, which pairs the parts: six MMAs per K step of 8.  Raw and operand
+// stages are separate rings, so TMA runs ahead of the converters and they
+// run ahead of the tensor cores.  The operands cross L2 once, as fp32, and
+// no split copy of the factors exists.
 //
 // Measured alternatives, each worse on the 2000 x 2000 rank-50 workload:
+// splitting the factors into three TF32 copies in global memory by a
+// separate launch (6.3 us, and three times the operand bytes through L2);
+// converting in place in the operand stage (TMA, conversion and MMA then
+// share two buffers and their latencies add) with two epilogue groups on
+// alternate quarters (while both compute, no epilogue input is in flight):
+// 37.5 us against 30.2 us + 6.3 us; the same with separate raw and operand
+// rings and one epilogue group storing each row's float4 directly (32 lines
+// per warp-wide store): 36.3 us;
 // two-term splitting (a_h b_h + a_h b_l + a_l b_h) represents a factor only
 // to 2^-22, and one accumulator shared by all six products loses the small
 // terms' low bits to the large running sum; both left a rel-KKT floor near
@@ -25,14 +42,20 @@
 // operands six times from L2.
 //
 // One persistent CTA per SM walks 128 x 128 output tiles.  Warp roles:
-//   warp 0   TMA producer of the operand stages (A^ and B^, three parts each)
+//   warp 0   TMA producer of the raw stages (fp32 slices of A and B)
 //   warp 1   MMA issuer: tcgen05.mma kind::tf32, M = 128, N = 128, K = 8
 //   warp 2   TMEM allocator (per buffer a 128-column accumulator for a_h b_h and
-//            one for the small products; two buffers: all 512 columns)
+//            one for the small products; two buffers: all 512 columns), then
+//            TMA store issuer of the results
 //   warp 3   TMA producer of the epilogue tiles: D, S_k, S_{k-1} in 32-column
 //            quarters (128-byte swizzle), double buffered
-//   warps 4-7 epilogue: tcgen05.ld of the accumulator (one TMEM lane quarter
-//            per warp, one row per thread), the elementwise step, stores.
+//   warps 4-11 epilogue, two groups of four on the two 16-column halves of
+//            each 32-column quarter: tcgen05.ld of the accumulator (one TMEM
+//            lane quarter per warp, one row per thread), the elementwise step;
+//            S_{k+1} and M are written over the D and S_k slots of the stage
+//            they came from (each thread rewrites what it read) and leave by
+//            TMA store, so the row-per-thread layout never meets the LSU
+//   warps 12-15 converters: the TF32 split of each raw stage.
 // So the HBM stream of the epilogue inputs runs while the tensor cores work
 // on the next tile, and the operands (L2-resident factors) never touch the
 // SIMT pipes.
@@ -57,14 +80,21 @@ constexpr int TBK = 16;    // K per operand stage: 64 bytes of fp32
 constexpr int HALF = 32;   // epilogue sub-tile columns (128 bytes of fp32)
 constexpr int OPS = 2;     // operand stages
 constexpr int EPS = 2;     // epilogue sub-tile buffers
-constexpr int NT = 256;
+constexpr int NT = 512;
+constexpr int EPI_W0 = 4;   // first epilogue warp (two groups of four)
+constexpr int CVT_W0 = 12;  // first converter warp
+constexpr int CVT_NW = 4;   // converter warps
 constexpr uint32_t A_BYTES = TBM * TBK * 4;             // 8 KB per part
 constexpr uint32_t B_BYTES = TBN * TBK * 4;             // 8 KB per part
 constexpr uint32_t OP_BYTES = 3 * A_BYTES + 3 * B_BYTES;  // three parts of each
+constexpr uint32_t OP_TX = A_BYTES + B_BYTES;             // bytes TMA brings per stage (fp32 slices)
+static_assert(A_BYTES == B_BYTES, "the converters address the parts of A and B with one stride");
 constexpr uint32_t EP_TILE = TBM * HALF * 4;            // 16 KB per array
 constexpr uint32_t EP_BYTES = 3 * EP_TILE;              // D, S_k, S_{k-1}
 constexpr uint32_t TMEM_COLS = 4 * TBN;  // two buffers x (large, small)
-constexpr size_t SMEM_BYTES = 1024 + OPS * (size_t)OP_BYTES + EPS * (size_t)EP_BYTES + 256;
+constexpr int RS = 2;       // raw stages (fp32 slices as TMA brings them)
+constexpr size_t SMEM_BYTES = 1024 + OPS * (size_t)OP_BYTES + EPS * (size_t)EP_BYTES + RS * (size_t)OP_TX + 256;
+static_assert(SMEM_BYTES <= 232448, "shared memory per block");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -130,6 +160,16 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// tile store from shared memory (bulk group of the issuing thread); the box
+// is clipped at the tensor's bounds
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(src)), "r"(x), "r"(y)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -171,18 +211,29 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+// 16 columns of two accumulators (at taddr and taddr + off) for this thread's
+// row, with one wait for both loads; the wait is in the same asm statement so
+// that no use of the registers can be scheduled before it
+__device__ __forceinline__ void tmem_ld16x2(uint32_t taddr, uint32_t off, float (&v)[16], float (&w)[16])
 {
-    uint32_t r[16];
+    uint32_t r[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%33];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr), "r"(taddr + off)
+        : "memory");
 #pragma unroll
-    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; i++) {
+        v[i] = __uint_as_float(r[i]);
+        w[i] = __uint_as_float(r[16 + i]);
+    }
 }
 
 __device__ __forceinline__ float tf32_rn(float x)
@@ -192,27 +243,32 @@ __device__ __forceinline__ float tf32_rn(float x)
     return __uint_as_float(r);
 }
 
-// live K of the contraction (the same on every role); the extended K is 6 K
-__device__ __forceinline__ int live_k(const int *rk, const int *rp, const Ctrl *ctrl)
+// live ranks of the contraction (the same on every role): K blocks [0, nk1)
+// walk the columns of A_k / B_k, blocks [nk1, nk1 + nk2) those of A_{k-1} /
+// B_{k-1}
+struct LiveK {
+    int rk, rp, nk1, nkb;
+};
+__device__ __forceinline__ LiveK live_k(const int *rk, const int *rp, const Ctrl *ctrl)
 {
-    const int a = rk ? *rk : 0;
-    const int b = (rp && ctrl->beta != 0.0) ? *rp : 0;
-    return a + b;
+    LiveK l;
+    l.rk = rk ? *rk : 0;
+    l.rp = (rp && ctrl->beta != 0.0) ? *rp : 0;
+    l.nk1 = (l.rk + TBK - 1) / TBK;
+    l.nkb = l.nk1 + (l.rp + TBK - 1) / TBK;
+    return l;
 }
 
 struct TcMaps {
-    CUtensorMap a[3], b[3];  // split factors: high, middle, low parts (K-major, 64-byte swizzle)
+    CUtensorMap a[2], b[2];  // fp32 factors: current, previous (K-major, 16-column boxes, 64-byte swizzle)
     CUtensorMap d, sk, sp;   // epilogue inputs (32-column boxes, 128-byte swizzle)
+    CUtensorMap so, mo;      // results S_{k+1} and M (same boxes)
 };
 
 struct TcArgs {
     int m, n;
     const uint32_t *Q;
     int64_t ldq;
-    float *Sout;
-    int64_t ldso;
-    float *M;
-    int64_t ldm;
     const int *rk, *rp;
     const Ctrl *ctrl;
     int has_sp;
@@ -229,12 +285,15 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *sOp = smem;                        // OPS x [A hi | A lo | B hi | B lo]
+    uint8_t *sOp = smem;                        // OPS x [A h | A m | A l | B h | B m | B l]
     uint8_t *sEp = smem + OPS * OP_BYTES;       // EPS x [D | S_k | S_{k-1}]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sEp + EPS * EP_BYTES);
-    uint64_t *op_full = bars, *op_empty = bars + OPS;
-    uint64_t *ep_full = bars + 2 * OPS, *ep_empty = ep_full + EPS;
-    uint64_t *acc_full = ep_empty + EPS, *acc_empty = acc_full + 2;
+    uint8_t *sRaw = sEp + EPS * EP_BYTES;       // RS x [A | B] (fp32)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sRaw + RS * OP_TX);
+    uint64_t *raw_full = bars, *raw_empty = bars + RS;
+    uint64_t *op_empty = bars + 2 * RS, *cvt_full = op_empty + OPS;
+    uint64_t *ep_full = cvt_full + OPS, *ep_empty = ep_full + EPS;
+    uint64_t *st_full = ep_empty + EPS;  // results of a stage written, ready to store
+    uint64_t *acc_full = st_full + EPS, *acc_empty = acc_full + 2;
     uint64_t *mma_done = acc_empty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -242,21 +301,26 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_n = (a.n + TBN - 1) / TBN;
     const int ntiles = ((a.m + TBM - 1) / TBM) * tiles_n;
-    const int K = live_k(a.rk, a.rp, a.ctrl);
-    const int nkb = (K + TBK - 1) / TBK;
+    const LiveK lk = live_k(a.rk, a.rp, a.ctrl);
+    const int nkb = lk.nkb;
 
     if (threadIdx.x == 0) {
+        for (int s = 0; s < RS; s++) {
+            mbar_init(&raw_full[s], 1);
+            mbar_init(&raw_empty[s], CVT_NW);  // one arrival per converter warp
+        }
         for (int s = 0; s < OPS; s++) {
-            mbar_init(&op_full[s], 1);
             mbar_init(&op_empty[s], 1);
+            mbar_init(&cvt_full[s], CVT_NW);
         }
         for (int s = 0; s < EPS; s++) {
             mbar_init(&ep_full[s], 1);
-            mbar_init(&ep_empty[s], 4);  // one arrival per epilogue warp
+            mbar_init(&ep_empty[s], 1);  // the store issuer, once the stores have read the stage
+            mbar_init(&st_full[s], 8);   // one arrival per epilogue warp
         }
         for (int s = 0; s < 2; s++) {
             mbar_init(&acc_full[s], 1);
-            mbar_init(&acc_empty[s], 4);
+            mbar_init(&acc_empty[s], 8);  // one arrival per epilogue warp
         }
         mbar_init(mma_done, 1);
         *abort_flag = 0;
@@ -280,22 +344,21 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
             for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
                 const int rb = (t / tiles_n) * TBM, cb = (t % tiles_n) * TBN;
                 for (int kb = 0; kb < nkb; kb++, i++) {
-                    const int s = i % OPS;
-                    if (i >= OPS && !mbar_wait(&op_empty[s], ((i / OPS) & 1) ^ 1, abort_flag)) break;
-                    uint8_t *st = sOp + s * OP_BYTES;
-                    mbar_expect_tx(&op_full[s], OP_BYTES);
-#pragma unroll
-                    for (int q = 0; q < 3; q++) {
-                        tma_load_2d(st + q * A_BYTES, &maps.a[q], &op_full[s], kb * TBK, rb);
-                        tma_load_2d(st + 3 * A_BYTES + q * B_BYTES, &maps.b[q], &op_full[s], kb * TBK, cb);
-                    }
+                    const int s = i % RS;
+                    if (i >= RS && !mbar_wait(&raw_empty[s], ((i / RS) & 1) ^ 1, abort_flag)) break;
+                    uint8_t *st = sRaw + s * OP_TX;
+                    const int src = kb < lk.nk1 ? 0 : 1;
+                    const int x = (kb < lk.nk1 ? kb : kb - lk.nk1) * TBK;
+                    mbar_expect_tx(&raw_full[s], OP_TX);
+                    tma_load_2d(st, &maps.a[src], &raw_full[s], x, rb);
+                    tma_load_2d(st + A_BYTES, &maps.b[src], &raw_full[s], x, cb);
                 }
             }
             // drain: the last phase issued on each stage has landed (time bound
             // only: no copy may still be in flight when the CTA exits)
-            for (int s = 0; s < OPS && s < i; s++) {
-                const int last = i - 1 - ((i - 1 - s) % OPS);
-                if (!mbar_wait(&op_full[s], (last / OPS) & 1, nullptr)) *abort_flag = 1;
+            for (int s = 0; s < RS && s < i; s++) {
+                const int last = i - 1 - ((i - 1 - s) % RS);
+                if (!mbar_wait(&raw_full[s], (last / RS) & 1, nullptr)) *abort_flag = 1;
             }
         }
     } else if (warp == 3) {
@@ -333,7 +396,7 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
                 bool ok = true;
                 for (int kb = 0; kb < nkb; kb++, i++) {
                     const int s = i % OPS;
-                    if (!mbar_wait(&op_full[s], (i / OPS) & 1, abort_flag)) {
+                    if (!mbar_wait(&cvt_full[s], (i / OPS) & 1, abort_flag)) {
                         ok = false;
                         break;
                     }
@@ -364,9 +427,37 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
             umma_commit(mma_done);
             if (!mbar_wait(mma_done, 0, nullptr)) *abort_flag = 1;
         }
-    } else if (warp >= 4) {
-        // epilogue: thread = one row of the tile
-        const int q = warp - 4;
+    } else if (warp == 2) {
+        // store issuer: S_{k+1} (D slot) and M (S_k slot) of each finished
+        // quarter; the stage goes back to the producer once the stores have
+        // read it
+        if (lane == 0) {
+            int i = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+                const int rb = (t / tiles_n) * TBM, cb = (t % tiles_n) * TBN;
+                bool ok = true;
+                for (int h = 0; h < TBN / HALF; h++, i++) {
+                    const int s = i % EPS;
+                    if (!mbar_wait(&st_full[s], (i / EPS) & 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint8_t *tD = sEp + s * EP_BYTES;
+                    tma_store_2d(&maps.so, tD, cb + h * HALF, rb);
+                    tma_store_2d(&maps.mo, tD + EP_TILE, cb + h * HALF, rb);
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                    mbar_arrive(&ep_empty[s]);
+                }
+                if (!ok) break;
+            }
+            // every store has completed before the CTA exits
+            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        }
+    } else if (warp >= EPI_W0 && warp < CVT_W0) {
+        // epilogue: thread = one row of the tile; group g takes columns
+        // [16 g, 16 g + 16) of every 32-column quarter
+        const int grp = (warp - EPI_W0) >> 2, q = (warp - EPI_W0) & 3;
         const int r = q * 32 + lane;
         const float beta = (float)a.ctrl->beta, tau = (float)a.ctrl->tau, thS = (float)a.ctrl->theta_S;
         int i = 0, lt = 0;
@@ -375,7 +466,7 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
             const int rb = (t / tiles_n) * TBM, cb = (t % tiles_n) * TBN;
             const int row = rb + r;
             // the row's mask words for this tile, loaded before the wait so that
-            // their latency overlaps it (one word per 32-column sub-tile)
+            // their latency overlaps it (one word per 32-column quarter)
             uint32_t words[TBN / HALF];
 #pragma unroll
             for (int w = 0; w < TBN / HALF; w++) {
@@ -392,29 +483,29 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
                     ok = false;
                     break;
                 }
-                float acc[HALF];
+                float acc[HALF / 2];
                 {
                     float v[16], w[16];
-                    const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * TBN + h * HALF);
+                    const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) +
+                                        (uint32_t)(buf * 2 * TBN + h * HALF + grp * (HALF / 2));
+                    tmem_ld16x2(ta, (uint32_t)TBN, v, w);
 #pragma unroll
-                    for (int half = 0; half < 2; half++) {
-                        tmem_ld16(ta + 16 * half, v);
-                        tmem_ld16(ta + TBN + 16 * half, w);
-#pragma unroll
-                        for (int j = 0; j < 16; j++) acc[16 * half + j] = nkb > 0 ? v[j] + w[j] : 0.f;
-                    }
+                    for (int j = 0; j < 16; j++) acc[j] = nkb > 0 ? v[j] + w[j] : 0.f;
                 }
-                const uint8_t *tD = sEp + s * EP_BYTES;
-                const uint8_t *tS = tD + EP_TILE;
+                uint8_t *tD = sEp + s * EP_BYTES;
+                uint8_t *tS = tD + EP_TILE;
                 const uint8_t *tP = a.has_sp ? tD + 2 * EP_TILE : tS;
-                const int c0 = cb + h * HALF;
+                const int c0 = cb + h * HALF + grp * (HALF / 2);
                 if (row < a.m) {
-                    const uint32_t word = words[h];  // 32 columns, one word
+                    const uint32_t word = words[h] >> (grp * (HALF / 2));
 #pragma unroll
-                    for (int c4 = 0; c4 < HALF / 4; c4++) {
+                    for (int c4 = 0; c4 < HALF / 8; c4++) {
                         const int col = c0 + 4 * c4;
-                        if (col >= a.n) break;
-                        const float4 dv = *swz4(tD, r, c4), sk = *swz4(tS, r, c4), sp = *swz4(tP, r, c4);
+                        if (col >= a.n) break;  // clipped by the store
+                        const int cc = grp * (HALF / 8) + c4;  // 16-byte chunk within the 32-column row
+                        float4 *pd = const_cast<float4 *>(swz4(tD, r, cc));
+                        float4 *ps = const_cast<float4 *>(swz4(tS, r, cc));
+                        const float4 dv = *pd, sk = *ps, sp = *swz4(tP, r, cc);
                         const float d4[4] = {dv.x, dv.y, dv.z, dv.w};
                         const float k4[4] = {sk.x, sk.y, sk.z, sk.w};
                         const float p4[4] = {sp.x, sp.y, sp.z, sp.w};
@@ -428,28 +519,76 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
                             so[j] = shrink(sh - tau * g, thS);
                             mo[j] = l - tau * g;
                         }
-                        if (col + 3 < a.n) {
-                            *reinterpret_cast<float4 *>(a.Sout + (int64_t)row * a.ldso + col) =
-                                make_float4(so[0], so[1], so[2], so[3]);
-                            *reinterpret_cast<float4 *>(a.M + (int64_t)row * a.ldm + col) =
-                                make_float4(mo[0], mo[1], mo[2], mo[3]);
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 4; j++)
-                                if (col + j < a.n) {
-                                    a.Sout[(int64_t)row * a.ldso + col + j] = so[j];
-                                    a.M[(int64_t)row * a.ldm + col + j] = mo[j];
-                                }
-                        }
+                        *pd = make_float4(so[0], so[1], so[2], so[3]);  // S_{k+1} over D
+                        *ps = make_float4(mo[0], mo[1], mo[2], mo[3]);  // M over S_k
                     }
                 }
+                // the results are read by the TMA stores (async proxy)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&ep_empty[s]);
+                if (lane == 0) mbar_arrive(&st_full[s]);
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[buf]);
             if (!ok) break;
+        }
+    } else if (warp >= CVT_W0) {
+        // converters: the TF32 split of each raw stage into an operand stage.
+        // A raw stage holds 512 float4 of A, then 512 of B; float4 g sits in
+        // tile row g / 4 at the 16-byte chunk (g % 4) ^ ((row / 2) % 4) of the
+        // 64-byte swizzle, i.e. K columns 4 ((g % 4) ^ ((row / 2) % 4)) ...;
+        // the parts go to the same offset of their slots
+        const int ct = threadIdx.x - CVT_W0 * 32;
+        const float ck = (float)(1.0 + a.ctrl->beta), cp = (float)(-a.ctrl->beta);
+        int i = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok && !*abort_flag; t += gridDim.x) {
+            for (int kb = 0; kb < nkb; kb++, i++) {
+                const int s = i % OPS, sr = i % RS;
+                if (!mbar_wait(&raw_full[sr], (i / RS) & 1, abort_flag) ||
+                    (i >= OPS && !mbar_wait(&op_empty[s], ((i / OPS) & 1) ^ 1, abort_flag))) {
+                    ok = false;
+                    break;
+                }
+                const uint8_t *rw = sRaw + sr * OP_TX;
+                uint8_t *st = sOp + s * OP_BYTES;
+                const bool cur = kb < lk.nk1;
+                const int k0 = (cur ? kb : kb - lk.nk1) * TBK;
+                const int lim = cur ? lk.rk : lk.rp;
+                const float ca = cur ? ck : cp;
+#pragma unroll
+                for (int u = 0; u < (2 * 512) / (CVT_NW * 32); u++) {
+                    const int f = ct + u * CVT_NW * 32;
+                    const int opnd = f >> 9, g = f & 511;
+                    uint8_t *p0 = st + (opnd ? 3 * A_BYTES : 0) + g * 16;
+                    const uint8_t *src = rw + (opnd ? A_BYTES : 0) + g * 16;
+                    const int tr = g >> 2;
+                    const int kc = k0 + 4 * ((g & 3) ^ ((tr >> 1) & 3));
+                    const float coef = opnd ? 1.f : ca;
+                    const float4 x = *reinterpret_cast<const float4 *>(src);
+                    const float xv[4] = {x.x, x.y, x.z, x.w};
+                    float hv[4], mv[4], lv[4];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const float v = kc + j < lim ? xv[j] * coef : 0.f;
+                        const float hi = tf32_rn(v), r1 = v - hi, md = tf32_rn(r1);
+                        hv[j] = hi;
+                        mv[j] = md;
+                        lv[j] = tf32_rn(r1 - md);
+                    }
+                    *reinterpret_cast<float4 *>(p0) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+                    *reinterpret_cast<float4 *>(p0 + A_BYTES) = make_float4(mv[0], mv[1], mv[2], mv[3]);
+                    *reinterpret_cast<float4 *>(p0 + 2 * A_BYTES) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+                }
+                // the parts are read by the tensor cores (async proxy)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&cvt_full[s]);
+                    mbar_arrive(&raw_empty[sr]);
+                }
+            }
         }
     }
 
@@ -459,44 +598,6 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
     if (warp == 2) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
-    }
-}
-
-// A^ = [(1 + beta) A_k, -beta A_{k-1}] and B^ = [B_k, B_{k-1}] split into
-// three TF32 parts each (P[0] high, P[1] middle, P[2] low; zero padding of the
-// live K to the next 16)
-struct SplitOut {
-    float *a[3], *b[3];
-};
-
-__global__ void tf32_split_kernel(int m, int n, const float *__restrict__ Ak, const float *__restrict__ Ap,
-                                  int64_t lda, const float *__restrict__ Bk, const float *__restrict__ Bp,
-                                  int64_t ldb, const int *rk_p, const int *rp_p, const Ctrl *ctrl, SplitOut o,
-                                  int64_t ldk)
-{
-    const int rk = rk_p ? *rk_p : 0;
-    const int rp = (rp_p && ctrl->beta != 0.0) ? *rp_p : 0;
-    const int K = rk + rp, Kp = (K + TBK - 1) / TBK * TBK;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= Kp) return;
-    const float ck = (float)(1.0 + ctrl->beta), cp = (float)(-ctrl->beta);
-    const int rows = max(m, n);
-    for (int row = blockIdx.y; row < rows; row += gridDim.y) {  // rows beyond the 65535 grid rows loop
-        if (row < m) {
-            const float v =
-                c < rk ? Ak[(int64_t)row * lda + c] * ck : (c < K ? Ap[(int64_t)row * lda + c - rk] * cp : 0.f);
-            const float h = tf32_rn(v), r1 = v - h, md = tf32_rn(r1);
-            o.a[0][(int64_t)row * ldk + c] = h;
-            o.a[1][(int64_t)row * ldk + c] = md;
-            o.a[2][(int64_t)row * ldk + c] = tf32_rn(r1 - md);
-        }
-        if (row < n) {
-            const float v = c < rk ? Bk[(int64_t)row * ldb + c] : (c < K ? Bp[(int64_t)row * ldb + c - rk] : 0.f);
-            const float h = tf32_rn(v), r1 = v - h, md = tf32_rn(r1);
-            o.b[0][(int64_t)row * ldk + c] = h;
-            o.b[1][(int64_t)row * ldk + c] = md;
-            o.b[2][(int64_t)row * ldk + c] = tf32_rn(r1 - md);
-        }
     }
 }
 
@@ -552,32 +653,26 @@ int sm_count()
 
 }  // namespace
 
-// three parts, each rows x round16(2 kmax)
-size_t pass_tc_split_elems(int rows, int kmax) { return 3 * (size_t)rows * (size_t)((2 * kmax + TBK - 1) / TBK * TBK); }
-
 // The fused fine pass on the tensor cores; false (nothing launched) when an
 // operand does not meet the TMA rules (16-byte aligned bases and strides) or
-// the tensor maps cannot be made.  A3 (m rows) and B3 (n rows) are scratch of
-// pass_tc_split_elems each: three parts of leading dimension ldk =
-// round16(2 kmax).
-bool launch_pass_tc(const PassArgs<float> &p, int kmax, float *A3, float *B3, int *err, cudaStream_t st)
+// the tensor maps cannot be made.
+bool launch_pass_tc(const PassArgs<float> &p, int *err, cudaStream_t st)
 {
     if (p.M == nullptr || p.Sout == nullptr || p.Ak == nullptr || p.Bk == nullptr) return false;
     if (p.ldfa != p.ldfap || p.ldfb != p.ldfbp) return false;
-    const int64_t ldk = (2 * kmax + TBK - 1) / TBK * TBK;
     const bool has_sp = p.Sp != nullptr && p.Sp != p.Sk;
     TcMaps maps;
-    SplitOut so;
-    for (int q = 0; q < 3; q++) {
-        so.a[q] = A3 + (size_t)q * p.m * ldk;
-        so.b[q] = B3 + (size_t)q * p.n * ldk;
-        if (!make_map_f32(&maps.a[q], so.a[q], (uint64_t)ldk, (uint64_t)p.m, (uint64_t)ldk, TBM, TBK)) return false;
-        if (!make_map_f32(&maps.b[q], so.b[q], (uint64_t)ldk, (uint64_t)p.n, (uint64_t)ldk, TBN, TBK)) return false;
-    }
+    const float *Ap = p.Ap ? p.Ap : p.Ak, *Bp = p.Bp ? p.Bp : p.Bk;
+    if (!make_map_f32(&maps.a[0], p.Ak, (uint64_t)p.ldfa, (uint64_t)p.m, (uint64_t)p.ldfa, TBM, TBK)) return false;
+    if (!make_map_f32(&maps.a[1], Ap, (uint64_t)p.ldfa, (uint64_t)p.m, (uint64_t)p.ldfa, TBM, TBK)) return false;
+    if (!make_map_f32(&maps.b[0], p.Bk, (uint64_t)p.ldfb, (uint64_t)p.n, (uint64_t)p.ldfb, TBN, TBK)) return false;
+    if (!make_map_f32(&maps.b[1], Bp, (uint64_t)p.ldfb, (uint64_t)p.n, (uint64_t)p.ldfb, TBN, TBK)) return false;
     if (!make_map_f32(&maps.d, p.D, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.ldd, TBM)) return false;
     if (!make_map_f32(&maps.sk, p.Sk, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.lds, TBM)) return false;
     if (!make_map_f32(&maps.sp, has_sp ? p.Sp : p.Sk, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.lds, TBM))
         return false;
+    if (!make_map_f32(&maps.so, p.Sout, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.ldso, TBM)) return false;
+    if (!make_map_f32(&maps.mo, p.M, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.ldm, TBM)) return false;
     static bool attr = false;
     if (!attr) {
         if (cudaFuncSetAttribute(pass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES) !=
@@ -585,23 +680,11 @@ bool launch_pass_tc(const PassArgs<float> &p, int kmax, float *A3, float *B3, in
             return false;
         attr = true;
     }
-    // split factors (one launch; threads over the padded live K), then the
-    // persistent pass
-    {
-        dim3 grid((unsigned)((ldk + 127) / 128), (unsigned)std::min(std::max(p.m, p.n), 65535));
-        CPCP_COUNT_LAUNCH();
-        tf32_split_kernel<<<grid, 128, 0, st>>>(p.m, p.n, p.Ak, p.Ap ? p.Ap : p.Ak, p.ldfa, p.Bk, p.Bp ? p.Bp : p.Bk,
-                                                p.ldfb, p.rk, p.Ap ? p.rp : nullptr, p.ctrl, so, ldk);
-    }
     TcArgs a;
     a.m = p.m;
     a.n = p.n;
     a.Q = p.Q;
     a.ldq = p.ldq;
-    a.Sout = p.Sout;
-    a.ldso = p.ldso;
-    a.M = p.M;
-    a.ldm = p.ldm;
     a.rk = p.rk;
     a.rp = p.Ap ? p.rp : nullptr;
     a.ctrl = p.ctrl;

@@ -651,9 +651,7 @@ struct SolveState {
     double *partial, *sums;
     int partial_blocks;
     bool bf16;  // contractions of the iteration's SVD in BF16 (mixed precision, before refinement)
-    // fine pass on the tensor cores: the split factors (three TF32 parts) and the error flag
-    float *A3 = nullptr, *B3 = nullptr;
-    int *tc_err = nullptr;
+    int *tc_err = nullptr;  // set: the fine pass runs on the tensor cores (its bounded-wait error flag)
     int side;   // half-step mode: warm subspace of the next iteration, 0 = right (Om), 1 = left (A[cur])
     std::vector<TransferDev<T>> tr;
 };
@@ -791,7 +789,7 @@ void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, 
         int tp = h->timer.open(CPCP_PHASE_PASS_FINE);
         bool done = false;
         if constexpr (std::is_same<T, float>::value) {
-            if (s.A3 != nullptr) done = launch_pass_tc(a, s.KM, s.A3, s.B3, s.tc_err, st);
+            if (s.tc_err != nullptr) done = launch_pass_tc(a, s.tc_err, st);
         }
         if (!done) launch_step_pass<T>(a, false, st);
         h->timer.close(tp);
@@ -950,8 +948,6 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
         CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
     }
     if (std::is_same<T, float>::value && o.tc_pass) {
-        s.A3 = wsT<float>(h, "tc_A3", pass_tc_split_elems(m, s.KM));
-        s.B3 = wsT<float>(h, "tc_B3", pass_tc_split_elems(n, s.KM));
         s.tc_err = wsT<int>(h, "tc_err", 1);
         CK(cudaMemsetAsync(s.tc_err, 0, sizeof(int), st));
     }
