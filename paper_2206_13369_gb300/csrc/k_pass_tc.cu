@@ -33,7 +33,13 @@
 // alternate quarters (while both compute, no epilogue input is in flight):
 // 37.5 us against 30.2 us + 6.3 us; the same with separate raw and operand
 // rings and one epilogue group storing each row's float4 directly (32 lines
-// per warp-wide store): 36.3 us;
+// per warp-wide store): 36.3 us; with TMA stores but two raw stages and two
+// 32-column epilogue stages: 33.2 us, where a %globaltimer trace showed each
+// 16-wide K stage taking about 1 us (a raw TMA from L2 takes about 1.1 us,
+// its conversion about 0.5 us, and two raw stages let only one be in flight
+// while the other converts) against 0.4 us of tensor-core work; a third raw
+// stage changed nothing: four converter warps rounding with cvt.rna.tf32 took
+// 1 us per stage (three conversions per element on a reduced-rate pipe);
 // two-term splitting (a_h b_h + a_h b_l + a_l b_h) represents a factor only
 // to 2^-22, and one accumulator shared by all six products loses the small
 // terms' low bits to the large running sum; both left a rel-KKT floor near
@@ -47,15 +53,15 @@
 //   warp 2   TMEM allocator (per buffer a 128-column accumulator for a_h b_h and
 //            one for the small products; two buffers: all 512 columns), then
 //            TMA store issuer of the results
-//   warp 3   TMA producer of the epilogue tiles: D, S_k, S_{k-1} in 32-column
-//            quarters (128-byte swizzle), double buffered
-//   warps 4-11 epilogue, two groups of four on the two 16-column halves of
-//            each 32-column quarter: tcgen05.ld of the accumulator (one TMEM
+//   warp 3   TMA producer of the epilogue tiles: D, S_k, S_{k-1} in 16-column
+//            slices (64-byte swizzle), three stages
+//   warps 4-11 epilogue, two groups of four on the two 8-column halves of
+//            each 16-column slice: tcgen05.ld of the accumulator (one TMEM
 //            lane quarter per warp, one row per thread), the elementwise step;
 //            S_{k+1} and M are written over the D and S_k slots of the stage
 //            they came from (each thread rewrites what it read) and leave by
 //            TMA store, so the row-per-thread layout never meets the LSU
-//   warps 12-15 converters: the TF32 split of each raw stage.
+//   warps 12-19 converters: the TF32 split of each raw stage.
 // So the HBM stream of the epilogue inputs runs while the tensor cores work
 // on the next tile, and the operands (L2-resident factors) never touch the
 // SIMT pipes.
@@ -77,22 +83,22 @@ namespace {
 constexpr int TBM = 128;   // tile rows = TMEM lanes
 constexpr int TBN = 128;   // tile columns = accumulator columns
 constexpr int TBK = 16;    // K per operand stage: 64 bytes of fp32
-constexpr int HALF = 32;   // epilogue sub-tile columns (128 bytes of fp32)
+constexpr int HALF = 16;   // epilogue sub-tile columns (64 bytes of fp32)
 constexpr int OPS = 2;     // operand stages
-constexpr int EPS = 2;     // epilogue sub-tile buffers
-constexpr int NT = 512;
+constexpr int EPS = 3;     // epilogue sub-tile buffers
+constexpr int NT = 640;
 constexpr int EPI_W0 = 4;   // first epilogue warp (two groups of four)
 constexpr int CVT_W0 = 12;  // first converter warp
-constexpr int CVT_NW = 4;   // converter warps
+constexpr int CVT_NW = 8;   // converter warps
 constexpr uint32_t A_BYTES = TBM * TBK * 4;             // 8 KB per part
 constexpr uint32_t B_BYTES = TBN * TBK * 4;             // 8 KB per part
 constexpr uint32_t OP_BYTES = 3 * A_BYTES + 3 * B_BYTES;  // three parts of each
 constexpr uint32_t OP_TX = A_BYTES + B_BYTES;             // bytes TMA brings per stage (fp32 slices)
 static_assert(A_BYTES == B_BYTES, "the converters address the parts of A and B with one stride");
-constexpr uint32_t EP_TILE = TBM * HALF * 4;            // 16 KB per array
+constexpr uint32_t EP_TILE = TBM * HALF * 4;            // 8 KB per array
 constexpr uint32_t EP_BYTES = 3 * EP_TILE;              // D, S_k, S_{k-1}
 constexpr uint32_t TMEM_COLS = 4 * TBN;  // two buffers x (large, small)
-constexpr int RS = 2;       // raw stages (fp32 slices as TMA brings them)
+constexpr int RS = 3;       // raw stages (fp32 slices as TMA brings them)
 constexpr size_t SMEM_BYTES = 1024 + OPS * (size_t)OP_BYTES + EPS * (size_t)EP_BYTES + RS * (size_t)OP_TX + 256;
 static_assert(SMEM_BYTES <= 232448, "shared memory per block");
 
@@ -211,36 +217,34 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
                  : "memory");
 }
 
-// 16 columns of two accumulators (at taddr and taddr + off) for this thread's
+// 8 columns of two accumulators (at taddr and taddr + off) for this thread's
 // row, with one wait for both loads; the wait is in the same asm statement so
 // that no use of the registers can be scheduled before it
-__device__ __forceinline__ void tmem_ld16x2(uint32_t taddr, uint32_t off, float (&v)[16], float (&w)[16])
+__device__ __forceinline__ void tmem_ld8x2(uint32_t taddr, uint32_t off, float (&v)[8], float (&w)[8])
 {
-    uint32_t r[32];
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%32];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%33];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr), "r"(taddr + off)
         : "memory");
 #pragma unroll
-    for (int i = 0; i < 16; i++) {
+    for (int i = 0; i < 8; i++) {
         v[i] = __uint_as_float(r[i]);
-        w[i] = __uint_as_float(r[16 + i]);
+        w[i] = __uint_as_float(r[8 + i]);
     }
 }
 
-__device__ __forceinline__ float tf32_rn(float x)
+// nearest TF32 value of a finite x (11 significant bits), ties away from zero:
+// half an ulp of the 11-bit significand added to the magnitude bits, then the
+// 13 low bits cleared (a carry into the exponent is the correct rounding).
+// Integer ALU work at full rate.
+__device__ __forceinline__ float tf32_round(float x)
 {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // live ranks of the contraction (the same on every role): K blocks [0, nk1)
@@ -261,7 +265,7 @@ __device__ __forceinline__ LiveK live_k(const int *rk, const int *rp, const Ctrl
 
 struct TcMaps {
     CUtensorMap a[2], b[2];  // fp32 factors: current, previous (K-major, 16-column boxes, 64-byte swizzle)
-    CUtensorMap d, sk, sp;   // epilogue inputs (32-column boxes, 128-byte swizzle)
+    CUtensorMap d, sk, sp;   // epilogue inputs (16-column boxes, 64-byte swizzle)
     CUtensorMap so, mo;      // results S_{k+1} and M (same boxes)
 };
 
@@ -275,10 +279,11 @@ struct TcArgs {
     int *err;
 };
 
-// element (r, c) of a 128-row x 32-column fp32 TMA box with 128-byte swizzle
-__device__ __forceinline__ const float4 *swz4(const uint8_t *tile, int r, int c4)
+// 16-byte chunk c4 (0..3) of row r of a 128-row x 16-column fp32 TMA box with
+// 64-byte swizzle: chunk bits [4, 6) of the offset XOR bits [7, 9)
+__device__ __forceinline__ float4 *swz4(uint8_t *tile, int r, int c4)
 {
-    return reinterpret_cast<const float4 *>(tile + r * 128 + ((c4 ^ (r & 7)) << 4));
+    return reinterpret_cast<float4 *>(tile + r * 64 + ((c4 ^ ((r >> 1) & 3)) << 4));
 }
 
 __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ TcMaps maps, TcArgs a)
@@ -429,7 +434,7 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
         }
     } else if (warp == 2) {
         // store issuer: S_{k+1} (D slot) and M (S_k slot) of each finished
-        // quarter; the stage goes back to the producer once the stores have
+        // slice; the stage goes back to the producer once the stores have
         // read it
         if (lane == 0) {
             int i = 0;
@@ -456,7 +461,7 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
         }
     } else if (warp >= EPI_W0 && warp < CVT_W0) {
         // epilogue: thread = one row of the tile; group g takes columns
-        // [16 g, 16 g + 16) of every 32-column quarter
+        // [8 g, 8 g + 8) of every 16-column slice
         const int grp = (warp - EPI_W0) >> 2, q = (warp - EPI_W0) & 3;
         const int r = q * 32 + lane;
         const float beta = (float)a.ctrl->beta, tau = (float)a.ctrl->tau, thS = (float)a.ctrl->theta_S;
@@ -466,11 +471,11 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
             const int rb = (t / tiles_n) * TBM, cb = (t % tiles_n) * TBN;
             const int row = rb + r;
             // the row's mask words for this tile, loaded before the wait so that
-            // their latency overlaps it (one word per 32-column quarter)
-            uint32_t words[TBN / HALF];
+            // their latency overlaps it (one word per 32 columns)
+            uint32_t words[TBN / 32];
 #pragma unroll
-            for (int w = 0; w < TBN / HALF; w++) {
-                const int c0 = cb + w * HALF;
+            for (int w = 0; w < TBN / 32; w++) {
+                const int c0 = cb + w * 32;
                 words[w] = (a.Q != nullptr && row < a.m && c0 < a.n) ? a.Q[(int64_t)row * a.ldq + (c0 >> 5)]
                                                                      : 0xffffffffu;
             }
@@ -485,26 +490,26 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
                 }
                 float acc[HALF / 2];
                 {
-                    float v[16], w[16];
+                    float v[HALF / 2], w[HALF / 2];
                     const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) +
                                         (uint32_t)(buf * 2 * TBN + h * HALF + grp * (HALF / 2));
-                    tmem_ld16x2(ta, (uint32_t)TBN, v, w);
+                    tmem_ld8x2(ta, (uint32_t)TBN, v, w);
 #pragma unroll
-                    for (int j = 0; j < 16; j++) acc[j] = nkb > 0 ? v[j] + w[j] : 0.f;
+                    for (int j = 0; j < HALF / 2; j++) acc[j] = nkb > 0 ? v[j] + w[j] : 0.f;
                 }
                 uint8_t *tD = sEp + s * EP_BYTES;
                 uint8_t *tS = tD + EP_TILE;
-                const uint8_t *tP = a.has_sp ? tD + 2 * EP_TILE : tS;
+                uint8_t *tP = a.has_sp ? tD + 2 * EP_TILE : tS;
                 const int c0 = cb + h * HALF + grp * (HALF / 2);
                 if (row < a.m) {
-                    const uint32_t word = words[h] >> (grp * (HALF / 2));
+                    const uint32_t word = words[(h * HALF) / 32] >> ((h * HALF) % 32 + grp * (HALF / 2));
 #pragma unroll
                     for (int c4 = 0; c4 < HALF / 8; c4++) {
                         const int col = c0 + 4 * c4;
                         if (col >= a.n) break;  // clipped by the store
-                        const int cc = grp * (HALF / 8) + c4;  // 16-byte chunk within the 32-column row
-                        float4 *pd = const_cast<float4 *>(swz4(tD, r, cc));
-                        float4 *ps = const_cast<float4 *>(swz4(tS, r, cc));
+                        const int cc = grp * (HALF / 8) + c4;  // 16-byte chunk within the 16-column row
+                        float4 *pd = swz4(tD, r, cc);
+                        float4 *ps = swz4(tS, r, cc);
                         const float4 dv = *pd, sk = *ps, sp = *swz4(tP, r, cc);
                         const float d4[4] = {dv.x, dv.y, dv.z, dv.w};
                         const float k4[4] = {sk.x, sk.y, sk.z, sk.w};
@@ -572,10 +577,10 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
 #pragma unroll
                     for (int j = 0; j < 4; j++) {
                         const float v = kc + j < lim ? xv[j] * coef : 0.f;
-                        const float hi = tf32_rn(v), r1 = v - hi, md = tf32_rn(r1);
+                        const float hi = tf32_round(v), r1 = v - hi, md = tf32_round(r1);
                         hv[j] = hi;
                         mv[j] = md;
-                        lv[j] = tf32_rn(r1 - md);
+                        lv[j] = tf32_round(r1 - md);
                     }
                     *reinterpret_cast<float4 *>(p0) = make_float4(hv[0], hv[1], hv[2], hv[3]);
                     *reinterpret_cast<float4 *>(p0 + A_BYTES) = make_float4(mv[0], mv[1], mv[2], mv[3]);
@@ -667,12 +672,12 @@ bool launch_pass_tc(const PassArgs<float> &p, int *err, cudaStream_t st)
     if (!make_map_f32(&maps.a[1], Ap, (uint64_t)p.ldfa, (uint64_t)p.m, (uint64_t)p.ldfa, TBM, TBK)) return false;
     if (!make_map_f32(&maps.b[0], p.Bk, (uint64_t)p.ldfb, (uint64_t)p.n, (uint64_t)p.ldfb, TBN, TBK)) return false;
     if (!make_map_f32(&maps.b[1], Bp, (uint64_t)p.ldfb, (uint64_t)p.n, (uint64_t)p.ldfb, TBN, TBK)) return false;
-    if (!make_map_f32(&maps.d, p.D, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.ldd, TBM)) return false;
-    if (!make_map_f32(&maps.sk, p.Sk, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.lds, TBM)) return false;
-    if (!make_map_f32(&maps.sp, has_sp ? p.Sp : p.Sk, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.lds, TBM))
+    if (!make_map_f32(&maps.d, p.D, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.ldd, TBM, HALF)) return false;
+    if (!make_map_f32(&maps.sk, p.Sk, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.lds, TBM, HALF)) return false;
+    if (!make_map_f32(&maps.sp, has_sp ? p.Sp : p.Sk, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.lds, TBM, HALF))
         return false;
-    if (!make_map_f32(&maps.so, p.Sout, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.ldso, TBM)) return false;
-    if (!make_map_f32(&maps.mo, p.M, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.ldm, TBM)) return false;
+    if (!make_map_f32(&maps.so, p.Sout, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.ldso, TBM, HALF)) return false;
+    if (!make_map_f32(&maps.mo, p.M, (uint64_t)p.n, (uint64_t)p.m, (uint64_t)p.ldm, TBM, HALF)) return false;
     static bool attr = false;
     if (!attr) {
         if (cudaFuncSetAttribute(pass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES) !=
