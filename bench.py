@@ -253,8 +253,9 @@ def run_ours(args):
     dom = "pass_fine" if tot["pass_fine"] >= tot["pass_coarse"] else "pass_coarse"
     avg_ms = tot[dom] / max(cnt[dom], 1)
     achieved = obs_bytes[dom] / (avg_ms / 1e3) / 1e9
-    # DRAM bytes of one fine-pass launch from ncu (null until measured on the current kernel)
-    traffic = {"pass_fine": None}.get(dom)
+    # DRAM bytes of one fine-pass launch from ncu (profiles/pass_tc_cpcp2000.md: read 50.66 MB +
+    # write 0.89 MB; the 32 MB of S and M writes are still in L2 when the launch ends)
+    traffic = {"pass_fine": 51.55e6}.get(dom)
     kname = {"pass_fine": "pass_tc_kernel (pass_fine)",
              "pass_coarse": "pass_kernel (pass_coarse)"}[dom]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",

@@ -101,6 +101,11 @@ def _load():
             lib.or_ialm.argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_int, C.c_double, C.c_double,
                                     C.c_int, C.c_double, _dp, _dp, C.c_void_p, C.POINTER(C.c_double)]
             lib.or_ialm.restype = C.c_int
+            lib.or_ialm_ex.argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_int, C.c_double, C.c_double,
+                                       C.c_int, C.c_double, _dp, _dp, C.c_void_p, C.POINTER(C.c_double), C.c_int]
+            lib.or_ialm_ex.restype = C.c_int
+            lib.or_restriction_orth.argtypes = [C.c_int, C.c_int, _dp]
+            lib.or_restriction_orth.restype = C.c_int
             lib.or_num_threads.restype = C.c_int
             lib.or_step.argtypes = [C.c_int, C.c_int, _dp, C.c_void_p, C.c_double, C.c_double, C.c_double,
                                     C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
@@ -187,6 +192,14 @@ def restriction(n: int, halvings: int, scaled: bool = True):
     return R, 1.0
 
 
+def restriction_orth(n: int, halvings: int):
+    """R (R^T R)^{-1/2} for the composite interpolation R of Sec. 3.1."""
+    nh = coarse_dim(n, halvings)
+    R = np.zeros((n, nh))
+    _load().or_restriction_orth(n, halvings, R)
+    return R
+
+
 def restriction_kappa(n: int, halvings: int) -> float:
     """Threshold of the coarse-gradient test for the unit-norm composite R."""
     R, _ = restriction(n, halvings, scaled=True)
@@ -264,9 +277,15 @@ def step(D, mask, lam, mu_k, beta, halvings, S_k, S_p, L_k, L_p):
     return S_out, L_out, int(r)
 
 
-def ialm(D, lam, levels=1, mu0=0.0, rho=0.0, max_iter=5000, tol=1e-7):
+_TRANSFER = {"unit": 0, "orth": 1, "unscaled": 2}
+
+
+def ialm(D, lam, levels=1, mu0=0.0, rho=0.0, max_iter=5000, tol=1e-7, transfer="unit"):
     """Paper-literal IALM (Alg. 1) or ML-IALM (Alg. 4, levels > 1) for eq. (rpca).
 
+    transfer (ML-IALM only): "unit" = R scaled to unit spectral norm (the
+    reading of Assumption 4), "orth" = R (R^T R)^{-1/2} (orthonormal columns,
+    same range), "unscaled" = the printed R.
     Returns (L, S, iters, fg) with fg the feasibility gap per iteration."""
     D = _f64(D)
     m, n = D.shape
@@ -274,8 +293,8 @@ def ialm(D, lam, levels=1, mu0=0.0, rho=0.0, max_iter=5000, tol=1e-7):
     S = np.zeros((m, n))
     fg = np.zeros(max_iter)
     last = C.c_double(0.0)
-    it = _load().or_ialm(m, n, D, float(lam), int(levels), float(mu0), float(rho), int(max_iter), float(tol),
-                         L, S, fg.ctypes.data_as(C.c_void_p), C.byref(last))
+    it = _load().or_ialm_ex(m, n, D, float(lam), int(levels), float(mu0), float(rho), int(max_iter), float(tol),
+                            L, S, fg.ctypes.data_as(C.c_void_p), C.byref(last), _TRANSFER[transfer])
     if it < 0:
         raise ValueError("oracle.ialm: needs n <= m")
     return L, S, it, fg[:it].copy()

@@ -19,7 +19,10 @@
  *     the coarse SVT + prolongation step of Alg. 4 (restrict -> SVD -> SVT ->
  *     prolong) and whose S-prox is the shrink of Alg. 3, with the joint step
  *     1/2 fixed by the 2-Lipschitz gradient (Sec. 2.3).
- *   - the paper-literal IALM (Alg. 1) and ML-IALM (Alg. 4).
+ *   - the paper-literal IALM (Alg. 1) and ML-IALM (Alg. 4), the latter also
+ *     with two other transfer operators for comparison: the printed R
+ *     unscaled, and R_o = R (R^T R)^{-1/2}, the operator with orthonormal
+ *     columns and the same range, for which Theorem LH-eps gives epsilon = 0.
  *
  * Readings taken where the paper is silent (stated once more in the design doc):
  *   * momentum: FISTA extrapolation on both L and S, restarted at level switches;
@@ -391,6 +394,43 @@ int or_restriction_scaled(int n, int halvings, double *R, double *scale_out)
     return nh;
 }
 
+/*
+ * R_o = R_p (R_p^T R_p)^{-1/2} with R_p the composite interpolation of
+ * Sec. 3.1 (unscaled): orthonormal columns spanning the range of R_p, so
+ * R_o R_o^T is the orthogonal projector onto that range.  Theorem LH-eps
+ * gives epsilon = 0 for such an R (its singular values are all 1); the paper
+ * sets it aside as dense.  (R_p^T R_p)^{-1/2} comes from the SVD of the
+ * symmetric positive definite R_p^T R_p, which is its eigendecomposition:
+ * V diag(s^{-1/2}) V^T.  Returns n_H, or -1 on allocation failure.
+ */
+int or_restriction_orth(int n, int halvings, double *R)
+{
+    int nh = or_restriction(n, halvings, R);
+    double *G = dalloc((size_t)nh * nh), *U = dalloc((size_t)nh * nh), *sv = dalloc((size_t)nh),
+           *V = dalloc((size_t)nh * nh), *W = dalloc((size_t)nh * nh), *Ro = dalloc((size_t)n * nh);
+    if (!G || !U || !sv || !V || !W || !Ro) {
+        free(G), free(U), free(sv), free(V), free(W), free(Ro);
+        return -1;
+    }
+    for (int a = 0; a < nh; a++)
+        for (int b = 0; b < nh; b++) {
+            double t = 0.0;
+            for (int j = 0; j < n; j++) t += R[(size_t)j * nh + a] * R[(size_t)j * nh + b];
+            G[(size_t)a * nh + b] = t;
+        }
+    or_svd(nh, nh, G, U, sv, V, NULL);
+    for (int a = 0; a < nh; a++)
+        for (int b = 0; b < nh; b++) {
+            double t = 0.0;
+            for (int c = 0; c < nh; c++) t += V[(size_t)a * nh + c] * V[(size_t)b * nh + c] / sqrt(sv[c]);
+            W[(size_t)a * nh + b] = t;
+        }
+    matmul(n, nh, nh, R, W, Ro);
+    memcpy(R, Ro, sizeof(double) * (size_t)n * nh);
+    free(G), free(U), free(sv), free(V), free(W), free(Ro);
+    return nh;
+}
+
 /* ------------------------------------------------------------------ */
 /* objective and gradient, eq. (cpcp) and eq. (cpcp-grad-LS)           */
 /* ------------------------------------------------------------------ */
@@ -744,7 +784,9 @@ int or_fista(int m, int n, const double *D, const unsigned char *mask, double la
 /* ------------------------------------------------------------------ */
 
 /*
- * Alg. 1 (levels == 1) or Alg. 4 (levels > 1, R scaled to unit norm):
+ * Alg. 1 (levels == 1) or Alg. 4 (levels > 1) with the transfer operator
+ * `transfer`: 0 = R scaled to unit spectral norm (the reading of Assumption
+ * 4), 1 = R_o of or_restriction_orth, 2 = the printed R unscaled:
  *   M   = D - S + Y / mu_k              (ML: M_H = M R)
  *   L   = U S_{1/mu_k}[Sigma] V^T        (ML: L = L_H R^T)
  *   S   = S_{lam/mu_k}[D - L + Y / mu_k]
@@ -755,8 +797,8 @@ int or_fista(int m, int n, const double *D, const unsigned char *mask, double la
  * 1.25 / ||D||_2.  Stops when the feasibility gap ||D-L-S||_F/||D||_F <= tol.
  * fg (optional) receives the gap after each iteration.  Returns iterations.
  */
-int or_ialm(int m, int n, const double *D, double lam, int levels, double mu0, double rho, int max_iter,
-            double tol, double *L, double *S, double *fg, double *final_fg)
+int or_ialm_ex(int m, int n, const double *D, double lam, int levels, double mu0, double rho, int max_iter,
+               double tol, double *L, double *S, double *fg, double *final_fg, int transfer)
 {
     if (n > m) return -1; /* the column restriction needs n <= m */
     size_t len = (size_t)m * n;
@@ -765,7 +807,12 @@ int or_ialm(int m, int n, const double *D, double lam, int levels, double mu0, d
     double *R = NULL;
     if (H > 0) {
         R = dalloc((size_t)n * nh);
-        or_restriction_scaled(n, H, R, NULL);
+        if (transfer == 1)
+            or_restriction_orth(n, H, R);
+        else if (transfer == 2)
+            or_restriction(n, H, R);
+        else
+            or_restriction_scaled(n, H, R, NULL);
     }
     double *Y = dalloc(len), *M = dalloc(len), *Vw = dalloc((size_t)nh * nh);
     for (int i = 0; i < nh; i++) Vw[(size_t)i * nh + i] = 1.0;
@@ -800,6 +847,12 @@ int or_ialm(int m, int n, const double *D, double lam, int levels, double mu0, d
     free(M);
     free(Vw);
     return k;
+}
+
+int or_ialm(int m, int n, const double *D, double lam, int levels, double mu0, double rho, int max_iter,
+            double tol, double *L, double *S, double *fg, double *final_fg)
+{
+    return or_ialm_ex(m, n, D, lam, levels, mu0, rho, max_iter, tol, L, S, fg, final_fg, 0);
 }
 
 /* Thread count the oracle uses (for reporting the CPU baseline). */
