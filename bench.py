@@ -380,14 +380,15 @@ def extras(device, stream, flush) -> dict:
     out["ialm_pcp"] = {"workload": "pcp-2000x2000-r50-ialm-fp32", "unit": "s", "tol_gap": 1e-5, "s": t,
                        "iters": info["iters"], "gap": info["relkkt"], "rank": info["rank"], "rel_err_L": err}
     del D, L
-    # IALM vs ML-IALM (Alg. 4, 3 levels) for the same iteration budget on a fully observed
-    # video-shaped matrix (19200 pixels x 400 frames), as in the fixed-budget comparisons
+    # IALM vs ML-IALM (Alg. 4, 3 levels; R scaled to unit norm, and an orthonormal basis of
+    # its range) for the same iteration budget on a fully observed video-shaped matrix
+    # (19200 pixels x 400 frames), as in the fixed-budget comparisons
     vv = workloads.video_cpcp(3, obs=1.0, levels=3)
     D = torch.as_tensor(vv["D"], dtype=torch.float32).cuda()
     nL0 = np.linalg.norm(vv["L0"])
     ml = {}
-    for name, lv in (("ialm", 1), ("ml_ialm_3lv", 3)):
-        with cpcp.Handle(device, stream=stream) as hh:
+    for name, lv, tr in (("ialm", 1, 0), ("ml_ialm_3lv", 3, 0), ("ml_ialm_3lv_orth", 3, 1)):
+        with cpcp.Handle(device, stream=stream, ialm_transfer=tr) as hh:
             hh.ialm(D, vv["lam"], levels=lv, rho=1.5, tol=1e-30, max_iter=15)
             t, (L, _, info) = _events_time(stream, lambda: hh.ialm(D, vv["lam"], levels=lv, rho=1.5, tol=1e-30,
                                                                    max_iter=15), 3, flush)

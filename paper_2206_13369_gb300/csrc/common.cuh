@@ -187,6 +187,15 @@ void launch_ialm_update(int m, int n, const T *D, int64_t ldd, const T *L, int64
                         double lam, double mu, double *partial, cudaStream_t st);
 // end == 0: theta_L = 1 / mu into the control block; 1: width bookkeeping
 void launch_ialm_ctrl(Ctrl *c, double mu, int end, cudaStream_t st);
+// the orthonormal-basis transfer of ML-IALM: C upper bidiagonal (diagonal cd,
+// super-diagonal ce, nh entries each).  Right solve in place: X C = Y for the
+// rows of X (rows x nh); left solve: Out = C^{-1} V for the first *kdyn
+// columns of V (nh x k)
+template <typename T>
+void launch_bidiag_right_solve(int rows, int nh, T *X, int64_t ld, const T *cd, const T *ce, cudaStream_t st);
+template <typename T>
+void launch_bidiag_left_solve(int nh, const T *V, int64_t ldv, const int *kdyn, int kmax, const T *cd, const T *ce,
+                              T *Out, int64_t ldo, cudaStream_t st);
 
 // small dense kernels (one CTA)
 // Cholesky pass of CholeskyQR: R = chol(X^T X) from row-split partial Gram

@@ -9,6 +9,10 @@
 //                per-block fp64 partial sums of ||E||_F^2    (the feasibility gap)
 //   ialm_ctrl    the SVT threshold 1 / mu_k into the control block, and the
 //                width bookkeeping after an iteration
+//   bidiag_*     ML-IALM with an orthonormal basis of the range of R (option):
+//                R C^{-1} with R^T R = C^T C; R^T R is tridiagonal (each row of
+//                the composite R has two adjacent nonzeros at most), so C is
+//                upper bidiagonal and M_H C^{-1}, C^{-1} V are two recurrences
 #include "common.cuh"
 
 namespace cpcp {
@@ -74,6 +78,40 @@ __global__ void ialm_ctrl_kernel(Ctrl *c, double mu, int end)
     }
 }
 
+// X C = Y in place, one thread per row: x_0 = y_0 / c_0,
+// x_a = (y_a - x_{a-1} e_{a-1}) / c_a (the rows are independent; n_H is short)
+template <typename T>
+__global__ void bidiag_right_solve_kernel(int rows, int nh, T *X, int64_t ld, const T *__restrict__ cd,
+                                          const T *__restrict__ ce)
+{
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+        T *x = X + r * ld;
+        T prev = x[0] / cd[0];
+        x[0] = prev;
+        for (int a = 1; a < nh; a++) {
+            prev = (x[a] - prev * ce[a - 1]) / cd[a];
+            x[a] = prev;
+        }
+    }
+}
+
+// Out = C^{-1} V, one thread per column: v'_{nh-1} = v_{nh-1} / c_{nh-1},
+// v'_a = (v_a - e_a v'_{a+1}) / c_a
+template <typename T>
+__global__ void bidiag_left_solve_kernel(int nh, const T *__restrict__ V, int64_t ldv, const int *kdyn,
+                                         const T *__restrict__ cd, const T *__restrict__ ce, T *__restrict__ Out,
+                                         int64_t ldo)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= *kdyn) return;
+    T next = V[(int64_t)(nh - 1) * ldv + c] / cd[nh - 1];
+    Out[(int64_t)(nh - 1) * ldo + c] = next;
+    for (int a = nh - 2; a >= 0; a--) {
+        next = (V[(int64_t)a * ldv + c] - ce[a] * next) / cd[a];
+        Out[(int64_t)a * ldo + c] = next;
+    }
+}
+
 }  // namespace
 
 constexpr int IALM_BLOCKS = 608;  // four per SM, a fixed count so the fp64 partial sums reduce in a fixed order
@@ -103,11 +141,30 @@ void launch_ialm_ctrl(Ctrl *c, double mu, int end, cudaStream_t st)
     ialm_ctrl_kernel<<<1, 1, 0, st>>>(c, mu, end);
 }
 
+template <typename T>
+void launch_bidiag_right_solve(int rows, int nh, T *X, int64_t ld, const T *cd, const T *ce, cudaStream_t st)
+{
+    const int blocks = (int)std::min<int64_t>(((int64_t)rows + 127) / 128, 1216);
+    CPCP_COUNT_LAUNCH();
+    bidiag_right_solve_kernel<T><<<blocks, 128, 0, st>>>(rows, nh, X, ld, cd, ce);
+}
+
+template <typename T>
+void launch_bidiag_left_solve(int nh, const T *V, int64_t ldv, const int *kdyn, int kmax, const T *cd, const T *ce,
+                              T *Out, int64_t ldo, cudaStream_t st)
+{
+    CPCP_COUNT_LAUNCH();
+    bidiag_left_solve_kernel<T><<<(kmax + 63) / 64, 64, 0, st>>>(nh, V, ldv, kdyn, cd, ce, Out, ldo);
+}
+
 #define INST(T)                                                                                                    \
     template void launch_ialm_m<T>(int, int, const T *, int64_t, const T *, const T *, int64_t, double, T *,        \
                                    int64_t, cudaStream_t);                                                         \
     template void launch_ialm_update<T>(int, int, const T *, int64_t, const T *, int64_t, T *, T *, int64_t, double, \
-                                        double, double *, cudaStream_t);
+                                        double, double *, cudaStream_t);                                            \
+    template void launch_bidiag_right_solve<T>(int, int, T *, int64_t, const T *, const T *, cudaStream_t);         \
+    template void launch_bidiag_left_solve<T>(int, const T *, int64_t, const int *, int, const T *, const T *, T *,  \
+                                              int64_t, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -609,7 +609,7 @@ int kmax_small<double>()
 // ---------------------------------------------------------------------------
 
 struct Opts {
-    int max_iter, check_every, k_max, p, q, qc, start_level, precision, half, tc_pass, graphs;
+    int max_iter, check_every, k_max, p, q, qc, start_level, precision, half, tc_pass, graphs, ialm_transfer;
     double eta, mu0, ratio, refine_at;
     uint64_t seed;
 };
@@ -631,6 +631,7 @@ Opts resolve(const cpcp_options &o)
     r.half = o.subspace_mode == 1;
     r.tc_pass = o.pass_simt == 0;
     r.graphs = o.plain_launches == 0;
+    r.ialm_transfer = o.ialm_transfer;
     r.refine_at = o.refine_at > 0 ? o.refine_at : 1e-3;
     r.seed = o.seed ? o.seed : 1;
     return r;
@@ -1211,6 +1212,38 @@ cpcp_status ialm_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, do
     double *partial = wsT<double>(h, "ia_partial", (size_t)std::max(nblk, 1024));
     double *sums = wsT<double>(h, "ia_sums", 4);
     SvdWork<T> w = svd_work<T>(h, "ia_svd_", m, n, kcap0);  // own tags: "ia_Y" is the multiplier
+    // orthonormal-basis transfer (option): R C^{-1} with R^T R = C^T C.  R^T R
+    // is tridiagonal (diagonal sum_j R_jc^2, off-diagonal sum_j R_jc R_j,c+1),
+    // so its Cholesky factor is upper bidiagonal
+    const bool orth = H > 0 && o.ialm_transfer == 1;
+    T *Cd = nullptr, *Ce = nullptr, *Vp = nullptr;
+    if (orth) {
+        const HostTransfer ht = build_transfer(n, H);
+        std::vector<double> dg(nh, 0.0), of(nh, 0.0);
+        for (int j = 0; j < n; j++) {
+            dg[ht.j0[j]] += ht.w0[j] * ht.w0[j];
+            if (ht.w1[j] != 0.0) {
+                dg[ht.j0[j] + 1] += ht.w1[j] * ht.w1[j];
+                of[ht.j0[j]] += ht.w0[j] * ht.w1[j];
+            }
+        }
+        std::vector<T> cd(nh), ce(nh, T(0));
+        double prev = 0.0;
+        for (int c = 0; c < nh; c++) {
+            const double v = dg[c] - prev * prev;
+            if (!(v > 0.0)) throw CpcpError{CPCP_ERR_NUMERIC, "R^T R is not positive definite"};
+            const double cc = std::sqrt(v);
+            prev = c + 1 < nh ? of[c] / cc : 0.0;
+            cd[c] = T(cc);
+            ce[c] = T(prev);
+        }
+        Cd = wsT<T>(h, "ia_cd", nh);
+        Ce = wsT<T>(h, "ia_ce", nh);
+        Vp = wsT<T>(h, "ia_Vp", (size_t)nh * KM);
+        CK(cudaMemcpyAsync(Cd, cd.data(), sizeof(T) * nh, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(Ce, ce.data(), sizeof(T) * nh, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));  // the host vectors must outlive the copies
+    }
 
     // ||D||_F, and ||D||_2 for the default mu0 (subspace SVD of D, 4 passes)
     const int nq = launch_sumsq<T>(m, n, D, ldd, partial, st);
@@ -1277,6 +1310,7 @@ cpcp_status ialm_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, do
         int64_t ldx = ldS;
         if (H > 0) {
             launch_restrict<T>(m, n, M, ldS, MH, ldh, tr, st);
+            if (orth) launch_bidiag_right_solve<T>(m, nh, MH, ldh, Cd, Ce, st);  // M R C^{-1}
             Mx = MH;
             ldx = ldh;
         }
@@ -1300,7 +1334,15 @@ cpcp_status ialm_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, do
         }
         prod_nn_small<T>(m, w.Qy, KM, w.Us, KM, A, KM, &ctrl->k, KM, st);
         prod_nn_small<T>(nh, w.Qz, KM, w.Wt, KM, Om, KM, &ctrl->k, KM, st);
-        launch_fill_prolong<T>(Om, KM, nh, ctrl, w.sig, KM, 0x1A12ull, n, B, KM, tr, st);
+        if (orth) {
+            // B = R C^{-1} V; the next start block keeps V (random columns
+            // into Vp are unused)
+            launch_bidiag_left_solve<T>(nh, Om, KM, &ctrl->k, KM, Cd, Ce, Vp, KM, st);
+            launch_fill_prolong<T>(Vp, KM, nh, ctrl, w.sig, KM, 0x1A12ull, n, B, KM, tr, st);
+            launch_fill_random<T>(Om, KM, nh, ctrl, 0, w.sig, KM, 0x1A14ull, st);
+        } else {
+            launch_fill_prolong<T>(Om, KM, nh, ctrl, w.sig, KM, 0x1A12ull, n, B, KM, tr, st);
+        }
         launch_reconstruct<T>(rc, st);
         launch_ialm_update<T>(m, n, D, ldd, L, ldS, S, Y, ldS, lam, mu, partial, st);
         launch_sum_partials(partial, nblk, 1, sums, st);

@@ -114,3 +114,29 @@ def test_ialm_invalid_arguments(cp):
         assert e.value.status == 1
         with pytest.raises(cp.CPCPError):
             h.ialm(torch.ones((20, 10), dtype=torch.float64, device="cuda"), -1.0)
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_ml_ialm_orthonormal_transfer_matches_oracle(cp, levels):
+    # ML-IALM with an orthonormal basis of the range of R (option ialm_transfer = 1;
+    # the oracle forms R (R^T R)^{-1/2}, the library R C^{-1}: the same range, so the
+    # same iterates).  A static video background (L0 = f 1^T) lies in that range,
+    # and both recover it as IALM does
+    p = W.video_cpcp(11, h=16, w=24, frames=64, rank=1, blocks=3, block=4, obs=1.0, levels=levels)
+    D, lam, L0 = p["D"], p["lam"], p["L0"]
+    mu0 = 1.25 / np.linalg.svd(D, compute_uv=False)[0]
+    Lr, Sr, it_r, fg_r = oracle.ialm(D, lam, levels=levels, mu0=mu0, rho=1.5, tol=1e-9, max_iter=300, transfer="orth")
+    with cp.Handle(0, power_iters=4, ialm_transfer=1) as h:
+        L, S, info = h.ialm(torch.as_tensor(D).cuda(), lam, levels=levels, mu0=mu0, rho=1.5, tol=1e-9, max_iter=300)
+    L, S = L.cpu().numpy(), S.cpu().numpy()
+    assert info["status"] == 0 and info["relkkt"] <= 1e-9
+    assert abs(info["iters"] - it_r) <= 1, (info["iters"], it_r)
+    n = min(it_r, info["iters"]) - 1
+    assert np.allclose(info["fg"][:n], fg_r[:n], rtol=1e-4, atol=0), (info["fg"][:n], fg_r[:n])
+    assert _rel(L, Lr) <= 2e-6 and _rel(S, Sr) <= 2e-6, (_rel(L, Lr), _rel(S, Sr))
+    assert _rel(L, L0) <= 1e-5
+    # the default transfer (R scaled to unit norm) loses the background
+    with cp.Handle(0, power_iters=4) as h:
+        Lu, _, _ = h.ialm(torch.as_tensor(D).cuda(), lam, levels=levels, mu0=mu0, rho=1.5, tol=1e-9, max_iter=300)
+    assert _rel(Lu.cpu().numpy(), L0) >= 0.5
+

@@ -1,0 +1,80 @@
+"""The transfer operator of ML-IALM (Alg. 4), evaluated in the oracle.
+
+Theorem LH-eps bounds the nuclear-norm defect of L_H R^T by
+epsilon = sum_k sigma_k(L_H) (1 - sigma_{n_H-k+1}(R)), which vanishes for an R
+with orthonormal columns.  R_o = R (R^T R)^{-1/2} is that operator for the
+range of the interpolation R of Sec. 3.1; with it Alg. 4's L-step is the exact
+minimiser of the augmented Lagrangian over {L_H R_o^T}, so ML-IALM is IALM on
+the problem restricted to that range.  With R scaled to unit spectral norm
+(the reading of Assumption 4) R R^T is about 0.86 on smooth vectors, and the
+iterate loses L as mu_k grows."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2206_13369_gb300 import workloads as W
+
+CASES = [(128, 1), (200, 2), (301, 2), (75, 3)]
+
+
+@pytest.mark.parametrize("n,h", CASES)
+def test_orth_transfer_orthonormal_same_range(n, h):
+    Ro = oracle.restriction_orth(n, h)
+    Rp, _ = oracle.restriction(n, h, scaled=False)
+    nh = Rp.shape[1]
+    assert Ro.shape == (n, nh)
+    assert np.abs(Ro.T @ Ro - np.eye(nh)).max() <= 1e-12
+    # the same range: R_o R_o^T is the orthogonal projector onto range(R_p)
+    assert np.abs(Ro @ (Ro.T @ Rp) - Rp).max() <= 1e-12 * np.abs(Rp).max()
+    # an independent route (LAPACK symmetric eigensolver) to (R^T R)^{-1/2}
+    w, V = np.linalg.eigh(Rp.T @ Rp)
+    assert np.abs(Ro - Rp @ (V @ np.diag(w ** -0.5) @ V.T)).max() <= 1e-12
+
+
+def test_constant_rows_lie_in_the_coarse_range():
+    # rows of the composite interpolation sum to one (the worked example after
+    # eq. (Rx)), so 1_H R^T = 1 and a constant-row background is representable
+    for n, h in CASES:
+        Rp, _ = oracle.restriction(n, h, scaled=False)
+        assert np.allclose(Rp.sum(axis=1), 1.0, atol=1e-14)
+        Ro = oracle.restriction_orth(n, h)
+        one = np.ones(n)
+        assert np.linalg.norm(one - Ro @ (Ro.T @ one)) <= 1e-12 * np.sqrt(n)
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_ml_ialm_orth_recovers_a_representable_background(levels):
+    # video-shaped, static background only (rank 1, L0 = f 1^T): L0 lies in
+    # the coarse range, so ML-IALM with R_o must recover it as IALM does; with
+    # the unit-norm R the iterate drifts away from it
+    p = W.video_cpcp(11, h=16, w=24, frames=64, rank=1, blocks=3, block=4, obs=1.0, levels=levels)
+    D, lam, L0 = p["D"], p["lam"], p["L0"]
+    mu0 = 1.25 / np.linalg.svd(D, compute_uv=False)[0]
+    L1, _, _, _ = oracle.ialm(D, lam, levels=1, mu0=mu0, rho=1.5, tol=1e-9, max_iter=300)
+    e1 = np.linalg.norm(L1 - L0) / np.linalg.norm(L0)
+    assert e1 <= 1e-6
+    Lo, So, it, fg = oracle.ialm(D, lam, levels=levels, mu0=mu0, rho=1.5, tol=1e-9, max_iter=300, transfer="orth")
+    assert fg[-1] <= 1e-9
+    assert np.linalg.norm(Lo - L0) / np.linalg.norm(L0) <= 1e-5
+    assert np.linalg.norm(So - p["S0"]) / np.linalg.norm(p["S0"]) <= 1e-5
+    Lu, _, _, _ = oracle.ialm(D, lam, levels=levels, mu0=mu0, rho=1.5, tol=1e-9, max_iter=300, transfer="unit")
+    assert np.linalg.norm(Lu - L0) / np.linalg.norm(L0) >= 0.5
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_ml_ialm_orth_error_at_the_projection_floor(levels):
+    # smooth but not representable (sinusoidal temporal components): the error
+    # of ML-IALM with R_o stays within 1.5x of ||L0 (I - R_o R_o^T)|| / ||L0||,
+    # the distance of L0 from the coarse range
+    p = W.video_cpcp(7, h=24, w=32, frames=128, rank=3, blocks=4, block=5, obs=1.0, levels=levels)
+    D, lam, L0 = p["D"], p["lam"], p["L0"]
+    mu0 = 1.25 / np.linalg.svd(D, compute_uv=False)[0]
+    Ro = oracle.restriction_orth(D.shape[1], levels - 1)
+    floor = np.linalg.norm(L0 - (L0 @ Ro) @ Ro.T) / np.linalg.norm(L0)
+    L, _, _, fg = oracle.ialm(D, lam, levels=levels, mu0=mu0, rho=1.5, tol=1e-7, max_iter=400, transfer="orth")
+    assert fg[-1] <= 1e-7
+    err = np.linalg.norm(L - L0) / np.linalg.norm(L0)
+    assert floor <= err <= 1.5 * floor, (err, floor)
+    # the printed R unscaled (R R^T up to 1.25 at the boundary) is unstable
+    Lx, _, _, _ = oracle.ialm(D, lam, levels=levels, mu0=mu0, rho=1.5, tol=1e-7, max_iter=400, transfer="unscaled")
+    assert not (np.linalg.norm(Lx - L0) / np.linalg.norm(L0) <= 0.5)
