@@ -106,6 +106,11 @@ def _load():
             lib.or_ialm_ex.restype = C.c_int
             lib.or_restriction_orth.argtypes = [C.c_int, C.c_int, _dp]
             lib.or_restriction_orth.restype = C.c_int
+            lib.or_fw_line_search.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)] * 2
+            lib.or_fw_line_search.restype = None
+            lib.or_fwt.argtypes = [C.c_int, C.c_int, _dp, C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int,
+                                   C.c_double, _dp, _dp, C.c_void_p, C.c_void_p]
+            lib.or_fwt.restype = C.c_int
             lib.or_num_threads.restype = C.c_int
             lib.or_step.argtypes = [C.c_int, C.c_int, _dp, C.c_void_p, C.c_double, C.c_double, C.c_double,
                                     C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
@@ -275,6 +280,30 @@ def step(D, mask, lam, mu_k, beta, halvings, S_k, S_p, L_k, L_p):
     r = _load().or_step(m, n, D, mp, float(lam), float(mu_k), float(beta), int(halvings), _f64(S_k), _f64(S_p),
                         _f64(L_k), _f64(L_p), S_out, L_out)
     return S_out, L_out, int(r)
+
+
+def fw_line_search(A, B, C_, ga, gb):
+    """Exact minimiser over [0,1]^2 of 1/2 (A a^2 + 2 C a b + B b^2) + ga a + gb b
+    (the two-segment line search of Alg. 3)."""
+    a, b = C.c_double(0.0), C.c_double(0.0)
+    _load().or_fw_line_search(float(A), float(B), float(C_), float(ga), float(gb), C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def fwt(D, mask, lam, mu, levels=1, max_iter=1000, tol=1e-3):
+    """FW-T (Alg. 3) or ML-FWT (Alg. 6, levels > 1) for eq. (cpcp) with weights
+    (mu, lam mu).  Returns (L, S, iters, ftrace, (t_L, t_S)) with ftrace the
+    epigraph objective after each iteration."""
+    D = _f64(D)
+    m, n = D.shape
+    mk, mp = _mask_ptr(mask, D.shape)
+    L = np.zeros((m, n))
+    S = np.zeros((m, n))
+    ft = np.zeros(max_iter)
+    ts = np.zeros(2)
+    it = _load().or_fwt(m, n, D, mp, float(lam), float(mu), int(levels), int(max_iter), float(tol), L, S,
+                        ft.ctypes.data_as(C.c_void_p), ts.ctypes.data_as(C.c_void_p))
+    return L, S, it, ft[:it].copy(), (float(ts[0]), float(ts[1]))
 
 
 _TRANSFER = {"unit": 0, "orth": 1, "unscaled": 2}

@@ -19,6 +19,8 @@
  *     the coarse SVT + prolongation step of Alg. 4 (restrict -> SVD -> SVT ->
  *     prolong) and whose S-prox is the shrink of Alg. 3, with the joint step
  *     1/2 fixed by the 2-Lipschitz gradient (Sec. 2.3).
+ *   - Frank-Wolfe Thresholding (Alg. 3) and ML-FWT (Alg. 6) for eq. (cpcp),
+ *     with the exact two-segment line search.
  *   - the paper-literal IALM (Alg. 1) and ML-IALM (Alg. 4), the latter also
  *     with two other transfer operators for comparison: the printed R
  *     unscaled, and R_o = R (R^T R)^{-1/2}, the operator with orthonormal
@@ -853,6 +855,192 @@ int or_ialm(int m, int n, const double *D, double lam, int levels, double mu0, d
             double tol, double *L, double *S, double *fg, double *final_fg)
 {
     return or_ialm_ex(m, n, D, lam, levels, mu0, rho, max_iter, tol, L, S, fg, final_fg, 0);
+}
+
+/* ------------------------------------------------------------------ */
+/* Frank-Wolfe Thresholding (Alg. 3) and its multilevel form (Alg. 6)  */
+/* ------------------------------------------------------------------ */
+
+static double clamp01(double x) { return x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x); }
+
+/*
+ * Exact minimiser over [0,1]^2 of the convex quadratic
+ *     q(a, b) = 1/2 (A a^2 + 2 C a b + B b^2) + ga a + gb b,
+ * the line search of Alg. 3 over the two segments [(L, t_L), (V_L, V_tL)]
+ * and [(S, t_S), (V_S, V_tS)]: A = ||P_Q[V_L - L]||^2, B = ||P_Q[V_S - S]||^2,
+ * C their inner product, ga and gb the derivatives of the objective along the
+ * segments at a = b = 0.  Candidates: the stationary point when it lies in
+ * the box, and the exact minimiser on each of the four edges; the smallest
+ * value wins (the minimiser of a convex function on a box is one of them).
+ */
+void or_fw_line_search(double A, double B, double C, double ga, double gb, double *a_out, double *b_out)
+{
+    double best = INFINITY, ba = 0.0, bb = 0.0;
+    double ca[6], cb[6];
+    int nc = 0;
+    const double det = A * B - C * C;
+    if (det > 0.0) {
+        const double a = (-ga * B + gb * C) / det, b = (-gb * A + ga * C) / det;
+        if (a >= 0.0 && a <= 1.0 && b >= 0.0 && b <= 1.0) {
+            ca[nc] = a;
+            cb[nc++] = b;
+        }
+    }
+    for (int e = 0; e < 2; e++) {
+        /* edge a = e: minimise 1/2 B b^2 + (gb + C e) b */
+        const double lin = gb + C * e;
+        ca[nc] = e;
+        cb[nc++] = B > 0.0 ? clamp01(-lin / B) : (lin < 0.0 ? 1.0 : 0.0);
+        /* edge b = e */
+        const double lin2 = ga + C * e;
+        ca[nc] = A > 0.0 ? clamp01(-lin2 / A) : (lin2 < 0.0 ? 1.0 : 0.0);
+        cb[nc++] = e;
+    }
+    for (int i = 0; i < nc; i++) {
+        const double a = ca[i], b = cb[i];
+        const double q = 0.5 * (A * a * a + 2.0 * C * a * b + B * b * b) + ga * a + gb * b;
+        if (q < best) {
+            best = q;
+            ba = a;
+            bb = b;
+        }
+    }
+    *a_out = ba;
+    *b_out = bb;
+}
+
+/*
+ * FW-T (Alg. 3; levels == 1) and ML-FWT (Alg. 6; levels > 1) for eq. (cpcp)
+ * with lambda_L = mu and lambda_S = lam mu, in the epigraph form of
+ * eq. (cpcp-fw): f = 1/2 ||P_Q[L + S - D]||_F^2 + lambda_L t_L + lambda_S t_S,
+ * ||L||_* <= t_L <= U_L, ||S||_1 <= t_S <= U_S.  Per iteration, with
+ * G = P_Q[L + S - D]:
+ *   - nuclear-ball LMO: M_L = -u v^T for the top singular pair (u, v) of G;
+ *     multilevel: the top pair (u, v_H) of G R and M_L = -u (R v_H)^T, the
+ *     coarse ball of radius 1 / ||R|| = 1 (R scaled to unit norm) lifted by
+ *     R^T (Sec. 3.4); <G, M_L> = -sigma_1 either way;
+ *   - l1-ball LMO: M_S = -sign(G_ij) e_i e_j^T at the largest |G_ij|;
+ *   - V_L = U_L M_L, V_tL = U_L unless lambda_L >= sigma_1 (then 0), and
+ *     likewise V_S, V_tS against max |G_ij|;
+ *   - exact line search over the two segments (or_fw_line_search);
+ *   - thresholding: S = shrink_{lambda_S}(S - P_Q[L + S - D]) with the new L
+ *     (the step of unit length of the S-block, whose gradient is 1-Lipschitz),
+ *     t_S = ||S||_1;
+ *   - bounds U_L = f / lambda_L, U_S = f / lambda_S at the new point.
+ * Starts from L = S = 0, t_L = t_S = 0, U = f_0 / lambda.  Stops when the
+ * relative objective decrease |f_{k-1} - f_k| <= tol f_{k-1} (the paper's
+ * 10^-3 criterion, taken from the FW-T reference it cites) or after
+ * max_iter iterations.  ftrace (optional) receives f after each iteration;
+ * tl_ts (optional) the final t_L, t_S.  Returns the iterations taken.
+ */
+int or_fwt(int m, int n, const double *D, const unsigned char *mask, double lam, double mu, int levels,
+           int max_iter, double tol, double *L, double *S, double *ftrace, double *tl_ts)
+{
+    const size_t len = (size_t)m * n;
+    const double lamL = mu, lamS = lam * mu;
+    const int H = levels - 1;
+    const int nh = or_coarse_dim(n, H);
+    double *R = NULL, *GR = NULL;
+    if (H > 0) {
+        R = dalloc((size_t)n * nh);
+        GR = dalloc((size_t)m * nh);
+        or_restriction_scaled(n, H, R, NULL);
+    }
+    const int nc = H > 0 ? nh : n;
+    const int p = m < nc ? m : nc;
+    double *G = dalloc(len), *PA = dalloc(len), *PB = dalloc(len), *U = dalloc((size_t)m * p),
+           *sv = dalloc((size_t)p), *V = dalloc((size_t)nc * p), *v = dalloc((size_t)n), *u = dalloc((size_t)m);
+    memset(L, 0, sizeof(double) * len);
+    memset(S, 0, sizeof(double) * len);
+    double tL = 0.0, tS = 0.0;
+    or_grad(m, n, D, mask, L, S, G);
+    double f = 0.5 * frob2(len, G);
+    double UL = f / lamL, US = f / lamS;
+    int k;
+    for (k = 0; k < max_iter; k++) {
+        const double fprev = f;
+        or_grad(m, n, D, mask, L, S, G);
+        /* nuclear-ball LMO (fine, or coarse and lifted) */
+        if (H > 0) {
+            matmul(m, n, nh, G, R, GR);
+            or_svd(m, nh, GR, U, sv, V, NULL);
+        } else {
+            or_svd(m, n, G, U, sv, V, NULL);
+        }
+        const double sig = sv[0];
+        for (int i = 0; i < m; i++) u[i] = U[(size_t)i * p];
+        if (H > 0) {
+            for (int j = 0; j < n; j++) {
+                double t = 0.0;
+                for (int c = 0; c < nh; c++) t += R[(size_t)j * nh + c] * V[(size_t)c * p];
+                v[j] = t;
+            }
+        } else {
+            for (int j = 0; j < n; j++) v[j] = V[(size_t)j * p];
+        }
+        const int useL = lamL < sig;
+        const double VtL = useL ? UL : 0.0;
+        /* l1-ball LMO: the first entry of largest magnitude */
+        size_t imax = 0;
+        double gmax = -1.0;
+        for (size_t i = 0; i < len; i++)
+            if (fabs(G[i]) > gmax) {
+                gmax = fabs(G[i]);
+                imax = i;
+            }
+        const int useS = lamS < gmax;
+        const double VtS = useS ? US : 0.0;
+        const double vs = useS ? -US * (G[imax] > 0.0 ? 1.0 : -1.0) : 0.0;
+        /* directions P_Q[V_L - L], P_Q[V_S - S] and the quadratic's coefficients */
+        double A = 0.0, B = 0.0, Cq = 0.0, ga = 0.0, gb = 0.0;
+        for (int i = 0; i < m; i++)
+            for (int j = 0; j < n; j++) {
+                const size_t q = (size_t)i * n + j;
+                const int obs = !mask || mask[q];
+                const double vl = useL ? -UL * u[i] * v[j] : 0.0;
+                const double vsq = q == imax ? vs : 0.0;
+                PA[q] = vl - L[q];
+                PB[q] = vsq - S[q];
+                if (obs) {
+                    A += PA[q] * PA[q];
+                    B += PB[q] * PB[q];
+                    Cq += PA[q] * PB[q];
+                    ga += G[q] * PA[q];
+                    gb += G[q] * PB[q];
+                }
+            }
+        ga += lamL * (VtL - tL);
+        gb += lamS * (VtS - tS);
+        double a, b;
+        or_fw_line_search(A, B, Cq, ga, gb, &a, &b);
+        for (size_t q = 0; q < len; q++) {
+            L[q] += a * PA[q];
+            S[q] += b * PB[q];
+        }
+        tL += a * (VtL - tL);
+        tS += b * (VtS - tS);
+        /* thresholding step of the S-block, then t_S = ||S||_1 */
+        or_grad(m, n, D, mask, L, S, G);
+        for (size_t q = 0; q < len; q++) PB[q] = S[q] - G[q];
+        or_shrink(len, PB, lamS, S);
+        tS = 0.0;
+        for (size_t q = 0; q < len; q++) tS += fabs(S[q]);
+        or_grad(m, n, D, mask, L, S, G);
+        f = 0.5 * frob2(len, G) + lamL * tL + lamS * tS;
+        UL = f / lamL;
+        US = f / lamS;
+        if (ftrace) ftrace[k] = f;
+        if (fabs(fprev - f) <= tol * fprev) {
+            k++;
+            break;
+        }
+    }
+    if (tl_ts) {
+        tl_ts[0] = tL;
+        tl_ts[1] = tS;
+    }
+    free(R), free(GR), free(G), free(PA), free(PB), free(U), free(sv), free(V), free(v), free(u);
+    return k;
 }
 
 /* Thread count the oracle uses (for reporting the CPU baseline). */
