@@ -214,6 +214,34 @@ cpcp_status cpcp_solve(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D
                        void *L_out, int64_t ldl, void *S_out, int64_t lds, cpcp_info *info);
 
 /*
+ * Frank-Wolfe Thresholding for eq. (cpcp): Alg. 3 (levels == 1) or ML-FWT,
+ * Alg. 6 (levels > 1), on the epigraph form eq. (cpcp-fw),
+ *   min 1/2 ||P_Q[L + S - D]||_F^2 + lambda_L t_L + lambda_S t_S,
+ *   ||L||_* <= t_L <= U_L, ||S||_1 <= t_S <= U_S,
+ * with lambda_L = mu and lambda_S = lambda * mu.  Each iteration takes the
+ * linear minimisation oracles at G = P_Q[L + S - D] (nuclear ball: the top
+ * singular pair of G, or of G R lifted by R for ML-FWT, from the subspace
+ * SVD of cpcp_solve, block width min(oversample, k_max, n_H, m) and
+ * power_iters passes, warm started from the last iteration's right vectors;
+ * at full width it is exact; l1 ball: the first entry
+ * of largest |G|), the exact minimiser of the objective over the two segments
+ * toward them, the thresholding step S = shrink_{lambda_S}(S - P_Q[L+S-D])
+ * with t_S = ||S||_1, and the bound updates U = f / lambda.  Starts from
+ * L = S = 0.  Stops when the relative decrease |f_{k-1} - f_k| <= tol f_{k-1}
+ * (OK; tol = 0 runs max_iter iterations, NOT_CONVERGED) or after max_iter
+ * iterations.  D, Q (optional, bit-packed as in cpcp_solve), L_out, S_out:
+ * device buffers (row-major, leading dimensions in elements).  ftrace
+ * (optional, host, max_iter doubles) receives f after each iteration;
+ * info->iters, relkkt (the last relative decrease), mu0 (the last f),
+ * seconds and launches are filled.
+ * Validation (INVALID_ARG): m, n >= 1; lambda, mu > 0; tol >= 0; max_iter >= 1;
+ * 1 <= levels <= 6 with n_H >= 1; device buffers.
+ */
+cpcp_status cpcp_fwt(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D, int64_t ldd, const uint32_t *Q,
+                     int64_t ldq, double lambda, double mu, int levels, int max_iter, double tol, void *L_out,
+                     int64_t ldl, void *S_out, int64_t lds, double *ftrace, cpcp_info *info);
+
+/*
  * Inexact augmented Lagrangian method for PCP, eq. (rpca) (min ||L||_* +
  * lambda ||S||_1 subject to L + S = D): Alg. 1 (levels == 1) or its
  * multilevel form Alg. 4 (levels > 1; every iteration takes the low-rank step

@@ -921,7 +921,7 @@ void or_fw_line_search(double A, double B, double C, double ga, double gb, doubl
  *     R^T (Sec. 3.4); <G, M_L> = -sigma_1 either way;
  *   - l1-ball LMO: M_S = -sign(G_ij) e_i e_j^T at the largest |G_ij|;
  *   - V_L = U_L M_L, V_tL = U_L unless lambda_L >= sigma_1 (then 0), and
- *     likewise V_S, V_tS against max |G_ij|;
+ *     likewise V_S, V_tS against max |G_ij| (with a relative margin, below);
  *   - exact line search over the two segments (or_fw_line_search);
  *   - thresholding: S = shrink_{lambda_S}(S - P_Q[L + S - D]) with the new L
  *     (the step of unit length of the S-block, whose gradient is 1-Lipschitz),
@@ -988,7 +988,11 @@ int or_fwt(int m, int n, const double *D, const unsigned char *mask, double lam,
                 gmax = fabs(G[i]);
                 imax = i;
             }
-        const int useS = lamS < gmax;
+        /* after a thresholding step every entry of the support of S has
+         * |G_ij| = lambda_S exactly (and the others |G_ij| <= lambda_S), so the
+         * test lambda_S >= max |G_ij| is taken with a relative margin of 1e-12:
+         * without it rounding would decide it */
+        const int useS = lamS * (1.0 + 1e-12) < gmax;
         const double VtS = useS ? US : 0.0;
         const double vs = useS ? -US * (G[imax] > 0.0 ? 1.0 : -1.0) : 0.0;
         /* directions P_Q[V_L - L], P_Q[V_S - S] and the quadratic's coefficients */

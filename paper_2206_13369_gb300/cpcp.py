@@ -98,6 +98,8 @@ def _load():
                                             C.POINTER(C.c_int64)]
     lib.cpcp_ialm.argtypes = [_vp, _int, _int, _int, _vp, _i64, _dbl, _int, _dbl, _dbl, _int, _dbl, _vp, _i64, _vp,
                               _i64, _vp, _vp]
+    lib.cpcp_fwt.argtypes = [_vp, _int, _int, _int, _vp, _i64, _vp, _i64, _dbl, _dbl, _int, _int, _dbl, _vp, _i64, _vp,
+                             _i64, _vp, _vp]
     return lib
 
 
@@ -105,7 +107,7 @@ _lib = _load()
 
 EXPORTED = ["cpcp_status_string", "cpcp_last_error", "cpcp_create", "cpcp_destroy", "cpcp_solve", "cpcp_step",
             "cpcp_restrict", "cpcp_prolong", "cpcp_transfer_info", "cpcp_svd", "cpcp_gemm_bf16",
-            "cpcp_solve_batched", "cpcp_backward", "cpcp_masked_norm_static", "cpcp_ialm"]
+            "cpcp_solve_batched", "cpcp_backward", "cpcp_masked_norm_static", "cpcp_ialm", "cpcp_fwt"]
 
 
 def lib():
@@ -263,6 +265,31 @@ class Handle:
             self._check(st, "cpcp_ialm")
         d = info.as_dict()
         d["fg"] = fg[:info.iters].copy()
+        return L_out, S_out, d
+
+    def fwt(self, D, Qbits, lam: float, mu: float, levels: int = 1, max_iter: int = 1000, tol: float = 1e-3,
+            L_out=None, S_out=None):
+        """Frank-Wolfe Thresholding (Alg. 3) / ML-FWT (Alg. 6, levels > 1) for
+        eq. (cpcp) on device tensors; returns (L, S, info) with info["f"] the
+        epigraph objective after each iteration."""
+        m, n = D.shape
+        dt = _dtype_code(D)
+        if L_out is None:
+            L_out = _empty_like(D, (m, n))
+        if S_out is None:
+            S_out = _empty_like(D, (m, n))
+        pD, ldd = _ptr(D)
+        pQ, ldq = _ptr(Qbits)
+        pL, ldl = _ptr(L_out)
+        pS, lds = _ptr(S_out)
+        ft = np.zeros(int(max_iter), dtype=np.float64)
+        info = Info()
+        st = _lib.cpcp_fwt(self._h, m, n, dt, pD, ldd, pQ, ldq if pQ else 0, float(lam), float(mu), int(levels),
+                           int(max_iter), float(tol), pL, ldl, pS, lds, ft.ctypes.data_as(_vp), C.byref(info))
+        if st not in (0, 5):
+            self._check(st, "cpcp_fwt")
+        d = info.as_dict()
+        d["f"] = ft[:info.iters].copy()
         return L_out, S_out, d
 
     def step(self, D, Qbits, lam, mu_k, beta, halvings, S_k, S_p, A_k, B_k, r_k, A_p, B_p, r_p, k, q=1,

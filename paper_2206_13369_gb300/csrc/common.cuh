@@ -187,6 +187,21 @@ void launch_ialm_update(int m, int n, const T *D, int64_t ldd, const T *L, int64
                         double lam, double mu, double *partial, cudaStream_t st);
 // end == 0: theta_L = 1 / mu into the control block; 1: width bookkeeping
 void launch_ialm_ctrl(Ctrl *c, double mu, int end, cudaStream_t st);
+// Frank-Wolfe Thresholding passes (k_fwt.cu): fwt_blocks() per-block
+// partials (1, 5 and 2 per block) and per-block argmax |G| (value, index)
+int fwt_blocks();
+template <typename T>
+void launch_fwt_grad(int m, int n, const T *D, int64_t ldd, const uint32_t *Q, int64_t ldq, const T *L, const T *S,
+                     int64_t ld, T *G, double *partial, double *amax_v, int64_t *amax_i, cudaStream_t st);
+template <typename T>
+void launch_fwt_coef(int m, int n, const uint32_t *Q, int64_t ldq, const T *L, const T *S, const T *G, int64_t ld,
+                     const T *u, int64_t ldu, const T *v, int64_t ldv, double cL, int64_t istar, double vs,
+                     double *partial, cudaStream_t st);
+template <typename T>
+void launch_fwt_update(int m, int n, const T *D, int64_t ldd, const uint32_t *Q, int64_t ldq, T *L, T *S, T *G,
+                       int64_t ld, const T *u, int64_t ldu, const T *v, int64_t ldv, double cL, int64_t istar,
+                       double vs, double a, double b, double lamS, double *partial, double *amax_v, int64_t *amax_i,
+                       cudaStream_t st);
 // the orthonormal-basis transfer of ML-IALM: C upper bidiagonal (diagonal cd,
 // super-diagonal ce, nh entries each).  Right solve in place: X C = Y for the
 // rows of X (rows x nh); left solve: Out = C^{-1} V for the first *kdyn

@@ -1391,6 +1391,196 @@ cpcp_status ialm_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, do
     return status;
 }
 
+// Exact minimiser over [0,1]^2 of 1/2 (A a^2 + 2 C a b + B b^2) + ga a + gb b
+// (convex: A, B >= 0, A B >= C^2): the stationary point if it lies in the box,
+// else the best of the four edge minimisers.  The two-segment line search of
+// Alg. 3.
+void fw_box_qp(double A, double B, double C, double ga, double gb, double *a_out, double *b_out)
+{
+    auto q = [&](double a, double b) { return 0.5 * (A * a * a + 2.0 * C * a * b + B * b * b) + ga * a + gb * b; };
+    auto c01 = [](double x) { return std::min(1.0, std::max(0.0, x)); };
+    double best_a = 0.0, best_b = 0.0, best = q(0.0, 0.0);
+    auto consider = [&](double a, double b) {
+        const double v = q(a, b);
+        if (v < best) {
+            best = v;
+            best_a = a;
+            best_b = b;
+        }
+    };
+    const double det = A * B - C * C;
+    if (det > 0.0) {
+        const double a = (C * gb - B * ga) / det, b = (C * ga - A * gb) / det;
+        if (a >= 0.0 && a <= 1.0 && b >= 0.0 && b <= 1.0) consider(a, b);
+    }
+    for (double e : {0.0, 1.0}) {
+        const double lb = gb + C * e, la = ga + C * e;
+        consider(e, B > 0.0 ? c01(-lb / B) : (lb < 0.0 ? 1.0 : 0.0));
+        consider(A > 0.0 ? c01(-la / A) : (la < 0.0 ? 1.0 : 0.0), e);
+    }
+    *a_out = best_a;
+    *b_out = best_b;
+}
+
+// FW-T (Alg. 3) / ML-FWT (Alg. 6) for eq. (cpcp) on device buffers; see
+// cpcp_fwt.  Scalars (t_L, t_S, U_L, U_S, the line search) on the host; the
+// m x n passes in k_fwt.cu; the top singular pair of G (or of G R) from the
+// warm-started subspace SVD of the CPCP path.
+template <typename T>
+cpcp_status fwt_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, const uint32_t *Q, int64_t ldq,
+                     double lam, double mu, int levels, int max_iter, double tol, T *L_out, int64_t ldl, T *S_out,
+                     int64_t lds, double *ftrace, cpcp_info *info)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const unsigned long long launches0 = g_kernel_launches;
+    cudaStream_t st = h->stream;
+    const Opts o = resolve(h->opt);
+    const int H = levels - 1;
+    const int64_t ld = round4(n);
+    TransferDev<T> tr = upload_transfer<T>(h, n, H, "fwt");
+    const int nh = tr.nh;
+    const int64_t ldh = round4(nh);
+    const int kcap0 = std::min({o.k_max, kmax_small<T>(), nh, m});
+    const int KM = (int)round4(kcap0);
+    const size_t mn = (size_t)m * ld;
+    T *L = wsT<T>(h, "fw_L", mn), *S = wsT<T>(h, "fw_S", mn), *G = wsT<T>(h, "fw_G", mn);
+    T *GR = H > 0 ? wsT<T>(h, "fw_GR", (size_t)m * ldh) : nullptr;
+    T *Om = wsT<T>(h, "fw_Om", (size_t)nh * KM), *Ub = wsT<T>(h, "fw_U", (size_t)m * KM);
+    T *Vb = wsT<T>(h, "fw_V", (size_t)nh * KM), *Vf = H > 0 ? wsT<T>(h, "fw_Vf", (size_t)n * KM) : nullptr;
+    Ctrl *ctrl = wsT<Ctrl>(h, "fw_ctrl", 1);
+    const int nb = fwt_blocks();
+    double *partial = wsT<double>(h, "fw_partial", (size_t)nb * 5), *amv = wsT<double>(h, "fw_amv", nb);
+    int64_t *ami = wsT<int64_t>(h, "fw_ami", nb);
+    SvdWork<T> w = svd_work<T>(h, "fw_svd_", m, n, kcap0);
+    std::vector<double> hp((size_t)nb * 5), hv(nb);
+    std::vector<int64_t> hi(nb);
+
+    Ctrl c0;
+    memset(&c0, 0, sizeof(c0));
+    c0.kcap = kcap0;
+    c0.k = std::min(kcap0, std::max(2, o.p));  // block width p (oversample): the LMO needs the top pair only
+    c0.k_next = c0.k;
+    c0.seed = o.seed;
+    c0.oversample = o.p;
+    CK(cudaMemcpyAsync(ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(L, 0, sizeof(T) * mn, st));
+    CK(cudaMemsetAsync(S, 0, sizeof(T) * mn, st));
+    launch_fill_random<T>(Om, KM, nh, ctrl, 1, nullptr, KM, 0xF3A1ull, st);
+    // sums of the per-block partials (fixed order) and the argmax of |G|
+    auto fetch = [&](int ns, bool am) {
+        CK(cudaMemcpyAsync(hp.data(), partial, sizeof(double) * nb * ns, cudaMemcpyDeviceToHost, st));
+        if (am) {
+            CK(cudaMemcpyAsync(hv.data(), amv, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(hi.data(), ami, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost, st));
+        }
+        CK(cudaStreamSynchronize(st));
+    };
+    auto psum = [&](int ns, int q) {
+        double t = 0.0;
+        for (int b = 0; b < nb; b++) t += hp[(size_t)b * ns + q];
+        return t;
+    };
+    auto pmax = [&](double &gmax, int64_t &istar) {
+        gmax = -1.0;
+        istar = INT64_MAX;
+        for (int b = 0; b < nb; b++)
+            if (hv[b] > gmax || (hv[b] == gmax && hi[b] < istar)) {
+                gmax = hv[b];
+                istar = hi[b];
+            }
+    };
+    launch_fwt_grad<T>(m, n, D, ldd, Q, ldq, L, S, ld, G, partial, amv, ami, st);
+    fetch(1, true);
+    double f = 0.5 * psum(1, 0), gmax;
+    int64_t istar;
+    pmax(gmax, istar);
+    const double lamL = mu, lamS = lam * mu;
+    double UL = f / lamL, US = f / lamS, tL = 0.0, tS = 0.0, rel = INFINITY;
+    cpcp_status status = CPCP_ERR_NOT_CONVERGED;
+    int k;
+    for (k = 0; k < max_iter; k++) {
+        const double fprev = f;
+        // LMO of the nuclear ball: top singular pair of G (or of G R, lifted by R)
+        const T *Mx = G;
+        int64_t ldx = ld;
+        if (H > 0) {
+            launch_restrict<T>(m, n, G, ld, GR, ldh, tr, st);
+            Mx = GR;
+            ldx = ldh;
+        }
+        subspace_svd<T>(h, w, m, nh, Mx, ldx, Om, o.q, &ctrl->k, nullptr);
+        prod_nn_small<T>(m, w.Qy, KM, w.Ut, KM, Ub, KM, &ctrl->k, KM, st);
+        prod_nn_small<T>(nh, w.Qz, KM, w.Wt, KM, Vb, KM, &ctrl->k, KM, st);
+        CK(cudaMemcpyAsync(Om, Vb, sizeof(T) * (size_t)nh * KM, cudaMemcpyDeviceToDevice, st));  // warm start
+        const T *vv = Vb;
+        if (H > 0) {
+            launch_prolong<T>(n, Vb, KM, Vf, KM, tr, &ctrl->k, KM, st);
+            vv = Vf;
+        }
+        T sig_t, gval;
+        CK(cudaMemcpyAsync(&sig_t, w.sig, sizeof(T), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&gval, G + (istar / n) * ld + (istar % n), sizeof(T), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const double sig = (double)sig_t;
+        // after a thresholding step every entry of the support of S has
+        // |G_ij| = lambda_S exactly, the others |G_ij| <= lambda_S: the l1 test
+        // takes a relative margin of a few hundred ulp of T, else rounding decides it
+        const double margin = sizeof(T) == 4 ? 1e-5 : 1e-12;
+        const bool useL = lamL < sig, useS = lamS * (1.0 + margin) < gmax;
+        const double cL = useL ? -UL : 0.0, VtL = useL ? UL : 0.0;
+        const double vs = useS ? -US * ((double)gval > 0.0 ? 1.0 : -1.0) : 0.0, VtS = useS ? US : 0.0;
+        launch_fwt_coef<T>(m, n, Q, ldq, L, S, G, ld, Ub, KM, vv, KM, cL, istar, vs, partial, st);
+        fetch(5, false);
+        const double A = psum(5, 0), B = psum(5, 1), C = psum(5, 2);
+        const double ga = psum(5, 3) + lamL * (VtL - tL), gb = psum(5, 4) + lamS * (VtS - tS);
+        double a, b;
+        fw_box_qp(A, B, C, ga, gb, &a, &b);
+        launch_fwt_update<T>(m, n, D, ldd, Q, ldq, L, S, G, ld, Ub, KM, vv, KM, cL, istar, vs, a, b, lamS, partial,
+                             amv, ami, st);
+        fetch(2, true);
+        tL += a * (VtL - tL);
+        tS = psum(2, 0);
+        f = 0.5 * psum(2, 1) + lamL * tL + lamS * tS;
+        pmax(gmax, istar);
+        UL = f / lamL;
+        US = f / lamS;
+        if (ftrace) ftrace[k] = f;
+        if (!std::isfinite(f)) {
+            status = CPCP_ERR_NUMERIC;
+            k++;
+            break;
+        }
+        rel = std::fabs(fprev - f) / fprev;
+        if (rel <= tol) {
+            status = CPCP_OK;
+            k++;
+            break;
+        }
+    }
+    if (L_out)
+        CK(cudaMemcpy2DAsync(L_out, sizeof(T) * ldl, L, sizeof(T) * ld, sizeof(T) * n, m, cudaMemcpyDeviceToDevice,
+                             st));
+    if (S_out)
+        CK(cudaMemcpy2DAsync(S_out, sizeof(T) * lds, S, sizeof(T) * ld, sizeof(T) * n, m, cudaMemcpyDeviceToDevice,
+                             st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    if (info) {
+        cpcp_info inf;
+        memset(&inf, 0, sizeof(inf));
+        inf.status = status;
+        inf.iters = k;
+        inf.level_iters[std::min(H, 7)] = k;
+        inf.final_level = H;
+        inf.relkkt = rel;
+        inf.mu0 = f;  // the epigraph objective at the last iterate
+        inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        inf.launches = (long long)(g_kernel_launches - launches0);
+        *info = inf;
+    }
+    return status;
+}
+
 template <typename T>
 cpcp_status ialm_dispatch(cpcp_context *h, int m, int n, const void *Dv, int64_t ldd, double lam, int levels,
                           double mu0, double rho, int max_iter, double tol, void *Lv, int64_t ldl, void *Sv,
@@ -2392,6 +2582,32 @@ cpcp_status cpcp_ialm(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D,
                                         lds, fg, info);
         return ialm_dispatch<double>(h, m, n, D, ldd, lambda, levels, mu0, rho, max_iter, tol, L_out, ldl, S_out, lds,
                                      fg, info);
+    });
+}
+
+cpcp_status cpcp_fwt(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D, int64_t ldd, const uint32_t *Q,
+                     int64_t ldq, double lambda, double mu, int levels, int max_iter, double tol, void *L_out,
+                     int64_t ldl, void *S_out, int64_t lds, double *ftrace, cpcp_info *info)
+{
+    if (!h) return CPCP_ERR_INVALID_ARG;
+    return guarded(h, [&]() -> cpcp_status {
+        if (m < 1 || n < 1 || !D || bad_dtype(dt)) throw CpcpError{CPCP_ERR_INVALID_ARG, "need m, n >= 1, D, dtype"};
+        if (!(lambda > 0) || !(mu > 0) || !(tol >= 0) || max_iter < 1)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "lambda and mu must be positive, tol >= 0, max_iter >= 1"};
+        if (levels < 1 || levels > 6) throw CpcpError{CPCP_ERR_INVALID_ARG, "levels must be in [1, 6]"};
+        if (ldd < n || (L_out && ldl < n) || (S_out && lds < n) || (Q && ldq < (n + 31) / 32))
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "leading dimension too small"};
+        if (coarse_dim(n, levels - 1) < 1) throw CpcpError{CPCP_ERR_INVALID_ARG, "coarse width below 1"};
+        if (!is_device_ptr(D) || (Q && !is_device_ptr(Q)) || (L_out && !is_device_ptr(L_out)) ||
+            (S_out && !is_device_ptr(S_out)))
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "cpcp_fwt takes device buffers"};
+        if (dt == CPCP_F32)
+            return fwt_core<float>(h, m, n, static_cast<const float *>(D), ldd, Q, ldq, lambda, mu, levels, max_iter,
+                                   tol, static_cast<float *>(L_out), ldl, static_cast<float *>(S_out), lds, ftrace,
+                                   info);
+        return fwt_core<double>(h, m, n, static_cast<const double *>(D), ldd, Q, ldq, lambda, mu, levels, max_iter,
+                                tol, static_cast<double *>(L_out), ldl, static_cast<double *>(S_out), lds, ftrace,
+                                info);
     });
 }
 
