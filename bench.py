@@ -147,6 +147,18 @@ def dist_setup():
     return world, rank, local
 
 
+def rank_max(vals, device):
+    """Each value's maximum over the ranks of the process group (the values
+    themselves without one): the job's time is its slowest replica's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in vals]
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
 def run_reference(args):
     world, rank, local = dist_setup()
     if rank != 0:
@@ -221,10 +233,7 @@ def run_ours(args):
         torch.distributed.barrier()
     ml = statistics.mean(t_ml)
     sl = statistics.mean(t_sl)
-    if world > 1:
-        t = torch.tensor([ml, sl], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ml, sl = float(t[0]), float(t[1])
+    ml, sl = rank_max([ml, sl], "cuda")
 
     # end to end through the C ABI with host buffers (H2D of D and the mask,
     # solve, D2H of L and S inside the timed region)

@@ -1,0 +1,69 @@
+"""The multi-rank (N > 1) path of bench.py on CPU with the gloo backend,
+world size 2: the max-over-ranks reduction of the timed values, and the
+reference arm launched by torchrun (rank 0 alone runs and prints one JSON line;
+the other rank exits 0 without work).  A solve does not shard, so ranks run
+replicas and share nothing but these host-side steps."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w, r, _ = bench.dist_setup()
+        vals = bench.rank_max([1.0 + r, 10.0 - r, 0.5], "cpu")
+        with open(os.path.join(out_dir, f"rank{r}.json"), "w") as f:
+            json.dump({"world": w, "rank": r, "vals": vals}, f)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_rank_max_over_two_gloo_ranks(tmp_path):
+    import torch.multiprocessing as mp
+    port = _free_port()
+    mp.start_processes(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    for r in range(2):
+        got = json.load(open(tmp_path / f"rank{r}.json"))
+        assert got["world"] == 2 and got["rank"] == r
+        assert got["vals"] == [2.0, 10.0, 0.5]
+
+
+def test_rank_max_single_process_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.rank_max([3.0, 1.5], "cpu") == [3.0, 1.5]
+
+
+def test_reference_arm_under_torchrun_prints_on_rank0_only():
+    port = _free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
+           "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
+           "--warmup", "0"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["higher_is_better"] is False
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
