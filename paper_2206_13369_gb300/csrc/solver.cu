@@ -1500,6 +1500,11 @@ cpcp_status fwt_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, con
     int k;
     for (k = 0; k < max_iter; k++) {
         const double fprev = f;
+        // no finite entry of G (NaN input): no argmax, nothing to step on
+        if (istar < 0 || istar >= (int64_t)m * n || !std::isfinite(f)) {
+            status = CPCP_ERR_NUMERIC;
+            break;
+        }
         // LMO of the nuclear ball: top singular pair of G (or of G R, lifted by R)
         const T *Mx = G;
         int64_t ldx = ld;
