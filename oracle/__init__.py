@@ -55,7 +55,7 @@ def build(force: bool = False) -> str:
 class _Opts(C.Structure):
     _fields_ = [("tau", C.c_double), ("eta", C.c_double), ("mu0", C.c_double),
                 ("check_every", C.c_int), ("max_iter", C.c_int), ("switch_ratio", C.c_double),
-                ("start_level", C.c_int), ("fixed_iters", C.c_int)]
+                ("start_level", C.c_int), ("fixed_iters", C.c_int), ("transfer", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -245,7 +245,7 @@ def relkkt(D, mask, lam, mu, L, S, tau: float = 0.5) -> float:
 
 
 def fista(D, mask, lam, mu, levels=1, tol=1e-10, *, tau=0.5, eta=0.9, mu0=0.0, check_every=10,
-          max_iter=20000, switch_ratio=0.9, start_level=-1, fixed_iters=0, trace_cap=4096):
+          max_iter=20000, switch_ratio=0.9, start_level=-1, fixed_iters=0, trace_cap=4096, transfer="unit"):
     """Multilevel accelerated proximal gradient for eq. (cpcp); returns (L, S, info).
 
     info: iters, final_level, rank, checks, status (0 ok, 3 not converged),
@@ -255,7 +255,8 @@ def fista(D, mask, lam, mu, levels=1, tol=1e-10, *, tau=0.5, eta=0.9, mu0=0.0, c
     mk, mp = _mask_ptr(mask, D.shape)
     L = np.zeros((m, n))
     S = np.zeros((m, n))
-    o = _Opts(tau, eta, mu0, check_every, max_iter, switch_ratio, start_level, fixed_iters)
+    o = _Opts(tau, eta, mu0, check_every, max_iter, switch_ratio, start_level, fixed_iters,
+              {"unit": 0, "orth": 1}[transfer])
     inf = _Info()
     tr = np.zeros(max(trace_cap, 1))
     st = _load().or_fista(m, n, D, mp, float(lam), float(mu), int(levels), float(tol), C.byref(o), L, S,

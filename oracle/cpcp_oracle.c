@@ -520,6 +520,8 @@ typedef struct {
     double switch_ratio; /* move finer when rel-KKT > ratio * previous check */
     int start_level;     /* halvings to start at; < 0 means levels - 1 */
     int fixed_iters;     /* > 0: run exactly this many iterations at start_level, no checks */
+    int transfer;        /* 0: R scaled to unit norm (Assumption 4); 1: R (R^T R)^{-1/2} (orthonormal
+                            columns, the same range; or_restriction_orth) */
 } or_opts;
 
 typedef struct {
@@ -594,7 +596,10 @@ static int fista_core(int m, int n, const double *D, const unsigned char *mask, 
     for (int h = 1; h <= H; h++) {
         nhs[h] = or_coarse_dim(n, h);
         R[h] = dalloc((size_t)n * nhs[h]);
-        or_restriction_scaled(n, h, R[h], NULL);
+        if (o->transfer == 1)
+            or_restriction_orth(n, h, R[h]);
+        else
+            or_restriction_scaled(n, h, R[h], NULL);
     }
     double *kappa = dalloc((size_t)H + 1);
     for (int h = 1; h <= H; h++) kappa[h] = or_restriction_kappa(n, nhs[h], R[h]);

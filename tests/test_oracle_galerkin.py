@@ -78,3 +78,19 @@ def test_ml_ialm_orth_error_at_the_projection_floor(levels):
     # the printed R unscaled (R R^T up to 1.25 at the boundary) is unstable
     Lx, _, _, _ = oracle.ialm(D, lam, levels=levels, mu0=mu0, rho=1.5, tol=1e-7, max_iter=400, transfer="unscaled")
     assert not (np.linalg.norm(Lx - L0) / np.linalg.norm(L0) <= 0.5)
+
+
+def test_cpcp_multilevel_with_orthonormal_transfer_reaches_the_optimum():
+    # the multilevel proximal-gradient solver finishes on the fine level, so with
+    # either transfer it reaches the single-level optimum of eq. (cpcp); on smooth
+    # data the orthonormal transfer leaves the fine level less to do
+    p = W.video_cpcp(7, h=16, w=24, frames=64, rank=2, blocks=3, block=4, obs=0.8, levels=3)
+    D, mask, lam, mu = p["D"], p["mask"], p["lam"], p["mu"]
+    L1, S1, i1 = oracle.fista(D, mask, lam, mu, levels=1, tol=1e-9)
+    Lo, So, io = oracle.fista(D, mask, lam, mu, levels=3, tol=1e-9, transfer="orth")
+    Lu, Su, iu = oracle.fista(D, mask, lam, mu, levels=3, tol=1e-9, transfer="unit")
+    for L, S, inf in ((Lo, So, io), (Lu, Su, iu)):
+        assert inf["status"] == 0 and inf["final_level"] == 0
+        assert np.linalg.norm(L - L1) / np.linalg.norm(L1) <= 1e-5
+        assert np.linalg.norm(S - S1) / np.linalg.norm(S1) <= 1e-5
+    assert io["level_iters"][0] < iu["level_iters"][0]
