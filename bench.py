@@ -397,7 +397,7 @@ def extras(device, stream, flush) -> dict:
     nL0 = np.linalg.norm(vv["L0"])
     ml = {}
     for name, lv, tr in (("ialm", 1, 0), ("ml_ialm_3lv", 3, 0), ("ml_ialm_3lv_orth", 3, 1)):
-        with cpcp.Handle(device, stream=stream, ialm_transfer=tr) as hh:
+        with cpcp.Handle(device, stream=stream, transfer=tr) as hh:
             hh.ialm(D, vv["lam"], levels=lv, rho=1.5, tol=1e-30, max_iter=15)
             t, (L, _, info) = _events_time(stream, lambda: hh.ialm(D, vv["lam"], levels=lv, rho=1.5, tol=1e-30,
                                                                    max_iter=15), 3, flush)

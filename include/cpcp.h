@@ -113,12 +113,14 @@ typedef struct {
                               the host; 0 (default) captures an iteration's kernels in a CUDA
                               graph the second time the same (level, buffer parity) comes up and
                               replays the graph for the iterations between residual checks */
-    int ialm_transfer;     /* cpcp_ialm with levels > 1: 0 (default) = Alg. 4 with R scaled to unit
-                              spectral norm (the reading of Assumption 4); 1 = R replaced by an
-                              orthonormal basis of its range, R C^{-1} with R^T R = C^T C (C upper
-                              bidiagonal, R^T R being tridiagonal), which makes the L-step the exact
-                              minimiser of the augmented Lagrangian over {L_H R^T} (epsilon = 0 in
-                              Theorem LH-eps); applied to M_H and V by two bidiagonal solves */
+    int transfer;          /* coarse levels of cpcp_solve and ML-IALM (cpcp_ialm, levels > 1):
+                              0 (default) = R scaled to unit spectral norm (the reading of
+                              Assumption 4); 1 = R replaced by an orthonormal basis of its range,
+                              R C^{-1} with R^T R = C^T C (C upper bidiagonal, R^T R being
+                              tridiagonal), which makes the coarse L-step the exact minimiser over
+                              {L_H R^T} (epsilon = 0 in Theorem LH-eps); applied to M_H (and the
+                              restricted gradient of the level test) and to V by two bidiagonal
+                              solves.  cpcp_solve rejects it with subspace_mode = 1 */
 } cpcp_options;
 
 /* Phases timed when cpcp_options.profile is set. */
@@ -247,7 +249,7 @@ cpcp_status cpcp_fwt(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D, 
  * multilevel form Alg. 4 (levels > 1; every iteration takes the low-rank step
  * on the coarse level, L = SVT_{1/mu_k}(M R) R^T with R the composite
  * restriction scaled to unit norm, or with the orthonormal basis R C^{-1} of
- * its range when cpcp_options.ialm_transfer = 1), with S_0 = Y_0 = 0 and
+ * its range when cpcp_options.transfer = 1), with S_0 = Y_0 = 0 and
  *   M = D - S + Y / mu_k;  L = SVT_{1/mu_k}(M)  (or the coarse step);
  *   S = shrink_{lambda/mu_k}(D - L + Y / mu_k);  Y += mu_k (D - L - S).
  * Penalty schedule: rho > 1 gives mu_{k+1} = rho mu_k, otherwise mu_k =

@@ -609,7 +609,7 @@ int kmax_small<double>()
 // ---------------------------------------------------------------------------
 
 struct Opts {
-    int max_iter, check_every, k_max, p, q, qc, start_level, precision, half, tc_pass, graphs, ialm_transfer;
+    int max_iter, check_every, k_max, p, q, qc, start_level, precision, half, tc_pass, graphs, transfer;
     double eta, mu0, ratio, refine_at;
     uint64_t seed;
 };
@@ -631,7 +631,7 @@ Opts resolve(const cpcp_options &o)
     r.half = o.subspace_mode == 1;
     r.tc_pass = o.pass_simt == 0;
     r.graphs = o.plain_launches == 0;
-    r.ialm_transfer = o.ialm_transfer;
+    r.transfer = o.transfer;
     r.refine_at = o.refine_at > 0 ? o.refine_at : 1e-3;
     r.seed = o.seed ? o.seed : 1;
     return r;
@@ -1215,7 +1215,7 @@ cpcp_status ialm_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, do
     // orthonormal-basis transfer (option): R C^{-1} with R^T R = C^T C.  R^T R
     // is tridiagonal (diagonal sum_j R_jc^2, off-diagonal sum_j R_jc R_j,c+1),
     // so its Cholesky factor is upper bidiagonal
-    const bool orth = H > 0 && o.ialm_transfer == 1;
+    const bool orth = H > 0 && o.transfer == 1;
     T *Cd = nullptr, *Ce = nullptr, *Vp = nullptr;
     if (orth) {
         const HostTransfer ht = build_transfer(n, H);

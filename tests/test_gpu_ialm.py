@@ -118,7 +118,7 @@ def test_ialm_invalid_arguments(cp):
 
 @pytest.mark.parametrize("levels", [2, 3])
 def test_ml_ialm_orthonormal_transfer_matches_oracle(cp, levels):
-    # ML-IALM with an orthonormal basis of the range of R (option ialm_transfer = 1;
+    # ML-IALM with an orthonormal basis of the range of R (option transfer = 1;
     # the oracle forms R (R^T R)^{-1/2}, the library R C^{-1}: the same range, so the
     # same iterates).  A static video background (L0 = f 1^T) lies in that range,
     # and both recover it as IALM does
@@ -126,7 +126,7 @@ def test_ml_ialm_orthonormal_transfer_matches_oracle(cp, levels):
     D, lam, L0 = p["D"], p["lam"], p["L0"]
     mu0 = 1.25 / np.linalg.svd(D, compute_uv=False)[0]
     Lr, Sr, it_r, fg_r = oracle.ialm(D, lam, levels=levels, mu0=mu0, rho=1.5, tol=1e-9, max_iter=300, transfer="orth")
-    with cp.Handle(0, power_iters=4, ialm_transfer=1) as h:
+    with cp.Handle(0, power_iters=4, transfer=1) as h:
         L, S, info = h.ialm(torch.as_tensor(D).cuda(), lam, levels=levels, mu0=mu0, rho=1.5, tol=1e-9, max_iter=300)
     L, S = L.cpu().numpy(), S.cpu().numpy()
     assert info["status"] == 0 and info["relkkt"] <= 1e-9
