@@ -326,12 +326,14 @@ def extras(device, stream, flush) -> dict:
     D = torch.as_tensor(v["D"], dtype=torch.float32).cuda()
     Q = torch.as_tensor(cpcp.pack_mask(v["mask"])).cuda()
     vm = {}
-    for name, prec, lv in (("mixed_4lv", 1, 4), ("fp32_4lv", 0, 4), ("mixed_1lv", 1, 1), ("fp32_1lv", 0, 1)):
-        with cpcp.Handle(device, stream=stream, precision=prec) as hh:
+    for name, prec, lv, tr in (("mixed_4lv", 1, 4, 0), ("fp32_4lv", 0, 4, 0), ("mixed_1lv", 1, 1, 0),
+                               ("fp32_1lv", 0, 1, 0), ("mixed_4lv_orth", 1, 4, 1), ("fp32_4lv_orth", 0, 4, 1)):
+        with cpcp.Handle(device, stream=stream, precision=prec, transfer=tr) as hh:
             hh.solve(D, Q, v["lam"], v["mu"], levels=lv, tol=TOL)
             t, (_, _, info) = _events_time(stream, lambda: hh.solve(D, Q, v["lam"], v["mu"], levels=lv, tol=TOL), 3,
                                            flush)
-        vm[name] = {"s": t, "iters": info["iters"], "bf16_iters": info["bf16_iters"], "relkkt": info["relkkt"]}
+        vm[name] = {"s": t, "iters": info["iters"], "level_iters": info["level_iters"][:lv], "bf16_iters": info["bf16_iters"],
+                    "relkkt": info["relkkt"]}
     out["video_mixed"] = {"workload": "video-19200x400-r5-cpcp", "unit": "s", "tol": TOL, **vm}
     del D, Q
     # 256 uneven instances in one persistent launch
@@ -367,8 +369,8 @@ def extras(device, stream, flush) -> dict:
     D = torch.as_tensor(c6["D"], dtype=torch.float32).cuda()
     Q = torch.as_tensor(cpcp.pack_mask(c6["mask"])).cuda()
     hs = {}
-    for name, lv in (("3lv", 3), ("1lv", 1)):
-        with cpcp.Handle(device, stream=stream) as hh:
+    for name, lv, tr in (("3lv", 3, 0), ("1lv", 1, 0), ("3lv_orth", 3, 1)):
+        with cpcp.Handle(device, stream=stream, transfer=tr) as hh:
             hh.solve(D, Q, c6["lam"], c6["mu"], levels=lv, tol=TOL)
             t, (_, _, info) = _events_time(stream, lambda: hh.solve(D, Q, c6["lam"], c6["mu"], levels=lv, tol=TOL), 3,
                                            flush)

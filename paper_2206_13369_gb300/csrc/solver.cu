@@ -410,6 +410,61 @@ TransferDev<T> upload_transfer(cpcp_context *h, int n, int halvings, const std::
     return d;
 }
 
+// Orthonormal basis of the range of the composite R (the unit-norm scaled one)
+// for `halvings` halvings: R C^{-1} with R^T R = C^T C.  R^T R is tridiagonal
+// (diagonal sum_j R_jc^2, off-diagonal sum_j R_jc R_j,c+1: each row of R has
+// two adjacent nonzeros at most), so C is upper bidiagonal (diagonal cd,
+// super-diagonal ce, uploaded as T).  kappa: the coarse-gradient threshold of
+// build_transfer for R C^{-1}, whose squared Frobenius norm is n_H and whose
+// column sums are 1^T R C^{-1} (the recurrence x C = 1^T R).
+template <typename T>
+struct OrthTransfer {
+    T *cd = nullptr, *ce = nullptr;
+    double kappa = 0.0;
+};
+
+template <typename T>
+OrthTransfer<T> upload_orth(cpcp_context *h, int n, int halvings, const std::string &tag)
+{
+    const HostTransfer ht = build_transfer(n, halvings);
+    const int nh = ht.nh;
+    std::vector<double> dg(nh, 0.0), of(nh, 0.0), cs(nh, 0.0);
+    for (int j = 0; j < n; j++) {
+        dg[ht.j0[j]] += ht.w0[j] * ht.w0[j];
+        cs[ht.j0[j]] += ht.w0[j];
+        if (ht.w1[j] != 0.0) {
+            dg[ht.j0[j] + 1] += ht.w1[j] * ht.w1[j];
+            of[ht.j0[j]] += ht.w0[j] * ht.w1[j];
+            cs[ht.j0[j] + 1] += ht.w1[j];
+        }
+    }
+    std::vector<T> cd(nh), ce(nh, T(0));
+    std::vector<double> cdd(nh), ced(nh, 0.0);
+    double prev = 0.0;
+    for (int c = 0; c < nh; c++) {
+        const double v = dg[c] - prev * prev;
+        if (!(v > 0.0)) throw CpcpError{CPCP_ERR_NUMERIC, "R^T R is not positive definite"};
+        cdd[c] = std::sqrt(v);
+        prev = c + 1 < nh ? of[c] / cdd[c] : 0.0;
+        ced[c] = prev;
+        cd[c] = T(cdd[c]);
+        ce[c] = T(prev);
+    }
+    double x = 0.0, cs2 = 0.0;
+    for (int c = 0; c < nh; c++) {
+        x = (cs[c] - (c > 0 ? x * ced[c - 1] : 0.0)) / cdd[c];
+        cs2 += x * x;
+    }
+    OrthTransfer<T> o;
+    o.kappa = std::sqrt(std::sqrt((double)nh / n) * std::sqrt(cs2 / n));
+    o.cd = wsT<T>(h, tag + "_cd", nh);
+    o.ce = wsT<T>(h, tag + "_ce", nh);
+    CK(cudaMemcpyAsync(o.cd, cd.data(), sizeof(T) * nh, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(o.ce, ce.data(), sizeof(T) * nh, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));  // the host vectors must outlive the copies
+    return o;
+}
+
 // ---------------------------------------------------------------------------
 // subspace-iteration SVD
 // ---------------------------------------------------------------------------
@@ -653,6 +708,11 @@ struct SolveState {
     int partial_blocks;
     bool bf16;  // contractions of the iteration's SVD in BF16 (mixed precision, before refinement)
     int *tc_err = nullptr;  // set: the fine pass runs on the tensor cores (its bounded-wait error flag)
+    // orthonormal-basis transfer on the coarse levels (option transfer = 1): per level the
+    // bidiagonal factor and level-test threshold, and a coarse n_H x KM scratch for C^{-1} V
+    bool orth = false;
+    std::vector<OrthTransfer<T>> ot;
+    T *Vp = nullptr;
     int side;   // half-step mode: warm subspace of the next iteration, 0 = right (Om), 1 = left (A[cur])
     std::vector<TransferDev<T>> tr;
 };
@@ -780,9 +840,12 @@ void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, 
         }
         int tp = h->timer.open(CPCP_PHASE_PASS_COARSE);
         int nb = launch_step_pass<T>(a, true, st);
+        // orthonormal basis of the coarse range: M_H C^{-1}
+        if (s.orth) launch_bidiag_right_solve<T>(s.m, tr.nh, s.MH, s.ldMH, s.ot[level].cd, s.ot[level].ce, st);
         h->timer.close(tp);
         if (want_g) {
             launch_sum_partials(s.partial, nb, 3, s.sums + 8, st);
+            if (s.orth) launch_bidiag_right_solve<T>(s.m, tr.nh, s.GH, s.ldMH, s.ot[level].cd, s.ot[level].ce, st);
             int nq = launch_sumsq<T>(s.m, tr.nh, s.GH, s.ldMH, s.partial, st);
             launch_sum_partials(s.partial, nq, 1, s.sums + 11, st);
         }
@@ -839,7 +902,15 @@ void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, 
     // new factors into the "previous" slot (its old content was consumed above)
     prod_nn_small<T>(s.m, w.Qy, w.KM, w.Us, w.KM, s.A[nxt], s.KM, &s.ctrl->k, w.KM, st);
     prod_nn_small<T>(tr.nh, w.Qz, w.KM, w.Wt, w.KM, s.Om, s.KM, &s.ctrl->k, w.KM, st);
-    launch_fill_prolong<T>(s.Om, s.KM, tr.nh, s.ctrl, w.sig, s.KM, 0x57E9ull, s.n, s.B[nxt], s.KM, tr, st);
+    if (s.orth && level > 0) {
+        // B = R C^{-1} V; the next start block keeps V (random columns into Vp are unused)
+        launch_bidiag_left_solve<T>(tr.nh, s.Om, s.KM, &s.ctrl->k, s.KM, s.ot[level].cd, s.ot[level].ce, s.Vp, s.KM,
+                                    st);
+        launch_fill_prolong<T>(s.Vp, s.KM, tr.nh, s.ctrl, w.sig, s.KM, 0x57E9ull, s.n, s.B[nxt], s.KM, tr, st);
+        launch_fill_random<T>(s.Om, s.KM, tr.nh, s.ctrl, 0, w.sig, s.KM, 0x57EBull, st);
+    } else {
+        launch_fill_prolong<T>(s.Om, s.KM, tr.nh, s.ctrl, w.sig, s.KM, 0x57E9ull, s.n, s.B[nxt], s.KM, tr, st);
+    }
     h->timer.close(ts);
     launch_ctrl_end(s.ctrl, st);
 }
@@ -929,6 +1000,14 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     s.ldMH = round4(nh1);
     s.MH = wsT<T>(h, "MH", (size_t)m * s.ldMH);
     s.GH = wsT<T>(h, "GH", (size_t)m * s.ldMH);
+    s.orth = H > 0 && o.transfer == 1;
+    s.ot.clear();
+    if (s.orth) {
+        if (o.half) throw CpcpError{CPCP_ERR_INVALID_ARG, "transfer = 1 is not available with subspace_mode = 1"};
+        s.ot.emplace_back();  // level 0: no transfer
+        for (int lv = 1; lv <= H; lv++) s.ot.push_back(upload_orth<T>(h, n, lv, "solve_o" + std::to_string(lv)));
+        s.Vp = wsT<T>(h, "Vp", (size_t)nh1 * s.KM);
+    }
     s.Om = wsT<T>(h, "Om", (size_t)n * s.KM);
     s.Omf = wsT<T>(h, "Omf", (size_t)n * s.KM);
     s.Ac = wsT<T>(h, "Ac", (size_t)m * s.KM);
@@ -1075,7 +1154,8 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
             double g2[4];
             CK(cudaMemcpyAsync(g2, s.sums + 8, sizeof(g2), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
-            if (g2[0] > 0.0 && std::sqrt(std::max(g2[3], 0.0)) < s.tr[level].kappa * std::sqrt(g2[0])) finer = true;
+            const double kap = s.orth ? s.ot[level].kappa : s.tr[level].kappa;
+            if (g2[0] > 0.0 && std::sqrt(std::max(g2[3], 0.0)) < kap * std::sqrt(g2[0])) finer = true;
         }
         if (!finer && at_final) {
             double spart;
@@ -1212,37 +1292,14 @@ cpcp_status ialm_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, do
     double *partial = wsT<double>(h, "ia_partial", (size_t)std::max(nblk, 1024));
     double *sums = wsT<double>(h, "ia_sums", 4);
     SvdWork<T> w = svd_work<T>(h, "ia_svd_", m, n, kcap0);  // own tags: "ia_Y" is the multiplier
-    // orthonormal-basis transfer (option): R C^{-1} with R^T R = C^T C.  R^T R
-    // is tridiagonal (diagonal sum_j R_jc^2, off-diagonal sum_j R_jc R_j,c+1),
-    // so its Cholesky factor is upper bidiagonal
+    // orthonormal-basis transfer (option): R C^{-1} with R^T R = C^T C
     const bool orth = H > 0 && o.transfer == 1;
     T *Cd = nullptr, *Ce = nullptr, *Vp = nullptr;
     if (orth) {
-        const HostTransfer ht = build_transfer(n, H);
-        std::vector<double> dg(nh, 0.0), of(nh, 0.0);
-        for (int j = 0; j < n; j++) {
-            dg[ht.j0[j]] += ht.w0[j] * ht.w0[j];
-            if (ht.w1[j] != 0.0) {
-                dg[ht.j0[j] + 1] += ht.w1[j] * ht.w1[j];
-                of[ht.j0[j]] += ht.w0[j] * ht.w1[j];
-            }
-        }
-        std::vector<T> cd(nh), ce(nh, T(0));
-        double prev = 0.0;
-        for (int c = 0; c < nh; c++) {
-            const double v = dg[c] - prev * prev;
-            if (!(v > 0.0)) throw CpcpError{CPCP_ERR_NUMERIC, "R^T R is not positive definite"};
-            const double cc = std::sqrt(v);
-            prev = c + 1 < nh ? of[c] / cc : 0.0;
-            cd[c] = T(cc);
-            ce[c] = T(prev);
-        }
-        Cd = wsT<T>(h, "ia_cd", nh);
-        Ce = wsT<T>(h, "ia_ce", nh);
+        const OrthTransfer<T> ot = upload_orth<T>(h, n, H, "ia");
+        Cd = ot.cd;
+        Ce = ot.ce;
         Vp = wsT<T>(h, "ia_Vp", (size_t)nh * KM);
-        CK(cudaMemcpyAsync(Cd, cd.data(), sizeof(T) * nh, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(Ce, ce.data(), sizeof(T) * nh, cudaMemcpyHostToDevice, st));
-        CK(cudaStreamSynchronize(st));  // the host vectors must outlive the copies
     }
 
     // ||D||_F, and ||D||_2 for the default mu0 (subspace SVD of D, 4 passes)
