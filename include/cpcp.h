@@ -319,6 +319,17 @@ cpcp_status cpcp_prolong(cpcp_handle h, int n, int halvings, int r, cpcp_dtype d
 cpcp_status cpcp_transfer_info(int n, int halvings, double *scale, int *nh);
 
 /*
+ * The orthonormal-basis transfer of cpcp_options.transfer = 1 for
+ * `halvings` >= 1 halvings of n: R^T R = C^T C with R the unit-norm composite
+ * operator and C upper bidiagonal, C's diagonal into cd and super-diagonal into
+ * ce (n_H doubles each, ce[n_H - 1] = 0; either may be NULL), and into *kappa
+ * (may be NULL) the coarse-gradient test's threshold for R C^{-1}: the
+ * geometric mean of ||R C^{-1}||_F / sqrt(n) and ||1^T R C^{-1}|| / sqrt(n).
+ * Host only.  INVALID_ARG unless n >= 1 and 1 <= halvings <= 5.
+ */
+cpcp_status cpcp_transfer_orth(int n, int halvings, double *cd, double *ce, double *kappa);
+
+/*
  * Truncated SVD of a device matrix M (m x n, ldm, m >= n) by subspace
  * iteration of width k (1 <= k <= n) with q power steps from Omega0 (n x k,
  * ldo; NULL = seeded random): M ~ U diag(sigma) V^T, U (m x k, ldu),

@@ -90,6 +90,7 @@ def _load():
     lib.cpcp_restrict.argtypes = [_vp, _int, _int, _int, _int, _vp, _i64, _vp, _i64]
     lib.cpcp_prolong.argtypes = [_vp, _int, _int, _int, _int, _vp, _i64, _vp, _i64]
     lib.cpcp_transfer_info.argtypes = [_int, _int, C.POINTER(_dbl), C.POINTER(_int)]
+    lib.cpcp_transfer_orth.argtypes = [_int, _int, _vp, _vp, C.POINTER(_dbl)]
     lib.cpcp_svd.argtypes = [_vp, _int, _int, _int, _vp, _i64, _int, _int, _vp, _i64, _vp, _i64, _vp, _i64, _vp]
     lib.cpcp_gemm_bf16.argtypes = [_vp, _int, _int, _int, _vp, _i64, _vp, _i64, _vp, _i64]
     lib.cpcp_solve_batched.argtypes = [_vp, _int, _vp, _dbl, _vp]
@@ -106,7 +107,7 @@ def _load():
 _lib = _load()
 
 EXPORTED = ["cpcp_status_string", "cpcp_last_error", "cpcp_create", "cpcp_destroy", "cpcp_solve", "cpcp_step",
-            "cpcp_restrict", "cpcp_prolong", "cpcp_transfer_info", "cpcp_svd", "cpcp_gemm_bf16",
+            "cpcp_restrict", "cpcp_prolong", "cpcp_transfer_info", "cpcp_transfer_orth", "cpcp_svd", "cpcp_gemm_bf16",
             "cpcp_solve_batched", "cpcp_backward", "cpcp_masked_norm_static", "cpcp_ialm", "cpcp_fwt"]
 
 
@@ -442,6 +443,20 @@ def unrolled_cpcp(D, lam, mu, rho: float, Qbits=None, levels: int = 3, K: int = 
     lam_t = lam if torch.is_tensor(lam) else torch.tensor(float(lam), dtype=torch.float64)
     mu_t = mu if torch.is_tensor(mu) else torch.tensor(float(mu), dtype=torch.float64)
     return _Unrolled.apply(D, lam_t, mu_t)
+
+
+def transfer_orth(n: int, halvings: int):
+    """(cd, ce, kappa) of the orthonormal-basis transfer: R^T R = C^T C with C
+    upper bidiagonal (diagonal cd, super-diagonal ce), and the level-test
+    threshold for R C^{-1}."""
+    nh = transfer_info(n, halvings)[1]
+    cd = np.zeros(nh)
+    ce = np.zeros(nh)
+    k = _dbl(0)
+    st = _lib.cpcp_transfer_orth(int(n), int(halvings), cd.ctypes.data, ce.ctypes.data, C.byref(k))
+    if st != 0:
+        raise CPCPError(st, "cpcp_transfer_orth")
+    return cd, ce, float(k.value)
 
 
 def transfer_info(n: int, halvings: int):

@@ -423,8 +423,9 @@ struct OrthTransfer {
     double kappa = 0.0;
 };
 
-template <typename T>
-OrthTransfer<T> upload_orth(cpcp_context *h, int n, int halvings, const std::string &tag)
+// Host part of OrthTransfer: cd, ce (n_H each) and kappa for `halvings`
+// halvings of n.
+double orth_factor(int n, int halvings, std::vector<double> &cd, std::vector<double> &ce)
 {
     const HostTransfer ht = build_transfer(n, halvings);
     const int nh = ht.nh;
@@ -438,25 +439,32 @@ OrthTransfer<T> upload_orth(cpcp_context *h, int n, int halvings, const std::str
             cs[ht.j0[j] + 1] += ht.w1[j];
         }
     }
-    std::vector<T> cd(nh), ce(nh, T(0));
-    std::vector<double> cdd(nh), ced(nh, 0.0);
+    cd.assign(nh, 0.0);
+    ce.assign(nh, 0.0);
     double prev = 0.0;
     for (int c = 0; c < nh; c++) {
         const double v = dg[c] - prev * prev;
         if (!(v > 0.0)) throw CpcpError{CPCP_ERR_NUMERIC, "R^T R is not positive definite"};
-        cdd[c] = std::sqrt(v);
-        prev = c + 1 < nh ? of[c] / cdd[c] : 0.0;
-        ced[c] = prev;
-        cd[c] = T(cdd[c]);
-        ce[c] = T(prev);
+        cd[c] = std::sqrt(v);
+        prev = c + 1 < nh ? of[c] / cd[c] : 0.0;
+        ce[c] = prev;
     }
     double x = 0.0, cs2 = 0.0;
     for (int c = 0; c < nh; c++) {
-        x = (cs[c] - (c > 0 ? x * ced[c - 1] : 0.0)) / cdd[c];
+        x = (cs[c] - (c > 0 ? x * ce[c - 1] : 0.0)) / cd[c];
         cs2 += x * x;
     }
+    return std::sqrt(std::sqrt((double)nh / n) * std::sqrt(cs2 / n));
+}
+
+template <typename T>
+OrthTransfer<T> upload_orth(cpcp_context *h, int n, int halvings, const std::string &tag)
+{
+    std::vector<double> cdd, ced;
     OrthTransfer<T> o;
-    o.kappa = std::sqrt(std::sqrt((double)nh / n) * std::sqrt(cs2 / n));
+    o.kappa = orth_factor(n, halvings, cdd, ced);
+    const int nh = (int)cdd.size();
+    std::vector<T> cd(cdd.begin(), cdd.end()), ce(ced.begin(), ced.end());
     o.cd = wsT<T>(h, tag + "_cd", nh);
     o.ce = wsT<T>(h, tag + "_ce", nh);
     CK(cudaMemcpyAsync(o.cd, cd.data(), sizeof(T) * nh, cudaMemcpyHostToDevice, h->stream));
@@ -2570,6 +2578,21 @@ void cpcp_destroy(cpcp_handle h)
     for (auto &kv : h->bufs)
         if (kv.second.p) cudaFree(kv.second.p);
     delete h;
+}
+
+cpcp_status cpcp_transfer_orth(int n, int halvings, double *cd, double *ce, double *kappa)
+{
+    if (n < 1 || halvings < 1 || halvings > 5) return CPCP_ERR_INVALID_ARG;
+    try {
+        std::vector<double> a, b;
+        const double k = orth_factor(n, halvings, a, b);
+        if (cd) std::copy(a.begin(), a.end(), cd);
+        if (ce) std::copy(b.begin(), b.end(), ce);
+        if (kappa) *kappa = k;
+        return CPCP_OK;
+    } catch (const CpcpError &e) {
+        return e.st;
+    }
 }
 
 cpcp_status cpcp_transfer_info(int n, int halvings, double *scale, int *nh)

@@ -66,6 +66,32 @@ def test_transfer_scale_matches_oracle(lib, n, h):
         assert abs(sc.value - sc_or) <= 1e-13 * sc_or
 
 
+@pytest.mark.parametrize("n,h", [(200, 1), (96, 2), (75, 3), (301, 2), (16, 3), (400, 2)])
+def test_transfer_orth_matches_oracle(lib, n, h):
+    # the host factor of the orthonormal-basis transfer: R^T R = C^T C with C upper
+    # bidiagonal for the unit-norm composite R; R C^{-1} has orthonormal columns and
+    # spans the oracle's R (R^T R)^{-1/2}; the level-test threshold is the oracle's
+    # formula applied to that basis
+    nh = oracle.coarse_dim(n, h)
+    cd = np.zeros(nh)
+    ce = np.zeros(nh)
+    kappa = ctypes.c_double(0)
+    lib.cpcp_transfer_orth.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_double)]
+    assert lib.cpcp_transfer_orth(n, h, cd.ctypes.data, ce.ctypes.data, ctypes.byref(kappa)) == 0
+    Cm = np.diag(cd) + np.diag(ce[:-1], 1)
+    assert ce[-1] == 0.0
+    R, _ = oracle.restriction(n, h, scaled=True)
+    assert np.abs(Cm.T @ Cm - R.T @ R).max() <= 1e-13
+    Q = R @ np.linalg.inv(Cm)
+    assert np.abs(Q.T @ Q - np.eye(nh)).max() <= 1e-11
+    Ro = oracle.restriction_orth(n, h)
+    assert np.abs(Q @ (Q.T @ Ro) - Ro).max() <= 1e-11
+    k_or = oracle._load().or_restriction_kappa(n, nh, np.ascontiguousarray(Ro))
+    assert abs(kappa.value - k_or) <= 1e-12 * k_or
+    assert lib.cpcp_transfer_orth(n, 0, None, None, None) == 1
+
+
 def test_transfer_rejects_bad_sizes(lib):
     sc = ctypes.c_double(0)
     nh = ctypes.c_int(0)
