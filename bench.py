@@ -293,6 +293,16 @@ def run_ours(args):
         dt, cores, sample = oracle_sample(p, ORACLE_SAMPLE_STEPS)
         line["cpu_baseline"] = {"value": dt * ITERS_MULTILEVEL, "unit": "s", "cores": cores, "kind": "oracle",
                                 "sample": sample}
+        if args.extras:
+            # the same oracle on one thread (one step)
+            import oracle
+            oracle.set_num_threads(1)
+            try:
+                dt1, _, sample1 = oracle_sample(p, 1)
+            finally:
+                oracle.set_num_threads(0)
+            line["cpu_baseline"]["single_thread"] = {"value": dt1 * ITERS_MULTILEVEL, "unit": "s", "cores": 1,
+                                                     "sample": sample1}
         print(json.dumps(line), flush=True)
     h.close()
     if world > 1:

@@ -112,6 +112,8 @@ def _load():
                                    C.c_double, _dp, _dp, C.c_void_p, C.c_void_p]
             lib.or_fwt.restype = C.c_int
             lib.or_num_threads.restype = C.c_int
+            lib.or_set_num_threads.argtypes = [C.c_int]
+            lib.or_set_num_threads.restype = None
             lib.or_step.argtypes = [C.c_int, C.c_int, _dp, C.c_void_p, C.c_double, C.c_double, C.c_double,
                                     C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
             lib.or_step.restype = C.c_int
@@ -135,6 +137,11 @@ def _mask_ptr(mask, shape):
 
 def num_threads() -> int:
     return int(_load().or_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Thread count of the oracle's parallel loops; n < 1 restores the default."""
+    _load().or_set_num_threads(int(n))
 
 
 def shrink(X, theta: float) -> np.ndarray:

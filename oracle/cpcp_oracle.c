@@ -1061,3 +1061,16 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* Sets the thread count of the oracle's parallel loops (for the single-thread
+ * CPU baseline); n < 1 restores the default. */
+void or_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    static int dflt = 0;
+    if (dflt == 0) dflt = omp_get_max_threads();
+    omp_set_num_threads(n >= 1 ? n : dflt);
+#else
+    (void)n;
+#endif
+}
