@@ -26,7 +26,7 @@
  *     unscaled, and R_o = R (R^T R)^{-1/2}, the operator with orthonormal
  *     columns and the same range, for which Theorem LH-eps gives epsilon = 0.
  *
- * Readings taken where the paper is silent (stated once more in the design doc):
+ * Readings taken where the paper is silent:
  *   * momentum: FISTA extrapolation on both L and S, restarted at level switches;
  *   * continuation: mu_k = max(mu_0 eta^k, mu_bar), eta = 0.9, mu_0 = ||P_Q D||_2;
  *   * residual: relative gradient-mapping norm at mu_bar on the fine level;
