@@ -387,7 +387,8 @@ def extras(device, stream, flush) -> dict:
         hs[name] = {"s": t, "iters": info["iters"], "level_iters": info["level_iters"][:lv], "relkkt": info["relkkt"],
                     "rank": info["rank"]}
     out["hyperspectral"] = {"workload": "hyperspectral-65536x128-r8-cpcp", "unit": "s", "tol": TOL, **hs,
-                            "multilevel_over_single": hs["3lv"]["s"] / hs["1lv"]["s"]}
+                            "multilevel_over_single": hs["3lv"]["s"] / hs["1lv"]["s"],
+                            "multilevel_orth_over_single": hs["3lv_orth"]["s"] / hs["1lv"]["s"]}
     del D, Q
     # IALM (Alg. 1) for PCP on a 2000 x 2000 planted problem, fp32, geometric penalty
     # (rho = 1.5), to a feasibility gap of 1e-5
