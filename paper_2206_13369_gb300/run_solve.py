@@ -38,6 +38,8 @@ def main() -> int:
     ap.add_argument("--plain-launches", action="store_true", help="no CUDA graph replay of iterations")
     ap.add_argument("--config", type=int, default=0, help="use workloads.config(N) instead of planted_cpcp")
     ap.add_argument("--precision", type=int, default=0, help="1: BF16 tensor-core contractions, then fp32")
+    ap.add_argument("--transfer", type=int, default=0,
+                    help="1: an orthonormal basis of the range of R on the coarse levels")
     ap.add_argument("--unroll", type=int, default=0, help="K > 0: the K-step differentiable program and its "
                     "reverse sweep (loss ||L_K - L0||^2)")
     ap.add_argument("--rho", type=float, default=1100.0, help="continuation scale of the unrolled program")
@@ -72,7 +74,7 @@ def main() -> int:
     Q = None if p["mask"] is None else torch.as_tensor(cpcp.pack_mask(p["mask"])).cuda()
     opts = dict(max_iter=args.max_iter, power_iters=args.power_iters, profile=int(args.profile),
                 pass_simt=int(args.pass_simt), plain_launches=int(args.plain_launches),
-                precision=args.precision)
+                precision=args.precision, transfer=args.transfer)
     if args.unroll > 0:
         opts.update(unroll=args.unroll, rho=args.rho)
     with cpcp.Handle(0, **opts) as h:
