@@ -120,7 +120,9 @@ typedef struct {
                               tridiagonal), which makes the coarse L-step the exact minimiser over
                               {L_H R^T} (epsilon = 0 in Theorem LH-eps); applied to M_H (and the
                               restricted gradient of the level test) and to V by two bidiagonal
-                              solves.  cpcp_solve rejects it with subspace_mode = 1 */
+                              solves.  cpcp_solve rejects it with subspace_mode = 1 or
+                              unroll > 0, cpcp_solve_batched rejects it; other values than
+                              0 and 1: INVALID_ARG */
 } cpcp_options;
 
 /* Phases timed when cpcp_options.profile is set. */

@@ -2633,8 +2633,12 @@ cpcp_status cpcp_solve(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D
         if (nh < 1) throw CpcpError{CPCP_ERR_INVALID_ARG, "coarse width below 1"};
         if (levels > 1 && 2 * nh > mm + 1)
             throw CpcpError{CPCP_ERR_INVALID_ARG, "coarse width exceeds (m+1)/2 (Assumption 2)"};
+        if (h->opt.transfer != 0 && h->opt.transfer != 1)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "transfer must be 0 or 1"};
         if (h->opt.unroll > 0) {
             if (dt != CPCP_F32) throw CpcpError{CPCP_ERR_INVALID_ARG, "the unrolled program is fp32"};
+            if (h->opt.transfer == 1)
+                throw CpcpError{CPCP_ERR_INVALID_ARG, "the unrolled program takes the unit-norm R (transfer = 0)"};
             return unroll_forward(h, m, n, static_cast<const float *>(D), ldd, Q, ldq, lambda, mu, levels,
                                   static_cast<float *>(L_out), ldl, static_cast<float *>(S_out), lds, info);
         }
@@ -2656,6 +2660,8 @@ cpcp_status cpcp_ialm(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D,
         if (!(lambda > 0) || !(tol > 0) || max_iter < 1)
             throw CpcpError{CPCP_ERR_INVALID_ARG, "lambda and tol must be positive, max_iter >= 1"};
         if (levels < 1 || levels > 6) throw CpcpError{CPCP_ERR_INVALID_ARG, "levels must be in [1, 6]"};
+        if (h->opt.transfer != 0 && h->opt.transfer != 1)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "transfer must be 0 or 1"};
         if (ldd < n || (L_out && ldl < n) || (S_out && lds < n))
             throw CpcpError{CPCP_ERR_INVALID_ARG, "leading dimension smaller than n"};
         const int nh = coarse_dim(n, levels - 1);
@@ -2792,7 +2798,11 @@ cpcp_status cpcp_backward(cpcp_handle h, const float *dL, int64_t ldgl, const fl
 cpcp_status cpcp_solve_batched(cpcp_handle h, int count, const cpcp_problem *probs, double tol, cpcp_info *infos)
 {
     if (!h) return CPCP_ERR_INVALID_ARG;
-    return guarded(h, [&]() -> cpcp_status { return batched_impl(h, count, probs, tol, infos); });
+    return guarded(h, [&]() -> cpcp_status {
+        if (h->opt.transfer != 0)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "the batched solve takes the unit-norm R (transfer = 0)"};
+        return batched_impl(h, count, probs, tol, infos);
+    });
 }
 
 cpcp_status cpcp_gemm_bf16(cpcp_handle h, int rows, int K, int N, const float *A, int64_t lda, const float *B,
