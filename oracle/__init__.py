@@ -111,6 +111,9 @@ def _load():
             lib.or_fwt.argtypes = [C.c_int, C.c_int, _dp, C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int,
                                    C.c_double, _dp, _dp, C.c_void_p, C.c_void_p]
             lib.or_fwt.restype = C.c_int
+            lib.or_fwt_ex.argtypes = [C.c_int, C.c_int, _dp, C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int,
+                                      C.c_double, _dp, _dp, C.c_void_p, C.c_void_p, C.c_int]
+            lib.or_fwt_ex.restype = C.c_int
             lib.or_num_threads.restype = C.c_int
             lib.or_set_num_threads.argtypes = [C.c_int]
             lib.or_set_num_threads.restype = None
@@ -298,7 +301,7 @@ def fw_line_search(A, B, C_, ga, gb):
     return a.value, b.value
 
 
-def fwt(D, mask, lam, mu, levels=1, max_iter=1000, tol=1e-3):
+def fwt(D, mask, lam, mu, levels=1, max_iter=1000, tol=1e-3, transfer="unit"):
     """FW-T (Alg. 3) or ML-FWT (Alg. 6, levels > 1) for eq. (cpcp) with weights
     (mu, lam mu).  Returns (L, S, iters, ftrace, (t_L, t_S)) with ftrace the
     epigraph objective after each iteration."""
@@ -309,8 +312,9 @@ def fwt(D, mask, lam, mu, levels=1, max_iter=1000, tol=1e-3):
     S = np.zeros((m, n))
     ft = np.zeros(max_iter)
     ts = np.zeros(2)
-    it = _load().or_fwt(m, n, D, mp, float(lam), float(mu), int(levels), int(max_iter), float(tol), L, S,
-                        ft.ctypes.data_as(C.c_void_p), ts.ctypes.data_as(C.c_void_p))
+    it = _load().or_fwt_ex(m, n, D, mp, float(lam), float(mu), int(levels), int(max_iter), float(tol), L, S,
+                           ft.ctypes.data_as(C.c_void_p), ts.ctypes.data_as(C.c_void_p),
+                           {"unit": 0, "orth": 1}[transfer])
     return L, S, it, ft[:it].copy(), (float(ts[0]), float(ts[1]))
 
 

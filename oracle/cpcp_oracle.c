@@ -923,7 +923,8 @@ void or_fw_line_search(double A, double B, double C, double ga, double gb, doubl
  *   - nuclear-ball LMO: M_L = -u v^T for the top singular pair (u, v) of G;
  *     multilevel: the top pair (u, v_H) of G R and M_L = -u (R v_H)^T, the
  *     coarse ball of radius 1 / ||R|| = 1 (R scaled to unit norm) lifted by
- *     R^T (Sec. 3.4); <G, M_L> = -sigma_1 either way;
+ *     R^T (Sec. 3.4); <G, M_L> = -sigma_1 either way.  transfer = 1 (or_fwt_ex)
+ *     takes R (R^T R)^{-1/2} instead, whose lifted vertices have nuclear norm 1;
  *   - l1-ball LMO: M_S = -sign(G_ij) e_i e_j^T at the largest |G_ij|;
  *   - V_L = U_L M_L, V_tL = U_L unless lambda_L >= sigma_1 (then 0), and
  *     likewise V_S, V_tS against max |G_ij| (with a relative margin, below);
@@ -938,8 +939,8 @@ void or_fw_line_search(double A, double B, double C, double ga, double gb, doubl
  * max_iter iterations.  ftrace (optional) receives f after each iteration;
  * tl_ts (optional) the final t_L, t_S.  Returns the iterations taken.
  */
-int or_fwt(int m, int n, const double *D, const unsigned char *mask, double lam, double mu, int levels,
-           int max_iter, double tol, double *L, double *S, double *ftrace, double *tl_ts)
+int or_fwt_ex(int m, int n, const double *D, const unsigned char *mask, double lam, double mu, int levels,
+              int max_iter, double tol, double *L, double *S, double *ftrace, double *tl_ts, int transfer)
 {
     const size_t len = (size_t)m * n;
     const double lamL = mu, lamS = lam * mu;
@@ -949,7 +950,10 @@ int or_fwt(int m, int n, const double *D, const unsigned char *mask, double lam,
     if (H > 0) {
         R = dalloc((size_t)n * nh);
         GR = dalloc((size_t)m * nh);
-        or_restriction_scaled(n, H, R, NULL);
+        if (transfer == 1)
+            or_restriction_orth(n, H, R); /* lifted vertices on the unit nuclear sphere */
+        else
+            or_restriction_scaled(n, H, R, NULL);
     }
     const int nc = H > 0 ? nh : n;
     const int p = m < nc ? m : nc;
@@ -1050,6 +1054,12 @@ int or_fwt(int m, int n, const double *D, const unsigned char *mask, double lam,
     }
     free(R), free(GR), free(G), free(PA), free(PB), free(U), free(sv), free(V), free(v), free(u);
     return k;
+}
+
+int or_fwt(int m, int n, const double *D, const unsigned char *mask, double lam, double mu, int levels,
+           int max_iter, double tol, double *L, double *S, double *ftrace, double *tl_ts)
+{
+    return or_fwt_ex(m, n, D, mask, lam, mu, levels, max_iter, tol, L, S, ftrace, tl_ts, 0);
 }
 
 /* Thread count the oracle uses (for reporting the CPU baseline). */

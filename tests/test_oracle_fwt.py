@@ -111,3 +111,23 @@ def test_stopping_rule_relative_decrease(small_cpcp):
     assert it < 1000
     assert abs(ft[-2] - ft[-1]) <= 1e-3 * ft[-2]
     assert np.all(np.abs(np.diff(ft[:-1])) > 1e-3 * ft[:-2])
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_ml_fwt_orthonormal_transfer_tracks_fwt(levels):
+    # with R (R^T R)^{-1/2} the lifted nuclear-ball vertex -u (R_o v_H)^T has nuclear
+    # norm 1, as the fine LMO's does; on data whose solution lies near the coarse
+    # range, ML-FWT then follows FW-T's objective iteration for iteration, while the
+    # unit-norm R (vertices inside the ball, ||R v_H|| < 1) lags behind
+    p = W.video_cpcp(11, h=12, w=16, frames=64, rank=1, blocks=3, block=3, obs=0.8, levels=levels)
+    D, mask, lam = p["D"], p["mask"], p["lam"]
+    mu = 0.05 * np.linalg.svd(np.where(mask, D, 0.0), compute_uv=False)[0]
+    Lf, Sf, _ = oracle.fista(D, mask, lam, mu, levels=1, tol=1e-11)
+    fstar = oracle.objective(D, mask, lam, mu, Lf, Sf)
+    _, _, _, f1, _ = oracle.fwt(D, mask, lam, mu, levels=1, max_iter=300, tol=0.0)
+    _, _, _, fo, _ = oracle.fwt(D, mask, lam, mu, levels=levels, max_iter=300, tol=0.0, transfer="orth")
+    _, _, _, fu, _ = oracle.fwt(D, mask, lam, mu, levels=levels, max_iter=300, tol=0.0, transfer="unit")
+    g1, go, gu = (f1[-1] - fstar) / fstar, (fo[-1] - fstar) / fstar, (fu[-1] - fstar) / fstar
+    assert np.all(np.diff(fo) <= 1e-12 * fo[:-1])
+    assert go <= 1.1 * g1, (go, g1)
+    assert gu >= 3.0 * go, (gu, go)
