@@ -113,7 +113,7 @@ typedef struct {
                               the host; 0 (default) captures an iteration's kernels in a CUDA
                               graph the second time the same (level, buffer parity) comes up and
                               replays the graph for the iterations between residual checks */
-    int transfer;          /* coarse levels of cpcp_solve and ML-IALM (cpcp_ialm, levels > 1):
+    int transfer;          /* coarse levels of cpcp_solve, ML-IALM (cpcp_ialm) and ML-FWT (cpcp_fwt):
                               0 (default) = R scaled to unit spectral norm (the reading of
                               Assumption 4); 1 = R replaced by an orthonormal basis of its range,
                               R C^{-1} with R^T R = C^T C (C upper bidiagonal, R^T R being
@@ -224,7 +224,8 @@ cpcp_status cpcp_solve(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D
  *   ||L||_* <= t_L <= U_L, ||S||_1 <= t_S <= U_S,
  * with lambda_L = mu and lambda_S = lambda * mu.  Each iteration takes the
  * linear minimisation oracles at G = P_Q[L + S - D] (nuclear ball: the top
- * singular pair of G, or of G R lifted by R for ML-FWT, from the subspace
+ * singular pair of G, or of G R lifted by R for ML-FWT (of G R C^{-1} lifted
+ * by R C^{-1} with cpcp_options.transfer = 1), from the subspace
  * SVD of cpcp_solve, block width min(oversample, k_max, n_H, m) and
  * power_iters passes, warm started from the last iteration's right vectors;
  * at full width it is exact; l1 ball: the first entry

@@ -1517,6 +1517,14 @@ cpcp_status fwt_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, con
     double *partial = wsT<double>(h, "fw_partial", (size_t)nb * 5), *amv = wsT<double>(h, "fw_amv", nb);
     int64_t *ami = wsT<int64_t>(h, "fw_ami", nb);
     SvdWork<T> w = svd_work<T>(h, "fw_svd_", m, n, kcap0);
+    // orthonormal-basis transfer (option): the coarse LMO on G R C^{-1}, lifted by R C^{-1}
+    const bool orth = H > 0 && o.transfer == 1;
+    OrthTransfer<T> ot;
+    T *Vp = nullptr;
+    if (orth) {
+        ot = upload_orth<T>(h, n, H, "fw");
+        Vp = wsT<T>(h, "fw_Vp", (size_t)nh * KM);
+    }
     std::vector<double> hp((size_t)nb * 5), hv(nb);
     std::vector<int64_t> hi(nb);
 
@@ -1575,6 +1583,7 @@ cpcp_status fwt_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, con
         int64_t ldx = ld;
         if (H > 0) {
             launch_restrict<T>(m, n, G, ld, GR, ldh, tr, st);
+            if (orth) launch_bidiag_right_solve<T>(m, nh, GR, ldh, ot.cd, ot.ce, st);
             Mx = GR;
             ldx = ldh;
         }
@@ -1584,7 +1593,12 @@ cpcp_status fwt_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, con
         CK(cudaMemcpyAsync(Om, Vb, sizeof(T) * (size_t)nh * KM, cudaMemcpyDeviceToDevice, st));  // warm start
         const T *vv = Vb;
         if (H > 0) {
-            launch_prolong<T>(n, Vb, KM, Vf, KM, tr, &ctrl->k, KM, st);
+            const T *vsrc = Vb;
+            if (orth) {
+                launch_bidiag_left_solve<T>(nh, Vb, KM, &ctrl->k, KM, ot.cd, ot.ce, Vp, KM, st);
+                vsrc = Vp;
+            }
+            launch_prolong<T>(n, vsrc, KM, Vf, KM, tr, &ctrl->k, KM, st);
             vv = Vf;
         }
         T sig_t, gval;
@@ -2689,6 +2703,8 @@ cpcp_status cpcp_fwt(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D, 
         if (ldd < n || (L_out && ldl < n) || (S_out && lds < n) || (Q && ldq < (n + 31) / 32))
             throw CpcpError{CPCP_ERR_INVALID_ARG, "leading dimension too small"};
         if (coarse_dim(n, levels - 1) < 1) throw CpcpError{CPCP_ERR_INVALID_ARG, "coarse width below 1"};
+        if (h->opt.transfer != 0 && h->opt.transfer != 1)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "transfer must be 0 or 1"};
         if (!is_device_ptr(D) || (Q && !is_device_ptr(Q)) || (L_out && !is_device_ptr(L_out)) ||
             (S_out && !is_device_ptr(S_out)))
             throw CpcpError{CPCP_ERR_INVALID_ARG, "cpcp_fwt takes device buffers"};

@@ -85,3 +85,20 @@ def test_fwt_rejects_host_buffers(cp):
         with pytest.raises(cp.CPCPError) as e:
             h.fwt(np.ones((8, 6)), None, 0.1, 1.0)
         assert e.value.status == 1
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_ml_fwt_orthonormal_transfer_matches_oracle(cp, levels):
+    # ML-FWT with an orthonormal basis of the range of R (option transfer = 1): the
+    # library lifts by R C^{-1}, the oracle by R (R^T R)^{-1/2}; both bases span the
+    # same range, so the lifted top singular vector, and with it every iterate, agree
+    p = W.planted_cpcp(60, 40, 3, 0.1, 0.8, seed=5, levels=levels)
+    D, mask, lam = p["D"], p["mask"], p["lam"]
+    mu = 0.05 * np.linalg.svd(np.where(mask, D, 0.0), compute_uv=False)[0]
+    Lr, Sr, it_r, fr, _ = oracle.fwt(D, mask, lam, mu, levels=levels, max_iter=60, tol=0.0, transfer="orth")
+    Qt = torch.as_tensor(cp.pack_mask(mask)).cuda()
+    with cp.Handle(0, oversample=64, power_iters=2, transfer=1) as h:
+        L, S, info = h.fwt(torch.as_tensor(D).cuda(), Qt, lam, mu, levels=levels, max_iter=60, tol=0.0)
+    assert info["status"] == 5 and info["iters"] == it_r == 60
+    assert np.allclose(info["f"], fr, rtol=1e-9, atol=0), np.abs(info["f"] / fr - 1).max()
+    assert _rel(L.cpu().numpy(), Lr) <= 1e-7 and _rel(S.cpu().numpy(), Sr) <= 1e-7
