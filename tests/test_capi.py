@@ -92,6 +92,31 @@ def test_transfer_orth_matches_oracle(lib, n, h):
     assert lib.cpcp_transfer_orth(n, 0, None, None, None) == 1
 
 
+@pytest.mark.parametrize("n,h", [(40, 1), (40, 2), (96, 3)])
+def test_orth_lift_is_basis_independent(lib, n, h):
+    # the coarse LMO of ML-FWT with transfer = 1: the top singular pair of G R C^{-1}
+    # lifted by R C^{-1} (library factor) equals, up to sign, the pair of G R_o lifted
+    # by R_o = R (R^T R)^{-1/2} (oracle): both bases span range(R)
+    nh = oracle.coarse_dim(n, h)
+    cd = np.zeros(nh)
+    ce = np.zeros(nh)
+    lib.cpcp_transfer_orth.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_double)]
+    assert lib.cpcp_transfer_orth(n, h, cd.ctypes.data, ce.ctypes.data, None) == 0
+    R, _ = oracle.restriction(n, h, scaled=True)
+    B = R @ np.linalg.inv(np.diag(cd) + np.diag(ce[:-1], 1))
+    Ro = oracle.restriction_orth(n, h)
+    G = np.random.default_rng(n + h).normal(size=(3 * n, n))
+    for basis in (B, Ro):
+        U, s_, Vt = np.linalg.svd(G @ basis, full_matrices=False)
+        lifted = np.outer(U[:, 0], basis @ Vt[0])
+        if basis is B:
+            ref, sig = lifted, s_[0]
+        else:
+            assert abs(s_[0] - sig) <= 1e-12 * sig
+            assert np.abs(lifted - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
 def test_transfer_rejects_bad_sizes(lib):
     sc = ctypes.c_double(0)
     nh = ctypes.c_int(0)
