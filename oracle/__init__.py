@@ -55,7 +55,8 @@ def build(force: bool = False) -> str:
 class _Opts(C.Structure):
     _fields_ = [("tau", C.c_double), ("eta", C.c_double), ("mu0", C.c_double),
                 ("check_every", C.c_int), ("max_iter", C.c_int), ("switch_ratio", C.c_double),
-                ("start_level", C.c_int), ("fixed_iters", C.c_int), ("transfer", C.c_int)]
+                ("start_level", C.c_int), ("fixed_iters", C.c_int), ("transfer", C.c_int),
+                ("early_test", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -255,7 +256,8 @@ def relkkt(D, mask, lam, mu, L, S, tau: float = 0.5) -> float:
 
 
 def fista(D, mask, lam, mu, levels=1, tol=1e-10, *, tau=0.5, eta=0.9, mu0=0.0, check_every=10,
-          max_iter=20000, switch_ratio=0.9, start_level=-1, fixed_iters=0, trace_cap=4096, transfer="unit"):
+          max_iter=20000, switch_ratio=0.9, start_level=-1, fixed_iters=0, trace_cap=4096, transfer="unit",
+          early_test=False):
     """Multilevel accelerated proximal gradient for eq. (cpcp); returns (L, S, info).
 
     info: iters, final_level, rank, checks, status (0 ok, 3 not converged),
@@ -266,7 +268,7 @@ def fista(D, mask, lam, mu, levels=1, tol=1e-10, *, tau=0.5, eta=0.9, mu0=0.0, c
     L = np.zeros((m, n))
     S = np.zeros((m, n))
     o = _Opts(tau, eta, mu0, check_every, max_iter, switch_ratio, start_level, fixed_iters,
-              {"unit": 0, "orth": 1}[transfer])
+              {"unit": 0, "orth": 1}[transfer], int(bool(early_test)))
     inf = _Info()
     tr = np.zeros(max(trace_cap, 1))
     st = _load().or_fista(m, n, D, mp, float(lam), float(mu), int(levels), float(tol), C.byref(o), L, S,
@@ -314,7 +316,7 @@ def fwt(D, mask, lam, mu, levels=1, max_iter=1000, tol=1e-3, transfer="unit"):
     ts = np.zeros(2)
     it = _load().or_fwt_ex(m, n, D, mp, float(lam), float(mu), int(levels), int(max_iter), float(tol), L, S,
                            ft.ctypes.data_as(C.c_void_p), ts.ctypes.data_as(C.c_void_p),
-                           {"unit": 0, "orth": 1}[transfer])
+                           {"unit": 0, "orth": 1}[transfer], int(bool(early_test)))
     return L, S, it, ft[:it].copy(), (float(ts[0]), float(ts[1]))
 
 

@@ -522,6 +522,8 @@ typedef struct {
     int fixed_iters;     /* > 0: run exactly this many iterations at start_level, no checks */
     int transfer;        /* 0: R scaled to unit norm (Assumption 4); 1: R (R^T R)^{-1/2} (orthonormal
                             columns, the same range; or_restriction_orth) */
+    int early_test;      /* nonzero: the coarse-gradient test also runs after the first iteration on
+                            each coarse level (a study of an alternative to the level rule) */
 } or_opts;
 
 typedef struct {
@@ -588,6 +590,7 @@ static int fista_core(int m, int n, const double *D, const unsigned char *mask, 
     double ratio = o->switch_ratio > 0 ? o->switch_ratio : 0.9;
     int level = o->start_level >= 0 ? o->start_level : H;
     if (level > H) level = H;
+    int level_start = 0; /* iteration at which the current level began */
 
     /* restriction operators for every level (level 0 = identity) */
     double **R = (double **)calloc((size_t)H + 1, sizeof(double *));
@@ -656,6 +659,20 @@ static int fista_core(int m, int n, const double *D, const unsigned char *mask, 
             }
             continue;
         }
+        if (o->early_test && level > 0 && k == level_start) {
+            /* the coarse-gradient test below, once at the level's first iteration */
+            matmul(m, n, nhs[level], G, R[level], GR);
+            double gn = sqrt(frob2(len, G)), grn = sqrt(frob2((size_t)m * nhs[level], GR));
+            if (gn > 0.0 && grn < kappa[level] * gn) {
+                level--;
+                level_start = k + 1;
+                prev = INFINITY;
+                t = 1.0;
+                memcpy(Lp, L, sizeof(double) * len);
+                memcpy(Sp, S, sizeof(double) * len);
+                continue;
+            }
+        }
         if ((k + 1) % c != 0) continue;
         int finer = 0;
         if (level > 0) {
@@ -681,6 +698,7 @@ static int fista_core(int m, int n, const double *D, const unsigned char *mask, 
         }
         if (finer) {
             level--;
+            level_start = k + 1;
             prev = INFINITY;
             t = 1.0; /* momentum restart */
             memcpy(Lp, L, sizeof(double) * len);

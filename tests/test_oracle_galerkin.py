@@ -94,3 +94,22 @@ def test_cpcp_multilevel_with_orthonormal_transfer_reaches_the_optimum():
         assert np.linalg.norm(L - L1) / np.linalg.norm(L1) <= 1e-5
         assert np.linalg.norm(S - S1) / np.linalg.norm(S1) <= 1e-5
     assert io["level_iters"][0] < iu["level_iters"][0]
+
+
+def test_early_coarse_gradient_test():
+    # a study of the level rule: with the coarse-gradient test also run after a
+    # level's first iteration, data whose solution is not coarse (Gaussian factors)
+    # leave the coarse levels after one iteration each, while smooth data keep them;
+    # both reach the single-level optimum
+    p = W.planted_cpcp(240, 200, 5, 0.1, 0.8, seed=3, levels=3)
+    D, mask, lam, mu = p["D"], p["mask"], p["lam"], p["mu"]
+    L1, S1, i1 = oracle.fista(D, mask, lam, mu, levels=1, tol=1e-8)
+    Le, Se, ie = oracle.fista(D, mask, lam, mu, levels=3, tol=1e-8, early_test=True)
+    Ln, Sn, i_n = oracle.fista(D, mask, lam, mu, levels=3, tol=1e-8)
+    assert list(ie["level_iters"][1:3]) == [1, 1] and i_n["level_iters"][1] >= 10
+    assert ie["iters"] <= i_n["iters"]
+    assert np.linalg.norm(Le - L1) / np.linalg.norm(L1) <= 1e-5
+    v = W.video_cpcp(7, h=16, w=24, frames=64, rank=2, blocks=3, block=4, obs=0.8, levels=3)
+    _, _, iv = oracle.fista(v["D"], v["mask"], v["lam"], v["mu"], levels=3, tol=1e-6, transfer="orth",
+                            early_test=True)
+    assert iv["level_iters"][2] >= 10
