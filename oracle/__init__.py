@@ -316,7 +316,7 @@ def fwt(D, mask, lam, mu, levels=1, max_iter=1000, tol=1e-3, transfer="unit"):
     ts = np.zeros(2)
     it = _load().or_fwt_ex(m, n, D, mp, float(lam), float(mu), int(levels), int(max_iter), float(tol), L, S,
                            ft.ctypes.data_as(C.c_void_p), ts.ctypes.data_as(C.c_void_p),
-                           {"unit": 0, "orth": 1}[transfer], int(bool(early_test)))
+                           {"unit": 0, "orth": 1}[transfer])
     return L, S, it, ft[:it].copy(), (float(ts[0]), float(ts[1]))
 
 
