@@ -19,8 +19,10 @@
  * soft threshold of Alg. 3.  R = R_n R_{n/2} ... R_{n_H} is the composite
  * linear-interpolation operator of eq. (Rx), scaled to unit spectral norm
  * (Assumption 4).  The solver starts on the coarsest level and moves one level
- * finer when the fine-level residual stalls; it always finishes on the fine
- * level, so single-level and multilevel runs share the optimum of eq. (cpcp).
+ * finer when the restricted gradient carries too small a share of the gradient
+ * (coarse-gradient test) or the fine-level residual stalls; it always finishes
+ * on the fine level, so single-level and multilevel runs share the optimum of
+ * eq. (cpcp).
  *
  * Conventions for every entry point:
  *   - Matrices are row-major with an explicit leading dimension in elements
@@ -123,6 +125,12 @@ typedef struct {
                               solves.  cpcp_solve rejects it with subspace_mode = 1 or
                               unroll > 0, cpcp_solve_batched rejects it; other values than
                               0 and 1: INVALID_ARG */
+    int early_test;        /* cpcp_solve level rule: 0 (default) or 1 = the coarse-gradient test
+                              (move one level finer when ||G R||_F < kappa ||G||_F) also runs after
+                              the first iteration on each coarse level, so data whose gradient is
+                              not coarse (no smooth column structure) leave the coarse levels at
+                              once; -1 = only every check_every iterations.  A handover skips
+                              that iteration's residual check.  Other values: INVALID_ARG */
 } cpcp_options;
 
 /* Phases timed when cpcp_options.profile is set. */
@@ -291,7 +299,13 @@ cpcp_status cpcp_ialm(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D,
  * U diag(sigma - mu_k/2)_+ and B_out (n x k, ldbo) = R V; *r_out = number of
  * singular values above mu_k/2 (columns beyond r_out are zero); sigma_out
  * (k doubles, host or device; may be NULL) the coarse singular values.
- * Requires n <= m (no internal transpose).  Errors: INVALID_ARG, NOMEM, CUDA.
+ * With CPCP_F32 at halvings = 0 the fused pass runs on the tensor cores, as
+ * in cpcp_solve, when the operands meet its TMA rules (D, S_k, S_p, S_out
+ * 16-byte aligned with leading dimensions that are multiples of 4; lda = ldap
+ * and ldb = ldbp, multiples of 4) and options.pass_simt is 0; otherwise on the
+ * SIMT cores.
+ * Requires n <= m (no internal transpose).  Errors: INVALID_ARG, NOMEM, CUDA,
+ * TIMEOUT (a bounded wait of the tensor-core pass expired).
  */
 cpcp_status cpcp_step(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D, int64_t ldd, const uint32_t *Q,
                       int64_t ldq, double lambda, double mu_k, double beta, int halvings, const void *S_k,
@@ -413,15 +427,15 @@ cpcp_status cpcp_gemm_bf16(cpcp_handle h, int rows, int K, int N, const float *A
  * that are NaN or infinite (nonfinite, host int64, may be NULL), computed
  * without allocating any memory.  The paper has no counterpart: this is a
  * service for callers that cannot allocate device memory while they run --
- * code inside a CUDA graph capture (a cudaMalloc there would break or stall
- * the capture), code whose device memory is all handed out up front by its own
- * pool or arena, and latency-critical loops that cannot afford the device-wide
+ * code whose device memory is all handed out up front by its own pool or
+ * arena (a framework's caching allocator, an inference server with a fixed
+ * budget), and latency-critical loops that cannot afford the device-wide
  * synchronisation of cudaMalloc/cudaFree.  It needs no handle.
  *
  * D (m x n, dtype, ldd) and Q (bit-packed mask as in cpcp_solve, or NULL) are
  * device pointers on the current device; the work is queued on `stream` (a
- * cudaStream_t, NULL = legacy default stream) and the call returns after the
- * results have been copied to the host.  The partial sums live in one static
+ * cudaStream_t, NULL = legacy default stream) and the call synchronises that
+ * stream: it returns after the results have been copied to the host.  The partial sums live in one static
  * device array of 1 MiB that every GPU loading the library holds until the
  * process exits; the largest accepted problem has ceil(m/64) * ceil(n/64) <=
  * 65536 tiles (for example 16384 x 16384) -- larger sizes return
@@ -431,7 +445,8 @@ cpcp_status cpcp_gemm_bf16(cpcp_handle h, int rows, int K, int N, const float *A
  * the array: calls that overlap on the GPU (different streams or threads on
  * the same device) race and must be serialised by the caller.  Every slot a
  * call reads is written by the same call, so nothing needs clearing.
- * Returns OK, INVALID_ARG or CUDA.
+ * Returns OK, INVALID_ARG or CUDA (also when either kernel launch fails; the
+ * results are then not written).
  */
 cpcp_status cpcp_masked_norm_static(void *stream, int m, int n, cpcp_dtype dt, const void *D, int64_t ldd,
                                     const uint32_t *Q, int64_t ldq, double *fro, int64_t *nonfinite);

@@ -659,21 +659,11 @@ static int fista_core(int m, int n, const double *D, const unsigned char *mask, 
             }
             continue;
         }
-        if (o->early_test && level > 0 && k == level_start) {
-            /* the coarse-gradient test below, once at the level's first iteration */
-            matmul(m, n, nhs[level], G, R[level], GR);
-            double gn = sqrt(frob2(len, G)), grn = sqrt(frob2((size_t)m * nhs[level], GR));
-            if (gn > 0.0 && grn < kappa[level] * gn) {
-                level--;
-                level_start = k + 1;
-                prev = INFINITY;
-                t = 1.0;
-                memcpy(Lp, L, sizeof(double) * len);
-                memcpy(Sp, S, sizeof(double) * len);
-                continue;
-            }
-        }
-        if ((k + 1) % c != 0) continue;
+        /* decisions: every c iterations, and with early_test also at a coarse
+           level's first iteration (the coarse-gradient test only) */
+        const int periodic = (k + 1) % c == 0;
+        const int early = o->early_test && level > 0 && k == level_start;
+        if (!periodic && !early) continue;
         int finer = 0;
         if (level > 0) {
             /* coarse-gradient test: keep the coarse model while the
@@ -682,7 +672,7 @@ static int fista_core(int m, int n, const double *D, const unsigned char *mask, 
             double gn = sqrt(frob2(len, G)), grn = sqrt(frob2((size_t)m * nhs[level], GR));
             if (gn > 0.0 && grn < kappa[level] * gn) finer = 1;
         }
-        if (!finer && mu_k == mu_bar) {
+        if (periodic && !finer && mu_k == mu_bar) {
             /* fine residual at the final weight: stop test, and on a coarse
                level a stall test */
             rel = relkkt_warm(m, n, D, mask, lam, mu_bar, tau, L, S, Vchk);

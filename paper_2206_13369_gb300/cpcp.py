@@ -37,7 +37,8 @@ class Options(C.Structure):
                 ("profile", C.c_int), ("precision", C.c_int), ("refine_at", C.c_double),
                 ("batch_threads", C.c_int), ("batch_autotune", C.c_int), ("unroll", C.c_int),
                 ("ckpt_every", C.c_int), ("rho", C.c_double), ("subspace_mode", C.c_int),
-                ("pass_simt", C.c_int), ("plain_launches", C.c_int), ("transfer", C.c_int)]
+                ("pass_simt", C.c_int), ("plain_launches", C.c_int), ("transfer", C.c_int),
+                ("early_test", C.c_int)]
 
 
 class Info(C.Structure):

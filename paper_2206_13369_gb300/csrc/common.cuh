@@ -286,6 +286,7 @@ struct BatchResult {
 
 struct BatchOpts {
     int max_iter, check_every, p, q, qc;
+    int early;  // coarse-gradient test also at a coarse level's first iteration
     double eta, ratio, tol;
     uint64_t seed;
 };

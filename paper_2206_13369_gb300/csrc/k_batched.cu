@@ -1006,6 +1006,7 @@ __device__ void solve_instance(const BatchInst &I, BatchResult *res, const Batch
     const double mu = I.mu, lam = I.lam;
     double t = 1.0, rel = INFINITY, prev = INFINITY;
     int cur = 0, rk = 0, iter = 0, checks = 0;
+    int level_start = 0;  // iteration at which the current level began
     int status = CPCP_ERR_NOT_CONVERGED;
     while (iter < o.max_iter) {
         const double mu_k = fmax(mu0 * pow(o.eta, (double)iter), mu);
@@ -1013,7 +1014,8 @@ __device__ void solve_instance(const BatchInst &I, BatchResult *res, const Batch
         const float beta = (float)((t - 1.0) / t1);
         const float thL = (float)(0.5 * mu_k), thS = (float)(0.5 * lam * mu_k);
         const bool decide = (iter + 1) % o.check_every == 0;
-        const bool want_g = decide && level > 0;
+        const bool early = o.early != 0 && level > 0 && iter == level_start;
+        const bool want_g = (decide || early) && level > 0;
         double gg[2];
         long long c0 = clock64();
         pass_step<NT>(I, od, level, cur, beta, thS, want_g, sm, red, gg);
@@ -1045,12 +1047,12 @@ __device__ void solve_instance(const BatchInst &I, BatchResult *res, const Batch
         cur = nxt;
         iter++;
         if (level < BATCH_LEVELS) out.level_iters[level]++;
-        if (!decide) continue;
+        if (!decide && !early) continue;
 
         const bool at_final = !(mu_k > mu);
         bool finer = false;
         if (level > 0 && gg[0] > 0.0 && sqrt(fmax(gg[1], 0.0)) < I.kappa[level] * sqrt(gg[0])) finer = true;
-        if (!finer && at_final) {
+        if (decide && !finer && at_final) {
             // fine residual check at (L_k, S_k)
             c0 = clock64();
             const float thLb = (float)(0.5 * mu), thSb = (float)(0.5 * lam * mu);
@@ -1086,6 +1088,7 @@ __device__ void solve_instance(const BatchInst &I, BatchResult *res, const Batch
             // one level finer: momentum restarts, the subspace is warm-started
             // from the restriction of the current right factor
             level--;
+            level_start = iter;
             prev = INFINITY;
             t = 1.0;
             const int kl = min(kcap(level), max(rk + o.p, 1));

@@ -673,6 +673,7 @@ int kmax_small<double>()
 
 struct Opts {
     int max_iter, check_every, k_max, p, q, qc, start_level, precision, half, tc_pass, graphs, transfer;
+    bool early_test;
     double eta, mu0, ratio, refine_at;
     uint64_t seed;
 };
@@ -695,6 +696,7 @@ Opts resolve(const cpcp_options &o)
     r.tc_pass = o.pass_simt == 0;
     r.graphs = o.plain_launches == 0;
     r.transfer = o.transfer;
+    r.early_test = o.early_test >= 0;
     r.refine_at = o.refine_at > 0 ? o.refine_at : 1e-3;
     r.seed = o.seed ? o.seed : 1;
     return r;
@@ -1102,14 +1104,17 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     inf.mu0 = mu0;
     inf.pqd_fro = pqd;
     int cur = 0, iter = 0, checks = 0, kf = cc.k, rank = 0;
+    int level_start = 0;  // iteration at which the current level began
     double rel = INFINITY, prev = INFINITY;
     cpcp_status status = CPCP_ERR_NOT_CONVERGED;
     IterGraphs graphs;
     for (iter = 0; iter < o.max_iter;) {
         // every check_every iterations: a level decision (coarse levels) and,
-        // once the weight is final, the fine residual check
+        // once the weight is final, the fine residual check; with the early
+        // test also the coarse-gradient test at a coarse level's first iteration
         const bool decide = (iter + 1) % o.check_every == 0;
-        const bool want_g = decide && level > 0;
+        const bool early = o.early_test && level > 0 && iter == level_start;
+        const bool want_g = (decide || early) && level > 0;
         if (use_graphs && !want_g && !s.bf16 && level < 8) {
             // the schedule update and the fused pass are launched directly (the
             // profile's events bracket the pass); the rest of the iteration is
@@ -1151,7 +1156,7 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
         if (level < 8) inf.level_iters[level]++;
         if (s.bf16) inf.bf16_iters++;
         iter++;
-        if (!decide) continue;
+        if (!decide && !early) continue;
         // weight of the iteration just done: mu_k = max(mu0 eta^k, mu)
         const double mu_k = std::max(mu0 * std::pow(o.eta, (double)(iter - 1)), mu);
         const bool at_final = !(mu_k > mu);
@@ -1165,7 +1170,7 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
             const double kap = s.orth ? s.ot[level].kappa : s.tr[level].kappa;
             if (g2[0] > 0.0 && std::sqrt(std::max(g2[3], 0.0)) < kap * std::sqrt(g2[0])) finer = true;
         }
-        if (!finer && at_final) {
+        if (decide && !finer && at_final) {
             double spart;
             rel = fine_check<T>(h, s, wf, cur, o, pqd, mu, &kf, &spart, &rank);
             if (h->opt.trace && checks < h->opt.trace_cap) h->opt.trace[checks] = rel;
@@ -1192,6 +1197,7 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
             // move one level finer: restart momentum, warm-start the subspace
             // from the restriction of the current right factor
             level--;
+            level_start = iter;
             prev = INFINITY;
             Ctrl cur_c;
             CK(cudaMemcpyAsync(&cur_c, s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
@@ -1807,6 +1813,7 @@ cpcp_status step_impl(cpcp_context *h, int m, int n, const void *Dv, int64_t ldd
     a.ctrl = cd;
     const T *Mx;
     int64_t ldx;
+    int *tc_err = nullptr;
     if (halvings > 0) {
         int64_t ldh = round4(nh);
         T *MH = wsT<T>(h, "st_MH", (size_t)m * ldh);
@@ -1822,7 +1829,17 @@ cpcp_status step_impl(cpcp_context *h, int m, int n, const void *Dv, int64_t ldd
         T *M = wsT<T>(h, "st_M", (size_t)m * ldm);
         a.M = M;
         a.ldm = ldm;
-        launch_step_pass<T>(a, false, st);
+        // fp32: the tensor-core fine pass where the operands meet its TMA rules
+        // (as in cpcp_solve), else the SIMT pass
+        bool tc = false;
+        if constexpr (std::is_same<T, float>::value) {
+            if (!h->opt.pass_simt) {
+                tc_err = wsT<int>(h, "st_tc_err", 1);
+                CK(cudaMemsetAsync(tc_err, 0, sizeof(int), st));
+                tc = launch_pass_tc(a, tc_err, st);
+            }
+        }
+        if (!tc) launch_step_pass<T>(a, false, st);
         Mx = M;
         ldx = ldm;
     }
@@ -1841,8 +1858,11 @@ cpcp_status step_impl(cpcp_context *h, int m, int n, const void *Dv, int64_t ldd
     Ctrl out;
     CK(cudaMemcpyAsync(&out, cd, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     if (sigma_out) CK(cudaMemcpyAsync(sigma_out, w.sig64, sizeof(double) * k, cudaMemcpyDefault, st));
+    int tc_flag = 0;
+    if (tc_err) CK(cudaMemcpyAsync(&tc_flag, tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
+    if (tc_flag) throw CpcpError{CPCP_ERR_TIMEOUT, "a bounded wait of the tensor-core pass expired"};
     if (r_out) *r_out = out.r_new;
     return CPCP_OK;
 }
@@ -2093,7 +2113,9 @@ cpcp_status batched_impl(cpcp_context *h, int count, const cpcp_problem *P, doub
     });
 
     BatchOpts bo;
+    memset(&bo, 0, sizeof(bo));  // hashed below, padding included
     bo.max_iter = o.max_iter;
+    bo.early = o.early_test ? 1 : 0;
     bo.check_every = o.check_every;
     bo.p = std::min(o.p, BATCH_KB);
     bo.q = o.q;
@@ -2649,6 +2671,8 @@ cpcp_status cpcp_solve(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D
             throw CpcpError{CPCP_ERR_INVALID_ARG, "coarse width exceeds (m+1)/2 (Assumption 2)"};
         if (h->opt.transfer != 0 && h->opt.transfer != 1)
             throw CpcpError{CPCP_ERR_INVALID_ARG, "transfer must be 0 or 1"};
+        if (h->opt.early_test < -1 || h->opt.early_test > 1)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "early_test must be -1, 0 or 1"};
         if (h->opt.unroll > 0) {
             if (dt != CPCP_F32) throw CpcpError{CPCP_ERR_INVALID_ARG, "the unrolled program is fp32"};
             if (h->opt.transfer == 1)

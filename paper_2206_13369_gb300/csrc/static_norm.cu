@@ -27,17 +27,21 @@ static __device__ __align__(256) double g_norm_scratch[2 * MAX_TILES + 2];
 // Device address of g_norm_scratch on each device, resolved once per device.
 static std::atomic<double *> g_scratch_addr[MAX_DEVICES];
 
+// One block per 64 x 64 tile on a one-dimensional grid (tile b is row tile
+// b / tiles_x, column tile b % tiles_x), so the tile count alone bounds the
+// grid: gridDim.x may reach 2^31 - 1, far above MAX_TILES.
 template <typename T>
-__global__ void __launch_bounds__(NT) masked_sq_tiles(int m, int n, const T *__restrict__ D, int64_t ldd,
-                                                      const uint32_t *__restrict__ Q, int64_t ldq,
+__global__ void __launch_bounds__(NT) masked_sq_tiles(int m, int n, int tiles_x, const T *__restrict__ D,
+                                                      int64_t ldd, const uint32_t *__restrict__ Q, int64_t ldq,
                                                       double *__restrict__ part)
 {
     __shared__ double red[NT / 32][2];
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-    const int col = blockIdx.x * TILE + 4 * tx;
+    const int bx = (int)(blockIdx.x % (unsigned)tiles_x), by = (int)(blockIdx.x / (unsigned)tiles_x);
+    const int col = bx * TILE + 4 * tx;
     double sq = 0.0, nf = 0.0;
     for (int i = 0; i < 4; i++) {
-        const int row = blockIdx.y * TILE + ty + 16 * i;
+        const int row = by * TILE + ty + 16 * i;
         if (row >= m) continue;
         uint32_t bits = 0xffffffffu;
         if (Q != nullptr && col < n) bits = Q[(int64_t)row * ldq + (col >> 5)] >> (col & 31);
@@ -60,7 +64,7 @@ __global__ void __launch_bounds__(NT) masked_sq_tiles(int m, int n, const T *__r
     if (t < 2) {
         double v = 0.0;
         for (int w = 0; w < NT / 32; w++) v += red[w][t];
-        part[2 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) + t] = v;
+        part[2 * (int64_t)blockIdx.x + t] = v;
     }
 }
 
@@ -130,14 +134,19 @@ extern "C" cpcp_status cpcp_masked_norm_static(void *stream, int m, int n, cpcp_
     cpcp_status st = scratch_address(dev, &scratch);
     if (st != CPCP_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    dim3 grid((unsigned)tx, (unsigned)ty);
+    cudaGetLastError();  // a launch error reported below is this call's own
+    const unsigned tiles = (unsigned)(tx * ty);
     CPCP_COUNT_LAUNCH();
     if (dt == CPCP_F32)
-        masked_sq_tiles<float><<<grid, NT, 0, s>>>(m, n, static_cast<const float *>(D), ldd, Q, ldq, scratch);
+        masked_sq_tiles<float><<<tiles, NT, 0, s>>>(m, n, (int)tx, static_cast<const float *>(D), ldd, Q, ldq,
+                                                    scratch);
     else
-        masked_sq_tiles<double><<<grid, NT, 0, s>>>(m, n, static_cast<const double *>(D), ldd, Q, ldq, scratch);
+        masked_sq_tiles<double><<<tiles, NT, 0, s>>>(m, n, (int)tx, static_cast<const double *>(D), ldd, Q, ldq,
+                                                     scratch);
+    if (cudaGetLastError() != cudaSuccess) return CPCP_ERR_CUDA;
     CPCP_COUNT_LAUNCH();
-    reduce_tiles<<<1, NT, 0, s>>>((int)(tx * ty), scratch, scratch + 2 * MAX_TILES);
+    reduce_tiles<<<1, NT, 0, s>>>((int)tiles, scratch, scratch + 2 * MAX_TILES);
+    if (cudaGetLastError() != cudaSuccess) return CPCP_ERR_CUDA;
     double res[2];
     if (cudaMemcpyAsync(res, scratch + 2 * MAX_TILES, sizeof(res), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {

@@ -108,8 +108,28 @@ def test_early_coarse_gradient_test():
     Ln, Sn, i_n = oracle.fista(D, mask, lam, mu, levels=3, tol=1e-8)
     assert list(ie["level_iters"][1:3]) == [1, 1] and i_n["level_iters"][1] >= 10
     assert ie["iters"] <= i_n["iters"]
+    assert ie["status"] == 0 and ie["final_level"] == 0
     assert np.linalg.norm(Le - L1) / np.linalg.norm(L1) <= 1e-5
+    assert np.linalg.norm(Se - S1) / np.linalg.norm(S1) <= 1e-5
     v = W.video_cpcp(7, h=16, w=24, frames=64, rank=2, blocks=3, block=4, obs=0.8, levels=3)
-    _, _, iv = oracle.fista(v["D"], v["mask"], v["lam"], v["mu"], levels=3, tol=1e-6, transfer="orth",
-                            early_test=True)
+    Lv1, Sv1, _ = oracle.fista(v["D"], v["mask"], v["lam"], v["mu"], levels=1, tol=1e-8)
+    Lv, Sv, iv = oracle.fista(v["D"], v["mask"], v["lam"], v["mu"], levels=3, tol=1e-8, transfer="orth",
+                              early_test=True)
     assert iv["level_iters"][2] >= 10
+    assert iv["status"] == 0 and iv["final_level"] == 0
+    assert np.linalg.norm(Lv - Lv1) / np.linalg.norm(Lv1) <= 1e-5
+    assert np.linalg.norm(Sv - Sv1) / np.linalg.norm(Sv1) <= 1e-5
+
+
+def test_early_handover_on_a_periodic_iteration():
+    # with c = 2 the handover at one halving (iteration 1, that level's first) falls
+    # on a periodic decision: the coarse-gradient test runs once, and a handover
+    # skips that iteration's residual check, as every handover does
+    p = W.planted_cpcp(120, 96, 3, 0.1, 0.8, seed=4, levels=3)
+    D, mask, lam, mu = p["D"], p["mask"], p["lam"], p["mu"]
+    L1, S1, i1 = oracle.fista(D, mask, lam, mu, levels=1, tol=1e-8, check_every=2)
+    Le, Se, ie = oracle.fista(D, mask, lam, mu, levels=3, tol=1e-8, check_every=2, early_test=True)
+    assert list(ie["level_iters"][:3]) == [ie["iters"] - 2, 1, 1]
+    assert ie["status"] == 0 and ie["final_level"] == 0
+    assert np.linalg.norm(Le - L1) / np.linalg.norm(L1) <= 1e-5
+    assert np.linalg.norm(Se - S1) / np.linalg.norm(S1) <= 1e-5

@@ -9,6 +9,7 @@ import math
 import os
 
 import numpy as np
+import scipy.linalg
 import pytest
 
 import oracle
@@ -202,6 +203,56 @@ def test_composite_mixed_parity_is_product_and_banded():
         assert np.allclose(R, P, atol=1e-15)
         assert np.all((R != 0).sum(1) <= 2)
         assert np.allclose(R.sum(1), 1.0, atol=1e-15)
+
+
+def _kappa_closed_form(n, h):
+    """Threshold of the coarse-gradient test from the closed-form rows of the
+    composite R (Sec. 3.1; node j at fine index j 2^h): ||R||_F^2, the column
+    sums 1^T R and the tridiagonal R^T R accumulated row by row, the unit-norm
+    scale from R^T R's largest eigenvalue (LAPACK), then
+    kappa = sqrt(||R||_F / sqrt(n) * ||1^T R|| / sqrt(n)) for R / ||R||_2."""
+    step = 2 ** h
+    nh = n // step
+    fro2, cs = 0.0, np.zeros(nh)
+    d, e = np.zeros(nh), np.zeros(max(nh - 1, 0))
+    for i in range(1, n + 1):
+        if i <= step:
+            ws = [(0, 1.0)]
+        else:
+            j = i // step
+            w = i / step - j
+            ws = [(j - 1, 1.0 - w)] + ([(j, w)] if w > 0 else [])
+        for c, wc in ws:
+            fro2 += wc * wc
+            cs[c] += wc
+            d[c] += wc * wc
+        if len(ws) == 2:
+            e[ws[0][0]] += ws[0][1] * ws[1][1]
+    lam = scipy.linalg.eigvalsh_tridiagonal(d, e)[-1]
+    return math.sqrt(math.sqrt(fro2 / n) * math.sqrt(float(cs @ cs) / n)) / math.sqrt(lam), fro2, cs, d, e
+
+
+@pytest.mark.parametrize("n,h", [(6, 1), (200, 1), (2000, 1), (8, 2), (1024, 2), (2000, 2), (16, 3), (400, 3),
+                                 (2000, 3)])
+def test_restriction_kappa_closed_form(n, h):
+    kap, fro2, cs, d, e = _kappa_closed_form(n, h)
+    if h == 1:
+        # one halving, n = 2 n_H: rows e_1, e_j (n_H of them) and (e_j + e_{j+1})/2
+        # (n_H - 1): ||R||_F^2 = (3 n_H + 1)/2; column sums 5/2, 2, ..., 2, 3/2;
+        # R^T R = tridiag(1/4; 9/4, 3/2, ..., 3/2, 5/4; 1/4)
+        nh = n // 2
+        assert fro2 == (3 * nh + 1) / 2
+        assert cs[0] == 2.5 and cs[-1] == 1.5 and np.all(cs[1:-1] == 2.0)
+        assert d[0] == 2.25 and d[-1] == 1.25 and np.all(d[1:-1] == 1.5) and np.all(e == 0.25)
+    assert abs(oracle.restriction_kappa(n, h) - kap) <= 1e-12 * kap
+    if n == 6:
+        # worked example of Sec. 3.1 by hand: ||R||_F^2 = 5, ||1^T R||^2 = 12.5,
+        # R^T R = [[9/4, 1/4, 0], [1/4, 3/2, 1/4], [0, 1/4, 5/4]]
+        lam = np.linalg.eigvalsh(np.array([[2.25, .25, 0], [.25, 1.5, .25], [0, .25, 1.25]]))[-1]
+        assert abs(kap - math.sqrt(math.sqrt(5 / 6 * 12.5 / 6)) / math.sqrt(lam)) <= 1e-14
+    if n == 2000:
+        # the values the level rule uses on the 2000-column workloads
+        assert abs(kap - {1: 0.7246, 2: 0.5728, 3: 0.4693}[h]) < 5e-5
 
 
 def test_single_level_sigma_ratio_at_most_two():

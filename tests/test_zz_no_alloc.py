@@ -1,9 +1,8 @@
 """The entry point that allocates nothing (cpcp_masked_norm_static).
 
-Some callers cannot allocate device memory while they run: code inside a CUDA
-graph capture, code whose device memory is all handed out up front by its own
-pool, and latency-critical loops that cannot pay for cudaMalloc's device-wide
-synchronisation.  For them the library computes ||P_Q[D]||_F with its scratch in
+Some callers cannot allocate device memory while they run: code whose device
+memory is all handed out up front by its own pool or arena, and latency-critical
+loops that cannot pay for cudaMalloc's device-wide synchronisation.  For them the library computes ||P_Q[D]||_F with its scratch in
 a fixed static device array.  This test calls it through the C ABI, twice in a
 row on each input (the scratch keeps the previous call's contents), and checks
 it against the same quantity reported by the handle-based cpcp_solve.
@@ -80,6 +79,23 @@ def test_static_norm_smaller_after_larger_and_nonfinite(cp):
     Dn[hid[0], hid[1]] = float("inf")
     _, nf = cp.masked_norm_static(Dn, Qbs)
     assert nf == 1
+
+
+def test_static_norm_tall_single_column_tile(cp):
+    # one column tile and 65536 row tiles: the largest tile count the scratch takes,
+    # with more row tiles than a grid's y dimension could hold (the tiles run on a
+    # one-dimensional grid)
+    m, n = 64 * 65535 + 1, 64
+    g = torch.Generator(device="cuda").manual_seed(11)
+    D = torch.randn((m, n), generator=g, device="cuda", dtype=torch.float32)
+    ref = float(torch.linalg.vector_norm(D.double()))
+    first = cp.masked_norm_static(D, None)
+    second = cp.masked_norm_static(D, None)
+    assert first == second
+    fro, nf = first
+    assert nf == 0
+    assert abs(fro - ref) <= 1e-12 * ref
+    del D
 
 
 def test_static_norm_rejects_sizes_beyond_the_scratch(cp):
