@@ -48,11 +48,11 @@ WORKLOAD = {"workload": "cpcp-2000x2000-r50-fp32-3lv", "m": 2000, "n": 2000, "ra
             "observed": 0.8, "levels": 3, "tol": 1e-6, "seed": 2000,
             "l2": "flushed between timed steps (256 MB write)"}
 TOL = 1e-6
-# iterations the multilevel solve takes on this workload (measured on the GPU
-# arm, which also reports its own count); the CPU arms scale a per-iteration
-# sample by it
-ITERS_MULTILEVEL = 100
-ORACLE_SAMPLE_STEPS = 2
+# iterations per level (fine first) and fine residual checks of the multilevel
+# solve on this workload, as the GPU arm measures them (it also reports its own);
+# the reference arm projects the oracle's time to tolerance over this mix
+LEVEL_ITERS = (98, 1, 1)
+CHECKS = 10
 
 
 def make_workload():
@@ -118,26 +118,59 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def oracle_sample(p, steps: int) -> tuple[float, int, str]:
-    """Seconds per iteration of the fp64 oracle on the full workload: `steps`
-    proximal steps at the coarsest level (n_H = 500) from the zero state.  A
-    lower bound of the oracle's per-iteration cost (fine-level steps need a
-    2000 x 2000 SVD)."""
+def oracle_level_steps(p, halvings) -> dict:
+    """Seconds of one fp64 oracle proximal step on the full workload at each
+    number of halvings in `halvings` (from the zero state, so each step's
+    Jacobi SVD starts cold: an upper estimate of the warm-started steps of a
+    solve)."""
     import numpy as np
 
     import oracle
     D, mask = p["D"], p["mask"]
     Z = np.zeros_like(D)
-    S, L = Z, Z
     mu0 = 100.0 * p["mu"]
-    t0 = time.perf_counter()
-    for i in range(steps):
-        S1, L1, _ = oracle.step(D, mask, p["lam"], mu0, 0.0 if i == 0 else 0.3, 2, S, S, L, L)
-        S, L = S1, L1
-    dt = (time.perf_counter() - t0) / steps
-    sample = (f"{steps} fp64 oracle proximal steps at the coarsest level (n_H=500) of the full 2000x2000 "
-              f"workload; seconds per step x {ITERS_MULTILEVEL} iterations")
-    return dt, oracle.num_threads(), sample
+    out = {}
+    for hv in halvings:
+        t0 = time.perf_counter()
+        oracle.step(D, mask, p["lam"], mu0, 0.0, hv, Z, Z, Z, Z)
+        out[hv] = time.perf_counter() - t0
+    return out
+
+
+def oracle_projection(step_s: dict, level_iters, checks) -> float:
+    """Oracle time to tolerance over a level mix: each iteration at its level's
+    step time, each fine residual check at the fine step time (one full SVD)."""
+    return sum(it * step_s[hv] for hv, it in enumerate(level_iters) if it > 0) + checks * step_s[0]
+
+
+def golden_error(name: str, L, S) -> dict | None:
+    """Relative error of (L, S) against the fp64 oracle's optimum at the entries
+    sampled in tests/golden/cpcp_optimum_<name>.txt (1024 uniform entries and
+    512 from the support of S; written by tests/golden/make_fullsize_optima.py,
+    which calls only the oracle)."""
+    import numpy as np
+    import torch
+    path = os.path.join(ROOT, "tests", "golden", f"cpcp_optimum_{name}.txt")
+    if not os.path.exists(path):
+        return None
+    rows, relkkt = [], None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#"):
+                for tok in line[1:].split():
+                    if tok.startswith("relkkt="):
+                        relkkt = float(tok.split("=", 1)[1])
+                continue
+            i, j, lv, sv = line.split()
+            rows.append((int(i), int(j), float(lv), float(sv)))
+    a = np.array(rows)
+    ii = torch.as_tensor(a[:, 0].astype(np.int64), device=L.device)
+    jj = torch.as_tensor(a[:, 1].astype(np.int64), device=L.device)
+    Lg = L[ii, jj].double().cpu().numpy()
+    Sg = S[ii, jj].double().cpu().numpy()
+    return {"L": float(np.linalg.norm(Lg - a[:, 2]) / np.linalg.norm(a[:, 2])),
+            "S": float(np.linalg.norm(Sg - a[:, 3]) / np.linalg.norm(a[:, 3])),
+            "samples": int(len(a)), "oracle_relkkt": relkkt}
 
 
 def dist_setup():
@@ -160,21 +193,34 @@ def rank_max(vals, device):
 
 
 def run_reference(args):
+    """The fp64 oracle as the reference arm: each step times one oracle proximal
+    step at the coarsest level (n_H = 500) of the full workload and projects the
+    time to tolerance over the measured level mix, scaling each level's step by
+    the oracle's Jacobi cost model (m n_l^2 per sweep, the same sweep count)."""
     world, rank, local = dist_setup()
     if rank != 0:
         return 0
     p = make_workload()
+    n = p["D"].shape[1]
+    H = len(LEVEL_ITERS) - 1
+    nl = [math.ceil(n / 2 ** hv) for hv in range(H + 1)]
     vals = []
     for i in range(args.warmup + args.steps):
-        dt, cores, sample = oracle_sample(p, 1)
+        t = oracle_level_steps(p, [H])[H]
+        step_s = {hv: t * (nl[hv] / nl[H]) ** 2 for hv in range(H + 1)}
         if i >= args.warmup:
-            vals.append(dt * ITERS_MULTILEVEL)
+            vals.append(oracle_projection(step_s, LEVEL_ITERS, CHECKS))
+    import oracle
     v = statistics.mean(vals)
+    sample = (f"one fp64 oracle proximal step at the coarsest level (n_H={nl[H]}) of the full {p['D'].shape[0]}x{n} "
+              f"workload per step (cold Jacobi SVD), projected over {sum(LEVEL_ITERS)} iterations (per level, fine "
+              f"first: {list(LEVEL_ITERS)}) and {CHECKS} fine residual checks with each level's step scaled by "
+              f"(n_l / n_H)^2")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": WORKLOAD,
-            "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
-                             "sample": sample.replace(f"{ORACLE_SAMPLE_STEPS} fp64", "1 fp64")},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -234,6 +280,12 @@ def run_ours(args):
     ml = statistics.mean(t_ml)
     sl = statistics.mean(t_sl)
     ml, sl = rank_max([ml, sl], "cuda")
+    # error of the benchmarked solve against the fp64 oracle's optimum (sampled entries)
+    Lm, Sm, _ = solve(args.levels)
+    err_ml = golden_error("cpcp2000", Lm, Sm)
+    Ls1, Ss1, _ = solve(1)
+    err_sl = golden_error("cpcp2000", Ls1, Ss1)
+    del Lm, Sm, Ls1, Ss1
 
     # end to end through the C ABI with host buffers (H2D of D and the mask,
     # solve, D2H of L and S inside the timed region)
@@ -276,10 +328,10 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ml * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(WORKLOAD, parallelism="replicas" if world > 1 else "single"),
-            "single_level": {"value": sl, "unit": "s", "iters": inf_sl[-1]["iters"]},
+            "single_level": {"value": sl, "unit": "s", "iters": inf_sl[-1]["iters"], "err_vs_oracle": err_sl},
             "multilevel_over_single": ml / sl,
             "multilevel": {"iters": inf_ml[-1]["iters"], "level_iters": inf_ml[-1]["level_iters"][:3],
-                           "relkkt": inf_ml[-1]["relkkt"], "rank": inf_ml[-1]["rank"]},
+                           "relkkt": inf_ml[-1]["relkkt"], "rank": inf_ml[-1]["rank"], "err_vs_oracle": err_ml},
             "clocks": clocks_info,
             "e2e": {"value": statistics.mean(e2e), "unit": "s",
                     "h2d_bytes_per_step": int(Dh.nbytes + Qhp.nbytes),
@@ -290,19 +342,32 @@ def run_ours(args):
     if rank == 0 and args.extras:
         line.update(extras(local, stream, flush))
     if rank == 0:
-        dt, cores, sample = oracle_sample(p, ORACLE_SAMPLE_STEPS)
-        line["cpu_baseline"] = {"value": dt * ITERS_MULTILEVEL, "unit": "s", "cores": cores, "kind": "oracle",
-                                "sample": sample}
+        # the oracle on the host cores: one step per level the solve visited, projected
+        # over the GPU solve's own level mix and check count
+        import oracle
+        lv_it = inf_ml[-1]["level_iters"][:args.levels]
+        checks = inf_ml[-1]["checks"]
+        step_s = oracle_level_steps(p, [hv for hv, it in enumerate(lv_it) if it > 0 or hv == 0])
+        line["cpu_baseline"] = {
+            "value": oracle_projection(step_s, lv_it, checks), "unit": "s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": (f"one fp64 oracle proximal step (cold Jacobi SVD) at each level the GPU solve visited, on the "
+                       f"full workload ({ {hv: round(t, 2) for hv, t in step_s.items()} } s by halvings), projected "
+                       f"over the GPU solve's level mix {lv_it} and its {checks} fine residual checks (one fine step "
+                       f"each)")}
         if args.extras:
-            # the same oracle on one thread (one step)
-            import oracle
+            # one thread: the coarsest-level step, scaled by the all-core per-level ratios
+            Hc = max(step_s)
             oracle.set_num_threads(1)
             try:
-                dt1, _, sample1 = oracle_sample(p, 1)
+                t1 = oracle_level_steps(p, [Hc])[Hc]
             finally:
                 oracle.set_num_threads(0)
-            line["cpu_baseline"]["single_thread"] = {"value": dt1 * ITERS_MULTILEVEL, "unit": "s", "cores": 1,
-                                                     "sample": sample1}
+            step1 = {hv: t1 * t / step_s[Hc] for hv, t in step_s.items()}
+            line["cpu_baseline"]["single_thread"] = {
+                "value": oracle_projection(step1, lv_it, checks), "unit": "s", "cores": 1,
+                "sample": f"one step at {Hc} halvings on one thread ({t1:.2f} s), other levels scaled by the "
+                          f"all-core ratios"}
         print(json.dumps(line), flush=True)
     h.close()
     if world > 1:
@@ -340,10 +405,11 @@ def extras(device, stream, flush) -> dict:
                                ("fp32_1lv", 0, 1, 0), ("mixed_4lv_orth", 1, 4, 1), ("fp32_4lv_orth", 0, 4, 1)):
         with cpcp.Handle(device, stream=stream, precision=prec, transfer=tr) as hh:
             hh.solve(D, Q, v["lam"], v["mu"], levels=lv, tol=TOL)
-            t, (_, _, info) = _events_time(stream, lambda: hh.solve(D, Q, v["lam"], v["mu"], levels=lv, tol=TOL), 3,
-                                           flush)
+            t, (Lv, Sv, info) = _events_time(stream, lambda: hh.solve(D, Q, v["lam"], v["mu"], levels=lv, tol=TOL),
+                                             3, flush)
         vm[name] = {"s": t, "iters": info["iters"], "level_iters": info["level_iters"][:lv], "bf16_iters": info["bf16_iters"],
-                    "relkkt": info["relkkt"]}
+                    "relkkt": info["relkkt"], "err_vs_oracle": golden_error("video", Lv, Sv)}
+        del Lv, Sv
     out["video_mixed"] = {"workload": "video-19200x400-r5-cpcp", "unit": "s", "tol": TOL, **vm}
     del D, Q
     # 256 uneven instances in one persistent launch
@@ -355,11 +421,22 @@ def extras(device, stream, flush) -> dict:
         probs.append({"D": Dq, "Q": Qq, "lam": q["lam"], "mu": q["mu"], "levels": q["levels"]})
     with cpcp.Handle(device, stream=stream, batch_autotune=1) as hb:
         hb.solve_batched(probs, tol=TOL)
-        t, (_, _, infos, st) = _events_time(stream, lambda: hb.solve_batched(probs, tol=TOL), 3, flush)
+        t, (Lb, Sb, infos, st) = _events_time(stream, lambda: hb.solve_batched(probs, tol=TOL), 3, flush)
     its = [f["iters"] for f in infos]
+    # error against the fp64 oracle's optimum for the three smallest instances
+    import oracle
+    errs = []
+    for i in sorted(range(len(ps)), key=lambda i: ps[i]["D"].size)[:3]:
+        q = ps[i]
+        Lr, Sr, _ = oracle.fista(q["D"], q["mask"], q["lam"], q["mu"], levels=1, tol=1e-10)
+        errs.append({"instance": i, "shape": list(q["D"].shape), "relkkt": infos[i]["relkkt"],
+                     "L": float(np.linalg.norm(Lb[i].double().cpu().numpy() - Lr) / np.linalg.norm(Lr)),
+                     "S": float(np.linalg.norm(Sb[i].double().cpu().numpy() - Sr) / np.linalg.norm(Sr))})
     out["batched"] = {"workload": "batched-256-cpcp-fp32", "unit": "s", "s": t, "instances_per_s": 256 / t,
                       "status": st, "iters_mean": statistics.mean(its), "iters_max": max(its),
-                      "elements": int(sum(q["D"].size for q in ps)), "gpu_launches": int(infos[0]["launches"])}
+                      "elements": int(sum(q["D"].size for q in ps)), "gpu_launches": int(infos[0]["launches"]),
+                      "err_vs_oracle_smallest3": errs}
+    del Lb, Sb
     del probs
     # unrolled 1024 x 1024, 3 levels, 50 steps, forward and reverse sweep
     c5 = workloads.config(5)

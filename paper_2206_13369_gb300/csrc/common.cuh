@@ -221,6 +221,14 @@ void launch_chol(const T *partialG, int splits, int kmax, const int *kdyn, T *R,
 // ctrl (optional): skip rotations that cannot change SVT_{ctrl->theta_L};
 // stats (optional): calls and sweeps are added to stats[0], stats[1];
 // Us, svt (optional): the SVT of launch_svt_small fused into the epilogue
+// CholeskyQR2 of X (rows x k, k = *kdyn <= KM, ld KM) in one thread-block
+// cluster launch (k_small.cu): Q, and Rout (if given) with X = Q Rout; Q1, G,
+// R1, R1i, R2, R2i are workspace (ld KM), well receives the first pass's
+// skip flag, stats counts factorisations.  false (nothing launched): the
+// fused form is not available and the caller runs the multi-launch form.
+bool launch_cholqr2_cluster(int rows, const float *X, float *Q, float *Q1, int KM, const int *kdyn, float *G,
+                            float *R1, float *R1i, float *R2, float *R2i, float *Rout, int *well, int *stats,
+                            cudaStream_t st);
 template <typename T>
 void launch_jacobi(const T *Rz, int ldr, const int *kdyn, T *Ut, T *Wt, T *sig, int kmax, const Ctrl *ctrl,
                    cudaStream_t st, int *stats = nullptr, T *Us = nullptr, Ctrl *svt = nullptr);

@@ -14,7 +14,11 @@
 //   ctrl      momentum weight, continuation weight and thresholds.
 #include <cfloat>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace cpcp {
 
@@ -306,6 +310,237 @@ __global__ void __launch_bounds__(CHOL_NT, 1) chol_kernel(const T *__restrict__ 
         chol_body<T, 16, 4, 2>(partial, splits, kmax, k, R, Rinv, Rprev, Rtot, ldr, well_out, sm, red);
     else
         chol_body<T, 16, 8, 4>(partial, splits, kmax, k, R, Rinv, Rprev, Rtot, ldr, well_out, sm, red);
+}
+
+// ---------------------------------------------------------------------------
+// CholeskyQR2 of a tall block in one thread-block cluster
+// ---------------------------------------------------------------------------
+// The two CholeskyQR passes (Gram, Cholesky, Q = X R^{-1}, twice) as one
+// launch of a cluster of CQR_CL CTAs: every CTA takes a contiguous range of
+// rows; the partial Gram matrices meet in distributed shared memory and are
+// summed in rank order (each CTA sums one share of the entries); CTA 0 runs the
+// equilibrated Cholesky (chol_body, the single-CTA factorisation above) and
+// every CTA then forms its rows of Q.  The second pass runs only when the first
+// found the equilibrated Gram matrix further than 0.5 from the identity (the
+// flag is uniform over the cluster); otherwise Q = Q1 and R = R1 exactly, as
+// in the multi-launch form.  fp32 only (k <= small_kmax<float>()).
+constexpr int CQR_NT = CHOL_NT;
+
+constexpr int CQR_CH = 64;  // rows of a staged chunk
+
+// rows [c0, c0 + nr) of X (ld ldx, a multiple of 4), columns [0, k4), into the
+// chunk buffer (ld k4 = round4(k)) with 16-byte loads
+template <typename T>
+__device__ __forceinline__ void cqr_load_chunk(const T *__restrict__ X, int64_t ldx, int c0, int nr, int k4, T *ch)
+{
+    const int q4 = k4 / 4;
+    for (int e = threadIdx.x; e < nr * q4; e += CQR_NT) {
+        const int r = e / q4, q = e - r * q4;
+        *reinterpret_cast<float4 *>(ch + r * k4 + 4 * q) =
+            *reinterpret_cast<const float4 *>(X + (int64_t)(c0 + r) * ldx + 4 * q);
+    }
+}
+
+// Gp (k x k, ld k, upper 4 x 4 tiles; the rest zero) = X[r0:r1]^T X[r0:r1].
+// Rows come through the chunk buffer; thread t takes tile t % T of the T upper
+// tiles and the chunk rows g, g + G, ... (g = t / T, G = 512 / T groups); the
+// groups' tiles are summed in order.  scratch: 512 x 16, ch: CQR_CH x round4(k).
+template <typename T>
+__device__ void cqr_gram(const T *__restrict__ X, int64_t ldx, int r0, int r1, int k, T *Gp, T *scratch, T *ch)
+{
+    const int tid = threadIdx.x;
+    const int nb = (k + 3) / 4, ntile = nb * (nb + 1) / 2, k4 = 4 * nb;
+    const int groups = max(1, CQR_NT / ntile);
+    for (int e = tid; e < k * k; e += CQR_NT) Gp[e] = T(0);
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) acc[a][b] = T(0);
+    int bi = 0, bj = 0;
+    const bool act = tid < ntile * groups;
+    const int tile = tid % ntile, g = tid / ntile;
+    {
+        // tile -> (bi, bj) with bi <= bj, row by row of the upper block triangle
+        int t = tile;
+        while (t >= nb - bi) {
+            t -= nb - bi;
+            bi++;
+        }
+        bj = bi + t;
+    }
+    for (int c0 = r0; c0 < r1; c0 += CQR_CH) {
+        const int nr = min(CQR_CH, r1 - c0);
+        cqr_load_chunk<T>(X, ldx, c0, nr, k4, ch);
+        __syncthreads();
+        if (act) {
+            for (int r = g; r < nr; r += groups) {
+                const float4 u4 = *reinterpret_cast<const float4 *>(ch + r * k4 + 4 * bi);
+                const float4 v4 = *reinterpret_cast<const float4 *>(ch + r * k4 + 4 * bj);
+                const T u[4] = {u4.x, u4.y, u4.z, u4.w}, v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                for (int a = 0; a < 4; a++)
+#pragma unroll
+                    for (int b = 0; b < 4; b++) acc[a][b] = fma(u[a], v[b], acc[a][b]);
+            }
+        }
+        __syncthreads();
+    }
+    if (act) {
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int b = 0; b < 4; b++) scratch[(size_t)tid * 16 + a * 4 + b] = acc[a][b];
+    }
+    __syncthreads();
+    for (int e = tid; e < ntile * 16; e += CQR_NT) {
+        const int tl = e / 16, a = (e / 4) % 4, b = e % 4;
+        T s = T(0);
+        for (int q = 0; q < groups; q++) s += scratch[(size_t)(q * ntile + tl) * 16 + a * 4 + b];
+        int t = tl, i = 0;
+        while (t >= nb - i) {
+            t -= nb - i;
+            i++;
+        }
+        const int x = 4 * i + a, y = 4 * (i + t) + b;
+        if (x < k && y < k) Gp[x * k + y] = s;
+    }
+    __syncthreads();
+}
+
+// Y[r0:r1] (ld ldy) = X[r0:r1] B with B (k x k) staged in shared memory with
+// ld round4(k) and zero beyond k; X rows through the chunk buffer
+template <typename T>
+__device__ void cqr_apply(const T *__restrict__ X, int64_t ldx, int r0, int r1, int k, const T *Bs,
+                          T *__restrict__ Y, int64_t ldy, T *ch)
+{
+    const int k4 = (k + 3) / 4 * 4, nc = k4 / 4;
+    for (int c0 = r0; c0 < r1; c0 += CQR_CH) {
+        const int nr = min(CQR_CH, r1 - c0);
+        cqr_load_chunk<T>(X, ldx, c0, nr, k4, ch);
+        __syncthreads();
+        for (int tsk = threadIdx.x; tsk < nr * nc; tsk += CQR_NT) {
+            const int r = tsk / nc, c = 4 * (tsk - (tsk / nc) * nc);
+            const T *xr = ch + r * k4;
+            float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = 0; i < k; i++) {
+                const T xv = xr[i];
+                const float4 b = *reinterpret_cast<const float4 *>(Bs + i * k4 + c);
+                o.x = fma(xv, b.x, o.x);
+                o.y = fma(xv, b.y, o.y);
+                o.z = fma(xv, b.z, o.z);
+                o.w = fma(xv, b.w, o.w);
+            }
+            T *yr = Y + (int64_t)(c0 + r) * ldy + c;
+            if (c + 3 < k) {
+                *reinterpret_cast<float4 *>(yr) = o;
+            } else {
+                yr[0] = o.x;
+                if (c + 1 < k) yr[1] = o.y;
+                if (c + 2 < k) yr[2] = o.z;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// the cluster's partial Gram matrices summed in rank order into G (global, ld ldg);
+// CTA `rank` sums entries rank, rank + CL, ...
+template <typename T>
+__device__ void cqr_reduce(cg::cluster_group &cluster, T *Gp, int k, T *__restrict__ G, int ldg)
+{
+    const int cl = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+    for (int e = rank * CQR_NT + threadIdx.x; e < k * k; e += cl * CQR_NT) {
+        T s = T(0);
+        for (int q = 0; q < cl; q++) s += cluster.map_shared_rank(Gp, q)[e];
+        G[(int64_t)(e / k) * ldg + e % k] = s;
+    }
+}
+
+// B (k x k, ld ldb) into shared memory with ld round4(k), zero-padded
+template <typename T>
+__device__ void cqr_stage(const T *__restrict__ B, int ldb, int k, T *Bs)
+{
+    const int k4 = (k + 3) / 4 * 4;
+    for (int e = threadIdx.x; e < k * k4; e += CQR_NT) {
+        const int i = e / k4, c = e - i * k4;
+        Bs[e] = c < k ? B[(int64_t)i * ldb + c] : T(0);
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void cqr_chol(const T *G, int KM, int k, T *R, T *Rinv, const T *Rprev, T *Rtot,
+                                         int *well, T *ws, double *red)
+{
+    if (k <= 64)
+        chol_body<T, 16, 4, 2>(G, 1, KM, k, R, Rinv, Rprev, Rtot, KM, well, ws, red);
+    else
+        chol_body<T, 16, 8, 4>(G, 1, KM, k, R, Rinv, Rprev, Rtot, KM, well, ws, red);
+}
+
+// X (rows x k, ld KM) -> Q (rows x k, ld KM) with orthonormal columns and, if
+// Rout is given, X = Q Rout (k x k, ld KM); Q1, G, R1, R1i, R2, R2i: workspace
+// (rows x KM and KM x KM, ld KM); well: the first pass's flag; stats: count of
+// factorisations run.
+template <typename T>
+__global__ void __launch_bounds__(CQR_NT, 1)
+    cholqr2_cluster_kernel(int rows, const T *__restrict__ X, T *__restrict__ Q, T *__restrict__ Q1, int KM,
+                           const int *kdyn, T *G, T *R1, T *R1i, T *R2, T *R2i, T *Rout, int *well, int *stats,
+                           int gp_off)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double red[CQR_NT / 32];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cl = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+    const int k = *kdyn;
+    if (k < 1) return;  // uniform over the cluster
+    // Cholesky workspace; outside the factorisations it holds the Gram scratch
+    // (512 x 16) and the chunk of staged rows (CQR_CH x round4(k))
+    T *ws = reinterpret_cast<T *>(smraw);
+    T *ch = ws + CQR_NT * 16;
+    T *Gp = reinterpret_cast<T *>(smraw + gp_off);  // this CTA's partial Gram matrix (k x k), or a staged factor
+    const int rpc = (rows + cl - 1) / cl;
+    const int r0 = min(rows, rank * rpc), r1 = min(rows, r0 + rpc);
+
+    // pass 1: Gram of X, Cholesky on CTA 0
+    cqr_gram<T>(X, KM, r0, r1, k, Gp, ws, ch);
+    cluster.sync();
+    cqr_reduce<T>(cluster, Gp, k, G, KM);
+    __threadfence();
+    cluster.sync();
+    if (rank == 0) {
+        if (stats != nullptr && threadIdx.x == 0) atomicAdd(stats, 1);
+        cqr_chol<T>(G, KM, k, R1, R1i, nullptr, nullptr, well, ws, red);
+        __threadfence();
+    }
+    cluster.sync();
+    const bool skip2 = *reinterpret_cast<volatile int *>(well) != 0;
+    cqr_stage<T>(R1i, KM, k, Gp);
+    cqr_apply<T>(X, KM, r0, r1, k, Gp, skip2 ? Q : Q1, KM, ch);
+    if (skip2) {
+        // second pass not needed: Q = Q1, R = R1
+        if (Rout != nullptr && rank == 0)
+            for (int e = threadIdx.x; e < k * k; e += CQR_NT)
+                Rout[(int64_t)(e / k) * KM + e % k] = R1[(int64_t)(e / k) * KM + e % k];
+        return;
+    }
+    __syncthreads();  // this CTA's rows of Q1 are written (and re-read below)
+
+    // pass 2: Gram of Q1, Cholesky on CTA 0 (Rout = R2 R1)
+    cqr_gram<T>(Q1, KM, r0, r1, k, Gp, ws, ch);
+    cluster.sync();
+    cqr_reduce<T>(cluster, Gp, k, G, KM);
+    __threadfence();
+    cluster.sync();
+    if (rank == 0) {
+        if (stats != nullptr && threadIdx.x == 0) atomicAdd(stats, 1);
+        cqr_chol<T>(G, KM, k, R2, R2i, Rout != nullptr ? R1 : nullptr, Rout, nullptr, ws, red);
+        __threadfence();
+    }
+    cluster.sync();
+    cqr_stage<T>(R2i, KM, k, Gp);
+    cqr_apply<T>(Q1, KM, r0, r1, k, Gp, Q, KM, ch);
 }
 
 // ---------------------------------------------------------------------------
@@ -690,6 +925,61 @@ void launch_chol(const T *partialG, int splits, int kmax, const int *kdyn, T *R,
     CPCP_COUNT_LAUNCH();
     chol_kernel<T><<<1, CHOL_NT, chol_smem<T>(kmax), st>>>(partialG, splits, kmax, kdyn, R, Rinv, Rprev, Rtot, ldr,
                                                           well_out, skip_in, stats);
+}
+
+bool launch_cholqr2_cluster(int rows, const float *X, float *Q, float *Q1, int KM, const int *kdyn, float *G,
+                            float *R1, float *R1i, float *R2, float *R2i, float *Rout, int *well, int *stats,
+                            cudaStream_t st)
+{
+    // a cluster of 16 CTAs (non-portable size) where the device accepts it, else 8
+    static int attr = 0;  // 0: not set, 1: set, -1: the kernel cannot be launched
+    static int cl_max = 16;
+    if (KM > small_kmax<float>() || rows < 1) return false;
+    // Cholesky workspace (it also holds the Gram scratch of 512 4 x 4 register
+    // tiles), then one k x k partial Gram matrix
+    const int kx = small_kmax<float>();
+    const size_t ws = std::max(chol_smem<float>(kx), (size_t)(CQR_NT * 16 + CQR_CH * kx) * sizeof(float));
+    const int gp_off = (int)((ws + 255) / 256 * 256);
+    const size_t smem = (size_t)gp_off + (size_t)kx * kx * sizeof(float);
+    if (attr == 0) {
+        attr = 1;
+        if (cudaFuncSetAttribute(cholqr2_cluster_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            attr = -1;
+        if (cudaFuncSetAttribute(cholqr2_cluster_kernel<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess)
+            cl_max = 8;
+        cudaGetLastError();
+    }
+    if (attr < 0) return false;
+    for (;;) {
+        const int cl = std::min(cl_max, std::max(1, rows / 16));
+        int c = 1;
+        while (c * 2 <= cl) c *= 2;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)c);
+        cfg.blockDim = dim3(CQR_NT);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)c;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        CPCP_COUNT_LAUNCH();
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, cholqr2_cluster_kernel<float>, rows, X, Q, Q1, KM, kdyn, G,
+                                                 R1, R1i, R2, R2i, Rout, well, stats, gp_off);
+        if (e == cudaSuccess) return true;
+        cudaGetLastError();
+        --g_kernel_launches;
+        if (c <= 8) {
+            attr = -1;  // not launchable here: the caller uses the multi-launch form from now on
+            return false;
+        }
+        cl_max = 8;
+    }
 }
 
 template <typename T>

@@ -584,6 +584,13 @@ void orth(cpcp_context *h, SvdWork<T> &w, int rows, const T *X, T *Q, T *Rout, c
     cudaStream_t st = h->stream;
     const int KM = w.KM;
     int *well = w.well + slot;
+    if constexpr (std::is_same<T, float>::value) {
+        // both passes in one thread-block cluster launch where available
+        if (h->opt.cholqr_fused != 0 &&
+            launch_cholqr2_cluster(rows, X, Q, w.Q1, KM, kdyn, w.Gpart, w.R1, w.R1i, w.R2, w.R2i, Rout, well,
+                                   w.stats ? w.stats + 2 : nullptr, st))
+            return;
+    }
     int sp = prod_gram<T>(w, rows, X, kdyn, nullptr, st);
     launch_chol<T>(w.Gpart, sp, KM, kdyn, w.R1, w.R1i, nullptr, nullptr, KM, well, nullptr, st,
                    w.stats ? w.stats + 2 : nullptr);
@@ -961,12 +968,13 @@ struct IterGraph {
 };
 
 struct IterGraphs {
-    IterGraph g[8][2];
+    IterGraph g[8][2][2];  // level, buffer parity, half-step side
     ~IterGraphs()
     {
         for (auto &row : g)
-            for (auto &x : row)
-                if (x.exec) cudaGraphExecDestroy(x.exec);
+            for (auto &pair : row)
+                for (auto &x : pair)
+                    if (x.exec) cudaGraphExecDestroy(x.exec);
     }
 };
 
@@ -981,7 +989,7 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     // (captured the second time the same level and buffer parity come up,
     // once every workspace buffer exists); the kernels read the iteration's
     // scalars (weights, widths, ranks) from the device control block
-    const bool use_graphs = o.graphs && !o.half;
+    const bool use_graphs = o.graphs;
     PrivateStream ps(h, use_graphs);
     cudaStream_t st = h->stream;
     const int H = levels - 1;
@@ -1120,7 +1128,10 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
             // profile's events bracket the pass); the rest of the iteration is
             // the graph
             one_iteration<T>(h, s, w, level, cur, o, false, 1);
-            IterGraph &G = graphs.g[level][cur];
+            // the half-step mode alternates its projection side (host state that
+            // part 2 flips): one graph per side
+            const int side0 = s.side;
+            IterGraph &G = graphs.g[level][cur][o.half ? side0 : 0];
             if (G.exec == nullptr && G.seen) {
                 const unsigned long long l0 = g_kernel_launches;
                 CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -1139,11 +1150,13 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
                 CK(ie);
                 G.launches = g_kernel_launches - l0;
                 g_kernel_launches = l0;
+                s.side = side0;  // the capture did not run the iteration
             }
             const int ts = h->timer.open(CPCP_PHASE_SVT);
             if (G.exec != nullptr) {
                 CK(cudaGraphLaunch(G.exec, st));
                 g_kernel_launches += G.launches;
+                if (o.half) s.side = side0 ^ 1;
             } else {
                 G.seen = true;
                 one_iteration<T>(h, s, w, level, cur, o, false, 2);

@@ -52,13 +52,13 @@ def write(name: str) -> str:
     with open(path, "w") as f:
         f.write(f"# fp64 oracle optimum of eq. (cpcp), sampled entries; workload {name}: m={m} n={n}\n")
         f.write(f"# lam={p['lam']!r} mu={p['mu']!r}; D rounded to fp32; oracle.fista levels=1 tol={TOL}\n")
-        f.write(f"# status={info['status']} iters={info['iters']} relkkt={info['relkkt']!r} rank={info['rank']} "
-                f"objective={info['objective']!r} seconds={dt:.0f}\n")
-        f.write(f"# fro_L={np.linalg.norm(L)!r} fro_S={np.linalg.norm(S)!r} nnz_S={int(supp.size)}\n")
+        f.write(f"# status={info['status']} iters={info['iters']} relkkt={float(info['relkkt'])!r} "
+                f"rank={info['rank']} objective={float(info['objective'])!r} seconds={dt:.0f}\n")
+        f.write(f"# fro_L={float(np.linalg.norm(L))!r} fro_S={float(np.linalg.norm(S))!r} nnz_S={int(supp.size)}\n")
         f.write("# i j L S  (first 1024 uniform, then entries of supp(S))\n")
         for q in idx:
             i, j = divmod(int(q), n)
-            f.write(f"{i} {j} {L[i, j]!r} {S[i, j]!r}\n")
+            f.write(f"{i} {j} {float(L[i, j])!r} {float(S[i, j])!r}\n")
     return path
 
 
