@@ -10,10 +10,13 @@ Workload (one "step" = one full solve, all of the hot path):
   Between timed steps a 256 MB buffer is written to flush the 129 MB L2.
 
 JSON fields beyond the base contract: the single-level time on the same
-inputs, the roofline of the fused iteration pass (algorithmic bytes per launch
-over its CUDA-event duration, against the measured HBM copy bandwidth), the
-end-to-end time through the C ABI with host buffers, the clocks seen during the
-timed region, and the fp64 oracle timed on the host cores on a bounded sample.
+inputs, each result's error against the fp64 oracle's optimum (sampled entries
+stored by tests/golden/make_fullsize_optima.py), the roofline of the kernel
+family with the largest share of a profiled solve (CUDA events around every
+launch) with every family's share and roofline fraction, the whole solve's
+algorithmic bytes against HBM, the end-to-end time through the C ABI with host
+buffers, the clocks seen during the timed region, and the fp64 oracle timed
+on the host cores (one step per level, projected over the solve's level mix).
 
 Three more measurements go into the same line (skipped with --no-extras):
   "video_mixed": the 19200 x 400 video-shaped workload (4 levels) solved with
@@ -173,6 +176,57 @@ def golden_error(name: str, L, S) -> dict | None:
             "samples": int(len(a)), "oracle_relkkt": relkkt}
 
 
+# DRAM bytes per launch from ncu captures of the same kernels on this workload
+# (dram__bytes_read.sum + dram__bytes_write.sum); None where not captured for the
+# kernel as it stands
+TRAFFIC = {
+    "fused fine pass": (51.55e6, "profiles/pass_tc_cpcp2000.md"),
+}
+FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
+
+
+def kernel_families(prof: dict, m: int, n: int, peaks: dict) -> list:
+    """Per kernel family of a profiled solve (cpcp_info with profile = 2): time,
+    share, launches, average launch time, algorithmic work per launch, and the
+    roofline it is held to (HBM bytes, or FP32 FLOPs for the k x k stages that
+    run on one SM or one cluster: those are latency-bound chains, far below it)."""
+    ph, det, cnt = prof["phase_ms"], prof["svt_detail_ms"], prof["phase_count"]
+    its = max(cnt["svt"], 1)
+    k = min(prof["rank"] + 10, n)
+    sweeps = prof["jacobi_sweeps"] / max(prof["jacobi_calls"], 1)
+    fam = [
+        ("fused fine pass", "pass_tc_kernel", ph["pass_fine"], cnt["pass_fine"], "hbm",
+         20 * m * n + 4 * m * math.ceil(n / 32)),
+        ("coarse pass", "pass_kernel (step, with restriction)", ph["pass_coarse"], cnt["pass_coarse"], "hbm",
+         16 * m * n + 4 * m * math.ceil(n / 32) + 4 * m * math.ceil(n / 2)),
+        ("products with M", "ts_gemm_kernel (M Omega, M^T Q)", det["products"], 2 * its, "hbm",
+         4 * (m * n + n * k + m * k)),
+        ("CholeskyQR2", "chol_kernel with ts_gemm Gram and Q products", det["cholqr"], 2 * its, "alu",
+         2 * (3 * m * k * k + k ** 3 / 3)),
+        ("core Jacobi SVD", "jacobi_kernel", det["jacobi"], its, "alu", sweeps * (k * k / 2) * 12 * k),
+        ("factor products", "ts_gemm_kernel (A = Q U, V = Q W) and fill_prolong", det["factors"], 3 * its, "hbm",
+         4 * (2 * m * k + 2 * n * k + 2 * k * k)),
+        ("residual checks", "pass_kernel (check, diff) and the fine subspace SVD", ph["check"], max(cnt["check"], 1),
+         "hbm", 2 * 20 * m * n + 4 * 4 * 4 * m * n),
+    ]
+    total = sum(f[2] for f in fam)
+    out = []
+    for name, kern, ms, launches, bound, work in fam:
+        if ms <= 0:
+            continue
+        avg = ms / max(launches, 1)
+        if bound == "hbm":
+            ach, peak, unit, src = work / (avg / 1e3) / 1e9, peaks["hbm_gbs"], "GB/s", peaks["source"] + " (hbm_gbs)"
+        else:
+            ach, peak, unit, src = work / (avg / 1e3) / 1e12, FP32_TFLOPS, "TFLOP/s", "FP32 lanes x 2070 MHz"
+        tr = TRAFFIC.get(name)
+        out.append({"family": name, "kernel": kern, "ms": ms, "share": ms / total, "launches": launches,
+                    "avg_launch_ms": avg, "work_per_launch": work, "bound": bound, "achieved": ach, "peak": peak,
+                    "unit": unit, "frac": ach / peak, "peak_source": src,
+                    "traffic": tr[0] if tr else None, "traffic_source": tr[1] if tr else None})
+    return out
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -303,26 +357,34 @@ def run_ours(args):
         if i > 0:
             e2e.append(time.perf_counter() - t0)
 
-    # roofline of the fused iteration pass from the events recorded inside the
-    # timed solves: algorithmic bytes per launch / average launch duration
+    # kernel families of the solve, timed with CUDA events in one more multilevel
+    # solve with profile = 2 (every kernel launched from the host), and the
+    # roofline of the family with the largest share
     peaks = measured_peaks()
-    nh = math.ceil(n / 4)
-    obs_bytes = {"pass_fine": (4 + 4 + 4 + 4 + 4) * m * n + m * math.ceil(n / 32) * 4,
-                 "pass_coarse": (4 + 4 + 4 + 4) * m * n + m * math.ceil(n / 32) * 4 + 4 * m * nh}
+    with cpcp.Handle(local, stream=stream, profile=2) as hp:
+        hp.solve(D, Q, p["lam"], p["mu"], levels=args.levels, tol=TOL)
+        flush.zero_()
+        _, _, prof = hp.solve(D, Q, p["lam"], p["mu"], levels=args.levels, tol=TOL)
+    kernels = kernel_families(prof, m, n, peaks)
+    dom = max((k for k in kernels if k["family"] != "residual checks"), key=lambda k: k["ms"])
+    roofline = {key: dom[key] for key in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel",
+                                          "avg_launch_ms", "work_per_launch", "peak_source")}
+    roofline["share"] = dom["share"]
+    roofline["timing"] = ("CUDA events around each launch in a profiled multilevel solve after the timed region "
+                          "(profile = 2: plain launches)")
     tot = {k: sum(i["phase_ms"][k] for i in inf_ml) for k in ("pass_fine", "pass_coarse", "svt", "check")}
-    cnt = {k: sum(i["phase_count"][k] for i in inf_ml) for k in ("pass_fine", "pass_coarse", "svt", "check")}
-    dom = "pass_fine" if tot["pass_fine"] >= tot["pass_coarse"] else "pass_coarse"
-    avg_ms = tot[dom] / max(cnt[dom], 1)
-    achieved = obs_bytes[dom] / (avg_ms / 1e3) / 1e9
-    # DRAM bytes of one fine-pass launch from ncu (profiles/pass_tc_cpcp2000.md: read 50.66 MB +
-    # write 0.89 MB; the 32 MB of S and M writes are still in L2 when the launch ends)
-    traffic = {"pass_fine": 51.55e6}.get(dom)
-    kname = {"pass_fine": "pass_tc_kernel (pass_fine)",
-             "pass_coarse": "pass_kernel (pass_coarse)"}[dom]
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname,
-                "bytes_per_launch": obs_bytes[dom], "avg_launch_ms": avg_ms, "peak_source": peaks["source"],
-                "phase_share": {k: tot[k] / max(sum(tot.values()), 1e-30) for k in tot}}
+    roofline["phase_share_timed"] = {k: tot[k] / max(sum(tot.values()), 1e-30) for k in tot}
+    roofline["kernels"] = kernels
+    # the whole solve against HBM: algorithmic bytes of every iteration and check over the solve time
+    nh = [math.ceil(n / 2 ** hv) for hv in range(args.levels)]
+    lv_it = inf_ml[-1]["level_iters"][:args.levels]
+    it_bytes = sum(it * (20 * m * n + 4 * m * math.ceil(n / 32) + 6 * 4 * m * nh[hv]) for hv, it in enumerate(lv_it))
+    ck_bytes = inf_ml[-1]["checks"] * (2 * 20 * m * n + 4 * 4 * 4 * m * n)
+    roofline["solve"] = {"bytes": it_bytes + ck_bytes, "achieved_gbs": (it_bytes + ck_bytes) / ml / 1e9,
+                         "frac": (it_bytes + ck_bytes) / ml / 1e9 / peaks["hbm_gbs"],
+                         "model": "per iteration 20 B/elem fused pass + mask + 6 passes over the m x n_H "
+                                  "matrix (write, Y, Z, and the restriction); per check two m x n passes and "
+                                  "four subspace products (two power steps)"}
 
     line = {"metric": METRIC, "value": ml, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ml * 1e3, "higher_is_better": False, "scaling": "weak",

@@ -83,7 +83,10 @@ typedef struct {
     uint64_t seed;         /* seed of the random start block of the subspace (1) */
     double *trace;         /* optional host array: rel-KKT of each residual check */
     int trace_cap;         /* capacity of trace (entries written: info.checks) */
-    int profile;           /* nonzero: time the phases with CUDA events (info.phase_*) */
+    int profile;           /* nonzero: time the phases with CUDA events (info.phase_*); 2: also
+                              the kernel families of the iterations' SVT phase
+                              (info.svt_detail_ms), with every kernel launched from the host
+                              (no graph replay) */
     int precision;         /* CPCP_F32 solves only.  0: fp32 contractions.  1 (mixed):
                               the two passes over the restricted iterate in each
                               subspace step (M_H Omega and M_H^T Q) run on the tensor
@@ -101,10 +104,11 @@ typedef struct {
                               an exact SVT, recording checkpoints for the reverse sweep */
     int ckpt_every;        /* steps between checkpoints of the unrolled run (10) */
     double rho;            /* unrolled run: mu_k = mu max(rho eta^k, 1); must be > 0 */
-    int subspace_mode;     /* cpcp_solve: 0 = power_iters full range passes per iteration;
-                              1 = half steps: each iteration projects once onto the previous
-                              iteration's right or left singular subspace, alternating
-                              (one contraction with M_H, one CholeskyQR2, one core SVD) */
+    int subspace_mode;     /* cpcp_solve: must be 0 (power_iters full range passes per
+                              iteration); other values: INVALID_ARG.  (A half-step form that
+                              projected onto the previous iteration's singular subspace without
+                              re-orthonormalising it diverged once the width grew, and was
+                              removed.) */
     int pass_simt;         /* cpcp_solve, fp32: nonzero runs the fused fine pass on the SIMT
                               cores.  0 (default): the tensor-core pass (tcgen05, each factor
                               entry split into three TF32 parts, the six products of order
@@ -122,9 +126,9 @@ typedef struct {
                               tridiagonal), which makes the coarse L-step the exact minimiser over
                               {L_H R^T} (epsilon = 0 in Theorem LH-eps); applied to M_H (and the
                               restricted gradient of the level test) and to V by two bidiagonal
-                              solves.  cpcp_solve rejects it with subspace_mode = 1 or
-                              unroll > 0, cpcp_solve_batched rejects it; other values than
-                              0 and 1: INVALID_ARG */
+                              solves.  cpcp_solve rejects it with unroll > 0,
+                              cpcp_solve_batched rejects it; other values than 0 and 1:
+                              INVALID_ARG */
     int early_test;        /* cpcp_solve level rule: 0 (default) or 1 = the coarse-gradient test
                               (move one level finer when ||G R||_F < kappa ||G||_F) also runs after
                               the first iteration on each coarse level, so data whose gradient is
@@ -166,9 +170,11 @@ typedef struct {
     int phase_count[4];    /* timed intervals per phase */
     long long launches;    /* CUDA kernels launched by the solve */
     int bf16_iters;        /* iterations whose contractions ran in BF16 (precision 1) */
-    double svt_detail_ms[4]; /* cpcp_solve_batched only: the instance's SVT phase split into
-                                the products with M, CholeskyQR, the core Jacobi SVD and the
-                                factor products (SM cycle counter at the nominal clock) */
+    double svt_detail_ms[4]; /* the SVT phase split into the products with M, CholeskyQR, the
+                                core Jacobi SVD and the factor products with the next start
+                                block: cpcp_solve_batched (the instance's, SM cycle counter at the
+                                nominal clock) and cpcp_solve with profile = 2 (the iterations',
+                                CUDA events; residual checks excluded) */
     int jacobi_calls;      /* cpcp_solve: core Jacobi SVDs run (iterations and checks) */
     int jacobi_sweeps;     /* cpcp_solve: their sweeps, summed */
     int chol_factors;      /* cpcp_solve: Cholesky factorisations of CholeskyQR run (second

@@ -187,6 +187,31 @@ void launch_ialm_update(int m, int n, const T *D, int64_t ldd, const T *L, int64
                         double lam, double mu, double *partial, cudaStream_t st);
 // end == 0: theta_L = 1 / mu into the control block; 1: width bookkeeping
 void launch_ialm_ctrl(Ctrl *c, double mu, int end, cudaStream_t st);
+// Device-resident scalars of an FW-T / ML-FWT run (k_fwt.cu): the epigraph
+// objective, the bounds and variables t_L, t_S, U_L, U_S, the argmax of |G|,
+// this iteration's vertices and step sizes, and the stop state.  Every kernel
+// of an iteration reads them here, so an iteration needs no host round trip
+// and can be replayed as a CUDA graph.
+struct FwScal {
+    double f, tL, tS, UL, US, gmax, rel;
+    double cL, vs, VtL, VtS, a, b;  // V_L = cL u v^T, V_S = vs e_{i*}; step sizes
+    double lamL, lamS, tol, margin;
+    int64_t istar;
+    int done;   // 0 running; 1 the relative decrease reached tol; 2 numeric failure
+    int iters;  // iterations completed
+};
+// start: f and the argmax of |G| from fwt_grad's partials; t_L = t_S = 0
+void launch_fwt_first(FwScal *sc, const double *partial, const double *amax_v, const int64_t *amax_i,
+                      cudaStream_t st);
+// the LMOs' vertices from the top singular value sig[0] and G[i*] (done = 2 when
+// no finite entry of G exists)
+template <typename T>
+void launch_fwt_lmo(FwScal *sc, const T *sig, const T *G, int64_t ld, int m, int n, cudaStream_t st);
+// the two-segment line search from fwt_coef's partials
+void launch_fwt_ls(FwScal *sc, const double *partial, cudaStream_t st);
+// after fwt_update: t_L, t_S, f, U_L, U_S, the argmax; trace[iters] = f; the stop test
+void launch_fwt_post(FwScal *sc, const double *partial, const double *amax_v, const int64_t *amax_i, double *trace,
+                     cudaStream_t st);
 // Frank-Wolfe Thresholding passes (k_fwt.cu): fwt_blocks() per-block
 // partials (1, 5 and 2 per block) and per-block argmax |G| (value, index)
 int fwt_blocks();
@@ -195,13 +220,12 @@ void launch_fwt_grad(int m, int n, const T *D, int64_t ldd, const uint32_t *Q, i
                      int64_t ld, T *G, double *partial, double *amax_v, int64_t *amax_i, cudaStream_t st);
 template <typename T>
 void launch_fwt_coef(int m, int n, const uint32_t *Q, int64_t ldq, const T *L, const T *S, const T *G, int64_t ld,
-                     const T *u, int64_t ldu, const T *v, int64_t ldv, double cL, int64_t istar, double vs,
-                     double *partial, cudaStream_t st);
+                     const T *u, int64_t ldu, const T *v, int64_t ldv, const FwScal *sc, double *partial,
+                     cudaStream_t st);
 template <typename T>
 void launch_fwt_update(int m, int n, const T *D, int64_t ldd, const uint32_t *Q, int64_t ldq, T *L, T *S, T *G,
-                       int64_t ld, const T *u, int64_t ldu, const T *v, int64_t ldv, double cL, int64_t istar,
-                       double vs, double a, double b, double lamS, double *partial, double *amax_v, int64_t *amax_i,
-                       cudaStream_t st);
+                       int64_t ld, const T *u, int64_t ldu, const T *v, int64_t ldv, const FwScal *sc,
+                       double *partial, double *amax_v, int64_t *amax_i, cudaStream_t st);
 // the orthonormal-basis transfer of ML-IALM: C upper bidiagonal (diagonal cd,
 // super-diagonal ce, nh entries each).  Right solve in place: X C = Y for the
 // rows of X (rows x nh); left solve: Out = C^{-1} V for the first *kdyn

@@ -107,9 +107,12 @@ __global__ void __launch_bounds__(FWT_NT) fwt_coef_kernel(int m, int n, const ui
                                                           const T *__restrict__ L, const T *__restrict__ S,
                                                           const T *__restrict__ G, int64_t ld,
                                                           const T *__restrict__ u, int64_t ldu,
-                                                          const T *__restrict__ v, int64_t ldv, T cL, int64_t istar,
-                                                          T vs, double *partial)
+                                                          const T *__restrict__ v, int64_t ldv,
+                                                          const FwScal *__restrict__ sc, double *partial)
 {
+    if (sc->done) return;
+    const T cL = T(sc->cL), vs = T(sc->vs);
+    const int64_t istar = sc->istar;
     double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     const int64_t total = (int64_t)m * n;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -133,10 +136,13 @@ __global__ void __launch_bounds__(FWT_NT) fwt_update_kernel(int m, int n, const 
                                                             const uint32_t *__restrict__ Q, int64_t ldq,
                                                             T *__restrict__ L, T *__restrict__ S, T *__restrict__ G,
                                                             int64_t ld, const T *__restrict__ u, int64_t ldu,
-                                                            const T *__restrict__ v, int64_t ldv, T cL,
-                                                            int64_t istar, T vs, T a, T b, T lamS, double *partial,
+                                                            const T *__restrict__ v, int64_t ldv,
+                                                            const FwScal *__restrict__ sc, double *partial,
                                                             double *amax_v, int64_t *amax_i)
 {
+    if (sc->done) return;
+    const T cL = T(sc->cL), vs = T(sc->vs), a = T(sc->a), b = T(sc->b), lamS = T(sc->lamS);
+    const int64_t istar = sc->istar;
     double s[2] = {0.0, 0.0}, amv = -1.0;
     int64_t amix = INT64_MAX;
     const int64_t total = (int64_t)m * n;
@@ -161,7 +167,196 @@ __global__ void __launch_bounds__(FWT_NT) fwt_update_kernel(int m, int n, const 
     block_sums<2>(s, amv, amix, partial, amax_v, amax_i);
 }
 
+// sum over the FWT_BLOCKS blocks of slot q (of ns per block) by one warp, in a
+// fixed order (lane-strided partial sums, then a fixed shuffle tree)
+__device__ __forceinline__ double warp_block_sum(const double *partial, int ns, int q)
+{
+    const int lane = threadIdx.x & 31;
+    double t = 0.0;
+    for (int b = lane; b < FWT_BLOCKS; b += 32) t += partial[(int64_t)b * ns + q];
+    return warp_sum(t);
+}
+
+// argmax over the blocks' (value, index) by one warp, ties to the smaller index
+__device__ __forceinline__ void warp_block_amax(const double *amax_v, const int64_t *amax_i, double &v, int64_t &ix)
+{
+    const int lane = threadIdx.x & 31;
+    v = -1.0;
+    ix = INT64_MAX;
+    for (int b = lane; b < FWT_BLOCKS; b += 32) amax_merge(v, ix, amax_v[b], amax_i[b]);
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const int64_t i2 = __shfl_xor_sync(0xffffffffu, ix, o);
+        amax_merge(v, ix, v2, i2);
+    }
+}
+
+// Exact minimiser over [0,1]^2 of 1/2 (A a^2 + 2 C a b + B b^2) + ga a + gb b
+// (convex: A, B >= 0, A B >= C^2): the stationary point if it lies in the box,
+// else the best of the four edge minimisers.  The two-segment line search of
+// Alg. 3.
+__device__ void fw_box_qp(double A, double B, double C, double ga, double gb, double *a_out, double *b_out)
+{
+    double best_a = 0.0, best_b = 0.0, best = 0.0;  // q(0, 0) = 0
+    auto q = [&](double a, double b) { return 0.5 * (A * a * a + 2.0 * C * a * b + B * b * b) + ga * a + gb * b; };
+    auto c01 = [](double x) { return fmin(1.0, fmax(0.0, x)); };
+    auto consider = [&](double a, double b) {
+        const double v = q(a, b);
+        if (v < best) {
+            best = v;
+            best_a = a;
+            best_b = b;
+        }
+    };
+    const double det = A * B - C * C;
+    if (det > 0.0) {
+        const double a = (C * gb - B * ga) / det, b = (C * ga - A * gb) / det;
+        if (a >= 0.0 && a <= 1.0 && b >= 0.0 && b <= 1.0) consider(a, b);
+    }
+    for (int ei = 0; ei < 2; ei++) {
+        const double e = (double)ei;
+        const double lb = gb + C * e, la = ga + C * e;
+        consider(e, B > 0.0 ? c01(-lb / B) : (lb < 0.0 ? 1.0 : 0.0));
+        consider(A > 0.0 ? c01(-la / A) : (la < 0.0 ? 1.0 : 0.0), e);
+    }
+    *a_out = best_a;
+    *b_out = best_b;
+}
+
+__global__ void fwt_first_kernel(FwScal *sc, const double *__restrict__ partial, const double *__restrict__ amax_v,
+                                 const int64_t *__restrict__ amax_i)
+{
+    // one warp
+    const double g2 = warp_block_sum(partial, 1, 0);
+    double v;
+    int64_t ix;
+    warp_block_amax(amax_v, amax_i, v, ix);
+    if (threadIdx.x == 0) {
+        sc->f = 0.5 * g2;
+        sc->gmax = v;
+        sc->istar = ix;
+        sc->UL = sc->f / sc->lamL;
+        sc->US = sc->f / sc->lamS;
+        sc->tL = 0.0;
+        sc->tS = 0.0;
+        sc->rel = INFINITY;
+        sc->done = 0;
+        sc->iters = 0;
+    }
+}
+
+template <typename T>
+__global__ void fwt_lmo_kernel(FwScal *sc, const T *__restrict__ sig, const T *__restrict__ G, int64_t ld, int m,
+                               int n)
+{
+    if (sc->done) return;
+    const int64_t istar = sc->istar;
+    // no finite entry of G (non-finite input): no argmax, nothing to step on
+    if (istar < 0 || istar >= (int64_t)m * n || !isfinite(sc->f)) {
+        sc->done = 2;
+        return;
+    }
+    const double s0 = (double)sig[0];
+    const double gval = (double)G[(istar / n) * ld + (istar % n)];
+    // after a thresholding step every entry of the support of S has
+    // |G_ij| = lambda_S exactly, the others |G_ij| <= lambda_S: the l1 test takes
+    // a relative margin of a few hundred units of rounding of T
+    const bool useL = sc->lamL < s0, useS = sc->lamS * (1.0 + sc->margin) < sc->gmax;
+    sc->cL = useL ? -sc->UL : 0.0;
+    sc->VtL = useL ? sc->UL : 0.0;
+    sc->vs = useS ? -sc->US * (gval > 0.0 ? 1.0 : -1.0) : 0.0;
+    sc->VtS = useS ? sc->US : 0.0;
+}
+
+__global__ void fwt_ls_kernel(FwScal *sc, const double *__restrict__ partial)
+{
+    // five warps, one per coefficient
+    __shared__ double c[5];
+    if (sc->done) return;
+    const int w = threadIdx.x >> 5;
+    const double t = warp_block_sum(partial, 5, w);
+    if ((threadIdx.x & 31) == 0) c[w] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double ga = c[3] + sc->lamL * (sc->VtL - sc->tL), gb = c[4] + sc->lamS * (sc->VtS - sc->tS);
+        double a, b;
+        fw_box_qp(c[0], c[1], c[2], ga, gb, &a, &b);
+        sc->a = a;
+        sc->b = b;
+    }
+}
+
+__global__ void fwt_post_kernel(FwScal *sc, const double *__restrict__ partial, const double *__restrict__ amax_v,
+                                const int64_t *__restrict__ amax_i, double *trace)
+{
+    // three warps: ||S||_1, ||G||_F^2, argmax |G|
+    __shared__ double c[2];
+    __shared__ double sv;
+    __shared__ int64_t si;
+    if (sc->done) return;
+    const int w = threadIdx.x >> 5;
+    if (w < 2) {
+        const double t = warp_block_sum(partial, 2, w);
+        if ((threadIdx.x & 31) == 0) c[w] = t;
+    } else {
+        double v;
+        int64_t ix;
+        warp_block_amax(amax_v, amax_i, v, ix);
+        if ((threadIdx.x & 31) == 0) {
+            sv = v;
+            si = ix;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double fprev = sc->f;
+        sc->tL += sc->a * (sc->VtL - sc->tL);
+        sc->tS = c[0];
+        const double f = 0.5 * c[1] + sc->lamL * sc->tL + sc->lamS * sc->tS;
+        sc->f = f;
+        sc->gmax = sv;
+        sc->istar = si;
+        sc->UL = f / sc->lamL;
+        sc->US = f / sc->lamS;
+        if (trace != nullptr) trace[sc->iters] = f;
+        sc->iters += 1;
+        if (!isfinite(f)) {
+            sc->done = 2;
+        } else {
+            sc->rel = fabs(fprev - f) / fprev;
+            if (sc->rel <= sc->tol) sc->done = 1;
+        }
+    }
+}
+
 }  // namespace
+
+void launch_fwt_first(FwScal *sc, const double *partial, const double *amax_v, const int64_t *amax_i,
+                      cudaStream_t st)
+{
+    CPCP_COUNT_LAUNCH();
+    fwt_first_kernel<<<1, 32, 0, st>>>(sc, partial, amax_v, amax_i);
+}
+
+template <typename T>
+void launch_fwt_lmo(FwScal *sc, const T *sig, const T *G, int64_t ld, int m, int n, cudaStream_t st)
+{
+    CPCP_COUNT_LAUNCH();
+    fwt_lmo_kernel<T><<<1, 1, 0, st>>>(sc, sig, G, ld, m, n);
+}
+
+void launch_fwt_ls(FwScal *sc, const double *partial, cudaStream_t st)
+{
+    CPCP_COUNT_LAUNCH();
+    fwt_ls_kernel<<<1, 160, 0, st>>>(sc, partial);
+}
+
+void launch_fwt_post(FwScal *sc, const double *partial, const double *amax_v, const int64_t *amax_i, double *trace,
+                     cudaStream_t st)
+{
+    CPCP_COUNT_LAUNCH();
+    fwt_post_kernel<<<1, 96, 0, st>>>(sc, partial, amax_v, amax_i, trace);
+}
 
 int fwt_blocks() { return FWT_BLOCKS; }
 
@@ -175,34 +370,32 @@ void launch_fwt_grad(int m, int n, const T *D, int64_t ldd, const uint32_t *Q, i
 
 template <typename T>
 void launch_fwt_coef(int m, int n, const uint32_t *Q, int64_t ldq, const T *L, const T *S, const T *G, int64_t ld,
-                     const T *u, int64_t ldu, const T *v, int64_t ldv, double cL, int64_t istar, double vs,
-                     double *partial, cudaStream_t st)
+                     const T *u, int64_t ldu, const T *v, int64_t ldv, const FwScal *sc, double *partial,
+                     cudaStream_t st)
 {
     CPCP_COUNT_LAUNCH();
-    fwt_coef_kernel<T><<<FWT_BLOCKS, FWT_NT, 0, st>>>(m, n, Q, ldq, L, S, G, ld, u, ldu, v, ldv, T(cL), istar, T(vs),
-                                                      partial);
+    fwt_coef_kernel<T><<<FWT_BLOCKS, FWT_NT, 0, st>>>(m, n, Q, ldq, L, S, G, ld, u, ldu, v, ldv, sc, partial);
 }
 
 template <typename T>
 void launch_fwt_update(int m, int n, const T *D, int64_t ldd, const uint32_t *Q, int64_t ldq, T *L, T *S, T *G,
-                       int64_t ld, const T *u, int64_t ldu, const T *v, int64_t ldv, double cL, int64_t istar,
-                       double vs, double a, double b, double lamS, double *partial, double *amax_v, int64_t *amax_i,
-                       cudaStream_t st)
+                       int64_t ld, const T *u, int64_t ldu, const T *v, int64_t ldv, const FwScal *sc,
+                       double *partial, double *amax_v, int64_t *amax_i, cudaStream_t st)
 {
     CPCP_COUNT_LAUNCH();
-    fwt_update_kernel<T><<<FWT_BLOCKS, FWT_NT, 0, st>>>(m, n, D, ldd, Q, ldq, L, S, G, ld, u, ldu, v, ldv, T(cL),
-                                                        istar, T(vs), T(a), T(b), T(lamS), partial, amax_v, amax_i);
+    fwt_update_kernel<T><<<FWT_BLOCKS, FWT_NT, 0, st>>>(m, n, D, ldd, Q, ldq, L, S, G, ld, u, ldu, v, ldv, sc, partial,
+                                                        amax_v, amax_i);
 }
 
 #define INST(T)                                                                                                      \
     template void launch_fwt_grad<T>(int, int, const T *, int64_t, const uint32_t *, int64_t, const T *, const T *,  \
                                      int64_t, T *, double *, double *, int64_t *, cudaStream_t);                     \
     template void launch_fwt_coef<T>(int, int, const uint32_t *, int64_t, const T *, const T *, const T *, int64_t,  \
-                                     const T *, int64_t, const T *, int64_t, double, int64_t, double, double *,      \
-                                     cudaStream_t);                                                                  \
+                                     const T *, int64_t, const T *, int64_t, const FwScal *, double *, cudaStream_t); \
     template void launch_fwt_update<T>(int, int, const T *, int64_t, const uint32_t *, int64_t, T *, T *, T *,       \
-                                       int64_t, const T *, int64_t, const T *, int64_t, double, int64_t, double,     \
-                                       double, double, double, double *, double *, int64_t *, cudaStream_t);
+                                       int64_t, const T *, int64_t, const T *, int64_t, const FwScal *, double *,    \
+                                       double *, int64_t *, cudaStream_t);                                           \
+    template void launch_fwt_lmo<T>(FwScal *, const T *, const T *, int64_t, int, int, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -110,7 +110,7 @@ __device__ __forceinline__ T chol_gram_entry(const T *__restrict__ partial, int 
     return (s0 + s1) + (s2 + s3);
 }
 
-template <typename T, int RG, int RA, int CB>
+template <typename T, int RG, int RA, int CB, int NT = CHOL_NT>
 __device__ __forceinline__ void chol_body(const T *__restrict__ partial, int splits, int kmax, int k,
                                           T *__restrict__ R, T *__restrict__ Rinv, const T *__restrict__ Rprev,
                                           T *__restrict__ Rtot, int ldr, int *well_out, T *sm, double *red)
@@ -127,7 +127,7 @@ __device__ __forceinline__ void chol_body(const T *__restrict__ partial, int spl
     const int64_t slice = (int64_t)kmax * kmax;
     const T tol = eps_of<T>() * eps_of<T>();
 
-    for (int c = tid; c < k; c += CHOL_NT) {
+    for (int c = tid; c < k; c += NT) {
         const T g = chol_gram_entry(partial, splits, slice, kmax, c, c);
         d[c] = (g > T(0) && isfinite(g)) ? sqrt(g) : T(0);
     }
@@ -165,7 +165,7 @@ __device__ __forceinline__ void chol_body(const T *__restrict__ partial, int spl
     __syncthreads();
     if (tid == 0 && well_out != nullptr) {
         double tot = 0.0;
-        for (int q = 0; q < CHOL_NT / 32; q++) tot += red[q];
+        for (int q = 0; q < NT / 32; q++) tot += red[q];
         *well_out = tot <= 0.25 ? 1 : 0;
     }
 
@@ -268,12 +268,12 @@ __device__ __forceinline__ void chol_body(const T *__restrict__ partial, int spl
         }
     }
     if (Rprev == nullptr) return;
-    for (int idx = tid; idx < k * k; idx += CHOL_NT) {
+    for (int idx = tid; idx < k * k; idx += NT) {
         const int i = idx / k, c = idx - (idx / k) * k;
         Ps[i * ld + c] = Rprev[(int64_t)i * ldr + c];
     }
     __syncthreads();
-    for (int idx = tid; idx < k * k; idx += CHOL_NT) {
+    for (int idx = tid; idx < k * k; idx += NT) {
         const int x = idx / k, y = idx - (idx / k) * k;
         if (y < x) continue;
         T s = T(0);
@@ -282,18 +282,18 @@ __device__ __forceinline__ void chol_body(const T *__restrict__ partial, int spl
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(CHOL_NT, 1) chol_kernel(const T *__restrict__ partial, int splits, int kmax,
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, 1) chol_kernel(const T *__restrict__ partial, int splits, int kmax,
                                                        const int *kdyn, T *__restrict__ R, T *__restrict__ Rinv,
                                                        const T *__restrict__ Rprev, T *__restrict__ Rtot, int ldr,
                                                        int *well_out, const int *skip_in, int *stats)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ double red[CHOL_NT / 32];
+    __shared__ double red[NT / 32];
     const int k = *kdyn;
     const int tid = threadIdx.x;
     if (skip_in != nullptr && *skip_in) {
-        for (int idx = tid; idx < k * k; idx += CHOL_NT) {
+        for (int idx = tid; idx < k * k; idx += NT) {
             int i = idx / k, c = idx % k;
             R[(int64_t)i * ldr + c] = (i == c) ? T(1) : T(0);
             Rinv[(int64_t)i * ldr + c] = (i == c) ? T(1) : T(0);
@@ -306,10 +306,19 @@ __global__ void __launch_bounds__(CHOL_NT, 1) chol_kernel(const T *__restrict__ 
     // 16 warps x rows per warp x columns per lane: 4 x 2 covers k <= 64, 8 x 4
     // covers k <= 128.  (With 4 warps and 32 positions per thread a step took
     // three times as long: the step is latency-bound, and more warps hide it.)
-    if (k <= 64)
-        chol_body<T, 16, 4, 2>(partial, splits, kmax, k, R, Rinv, Rprev, Rtot, ldr, well_out, sm, red);
-    else
-        chol_body<T, 16, 8, 4>(partial, splits, kmax, k, R, Rinv, Rprev, Rtot, ldr, well_out, sm, red);
+    // NT / 32 warps in the elimination: 512 threads with 8 positions each, or
+    // 1024 threads with 4 (k <= 64) or 16 (k <= 128) positions each
+    if constexpr (NT == 1024) {
+        if (k <= 64)
+            chol_body<T, 32, 2, 2, NT>(partial, splits, kmax, k, R, Rinv, Rprev, Rtot, ldr, well_out, sm, red);
+        else
+            chol_body<T, 32, 4, 4, NT>(partial, splits, kmax, k, R, Rinv, Rprev, Rtot, ldr, well_out, sm, red);
+    } else {
+        if (k <= 64)
+            chol_body<T, 16, 4, 2, NT>(partial, splits, kmax, k, R, Rinv, Rprev, Rtot, ldr, well_out, sm, red);
+        else
+            chol_body<T, 16, 8, 4, NT>(partial, splits, kmax, k, R, Rinv, Rprev, Rtot, ldr, well_out, sm, red);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -550,17 +559,17 @@ constexpr int JAC_NT = 512;
 
 __host__ __device__ constexpr int jac_ld(int k) { return (k + 31) / 32 * 32 + 8; }
 
-// Eight consecutive lanes share one column pair (64 pairs per round at most,
+// TPP consecutive lanes share one column pair (16 lanes for k <= 64, so the
+// 32 pairs of a round fill the 512 threads; 8 lanes and up to 64 pairs for
 // k <= 128); each lane keeps its EL elements of the two columns in registers
 // between the dot product and the rotation.
-template <typename T, int EL>
+template <typename T, int EL, int TPP>
 __device__ __forceinline__ void jacobi_body(const T *__restrict__ Rz, int ldr, int k, T *__restrict__ Ut,
                                             T *__restrict__ Wt, T *__restrict__ sig, const Ctrl *ctrl, int *stats,
                                             T *__restrict__ Us, Ctrl *svt, T *sm, T *wmax, T *amax_p)
 {
-    constexpr int TPP = 8;
-    // columns 8 banks apart (ld = 8 mod 32): the four pairs a warp serves
-    // read 32 distinct banks
+    // columns 8 banks apart (ld = 8 mod 32): with 8 lanes per pair the four
+    // pairs a warp serves read 32 distinct banks
     const int ld = jac_ld(k);
     const int N = k + (k & 1);
     T *X = sm;          // X[c * ld + i]: column c of C
@@ -570,7 +579,7 @@ __device__ __forceinline__ void jacobi_body(const T *__restrict__ Rz, int ldr, i
     const int tid = threadIdx.x, nt = JAC_NT, lane = tid & 31, warp = tid >> 5;
     const T th2 = ctrl != nullptr ? T(ctrl->theta_L) * T(ctrl->theta_L) : T(-1);
     const int slot = tid / TPP, sub = tid % TPP, nslot = JAC_NT / TPP;
-    const unsigned gmask = 0xFFu << (lane & ~(TPP - 1));
+    const unsigned gmask = TPP == 32 ? 0xffffffffu : (((1u << TPP) - 1u) << (lane & ~(TPP - 1)));
 
     for (int idx = tid; idx < k * k; idx += nt) {
         int c = idx / k, i = idx % k;
@@ -580,7 +589,7 @@ __device__ __forceinline__ void jacobi_body(const T *__restrict__ Rz, int ldr, i
     __syncthreads();
 
     // a pair is rotated when |x_p . x_q| exceeds the rounding bound of the
-    // group dot product (k/8 terms per lane in two chains + a 3-level tree)
+    // group dot product (k/TPP terms per lane in two chains + a shuffle tree)
     const T tol = T(2) * T((k + TPP - 1) / TPP + 4) * eps_of<T>();
     // columns whose norm is below the rounding noise of the largest one carry
     // no information; rotating them against large columns only moves noise
@@ -768,10 +777,11 @@ __global__ void __launch_bounds__(JAC_NT) jacobi_kernel(const T *__restrict__ Rz
     __shared__ T amax;
     const int k = *kdyn;
     T *sm = reinterpret_cast<T *>(smraw);
+    // k <= 64: 16 lanes per column pair (32 pairs fill the 512 threads); else 8
     if (k <= 64)
-        jacobi_body<T, 8>(Rz, ldr, k, Ut, Wt, sig, ctrl, stats, Us, svt, sm, wmax, &amax);
+        jacobi_body<T, 4, 16>(Rz, ldr, k, Ut, Wt, sig, ctrl, stats, Us, svt, sm, wmax, &amax);
     else
-        jacobi_body<T, 16>(Rz, ldr, k, Ut, Wt, sig, ctrl, stats, Us, svt, sm, wmax, &amax);
+        jacobi_body<T, 16, 8>(Rz, ldr, k, Ut, Wt, sig, ctrl, stats, Us, svt, sm, wmax, &amax);
 }
 
 // ---------------------------------------------------------------------------
@@ -890,6 +900,14 @@ __global__ void ctrl_end_kernel(Ctrl *c)
     c->eta_k *= c->eta;
 }
 
+// threads of the Cholesky kernel: fp32 1024 (more warps hide the latency of
+// each elimination step), fp64 512 (register budget)
+template <typename T>
+constexpr int chol_nt()
+{
+    return sizeof(T) == 4 ? 1024 : 512;
+}
+
 template <typename T>
 size_t chol_smem(int kmax)
 {
@@ -908,7 +926,7 @@ void ensure_small_attrs()
 {
     static bool done = false;
     if (done) return;
-    cudaFuncSetAttribute(chol_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(chol_kernel<T, chol_nt<T>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)chol_smem<T>(small_kmax<T>()));
     cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)jacobi_smem<T>(small_kmax<T>()));
@@ -923,7 +941,8 @@ void launch_chol(const T *partialG, int splits, int kmax, const int *kdyn, T *R,
 {
     ensure_small_attrs<T>();
     CPCP_COUNT_LAUNCH();
-    chol_kernel<T><<<1, CHOL_NT, chol_smem<T>(kmax), st>>>(partialG, splits, kmax, kdyn, R, Rinv, Rprev, Rtot, ldr,
+    chol_kernel<T, chol_nt<T>()><<<1, chol_nt<T>(), chol_smem<T>(kmax), st>>>(partialG, splits, kmax, kdyn, R, Rinv,
+                                                                            Rprev, Rtot, ldr,
                                                           well_out, skip_in, stats);
 }
 

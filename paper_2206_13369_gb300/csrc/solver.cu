@@ -73,12 +73,21 @@ struct PhaseTimer {
         cudaEvent_t a, b;
         int phase;
     };
+    // phases 0-3: CPCP_PHASE_*; with profile >= 2 also the SVT phase of the
+    // iterations split into 4: products with M, 5: CholeskyQR, 6: core Jacobi SVD,
+    // 7: factor products and the next start block (DETAIL_* below)
+    static constexpr int NPH = 8;
     std::vector<cudaEvent_t> pool;
     std::vector<Pair> pending;
-    double ms[CPCP_NUM_PHASES] = {0, 0, 0, 0};
-    int count[CPCP_NUM_PHASES] = {0, 0, 0, 0};
+    double ms[NPH] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int count[NPH] = {0, 0, 0, 0, 0, 0, 0, 0};
     bool on = false;
+    bool detail = false;   // profile >= 2
+    bool in_iter = false;  // inside an iteration's SVT phase (not a residual check)
     cudaStream_t st = nullptr;
+
+    // a sub-interval of an iteration's SVT phase (profile >= 2 only)
+    int open_sub(int phase) { return (detail && in_iter) ? open(phase) : -1; }
 
     cudaEvent_t take()
     {
@@ -118,14 +127,16 @@ struct PhaseTimer {
         }
         pending.clear();
     }
-    void reset(bool enable, cudaStream_t s)
+    void reset(bool enable, cudaStream_t s, bool sub = false)
     {
         harvest();
-        for (int i = 0; i < CPCP_NUM_PHASES; i++) {
+        for (int i = 0; i < NPH; i++) {
             ms[i] = 0;
             count[i] = 0;
         }
         on = enable;
+        detail = enable && sub;
+        in_iter = false;
         st = s;
     }
     ~PhaseTimer()
@@ -156,6 +167,8 @@ struct cpcp_context {
 };
 
 namespace {
+
+enum { DETAIL_PROD_M = 4, DETAIL_CHOLQR = 5, DETAIL_JACOBI = 6, DETAIL_FACTORS = 7 };
 
 struct CpcpError {
     cpcp_status st;
@@ -579,7 +592,18 @@ int prod_gram(SvdWork<T> &w, int rows, const T *X, const int *kdyn, const int *s
 // found X nearly orthogonal after column equilibration (the warm-started
 // steady state), since it would then leave Q unchanged to rounding.
 template <typename T>
+void orth_impl(cpcp_context *h, SvdWork<T> &w, int rows, const T *X, T *Q, T *Rout, const int *kdyn, int slot);
+
+template <typename T>
 void orth(cpcp_context *h, SvdWork<T> &w, int rows, const T *X, T *Q, T *Rout, const int *kdyn, int slot)
+{
+    const int tq = h->timer.open_sub(DETAIL_CHOLQR);
+    orth_impl<T>(h, w, rows, X, Q, Rout, kdyn, slot);
+    h->timer.close(tq);
+}
+
+template <typename T>
+void orth_impl(cpcp_context *h, SvdWork<T> &w, int rows, const T *X, T *Q, T *Rout, const int *kdyn, int slot)
 {
     cudaStream_t st = h->stream;
     const int KM = w.KM;
@@ -613,22 +637,30 @@ void subspace_svd_bf16(cpcp_context *h, SvdWork<float> &w, int m, int nc, const 
     cudaStream_t st = h->stream;
     const int KM = w.KM, NB = round16(KM);
     const int mp = umma_pad_rows(m), ncp = umma_pad_rows(nc), kpm = umma_pad_k(m), kpn = umma_pad_k(nc);
+    int tp = h->timer.open_sub(DETAIL_PROD_M);
     launch_bf16_pair(m, nc, Mx, ldx, w.Mb, mp, kpn, w.Mt, ncp, kpm, st);
+    h->timer.close(tp);
     const float *Om = Omega;
     for (int s = 0; s < q; s++) {
+        tp = h->timer.open_sub(DETAIL_PROD_M);
         launch_bf16_pair(nc, KM, Om, KM, nullptr, 0, 0, w.Bt, NB, kpn, st);
         int sp = launch_umma_tn(m, mp, kpn, w.Mb, kpn, w.Bt, NB, kpn, NB, kdyn, w.Ypart, KM, 16, w.err, st);
         if (sp < 0) throw CpcpError{CPCP_ERR_CUDA, "could not encode the TMA tensor maps"};
         launch_reduce_partial<float>(w.Ypart, sp, m, KM, w.Y, KM, nullptr, kdyn, st);
+        h->timer.close(tp);
         orth<float>(h, w, m, w.Y, w.Qy, nullptr, kdyn, 0);
+        tp = h->timer.open_sub(DETAIL_PROD_M);
         launch_bf16_pair(m, KM, w.Qy, KM, nullptr, 0, 0, w.Bt, NB, kpm, st);
         sp = launch_umma_tn(nc, ncp, kpm, w.Mt, kpm, w.Bt, NB, kpm, NB, kdyn, w.Zpart, KM, 64, w.err, st);
         if (sp < 0) throw CpcpError{CPCP_ERR_CUDA, "could not encode the TMA tensor maps"};
         launch_reduce_partial<float>(w.Zpart, sp, nc, KM, w.Z, KM, nullptr, kdyn, st);
+        h->timer.close(tp);
         orth<float>(h, w, nc, w.Z, w.Qz, w.Rz, kdyn, 1);
         Om = w.Qz;
     }
+    const int tj = h->timer.open_sub(DETAIL_JACOBI);
     launch_jacobi<float>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st, w.stats, Us, svt);
+    h->timer.close(tj);
 }
 
 // Rank-k SVD of Mx (m x nc, ld ldx): q range passes from Omega (nc x k).
@@ -652,13 +684,19 @@ void subspace_svd(cpcp_context *h, SvdWork<T> &w, int m, int nc, const T *Mx, in
     const int KM = w.KM;
     const T *Om = Omega;
     for (int s = 0; s < q; s++) {
+        int tp = h->timer.open_sub(DETAIL_PROD_M);
         prod_y<T>(w, m, nc, Mx, ldx, Om, kdyn, st);
+        h->timer.close(tp);
         orth<T>(h, w, m, w.Y, w.Qy, nullptr, kdyn, 0);
+        tp = h->timer.open_sub(DETAIL_PROD_M);
         prod_z<T>(w, m, nc, Mx, ldx, w.Qy, KM, kdyn, st);
+        h->timer.close(tp);
         orth<T>(h, w, nc, w.Z, w.Qz, w.Rz, kdyn, 1);
         Om = w.Qz;
     }
+    const int tj = h->timer.open_sub(DETAIL_JACOBI);
     launch_jacobi<T>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st, w.stats, Us, svt);
+    h->timer.close(tj);
 }
 
 template <typename T>
@@ -679,7 +717,7 @@ int kmax_small<double>()
 // ---------------------------------------------------------------------------
 
 struct Opts {
-    int max_iter, check_every, k_max, p, q, qc, start_level, precision, half, tc_pass, graphs, transfer;
+    int max_iter, check_every, k_max, p, q, qc, start_level, precision, tc_pass, graphs, transfer;
     bool early_test;
     double eta, mu0, ratio, refine_at;
     uint64_t seed;
@@ -699,7 +737,6 @@ Opts resolve(const cpcp_options &o)
     r.qc = o.check_power_iters > 0 ? o.check_power_iters : 2;
     r.start_level = o.start_level;
     r.precision = o.precision;
-    r.half = o.subspace_mode == 1;
     r.tc_pass = o.pass_simt == 0;
     r.graphs = o.plain_launches == 0;
     r.transfer = o.transfer;
@@ -730,7 +767,6 @@ struct SolveState {
     bool orth = false;
     std::vector<OrthTransfer<T>> ot;
     T *Vp = nullptr;
-    int side;   // half-step mode: warm subspace of the next iteration, 0 = right (Om), 1 = left (A[cur])
     std::vector<TransferDev<T>> tr;
 };
 
@@ -878,44 +914,10 @@ void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, 
     }
     if (part == 1) return;
     const int ts = part == 0 ? h->timer.open(CPCP_PHASE_SVT) : -1;
-    if (o.half && !s.bf16) {
-        // Half-step subspace iteration: one projection per iteration onto the
-        // previous iteration's right (V) or left (U) singular subspace,
-        // alternating; at a fixed point it is the power method on M, so the
-        // SVT it converges to is exact.  Either way L = A B^T keeps only the
-        // singular values above theta.
-        const int *kd = &s.ctrl->k;
-        const int KM = w.KM;
-        if (s.side == 0) {
-            // Y = M V = Qy Rz, Rz^T = Ut diag(sig) Wt^T: M ~ (Qy Wt) diag(sig) (V Ut)^T
-            prod_y<T>(w, s.m, tr.nh, Mx, ldx, s.Om, kd, st);
-            orth<T>(h, w, s.m, w.Y, w.Qy, w.Rz, kd, 0);
-            launch_jacobi<T>(w.Rz, KM, kd, w.Ut, w.Wt, w.sig, w.kcap, s.ctrl, st, w.stats);
-            launch_svt_small<T>(w.Ut, w.sig, KM, s.ctrl, w.Us, nullptr, st);
-            // A = Qy Wt (unscaled: it is also the next warm left subspace), B = R (V Ut diag(sig - theta))
-            prod_nn_small<T>(s.m, w.Qy, KM, w.Wt, KM, s.A[nxt], s.KM, kd, KM, st);
-            prod_nn_small<T>(tr.nh, s.Om, KM, w.Us, KM, w.Z, KM, kd, KM, st);
-            launch_fill_random<T>(s.A[nxt], s.KM, s.m, s.ctrl, 0, w.sig, s.KM, 0x57EAull, st);
-            launch_prolong<T>(s.n, w.Z, KM, s.B[nxt], s.KM, tr, &s.ctrl->r_new, s.KM, st);
-            s.side = 1;
-        } else {
-            // Z = M^T U = Qz Rz, Rz^T = Ut diag(sig) Wt^T: M ~ (U Ut) diag(sig) (Qz Wt)^T
-            prod_z<T>(w, s.m, tr.nh, Mx, ldx, s.A[cur], s.KM, kd, st);
-            orth<T>(h, w, tr.nh, w.Z, w.Qz, w.Rz, kd, 1);
-            launch_jacobi<T>(w.Rz, KM, kd, w.Ut, w.Wt, w.sig, w.kcap, s.ctrl, st, w.stats);
-            launch_svt_small<T>(w.Ut, w.sig, KM, s.ctrl, w.Us, nullptr, st);
-            // A = U Ut diag(sig - theta), V = Qz Wt (unscaled: the next warm right subspace), B = R V
-            prod_nn_small<T>(s.m, s.A[cur], s.KM, w.Us, KM, s.A[nxt], s.KM, kd, KM, st);
-            prod_nn_small<T>(tr.nh, w.Qz, KM, w.Wt, KM, s.Om, s.KM, kd, KM, st);
-            launch_fill_random<T>(s.Om, s.KM, tr.nh, s.ctrl, 0, w.sig, s.KM, 0x57E9ull, st);
-            launch_prolong<T>(s.n, s.Om, s.KM, s.B[nxt], s.KM, tr, &s.ctrl->r_new, s.KM, st);
-            s.side = 0;
-        }
-        h->timer.close(ts);
-        launch_ctrl_end(s.ctrl, st);
-        return;
-    }
+    h->timer.in_iter = true;
     subspace_svd<T>(h, w, s.m, tr.nh, Mx, ldx, s.Om, o.q, &s.ctrl->k, s.ctrl, s.bf16, w.Us, s.ctrl);
+    const int tf = h->timer.open_sub(DETAIL_FACTORS);
+    h->timer.in_iter = false;
     // new factors into the "previous" slot (its old content was consumed above)
     prod_nn_small<T>(s.m, w.Qy, w.KM, w.Us, w.KM, s.A[nxt], s.KM, &s.ctrl->k, w.KM, st);
     prod_nn_small<T>(tr.nh, w.Qz, w.KM, w.Wt, w.KM, s.Om, s.KM, &s.ctrl->k, w.KM, st);
@@ -928,6 +930,7 @@ void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, 
     } else {
         launch_fill_prolong<T>(s.Om, s.KM, tr.nh, s.ctrl, w.sig, s.KM, 0x57E9ull, s.n, s.B[nxt], s.KM, tr, st);
     }
+    h->timer.close(tf);
     h->timer.close(ts);
     launch_ctrl_end(s.ctrl, st);
 }
@@ -968,13 +971,12 @@ struct IterGraph {
 };
 
 struct IterGraphs {
-    IterGraph g[8][2][2];  // level, buffer parity, half-step side
+    IterGraph g[8][2];  // level, buffer parity
     ~IterGraphs()
     {
         for (auto &row : g)
-            for (auto &pair : row)
-                for (auto &x : pair)
-                    if (x.exec) cudaGraphExecDestroy(x.exec);
+            for (auto &x : row)
+                if (x.exec) cudaGraphExecDestroy(x.exec);
     }
 };
 
@@ -989,11 +991,12 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     // (captured the second time the same level and buffer parity come up,
     // once every workspace buffer exists); the kernels read the iteration's
     // scalars (weights, widths, ranks) from the device control block
-    const bool use_graphs = o.graphs;
+    // (profile >= 2 times kernel families inside the iteration: plain launches)
+    const bool use_graphs = o.graphs && h->opt.profile < 2;
     PrivateStream ps(h, use_graphs);
     cudaStream_t st = h->stream;
     const int H = levels - 1;
-    h->timer.reset(h->opt.profile != 0, st);
+    h->timer.reset(h->opt.profile != 0, st, h->opt.profile >= 2);
     const unsigned long long launches0 = g_kernel_launches;
     SolveState<T> s;
     s.m = m;
@@ -1021,7 +1024,6 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     s.orth = H > 0 && o.transfer == 1;
     s.ot.clear();
     if (s.orth) {
-        if (o.half) throw CpcpError{CPCP_ERR_INVALID_ARG, "transfer = 1 is not available with subspace_mode = 1"};
         s.ot.emplace_back();  // level 0: no transfer
         for (int lv = 1; lv <= H; lv++) s.ot.push_back(upload_orth<T>(h, n, lv, "solve_o" + std::to_string(lv)));
         s.Vp = wsT<T>(h, "Vp", (size_t)nh1 * s.KM);
@@ -1040,7 +1042,6 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     w.stats = wf.stats = wsT<int>(h, "svd_stats", 4);
     CK(cudaMemsetAsync(w.stats, 0, sizeof(int) * 4, st));
     s.bf16 = o.precision == 1;
-    s.side = 0;
     if (s.bf16) {
         svd_work_bf16<T>(h, w, "it_", m, n);
         CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
@@ -1128,10 +1129,7 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
             // profile's events bracket the pass); the rest of the iteration is
             // the graph
             one_iteration<T>(h, s, w, level, cur, o, false, 1);
-            // the half-step mode alternates its projection side (host state that
-            // part 2 flips): one graph per side
-            const int side0 = s.side;
-            IterGraph &G = graphs.g[level][cur][o.half ? side0 : 0];
+            IterGraph &G = graphs.g[level][cur];
             if (G.exec == nullptr && G.seen) {
                 const unsigned long long l0 = g_kernel_launches;
                 CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -1150,13 +1148,11 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
                 CK(ie);
                 G.launches = g_kernel_launches - l0;
                 g_kernel_launches = l0;
-                s.side = side0;  // the capture did not run the iteration
             }
             const int ts = h->timer.open(CPCP_PHASE_SVT);
             if (G.exec != nullptr) {
                 CK(cudaGraphLaunch(G.exec, st));
                 g_kernel_launches += G.launches;
-                if (o.half) s.side = side0 ^ 1;
             } else {
                 G.seen = true;
                 one_iteration<T>(h, s, w, level, cur, o, false, 2);
@@ -1229,7 +1225,6 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
             CK(cudaMemcpyAsync(ctmp, &tmp, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
             launch_fill_random<T>(s.Om, s.KM, s.tr[level].nh, ctmp, 0, nullptr, s.KM, 0x77ull + level, st);
             CK(cudaStreamSynchronize(st));
-            s.side = 0;  // the warm subspace is the restricted right factor
         }
     }
     inf.iters = iter;
@@ -1272,6 +1267,7 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     for (int i = 0; i < CPCP_NUM_PHASES; i++) {
         inf.phase_ms[i] = h->timer.ms[i];
         inf.phase_count[i] = h->timer.count[i];
+        inf.svt_detail_ms[i] = h->timer.ms[DETAIL_PROD_M + i];
     }
     if (info) *info = inf;
     return status;
@@ -1475,41 +1471,14 @@ cpcp_status ialm_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, do
     return status;
 }
 
-// Exact minimiser over [0,1]^2 of 1/2 (A a^2 + 2 C a b + B b^2) + ga a + gb b
-// (convex: A, B >= 0, A B >= C^2): the stationary point if it lies in the box,
-// else the best of the four edge minimisers.  The two-segment line search of
-// Alg. 3.
-void fw_box_qp(double A, double B, double C, double ga, double gb, double *a_out, double *b_out)
-{
-    auto q = [&](double a, double b) { return 0.5 * (A * a * a + 2.0 * C * a * b + B * b * b) + ga * a + gb * b; };
-    auto c01 = [](double x) { return std::min(1.0, std::max(0.0, x)); };
-    double best_a = 0.0, best_b = 0.0, best = q(0.0, 0.0);
-    auto consider = [&](double a, double b) {
-        const double v = q(a, b);
-        if (v < best) {
-            best = v;
-            best_a = a;
-            best_b = b;
-        }
-    };
-    const double det = A * B - C * C;
-    if (det > 0.0) {
-        const double a = (C * gb - B * ga) / det, b = (C * ga - A * gb) / det;
-        if (a >= 0.0 && a <= 1.0 && b >= 0.0 && b <= 1.0) consider(a, b);
-    }
-    for (double e : {0.0, 1.0}) {
-        const double lb = gb + C * e, la = ga + C * e;
-        consider(e, B > 0.0 ? c01(-lb / B) : (lb < 0.0 ? 1.0 : 0.0));
-        consider(A > 0.0 ? c01(-la / A) : (la < 0.0 ? 1.0 : 0.0), e);
-    }
-    *a_out = best_a;
-    *b_out = best_b;
-}
-
 // FW-T (Alg. 3) / ML-FWT (Alg. 6) for eq. (cpcp) on device buffers; see
-// cpcp_fwt.  Scalars (t_L, t_S, U_L, U_S, the line search) on the host; the
-// m x n passes in k_fwt.cu; the top singular pair of G (or of G R) from the
-// warm-started subspace SVD of the CPCP path.
+// cpcp_fwt.  The m x n passes and the scalars (t_L, t_S, U_L, U_S, the LMOs'
+// vertices, the line search, the stop test) in k_fwt.cu, in device memory
+// (FwScal); the top singular pair of G (or of G R) from the warm-started
+// subspace SVD of the CPCP path.  An iteration is a fixed sequence of launches
+// with no host round trip: it is captured once as a CUDA graph and replayed,
+// and the host reads the stop state every check_every iterations (kernels of
+// iterations after the stop return at once).
 template <typename T>
 cpcp_status fwt_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, const uint32_t *Q, int64_t ldq,
                      double lam, double mu, int levels, int max_iter, double tol, T *L_out, int64_t ldl, T *S_out,
@@ -1517,8 +1486,11 @@ cpcp_status fwt_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, con
 {
     auto t0 = std::chrono::steady_clock::now();
     const unsigned long long launches0 = g_kernel_launches;
-    cudaStream_t st = h->stream;
     const Opts o = resolve(h->opt);
+    // graph replay runs on the handle's private stream (the caller's may be the
+    // legacy default stream, which cannot be captured)
+    PrivateStream ps(h, o.graphs);
+    cudaStream_t st = h->stream;
     const int H = levels - 1;
     const int64_t ld = round4(n);
     TransferDev<T> tr = upload_transfer<T>(h, n, H, "fwt");
@@ -1544,8 +1516,18 @@ cpcp_status fwt_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, con
         ot = upload_orth<T>(h, n, H, "fw");
         Vp = wsT<T>(h, "fw_Vp", (size_t)nh * KM);
     }
-    std::vector<double> hp((size_t)nb * 5), hv(nb);
-    std::vector<int64_t> hi(nb);
+    FwScal *sc = wsT<FwScal>(h, "fw_scal", 1);
+    double *trace = wsT<double>(h, "fw_trace", (size_t)max_iter);
+    const double lamL = mu, lamS = lam * mu;
+    {
+        FwScal s0;
+        memset(&s0, 0, sizeof(s0));
+        s0.lamL = lamL;
+        s0.lamS = lamS;
+        s0.tol = tol;
+        s0.margin = sizeof(T) == 4 ? 1e-5 : 1e-12;
+        CK(cudaMemcpyAsync(sc, &s0, sizeof(FwScal), cudaMemcpyHostToDevice, st));
+    }
 
     Ctrl c0;
     memset(&c0, 0, sizeof(c0));
@@ -1558,46 +1540,12 @@ cpcp_status fwt_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, con
     CK(cudaMemsetAsync(L, 0, sizeof(T) * mn, st));
     CK(cudaMemsetAsync(S, 0, sizeof(T) * mn, st));
     launch_fill_random<T>(Om, KM, nh, ctrl, 1, nullptr, KM, 0xF3A1ull, st);
-    // sums of the per-block partials (fixed order) and the argmax of |G|
-    auto fetch = [&](int ns, bool am) {
-        CK(cudaMemcpyAsync(hp.data(), partial, sizeof(double) * nb * ns, cudaMemcpyDeviceToHost, st));
-        if (am) {
-            CK(cudaMemcpyAsync(hv.data(), amv, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
-            CK(cudaMemcpyAsync(hi.data(), ami, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost, st));
-        }
-        CK(cudaStreamSynchronize(st));
-    };
-    auto psum = [&](int ns, int q) {
-        double t = 0.0;
-        for (int b = 0; b < nb; b++) t += hp[(size_t)b * ns + q];
-        return t;
-    };
-    auto pmax = [&](double &gmax, int64_t &istar) {
-        gmax = -1.0;
-        istar = INT64_MAX;
-        for (int b = 0; b < nb; b++)
-            if (hv[b] > gmax || (hv[b] == gmax && hi[b] < istar)) {
-                gmax = hv[b];
-                istar = hi[b];
-            }
-    };
     launch_fwt_grad<T>(m, n, D, ldd, Q, ldq, L, S, ld, G, partial, amv, ami, st);
-    fetch(1, true);
-    double f = 0.5 * psum(1, 0), gmax;
-    int64_t istar;
-    pmax(gmax, istar);
-    const double lamL = mu, lamS = lam * mu;
-    double UL = f / lamL, US = f / lamS, tL = 0.0, tS = 0.0, rel = INFINITY;
-    cpcp_status status = CPCP_ERR_NOT_CONVERGED;
-    int k;
-    for (k = 0; k < max_iter; k++) {
-        const double fprev = f;
-        // no finite entry of G (NaN input): no argmax, nothing to step on
-        if (istar < 0 || istar >= (int64_t)m * n || !std::isfinite(f)) {
-            status = CPCP_ERR_NUMERIC;
-            break;
-        }
-        // LMO of the nuclear ball: top singular pair of G (or of G R, lifted by R)
+    launch_fwt_first(sc, partial, amv, ami, st);
+    // one iteration: the LMO of the nuclear ball (top singular pair of G, or of
+    // G R lifted by R) and of the l1 ball (from the device argmax), the line
+    // search, the update with the thresholding step, the scalars
+    auto iteration = [&]() {
         const T *Mx = G;
         int64_t ldx = ld;
         if (H > 0) {
@@ -1620,46 +1568,64 @@ cpcp_status fwt_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, con
             launch_prolong<T>(n, vsrc, KM, Vf, KM, tr, &ctrl->k, KM, st);
             vv = Vf;
         }
-        T sig_t, gval;
-        CK(cudaMemcpyAsync(&sig_t, w.sig, sizeof(T), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(&gval, G + (istar / n) * ld + (istar % n), sizeof(T), cudaMemcpyDeviceToHost, st));
+        launch_fwt_lmo<T>(sc, w.sig, G, ld, m, n, st);
+        launch_fwt_coef<T>(m, n, Q, ldq, L, S, G, ld, Ub, KM, vv, KM, sc, partial, st);
+        launch_fwt_ls(sc, partial, st);
+        launch_fwt_update<T>(m, n, D, ldd, Q, ldq, L, S, G, ld, Ub, KM, vv, KM, sc, partial, amv, ami, st);
+        launch_fwt_post(sc, partial, amv, ami, trace, st);
+    };
+    // the first iteration launched directly (every workspace buffer then exists),
+    // the rest replayed from a graph of one iteration
+    cudaGraphExec_t gexec = nullptr;
+    unsigned long long glaunches = 0;
+    struct GraphGuard {
+        cudaGraphExec_t &e;
+        ~GraphGuard()
+        {
+            if (e) cudaGraphExecDestroy(e);
+        }
+    } gguard{gexec};
+    const bool graphs = o.graphs;
+    FwScal fin;
+    int launched = 0;
+    const int batch = std::max(1, o.check_every);
+    for (;;) {
+        const int todo = std::min(batch, max_iter - launched);
+        for (int b = 0; b < todo; b++, launched++) {
+            if (launched == 0 || !graphs) {
+                iteration();
+                continue;
+            }
+            if (gexec == nullptr) {
+                const unsigned long long l0 = g_kernel_launches;
+                CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                cudaGraph_t graph = nullptr;
+                try {
+                    iteration();
+                } catch (...) {
+                    cudaStreamEndCapture(st, &graph);
+                    if (graph) cudaGraphDestroy(graph);
+                    cudaGetLastError();
+                    throw;
+                }
+                CK(cudaStreamEndCapture(st, &graph));
+                const cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
+                cudaGraphDestroy(graph);
+                CK(ie);
+                glaunches = g_kernel_launches - l0;
+                g_kernel_launches = l0;
+            }
+            CK(cudaGraphLaunch(gexec, st));
+            g_kernel_launches += glaunches;
+        }
+        CK(cudaMemcpyAsync(&fin, sc, sizeof(FwScal), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        const double sig = (double)sig_t;
-        // after a thresholding step every entry of the support of S has
-        // |G_ij| = lambda_S exactly, the others |G_ij| <= lambda_S: the l1 test
-        // takes a relative margin of a few hundred ulp of T, else rounding decides it
-        const double margin = sizeof(T) == 4 ? 1e-5 : 1e-12;
-        const bool useL = lamL < sig, useS = lamS * (1.0 + margin) < gmax;
-        const double cL = useL ? -UL : 0.0, VtL = useL ? UL : 0.0;
-        const double vs = useS ? -US * ((double)gval > 0.0 ? 1.0 : -1.0) : 0.0, VtS = useS ? US : 0.0;
-        launch_fwt_coef<T>(m, n, Q, ldq, L, S, G, ld, Ub, KM, vv, KM, cL, istar, vs, partial, st);
-        fetch(5, false);
-        const double A = psum(5, 0), B = psum(5, 1), C = psum(5, 2);
-        const double ga = psum(5, 3) + lamL * (VtL - tL), gb = psum(5, 4) + lamS * (VtS - tS);
-        double a, b;
-        fw_box_qp(A, B, C, ga, gb, &a, &b);
-        launch_fwt_update<T>(m, n, D, ldd, Q, ldq, L, S, G, ld, Ub, KM, vv, KM, cL, istar, vs, a, b, lamS, partial,
-                             amv, ami, st);
-        fetch(2, true);
-        tL += a * (VtL - tL);
-        tS = psum(2, 0);
-        f = 0.5 * psum(2, 1) + lamL * tL + lamS * tS;
-        pmax(gmax, istar);
-        UL = f / lamL;
-        US = f / lamS;
-        if (ftrace) ftrace[k] = f;
-        if (!std::isfinite(f)) {
-            status = CPCP_ERR_NUMERIC;
-            k++;
-            break;
-        }
-        rel = std::fabs(fprev - f) / fprev;
-        if (rel <= tol) {
-            status = CPCP_OK;
-            k++;
-            break;
-        }
+        if (fin.done != 0 || launched >= max_iter) break;
     }
+    const int k = fin.iters;
+    const cpcp_status status = fin.done == 1 ? CPCP_OK : (fin.done == 2 ? CPCP_ERR_NUMERIC : CPCP_ERR_NOT_CONVERGED);
+    const double rel = fin.rel, f = fin.f;
+    if (ftrace && k > 0) CK(cudaMemcpyAsync(ftrace, trace, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
     if (L_out)
         CK(cudaMemcpy2DAsync(L_out, sizeof(T) * ldl, L, sizeof(T) * ld, sizeof(T) * n, m, cudaMemcpyDeviceToDevice,
                              st));
@@ -2684,6 +2650,8 @@ cpcp_status cpcp_solve(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D
             throw CpcpError{CPCP_ERR_INVALID_ARG, "coarse width exceeds (m+1)/2 (Assumption 2)"};
         if (h->opt.transfer != 0 && h->opt.transfer != 1)
             throw CpcpError{CPCP_ERR_INVALID_ARG, "transfer must be 0 or 1"};
+        if (h->opt.subspace_mode != 0)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "subspace_mode must be 0"};
         if (h->opt.early_test < -1 || h->opt.early_test > 1)
             throw CpcpError{CPCP_ERR_INVALID_ARG, "early_test must be -1, 0 or 1"};
         if (h->opt.unroll > 0) {
