@@ -497,6 +497,8 @@ def extras(device, stream, flush) -> dict:
     out["batched"] = {"workload": "batched-256-cpcp-fp32", "unit": "s", "s": t, "instances_per_s": 256 / t,
                       "status": st, "iters_mean": statistics.mean(its), "iters_max": max(its),
                       "elements": int(sum(q["D"].size for q in ps)), "gpu_launches": int(infos[0]["launches"]),
+                      "autotuned": {"threads": infos[0]["batch_threads"],
+                                    "wide_tile": ["64x64", "128x64"][infos[0]["batch_tile"]]},
                       "err_vs_oracle_smallest3": errs}
     del Lb, Sb
     del probs
@@ -558,7 +560,41 @@ def extras(device, stream, flush) -> dict:
     out["ml_ialm_video"] = {"workload": "video-19200x400-r5-pcp-15-iterations", "unit": "s", **ml}
     del D, L
     out["fwt_cpcp"] = extra_fwt(device, stream, flush)
+    out["fwt_table2"] = extra_fwt_table2(device, stream, flush)
     return out
+
+
+def extra_fwt_table2(device, stream, flush) -> dict:
+    """FW-T (Alg. 3) vs ML-FWT (Alg. 6, 3 levels; R scaled to unit norm, and
+    the orthonormal basis of its range) at the shapes of the paper's synthetic
+    CPCP comparison (10000 x 500 and 10000 x 5000, rank 2), fp32, to the
+    paper's stopping rule (relative decrease of the objective below 1e-3), with
+    the objective reached and the time per iteration over 200 iterations.  The paper gives neither its weights nor its mask: planted recipe
+    with 10% corruptions U[-5, 5], mask Bernoulli(0.8), lambda = 1/sqrt(max(m, n)),
+    mu = 0.05 ||P_Q D||_2."""
+    import torch
+    from paper_2206_13369_gb300 import cpcp, workloads
+    res = {}
+    for (m, n) in ((10000, 500), (10000, 5000)):
+        q = workloads.planted_cpcp_fw(m, n, 2, 0.10, 0.8, seed=7000 + n)
+        D = torch.as_tensor(q["D"]).cuda()
+        Qb = torch.as_tensor(cpcp.pack_mask(q["mask"])).cuda()
+        row = {}
+        for name, lv, tr in (("fwt", 1, 0), ("ml_fwt_3lv", 3, 0), ("ml_fwt_3lv_orth", 3, 1)):
+            with cpcp.Handle(device, stream=stream, transfer=tr) as hh:
+                hh.fwt(D, Qb, q["lam"], q["mu"], levels=lv, max_iter=2000, tol=1e-3)
+                t, (_, _, info) = _events_time(
+                    stream, lambda: hh.fwt(D, Qb, q["lam"], q["mu"], levels=lv, max_iter=2000, tol=1e-3), 3, flush)
+                t200, (_, _, i200) = _events_time(
+                    stream, lambda: hh.fwt(D, Qb, q["lam"], q["mu"], levels=lv, max_iter=200, tol=0.0), 3, flush)
+            row[name] = {"s_to_1e-3": t, "iters_to_1e-3": info["iters"], "status": info["status"],
+                         "f": float(info["f"][-1]) if len(info["f"]) else None,
+                         "ms_per_iter_200": t200 / 200 * 1e3, "f_200": float(i200["f"][-1])}
+        row["ml_over_single_s_to_1e-3"] = row["ml_fwt_3lv"]["s_to_1e-3"] / row["fwt"]["s_to_1e-3"]
+        row["ml_orth_over_single_s_to_1e-3"] = row["ml_fwt_3lv_orth"]["s_to_1e-3"] / row["fwt"]["s_to_1e-3"]
+        res[f"{m}x{n}"] = row
+        del D, Qb
+    return {"workload": "cpcp-rank2-fw-shapes-fp32", "unit": "s", "tol_rel_decrease": 1e-3, **res}
 
 
 def extra_fwt(device, stream, flush) -> dict:

@@ -98,7 +98,10 @@ typedef struct {
     int batch_threads;     /* cpcp_solve_batched: threads per CTA, 256 or 512; 0 = the
                               tuned choice for this batch if one was measured, else 512 */
     int batch_autotune;    /* cpcp_solve_batched: nonzero = on the first call with a new
-                              batch, time every CTA size and keep the fastest */
+                              batch (sizes, levels, masks, tolerance, options), time every
+                              pair of CTA size (256, 512 threads) and output tile of the CTA
+                              products wider than 32 columns (64 x 64, 128 x 64) and keep the
+                              fastest for that batch (info.batch_threads, info.batch_tile) */
     int unroll;            /* K > 0: cpcp_solve runs the differentiable program instead
                               (see cpcp_backward): exactly K steps at the deepest level with
                               an exact SVT, recording checkpoints for the reverse sweep */
@@ -179,6 +182,9 @@ typedef struct {
     int jacobi_sweeps;     /* cpcp_solve: their sweeps, summed */
     int chol_factors;      /* cpcp_solve: Cholesky factorisations of CholeskyQR run (second
                               passes skipped on the device are not counted) */
+    int batch_threads;     /* cpcp_solve_batched: threads per CTA of the launch (256 or 512) */
+    int batch_tile;        /* cpcp_solve_batched: output tiles of the CTA products wider than 32
+                              columns, 0 = 64 x 64, 1 = 128 x 64 (the autotuner's choice, or 0) */
 } cpcp_info;
 
 /* One instance of cpcp_solve_batched (fp32, device pointers; conventions as

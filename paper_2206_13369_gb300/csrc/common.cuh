@@ -319,6 +319,7 @@ struct BatchResult {
 struct BatchOpts {
     int max_iter, check_every, p, q, qc;
     int early;  // coarse-gradient test also at a coarse level's first iteration
+    int tile;   // CTA GEMM output tiles for N > 32: 0 = 64 x 64, 1 = 128 x 64
     double eta, ratio, tol;
     uint64_t seed;
 };

@@ -51,6 +51,7 @@ struct Sm {
     float *small;  // k x k work (chol, Jacobi); aliases tile
     float *gw;     // GEMM staging
     float *arow;   // RB x KB rows of a factor
+    int wide;      // CTA GEMM tiles for N > 32: 0 = 64 x 64, 1 = 128 x 64 (BatchOpts::tile)
 };
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
@@ -281,8 +282,13 @@ template <int NT>
 __device__ void cta_gemm(int M, int N, int K, const float *A, int64_t sai, int64_t sak, const float *B, int64_t sbk,
                          int64_t sbj, float *C, int64_t ldc, const Sm &sm)
 {
+    // output tiles (register tiles with NT = 512 / 256): 128 x 32 (4 x 2 / 8 x 2)
+    // for N <= 32; for wider N 64 x 64 (2 x 4 / 4 x 4) or 128 x 64 (4 x 4 / 8 x 4),
+    // which the autotuner of the launch picks
     if (N <= 32)
         gemm_tiles<NT, 128, 32>(M, N, K, A, sai, sak, B, sbk, sbj, C, ldc, sm.gw);
+    else if (sm.wide && M > 64)
+        gemm_tiles<NT, 128, 64>(M, N, K, A, sai, sak, B, sbk, sbj, C, ldc, sm.gw);
     else
         gemm_tiles<NT, 64, 64>(M, N, K, A, sai, sak, B, sbk, sbj, C, ldc, sm.gw);
 }
@@ -1127,6 +1133,7 @@ __global__ void __launch_bounds__(NT, 512 / NT)
     sm.small = dsm;
     sm.gw = dsm + U_FLOATS;
     sm.arow = sm.gw + GW_FLOATS;
+    sm.wide = o.tile;
     static_assert(sizeof(BatchInst) % 4 == 0, "descriptor copy");
     for (;;) {
         if (threadIdx.x == 0) s_w = atomicAdd(next, 1);

@@ -57,7 +57,7 @@ struct UnrollRec {
 // the per-instance reports), replayed while the call signature is unchanged.
 struct BatchGraph {
     uint64_t sig = 0;
-    int nt = 0;
+    int nt = 0, tile = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cpcp::BatchResult *host_res = nullptr;  // pinned
@@ -157,13 +157,21 @@ struct cpcp_context {
     std::map<std::string, DevBuf> bufs;
     PhaseTimer timer;
     BatchGraph batch;
-    std::map<uint64_t, int> batch_tuned;  // signature -> measured best CTA size
+    std::map<uint64_t, std::pair<int, int>> batch_tuned;  // signature -> measured best (CTA size, GEMM tiles)
     UnrollRec unroll;
     // private non-blocking stream of the graph-replayed solve (the caller's
     // stream may be the legacy default stream, which cannot be captured) and
     // the two events that order it after and before the caller's stream
     cudaStream_t solve_stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // transfer tables already uploaded to this handle's workspace, by
+    // (operator, n, halvings, element size): built once, reused by every call
+    struct TransferCache {
+        int nh = 0;
+        double kappa = 0.0;
+        void *p[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    };
+    std::map<std::string, TransferCache> tcache;
 };
 
 namespace {
@@ -384,6 +392,24 @@ int coarse_dim(int n, int halvings)
 template <typename T>
 TransferDev<T> upload_transfer(cpcp_context *h, int n, int halvings, const std::string &tag)
 {
+    // the tables depend on (n, halvings, T) only: each set lives in workspace
+    // buffers of its own and is uploaded once per handle
+    (void)tag;
+    const std::string pre = "tr" + std::to_string(halvings) + "_n" + std::to_string(n) + "_" +
+                            std::to_string(sizeof(T)) + "_";
+    auto hit = h->tcache.find(pre);
+    if (hit != h->tcache.end()) {
+        TransferDev<T> d;
+        d.n = n;
+        d.nh = hit->second.nh;
+        d.kappa = hit->second.kappa;
+        d.j0 = static_cast<const int *>(hit->second.p[0]);
+        d.w0 = static_cast<const T *>(hit->second.p[1]);
+        d.w1 = static_cast<const T *>(hit->second.p[2]);
+        d.clo = static_cast<const int *>(hit->second.p[3]);
+        d.chi = static_cast<const int *>(hit->second.p[4]);
+        return d;
+    }
     HostTransfer t;
     if (halvings == 0) {
         t.n = n;
@@ -400,7 +426,6 @@ TransferDev<T> upload_transfer(cpcp_context *h, int n, int halvings, const std::
     }
     if (t.max_span > 64)
         throw CpcpError{CPCP_ERR_INVALID_ARG, "too many levels for the restriction tile (support wider than 64)"};
-    std::string pre = tag + "_tr" + std::to_string(halvings) + "_";
     int *j0 = wsT<int>(h, pre + "j0", n), *clo = wsT<int>(h, pre + "clo", t.nh), *chi = wsT<int>(h, pre + "chi", t.nh);
     T *w0 = wsT<T>(h, pre + "w0", n), *w1 = wsT<T>(h, pre + "w1", n);
     std::vector<T> w0t(t.w0.begin(), t.w0.end()), w1t(t.w1.begin(), t.w1.end());
@@ -420,6 +445,15 @@ TransferDev<T> upload_transfer(cpcp_context *h, int n, int halvings, const std::
     d.w1 = w1;
     d.clo = clo;
     d.chi = chi;
+    cpcp_context::TransferCache c;
+    c.nh = t.nh;
+    c.kappa = t.kappa;
+    c.p[0] = j0;
+    c.p[1] = w0;
+    c.p[2] = w1;
+    c.p[3] = clo;
+    c.p[4] = chi;
+    h->tcache[pre] = c;
     return d;
 }
 
@@ -473,16 +507,33 @@ double orth_factor(int n, int halvings, std::vector<double> &cd, std::vector<dou
 template <typename T>
 OrthTransfer<T> upload_orth(cpcp_context *h, int n, int halvings, const std::string &tag)
 {
-    std::vector<double> cdd, ced;
+    // uploaded once per handle, like the transfer tables
+    (void)tag;
+    const std::string pre = "orth" + std::to_string(halvings) + "_n" + std::to_string(n) + "_" +
+                            std::to_string(sizeof(T)) + "_";
     OrthTransfer<T> o;
+    auto hit = h->tcache.find(pre);
+    if (hit != h->tcache.end()) {
+        o.kappa = hit->second.kappa;
+        o.cd = static_cast<T *>(hit->second.p[0]);
+        o.ce = static_cast<T *>(hit->second.p[1]);
+        return o;
+    }
+    std::vector<double> cdd, ced;
     o.kappa = orth_factor(n, halvings, cdd, ced);
     const int nh = (int)cdd.size();
     std::vector<T> cd(cdd.begin(), cdd.end()), ce(ced.begin(), ced.end());
-    o.cd = wsT<T>(h, tag + "_cd", nh);
-    o.ce = wsT<T>(h, tag + "_ce", nh);
+    o.cd = wsT<T>(h, pre + "cd", nh);
+    o.ce = wsT<T>(h, pre + "ce", nh);
     CK(cudaMemcpyAsync(o.cd, cd.data(), sizeof(T) * nh, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(o.ce, ce.data(), sizeof(T) * nh, cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));  // the host vectors must outlive the copies
+    cpcp_context::TransferCache c;
+    c.nh = nh;
+    c.kappa = o.kappa;
+    c.p[0] = o.cd;
+    c.p[1] = o.ce;
+    h->tcache[pre] = c;
     return o;
 }
 
@@ -2134,38 +2185,50 @@ cpcp_status batched_impl(cpcp_context *h, int count, const cpcp_problem *P, doub
     const void *bufs[4] = {inst_dev, res_dev, order_dev, next_dev};
     gsig = fnv1a(bufs, sizeof(bufs), gsig);
 
+    // launch configuration: CTA size (256 or 512 threads) and the CTA GEMM's
+    // output tiles for wide products (64 x 64 or 128 x 64): the user's CTA size,
+    // else the tuned pair for this batch signature if one was measured, else
+    // (on the first call with batch_autotune) every pair timed and the fastest
+    // kept, else 512 threads with 64 x 64 tiles
     int nt = h->opt.batch_threads;
+    int tile = 0;
     if (nt != 0 && nt != 256 && nt != 512) throw CpcpError{CPCP_ERR_INVALID_ARG, "batch_threads must be 0, 256 or 512"};
     if (nt == 0) {
         auto it = h->batch_tuned.find(sig);
         if (it != h->batch_tuned.end()) {
-            nt = it->second;
+            nt = it->second.first;
+            tile = it->second.second;
         } else if (h->opt.batch_autotune) {
-            // time every CTA size on this batch and keep the fastest
             float best = 0.f;
             for (int cand : {256, 512}) {
-                cudaEvent_t e0, e1;
-                CK(cudaEventCreate(&e0));
-                CK(cudaEventCreate(&e1));
-                CK(cudaMemsetAsync(next_dev, 0, sizeof(int), bs));
-                CK(cudaEventRecord(e0, bs));
-                CK(launch_batched(inst_dev, res_dev, order_dev, count, next_dev, bo, cand, bs));
-                CK(cudaEventRecord(e1, bs));
-                CK(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, e0, e1));
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                if (nt == 0 || ms < best) {
-                    best = ms;
-                    nt = cand;
+                for (int tl : {0, 1}) {
+                    BatchOpts bt = bo;
+                    bt.tile = tl;
+                    cudaEvent_t e0, e1;
+                    CK(cudaEventCreate(&e0));
+                    CK(cudaEventCreate(&e1));
+                    CK(cudaMemsetAsync(next_dev, 0, sizeof(int), bs));
+                    CK(cudaEventRecord(e0, bs));
+                    CK(launch_batched(inst_dev, res_dev, order_dev, count, next_dev, bt, cand, bs));
+                    CK(cudaEventRecord(e1, bs));
+                    CK(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, e0, e1));
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    if (nt == 0 || ms < best) {
+                        best = ms;
+                        nt = cand;
+                        tile = tl;
+                    }
                 }
             }
-            h->batch_tuned[sig] = nt;
+            h->batch_tuned[sig] = {nt, tile};
         } else {
             nt = 512;
         }
     }
+    bo.tile = tile;
 
     if (g.host_cap < count) {
         if (g.host_res) cudaFreeHost(g.host_res);
@@ -2175,7 +2238,7 @@ cpcp_status batched_impl(cpcp_context *h, int count, const cpcp_problem *P, doub
         g.host_cap = count;
         g.sig = 0;  // the captured copy targets the old buffer
     }
-    if (!(g.exec && g.sig == gsig && g.nt == nt)) {
+    if (!(g.exec && g.sig == gsig && g.nt == nt && g.tile == tile)) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
         if (g.graph) cudaGraphDestroy(g.graph);
         g.exec = nullptr;
@@ -2196,6 +2259,7 @@ cpcp_status batched_impl(cpcp_context *h, int count, const cpcp_problem *P, doub
         CK(cudaGraphInstantiate(&g.exec, g.graph, 0));
         g.sig = gsig;
         g.nt = nt;
+        g.tile = tile;
     } else {
         CPCP_COUNT_LAUNCH();  // the replayed persistent kernel
     }
@@ -2227,6 +2291,8 @@ cpcp_status batched_impl(cpcp_context *h, int count, const cpcp_problem *P, doub
             f.pqd_fro = r.pqd;
             f.seconds = secs;
             f.launches = launches;
+            f.batch_threads = nt;
+            f.batch_tile = tile;
             // per-instance device time by phase, from the SM cycle counter at the nominal clock
             for (int ph = 0; ph < 4; ph++) {
                 f.phase_ms[ph] = khz > 0 ? (double)r.cycles[ph] / khz : 0.0;

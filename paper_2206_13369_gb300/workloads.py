@@ -48,6 +48,7 @@ __all__ = [
     "video_cpcp",
     "batched_cpcp",
     "hyperspectral_cpcp",
+    "planted_cpcp_fw",
     "config",
     "CONFIG_NAMES",
 ]
@@ -208,6 +209,30 @@ def hyperspectral_cpcp(seed: int, h: int = 256, w: int = 256, bands: int = 128, 
     S0 = np.where(support, rng.uniform(-1.0, 1.0, (m, bands)) * np.abs(L0).max(), 0.0)
     mask = rng.random((m, bands)) < obs
     return _finish(L0 + S0, mask, L0, S0, 1.0 / math.sqrt(max(m, bands)), levels)
+
+
+def planted_cpcp_fw(m: int, n: int, rank: int, rho: float, obs: float, seed: int, mu_rel: float = 0.05,
+                    levels: int = 1) -> dict:
+    """The planted CPCP recipe at the shapes of the Frank-Wolfe comparisons
+    (m x n up to 10000 x 5000), in float32 storage (fp64 generation).  The
+    weight mu = mu_rel ||P_Q D||_2 takes the spectral norm from 50 seeded power
+    steps instead of a full SVD (a workload parameter, not the method)."""
+    rng = np.random.default_rng(seed)
+    U = rng.normal(size=(m, rank))
+    V = rng.normal(size=(n, rank))
+    L0 = (U @ V.T) / math.sqrt(rank)
+    supp = rng.random((m, n)) < rho
+    S0 = np.where(supp, rng.uniform(-5.0, 5.0, size=(m, n)), 0.0)
+    mask = None if obs >= 1.0 else (rng.random((m, n)) < obs)
+    D = L0 + S0
+    PQD = D if mask is None else np.where(mask, D, 0.0)
+    x = rng.normal(size=n)
+    for _ in range(50):
+        x = PQD.T @ (PQD @ x)
+        x /= np.linalg.norm(x)
+    snorm = float(np.linalg.norm(PQD @ x))
+    return {"D": np.ascontiguousarray(PQD, dtype=np.float32), "mask": mask, "L0": L0, "S0": S0,
+            "lam": 1.0 / math.sqrt(max(m, n)), "mu": mu_rel * snorm, "levels": int(levels)}
 
 
 def _batched_levels(m: int, n: int, rank: int, max_levels: int = 3) -> int:
