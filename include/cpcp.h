@@ -138,6 +138,16 @@ typedef struct {
                               not coarse (no smooth column structure) leave the coarse levels at
                               once; -1 = only every check_every iterations.  A handover skips
                               that iteration's residual check.  Other values: INVALID_ARG */
+    int products_tc;       /* fp32 products of the subspace iteration with the (restricted)
+                              iterate, M_H Omega and M_H^T Q: 1 = on the tensor cores (tcgen05
+                              kind::tf32 with the three-part TF32 split of the fused pass, each
+                              accumulator drained into round-to-nearest fp32 sums every 32 of K,
+                              the long K split over CTAs with fixed-order partial sums); -1 = on
+                              the SIMT cores; 0 (default) = the tensor cores where the iterate
+                              has at least 4096 rows, SIMT otherwise.  The tensor-core path is
+                              taken only where the operands meet the TMA rules (16-byte aligned
+                              bases and leading dimensions, width <= 128), else SIMT.  Other
+                              values: INVALID_ARG */
     int cholqr_fused;      /* fp32 CholeskyQR2 of the subspace SVDs: 0 (default) = six launches
                               (Gram, Cholesky and product kernels per pass); nonzero = both passes
                               in one launch of a thread-block cluster (16 CTAs, or 8 where the

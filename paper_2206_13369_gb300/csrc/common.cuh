@@ -119,6 +119,13 @@ template <typename T> int launch_step_pass(const PassArgs<T> &a, bool coarse, cu
 // nothing, when an operand does not meet the TMA rules.  err: device flag set
 // when a bounded wait of the kernel expired.
 bool launch_pass_tc(const PassArgs<float> &p, int *err, cudaStream_t st);
+// the products of the subspace iteration with M on the tensor cores
+// (k_pass_tc.cu, three-part TF32 split): tn = 0 C = M B (M is P x K), tn = 1
+// C = M^T B (M is K x P), B (K x k, k = *kdyn <= bcols_max <= 128); writes
+// partial slices (returned count, 0 = not launched: an operand breaks the TMA
+// rules) for launch_reduce_partial.  err: set when a bounded wait expired.
+int launch_prod_tc(int tn, int P, int K, const float *M, int64_t ldm, const float *B, int64_t ldb, int bcols_max,
+                   const int *kdyn, float *part, int64_t ldc, int64_t slice, int max_splits, int *err, cudaStream_t st);
 // per-block fp64 partial sums of squares of X (rows x cols); returns the block count
 template <typename T> int launch_sumsq(int rows, int cols, const T *X, int64_t ld, double *partial, cudaStream_t st);
 // check pass at (L_k, S_k) with weight mu_bar: writes M = L - tau G and

@@ -72,6 +72,8 @@
 // copies it issued and frees its TMEM.
 #include <cuda.h>
 
+#include <algorithm>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -606,6 +608,295 @@ __global__ void __launch_bounds__(NT, 1) pass_tc_kernel(const __grid_constant__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// The products of the subspace iteration with the (restricted) iterate M,
+//     Y = M Omega   (rows P = m, K = n: A = M, K-major)
+//     Z = M^T Q     (rows P = n, K = m: A = M^T, read from M as stored)
+// on the tensor cores, with the three-part TF32 split of the fused pass (six
+// MMAs per K step of 8, the five small products and a_h b_h in separate fp32
+// accumulators).  One CTA per (128-row output tile, K range): the long K of
+// these tall-skinny products is split over CTAs so that about one CTA runs per
+// SM, each writing a partial tile that a fixed-order reduction sums.  TMA
+// brings 16-wide K slices of M and of the thin operand (Omega or Q, n x KM or
+// m x KM) as fp32; the converter warps split them and, for the operands not
+// already K-major (M^T, and the thin operand, whose K runs down its rows),
+// transpose them into the K-major operand layout on the way.  The live width
+// k (device value) sets the MMA's N = round16(k) <= 128; the converters zero
+// the thin operand's columns beyond k.
+//
+// The tensor cores add into an fp32 accumulator by aligning to the largest
+// term and dropping the bits below it, a one-sided error that grows with the
+// number of MMAs chained into one accumulator.  So an accumulator lives for
+// PP_DR stages only: the MMA warp alternates between two TMEM buffers, and the
+// epilogue warps drain each finished buffer into a round-to-nearest fp32 sum
+// in shared memory while the next one fills.
+//
+// Warp roles (512 threads): warp 0 TMA producer, warp 1 MMA issuer, warp 2
+// TMEM allocator, warps 4-7 epilogue (one TMEM lane quarter each, one output
+// row per thread while draining, one row per warp-wide store at the end),
+// warps 8-15 converters.  Every mbarrier wait is bounded as in the fused pass;
+// a timeout raises the error flag.
+constexpr int PP_M = 128;    // output rows per tile
+constexpr int PP_NB = 128;   // thin-operand columns a stage holds (the MMA's N is round16(k))
+constexpr int PP_K = 16;     // K per stage
+constexpr int PP_RS = 4;     // raw stages
+constexpr int PP_OPS = 2;    // operand stages
+constexpr int PP_DR = 2;     // stages per accumulator lifetime
+constexpr int PP_NT = 512;
+constexpr int PP_EPI_W0 = 4;
+constexpr int PP_CVT_W0 = 8;
+constexpr int PP_CVT_NW = 8;
+constexpr uint32_t PP_A = PP_M * PP_K * 4;    // 8 KB: one part of A, or the raw A slice
+constexpr uint32_t PP_B = PP_NB * PP_K * 4;   // 8 KB: one part of B, or the raw B slice
+constexpr uint32_t PP_RAW = PP_A + PP_B;
+constexpr uint32_t PP_OP = 3 * PP_A + 3 * PP_B;
+constexpr int PP_ACC_LD = PP_M + 1;           // running sums, column-major, padded against bank conflicts
+constexpr uint32_t PP_ACC = PP_NB * PP_ACC_LD * 4;
+constexpr uint32_t PP_TMEM = 4 * PP_NB;       // two buffers x (a_h b_h, the small products)
+constexpr size_t PP_SMEM = 1024 + PP_OPS * (size_t)PP_OP + PP_RS * (size_t)PP_RAW + PP_ACC + 256;
+static_assert(PP_SMEM <= 232448, "shared memory per block");
+
+struct ProdMaps {
+    CUtensorMap a;  // M: [P rows][16-col boxes], 64-byte swizzle (Y); [16 rows][128-col boxes], no swizzle (Z)
+    CUtensorMap b;  // thin operand: [16 rows][128-col boxes], no swizzle
+};
+
+struct ProdArgs {
+    int P, K, ldc, stages_per_split, total_stages;
+    int bcols;         // columns of the thin operand's TMA box: min(its leading dimension, 128)
+    int tn;            // 1: A = M^T
+    const int *kdyn;   // live width k
+    float *part;       // partial tiles: split s at part + s * slice, row-major with ld ldc
+    int64_t slice;
+    int *err;
+};
+
+__device__ __forceinline__ void split3(float v, float &h, float &m, float &l)
+{
+    h = tf32_round(v);
+    const float r1 = v - h;
+    m = tf32_round(r1);
+    l = tf32_round(r1 - m);
+}
+
+__global__ void __launch_bounds__(PP_NT, 1) prod_tc_kernel(const __grid_constant__ ProdMaps maps, ProdArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sOp = smem;                          // PP_OPS x [A h | A m | A l | B h | B m | B l]
+    uint8_t *sRaw = sOp + PP_OPS * PP_OP;         // PP_RS x [A | B] (fp32 as TMA brings them)
+    float *sAcc = reinterpret_cast<float *>(sRaw + PP_RS * PP_RAW);  // [column][PP_ACC_LD]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(sAcc) + PP_ACC);
+    uint64_t *raw_full = bars, *raw_empty = bars + PP_RS;
+    uint64_t *op_empty = bars + 2 * PP_RS, *cvt_full = op_empty + PP_OPS;
+    uint64_t *acc_full = cvt_full + PP_OPS, *acc_empty = acc_full + 2, *mma_done = acc_empty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p0 = blockIdx.x * PP_M;
+    const int s0 = blockIdx.y * a.stages_per_split;
+    const int s1 = min(a.total_stages, s0 + a.stages_per_split);
+    const int nst = max(0, s1 - s0);
+    const int k = min(*a.kdyn, PP_NB);
+    const int nmma = max(16, (k + 15) / 16 * 16);  // the MMA's N
+    const int nch = (nst + PP_DR - 1) / PP_DR;      // accumulator lifetimes
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < PP_RS; s++) {
+            mbar_init(&raw_full[s], 1);
+            mbar_init(&raw_empty[s], PP_CVT_NW);
+        }
+        for (int s = 0; s < PP_OPS; s++) {
+            mbar_init(&op_empty[s], 1);
+            mbar_init(&cvt_full[s], PP_CVT_NW);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);
+        }
+        mbar_init(mma_done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(PP_TMEM)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int i = 0;
+            for (; i < nst && !*abort_flag; i++) {
+                const int s = i % PP_RS;
+                if (i >= PP_RS && !mbar_wait(&raw_empty[s], ((i / PP_RS) & 1) ^ 1, abort_flag)) break;
+                uint8_t *st = sRaw + s * PP_RAW;
+                const int kk = (s0 + i) * PP_K;
+                mbar_expect_tx(&raw_full[s], PP_A + (uint32_t)(PP_K * a.bcols * 4));
+                if (a.tn)
+                    tma_load_2d(st, &maps.a, &raw_full[s], p0, kk);  // M rows kk.., columns p0..
+                else
+                    tma_load_2d(st, &maps.a, &raw_full[s], kk, p0);  // M rows p0.., columns kk..
+                tma_load_2d(st + PP_A, &maps.b, &raw_full[s], 0, kk);
+            }
+            for (int s = 0; s < PP_RS && s < i; s++) {
+                const int last = i - 1 - ((i - 1 - s) % PP_RS);
+                if (!mbar_wait(&raw_full[s], (last / PP_RS) & 1, nullptr)) *abort_flag = 1;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // kind::tf32, fp32 accumulator, M = 128, N = round16(k)
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nmma >> 3) << 17) |
+                                   ((uint32_t)(PP_M >> 4) << 24);
+            for (int i = 0; i < nst; i++) {
+                const int s = i % PP_OPS, c = i / PP_DR, b = c & 1;
+                const bool cfirst = (i % PP_DR) == 0;
+                // buffer b was last filled by lifetime c - 2: wait for its drain
+                if (cfirst && c >= 2 && !mbar_wait(&acc_empty[b], ((c >> 1) & 1) ^ 1, abort_flag)) break;
+                if (!mbar_wait(&cvt_full[s], (i / PP_OPS) & 1, abort_flag)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * 2 * PP_NB), dsm = d + (uint32_t)PP_NB;
+                const uint8_t *st = sOp + s * PP_OP;
+                uint64_t ad[3], bd[3];
+#pragma unroll
+                for (int q = 0; q < 3; q++) {
+                    ad[q] = smem_desc_sw64(st + q * PP_A);
+                    bd[q] = smem_desc_sw64(st + 3 * PP_A + q * PP_B);
+                }
+                constexpr int PA[5] = {1, 2, 0, 1, 0}, PB[5] = {1, 0, 2, 0, 1};
+#pragma unroll
+                for (int kk = 0; kk < PP_K / 8; kk++) {
+                    const uint32_t acc = (!cfirst || kk > 0) ? 1u : 0u;
+#pragma unroll
+                    for (int t = 0; t < 5; t++)
+                        umma_tf32(dsm, ad[PA[t]] + 2 * kk, bd[PB[t]] + 2 * kk, idesc, (acc || t > 0) ? 1u : 0u);
+                    umma_tf32(d, ad[0] + 2 * kk, bd[0] + 2 * kk, idesc, acc);
+                }
+                umma_commit(&op_empty[s]);
+                if (i % PP_DR == PP_DR - 1 || i == nst - 1) umma_commit(&acc_full[b]);
+            }
+            umma_commit(mma_done);
+            if (!mbar_wait(mma_done, 0, nullptr)) *abort_flag = 1;
+        }
+    } else if (warp >= PP_EPI_W0 && warp < PP_EPI_W0 + 4) {
+        // drain each accumulator lifetime into the running sums (one row per
+        // thread: the row's columns of both accumulators, summed in fp32)
+        const int q = warp - PP_EPI_W0;
+        const int rl = q * 32 + lane;
+        bool ok = true;
+        for (int c = 0; c < nch; c++) {
+            const int b = c & 1;
+            if (!mbar_wait(&acc_full[b], (c >> 1) & 1, abort_flag)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 2 * PP_NB);
+            for (int c0 = 0; c0 < nmma; c0 += 8) {
+                float v[8], w[8];
+                tmem_ld8x2(ta + (uint32_t)c0, (uint32_t)PP_NB, v, w);
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    float *p = sAcc + (c0 + j) * PP_ACC_LD + rl;
+                    const float t = v[j] + w[j];
+                    *p = c == 0 ? t : *p + t;
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+        }
+        // the warp's 32 rows, one row per store instruction
+        __syncwarp();
+        const bool have = ok && nch > 0;
+        for (int r = q * 32; r < q * 32 + 32; r++) {
+            const int row = p0 + r;
+            if (row >= a.P) break;
+            float *out = a.part + (int64_t)blockIdx.y * a.slice + (int64_t)row * a.ldc;
+            for (int cc = lane; cc < k; cc += 32) out[cc] = have ? sAcc[cc * PP_ACC_LD + r] : 0.f;
+        }
+    } else if (warp >= PP_CVT_W0) {
+        // the TF32 split of each raw stage into an operand stage.  Operand
+        // tiles are K-major with the 64-byte swizzle: the 16-byte chunk at
+        // physical position c4 of row r holds K columns 4 (c4 ^ ((r / 2) % 4)) ..
+        const int ct = threadIdx.x - PP_CVT_W0 * 32;
+        for (int i = 0; i < nst && !*abort_flag; i++) {
+            const int s = i % PP_OPS, sr = i % PP_RS;
+            if (!mbar_wait(&raw_full[sr], (i / PP_RS) & 1, abort_flag) ||
+                (i >= PP_OPS && !mbar_wait(&op_empty[s], ((i / PP_OPS) & 1) ^ 1, abort_flag)))
+                break;
+            const uint8_t *rw = sRaw + sr * PP_RAW;
+            const float *rB = reinterpret_cast<const float *>(rw + PP_A);
+            uint8_t *st = sOp + s * PP_OP;
+            // A: 128 rows x 4 chunks
+            for (int g = ct; g < PP_M * 4; g += PP_CVT_NW * 32) {
+                float xv[4];
+                uint8_t *dst;
+                if (!a.tn) {
+                    // M rows as TMA brought them (same swizzle as the operand)
+                    const float4 x = *reinterpret_cast<const float4 *>(rw + g * 16);
+                    xv[0] = x.x;
+                    xv[1] = x.y;
+                    xv[2] = x.z;
+                    xv[3] = x.w;
+                    dst = st + g * 16;
+                } else {
+                    // M^T: output row r gathers column r of the raw [16 K][128] slice
+                    const int r = g & (PP_M - 1), c4 = g >> 7;
+                    const int kc = 4 * (c4 ^ ((r >> 1) & 3));
+                    const float *rA = reinterpret_cast<const float *>(rw);
+#pragma unroll
+                    for (int j = 0; j < 4; j++) xv[j] = rA[(kc + j) * PP_M + r];
+                    dst = st + r * 64 + c4 * 16;
+                }
+                float hv[4], mv[4], lv[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) split3(xv[j], hv[j], mv[j], lv[j]);
+                *reinterpret_cast<float4 *>(dst) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+                *reinterpret_cast<float4 *>(dst + PP_A) = make_float4(mv[0], mv[1], mv[2], mv[3]);
+                *reinterpret_cast<float4 *>(dst + 2 * PP_A) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+            }
+            // B: row c of the operand gathers column c of the raw [16 K][128]
+            // slice of the thin operand (zero beyond the live width; k <= bcols)
+            for (int g = ct; g < nmma * 4; g += PP_CVT_NW * 32) {
+                const int r = g % nmma, c4 = g / nmma;
+                const int kc = 4 * (c4 ^ ((r >> 1) & 3));
+                float xv[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) xv[j] = r < k ? rB[(kc + j) * a.bcols + r] : 0.f;
+                float hv[4], mv[4], lv[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) split3(xv[j], hv[j], mv[j], lv[j]);
+                uint8_t *dst = st + 3 * PP_A + r * 64 + c4 * 16;
+                *reinterpret_cast<float4 *>(dst) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+                *reinterpret_cast<float4 *>(dst + PP_B) = make_float4(mv[0], mv[1], mv[2], mv[3]);
+                *reinterpret_cast<float4 *>(dst + 2 * PP_B) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&cvt_full[s]);
+                mbar_arrive(&raw_empty[sr]);
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) atomicExch(a.err, 1);
+    if (warp == 2) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(PP_TMEM) : "memory");
+    }
+}
+
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -641,6 +932,23 @@ bool make_map_f32(CUtensorMap *map, const float *base, uint64_t cols, uint64_t r
     const CUtensorMapSwizzle sw = box_cols == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// fp32 row-major map with boxes of box_rows x box_cols and no swizzle (rows of
+// box_cols * 4 bytes, a multiple of 16; at most 256 columns)
+bool make_map_f32_plain(CUtensorMap *map, const float *base, uint64_t cols, uint64_t rows, uint64_t ld,
+                        uint32_t box_rows, uint32_t box_cols)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (fn == nullptr) return false;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld * 4) % 16 != 0) return false;
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {ld * 4};
+    cuuint32_t box[2] = {box_cols, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -700,6 +1008,54 @@ bool launch_pass_tc(const PassArgs<float> &p, int *err, cudaStream_t st)
     CPCP_COUNT_LAUNCH();
     pass_tc_kernel<<<grid, NT, SMEM_BYTES, st>>>(maps, a);
     return true;
+}
+
+// C (P x k) = A B for the products of the subspace iteration on the tensor
+// cores (see prod_tc_kernel): tn = 0: A = M (P x K), tn = 1: A = M^T with M
+// (K x P); M with leading dimension ldm; B (K x k, leading dimension ldb <= 128
+// columns used) the thin operand.  Writes `splits` partial slices of part
+// (slice floats apart, leading dimension ldc) and returns their number, or 0
+// (nothing launched) when an operand does not meet the TMA rules.
+int launch_prod_tc(int tn, int P, int K, const float *M, int64_t ldm, const float *B, int64_t ldb, int bcols_max,
+                   const int *kdyn, float *part, int64_t ldc, int64_t slice, int max_splits, int *err, cudaStream_t st)
+{
+    if (P < 1 || K < 1 || bcols_max < 1 || bcols_max > PP_NB) return 0;
+    ProdMaps maps;
+    const int bcols = (int)std::min<int64_t>(ldb, PP_NB);
+    if (tn) {
+        if (!make_map_f32_plain(&maps.a, M, (uint64_t)P, (uint64_t)K, (uint64_t)ldm, PP_K, PP_M)) return 0;
+    } else {
+        if (!make_map_f32(&maps.a, M, (uint64_t)K, (uint64_t)P, (uint64_t)ldm, PP_M, PP_K)) return 0;
+    }
+    if (!make_map_f32_plain(&maps.b, B, (uint64_t)bcols, (uint64_t)K, (uint64_t)ldb, PP_K, (uint32_t)bcols)) return 0;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(prod_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PP_SMEM) !=
+            cudaSuccess)
+            return 0;
+        attr = true;
+    }
+    const int tiles = (P + PP_M - 1) / PP_M;
+    const int total = (K + PP_K - 1) / PP_K;
+    // about one CTA per SM, at least 4 stages per CTA
+    int splits = std::max(1, std::min({sm_count() / tiles, max_splits, std::max(1, total / 4)}));
+    const int per = (total + splits - 1) / splits;
+    splits = (total + per - 1) / per;
+    ProdArgs a;
+    a.P = P;
+    a.K = K;
+    a.ldc = (int)ldc;
+    a.stages_per_split = per;
+    a.total_stages = total;
+    a.bcols = bcols;
+    a.tn = tn;
+    a.kdyn = kdyn;
+    a.part = part;
+    a.slice = slice;
+    a.err = err;
+    CPCP_COUNT_LAUNCH();
+    prod_tc_kernel<<<dim3((unsigned)tiles, (unsigned)splits), PP_NT, PP_SMEM, st>>>(maps, a);
+    return splits;
 }
 
 }  // namespace cpcp

@@ -322,6 +322,199 @@ __global__ void __launch_bounds__(NT, 1) chol_kernel(const T *__restrict__ parti
 }
 
 // ---------------------------------------------------------------------------
+// The same factorisation in fp32 with column quarters per thread (k <= 64)
+// ---------------------------------------------------------------------------
+// Thread (q, y) = (tid / 64, tid % 64) of the 256 owns rows 16q .. 16q + 15
+// of column y of S in registers (rows unrolled), so a step needs no
+// per-position index logic: at step j the owners of columns y > j eliminate
+// rows j < x <= y of the upper triangle (G[x][y] -= G[j][x] G[j][y] / p_j),
+// and the owners of columns y <= j update every row x > j of W^T (W[y][x] -=
+// W[y][j] G[j][x] / p_j, W[j][j] = 1).  Both are S[x][y] -= c_y S[j][x] with
+// one coefficient per column, over rows (j, xmax(y)].  Row j of S goes
+// through a double-buffered shared row, with a copy zeroed up to column j
+// that serves as G[j][x] for x > j; one barrier per step.  A quarter wholly
+// at or above row j skips the step (warp-uniform).  Wider subspaces
+// (64 < k <= 128) take chol_body with 256 threads.  Same outputs, pivot
+// rule, equilibration and well-conditioning test as chol_body.
+constexpr int CQ_NT = 256;
+
+size_t chol_q_smem(int kmax)
+{
+    const size_t narrow = (size_t)(2 * kmax * (kmax + 1) + 2 * kmax + 4 * 64 + 2) * sizeof(float) + 64;
+    const size_t wide = (size_t)(4 * kmax + 2) * sizeof(float) + (size_t)2 * kmax * (kmax + 1) * sizeof(float) + 16;
+    return std::max(narrow, wide);
+}
+
+__global__ void __launch_bounds__(CQ_NT, 1) chol_q_kernel(const float *__restrict__ partial, int splits, int kmax,
+                                                           const int *kdyn, float *__restrict__ R,
+                                                           float *__restrict__ Rinv, const float *__restrict__ Rprev,
+                                                           float *__restrict__ Rtot, int ldr, int *well_out,
+                                                           const int *skip_in, int *stats)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double red[CQ_NT / 32];
+    const int k = *kdyn;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (skip_in != nullptr && *skip_in) {
+        for (int idx = tid; idx < k * k; idx += CQ_NT) {
+            const int i = idx / k, c = idx % k;
+            R[(int64_t)i * ldr + c] = (i == c) ? 1.f : 0.f;
+            Rinv[(int64_t)i * ldr + c] = (i == c) ? 1.f : 0.f;
+            if (Rtot != nullptr) Rtot[(int64_t)i * ldr + c] = Rprev[(int64_t)i * ldr + c];
+        }
+        return;
+    }
+    if (stats != nullptr && tid == 0) atomicAdd(stats, 1);
+    if (k > 64) {
+        chol_body<float, 8, 16, 4, CQ_NT>(partial, splits, kmax, k, R, Rinv, Rprev, Rtot, ldr, well_out,
+                                          reinterpret_cast<float *>(smraw), red);
+        return;
+    }
+    // shared: row buffers (16-byte aligned), then Gs and Ps (kmax x (kmax + 1)), scales, pivots
+    float *rowf = reinterpret_cast<float *>(smraw);  // 2 x 64: row j of S
+    float *rowg = rowf + 2 * 64;                      // 2 x 64: row j of S, zero in columns <= j
+    const int ldg = kmax + 1;
+    float *Gs = rowg + 2 * 64;     // equilibrated Gram (upper), the final columns of S, then R (upper)
+    float *Ps = Gs + kmax * ldg;   // Rprev
+    float *dsc = Ps + kmax * ldg;  // column scales
+    float *piv = dsc + kmax;       // square roots of the pivots (0 = dropped)
+    float *rinv = piv + kmax;      // 2: 1 / pivot of row j (0 = dropped)
+    const int64_t slice = (int64_t)kmax * kmax;
+    const float tol = FLT_EPSILON * FLT_EPSILON;
+
+    // column scales, then the equilibrated Gram matrix and its distance from I
+    for (int c = tid; c < k; c += CQ_NT) {
+        const float g = chol_gram_entry(partial, splits, slice, kmax, c, c);
+        dsc[c] = (g > 0.f && isfinite(g)) ? sqrtf(g) : 0.f;
+    }
+    for (int c = tid; c < 4 * 64; c += CQ_NT) rowf[c] = 0.f;  // rowf and rowg
+    __syncthreads();
+    double defect = 0.0;
+    for (int idx = tid; idx < k * k; idx += CQ_NT) {
+        const int x = idx / k, y = idx - (idx / k) * k;
+        if (x > y) continue;
+        const float dx = dsc[x], dy = dsc[y];
+        const float v = (dx > 0.f && dy > 0.f) ? chol_gram_entry(partial, splits, slice, kmax, x, y) / dx / dy : 0.f;
+        Gs[x * ldg + y] = v;
+        const float ev = v - (x == y ? 1.f : 0.f);
+        defect += (x == y ? 1.0 : 2.0) * (double)(ev * ev);
+    }
+    defect = warp_sum(defect);
+    if (lane == 0) red[warp] = defect;
+    if (Rprev != nullptr)
+        for (int idx = tid; idx < k * k; idx += CQ_NT) {
+            const int i = idx / k, c = idx - (idx / k) * k;
+            Ps[i * ldg + c] = Rprev[(int64_t)i * ldr + c];
+        }
+    __syncthreads();
+    if (tid == 0 && well_out != nullptr) {
+        double tot = 0.0;
+        for (int q = 0; q < CQ_NT / 32; q++) tot += red[q];
+        *well_out = tot <= 0.25 ? 1 : 0;
+    }
+
+    const int y = tid & 63, q = tid >> 6, x0 = 16 * q;
+    float S[16];
+#pragma unroll
+    for (int t = 0; t < 16; t++) S[t] = (y < k && x0 + t <= y) ? Gs[(x0 + t) * ldg + y] : 0.f;
+    if (q == 0) {
+        const float r0 = y < k ? S[0] : 0.f;
+        rowf[y] = r0;
+        rowg[y] = y > 0 ? r0 : 0.f;
+        if (y == 0) {
+            const bool dj = !(r0 > tol);
+            rinv[0] = dj ? 0.f : 1.f / r0;
+            piv[0] = dj ? 0.f : sqrtf(r0);
+        }
+    }
+    for (int j = 0; j < k; j++) {
+        __syncthreads();
+        const int b = j & 1;
+        if (x0 + 15 > j && x0 < k) {
+            const float inv = rinv[b];
+            const float f = y == j ? 1.f : rowf[b * 64 + y];
+            const float cf = f * inv;
+            // rows (j, xmax] of this column change; none for columns >= k
+            const int xmax = y >= k ? j : (y <= j ? k - 1 : y);
+            const float4 *g4 = reinterpret_cast<const float4 *>(rowg + b * 64 + x0);
+            float g[16];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const float4 v = g4[u];
+                g[4 * u] = v.x;
+                g[4 * u + 1] = v.y;
+                g[4 * u + 2] = v.z;
+                g[4 * u + 3] = v.w;
+            }
+#pragma unroll
+            for (int t = 0; t < 16; t++)
+                if (x0 + t <= xmax) S[t] = fmaf(-cf, g[t], S[t]);
+        }
+        // publish row j + 1 (the owner of its diagonal: the pivot); S[jn - x0]
+        // by selects that the compiler cannot turn into an indexed
+        // (local-memory) load, which would take S out of registers
+        const int jn = j + 1;
+        if (jn < k && (jn >> 4) == q) {
+            float pub = 0.f;
+#pragma unroll
+            for (int t = 0; t < 16; t++)
+                asm("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %2, %3;\n\tselp.f32 %0, %1, %0, p;\n\t}"
+                    : "+f"(pub)
+                    : "f"(S[t]), "r"(x0 + t), "r"(jn));
+            if (y >= k) pub = 0.f;
+            rowf[(b ^ 1) * 64 + y] = pub;
+            rowg[(b ^ 1) * 64 + y] = y > jn ? pub : 0.f;
+            if (y == jn) {
+                const bool dj = !(pub > tol);
+                rinv[b ^ 1] = dj ? 0.f : 1.f / pub;
+                piv[jn] = dj ? 0.f : sqrtf(pub);
+            }
+        }
+    }
+    // the columns back to shared memory (each thread its own quarter)
+    if (y < k) {
+#pragma unroll
+        for (int t = 0; t < 16; t++)
+            if (x0 + t < k) Gs[(x0 + t) * ldg + y] = S[t];
+    }
+    __syncthreads();
+    // undo the equilibration (as in chol_body): R = P U D, R^{-1} = D^{-1} W P^{-1}
+    for (int idx = tid; idx < k * k; idx += CQ_NT) {
+        const int yy = idx / k, x = idx - (idx / k) * k;  // column yy of S, row x
+        const float px = piv[x], dy = dsc[yy], sx = Gs[x * ldg + yy];
+        if (x < yy) {
+            const float rv = sx * (px > 0.f ? 1.f / px : 0.f) * dy;
+            R[(int64_t)x * ldr + yy] = rv;
+            R[(int64_t)yy * ldr + x] = 0.f;
+            Rinv[(int64_t)yy * ldr + x] = 0.f;
+            if (Rprev != nullptr) Rtot[(int64_t)yy * ldr + x] = 0.f;
+        } else if (x == yy) {
+            R[(int64_t)x * ldr + x] = px * dy;
+            Rinv[(int64_t)x * ldr + x] = (px > 0.f && dy > 0.f) ? 1.f / px / dy : 0.f;
+        } else {
+            Rinv[(int64_t)yy * ldr + x] = (px > 0.f && dy > 0.f) ? sx / px / dy : 0.f;
+        }
+    }
+    if (Rprev == nullptr) return;
+    __syncthreads();
+    // R (upper) into Gs for Rtot = R Rprev
+    for (int idx = tid; idx < k * k; idx += CQ_NT) {
+        const int x = idx / k, yy = idx - (idx / k) * k;
+        if (yy < x) continue;
+        const float px = piv[x], dy = dsc[yy];
+        Gs[x * ldg + yy] = x == yy ? px * dy : Gs[x * ldg + yy] * (px > 0.f ? 1.f / px : 0.f) * dy;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < k * k; idx += CQ_NT) {
+        const int x = idx / k, yy = idx - (idx / k) * k;
+        if (yy < x) continue;
+        float s = 0.f;
+        for (int p = x; p <= yy; p++) s = fmaf(Gs[x * ldg + p], Ps[p * ldg + yy], s);
+        Rtot[(int64_t)x * ldr + yy] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // CholeskyQR2 of a tall block in one thread-block cluster
 // ---------------------------------------------------------------------------
 // The two CholeskyQR passes (Gram, Cholesky, Q = X R^{-1}, twice) as one
@@ -930,6 +1123,9 @@ void ensure_small_attrs()
                          (int)chol_smem<T>(small_kmax<T>()));
     cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)jacobi_smem<T>(small_kmax<T>()));
+    if (std::is_same<T, float>::value)
+        cudaFuncSetAttribute(chol_q_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)chol_q_smem(small_kmax<float>()));
     done = true;
 }
 
@@ -941,6 +1137,13 @@ void launch_chol(const T *partialG, int splits, int kmax, const int *kdyn, T *R,
 {
     ensure_small_attrs<T>();
     CPCP_COUNT_LAUNCH();
+    if constexpr (std::is_same<T, float>::value) {
+        if (kmax <= small_kmax<float>()) {
+            chol_q_kernel<<<1, CQ_NT, chol_q_smem(kmax), st>>>(partialG, splits, kmax, kdyn, R, Rinv, Rprev, Rtot, ldr,
+                                                              well_out, skip_in, stats);
+            return;
+        }
+    }
     chol_kernel<T, chol_nt<T>()><<<1, chol_nt<T>(), chol_smem<T>(kmax), st>>>(partialG, splits, kmax, kdyn, R, Rinv,
                                                                             Rprev, Rtot, ldr,
                                                           well_out, skip_in, stats);

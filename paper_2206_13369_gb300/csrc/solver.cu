@@ -557,6 +557,8 @@ struct SvdWork {
     int *err = nullptr;
     // optional counters: Jacobi calls, Jacobi sweeps, Cholesky factorisations
     int *stats = nullptr;
+    // fp32: the products with M on the tensor cores (options.products_tc)
+    bool tc = false;
 };
 
 template <typename T>
@@ -586,6 +588,10 @@ SvdWork<T> svd_work(cpcp_context *h, const std::string &tag, int m, int ncols, i
     w.Us = wsT<T>(h, tag + "Us", KM * KM);
     w.sig = wsT<T>(h, tag + "sig", KM);
     w.sig64 = wsT<double>(h, tag + "sig64", KM);
+    // bounded-wait error flag of the tensor-core kernels (shared, cleared per solve)
+    w.err = wsT<int>(h, "umma_err", 1);
+    const int ptc = h->opt.products_tc;
+    w.tc = std::is_same<T, float>::value && KM <= 128 && (ptc == 1 || (ptc == 0 && m >= 4096));
     return w;
 }
 
@@ -598,6 +604,17 @@ void svd_work_bf16(cpcp_context *h, SvdWork<T> &w, const std::string &tag, int m
     w.Mt = wsT<__nv_bfloat16>(h, tag + "Mt", (size_t)umma_pad_rows(ncols) * kpm);
     w.Bt = wsT<__nv_bfloat16>(h, tag + "Bt", (size_t)round16(w.KM) * std::max(kpm, kpn));
     w.err = wsT<int>(h, "umma_err", 1);
+}
+
+// the bounded-wait error flag of the tensor-core kernels an SVD workspace uses:
+// cleared before a call's first launch, read after its last
+void tc_err_clear(const int *err, cudaStream_t st) { CK(cudaMemsetAsync(const_cast<int *>(err), 0, sizeof(int), st)); }
+void tc_err_check(const int *err, cudaStream_t st)
+{
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (e) throw CpcpError{CPCP_ERR_TIMEOUT, "a bounded wait of a tensor-core kernel expired"};
 }
 
 // products of the subspace SVD: the cluster-reduced tall-skinny kernels, or the
@@ -614,7 +631,19 @@ void prod_nn_small(int rows, const T *A, int64_t lda, const T *B, int64_t ldb, T
 template <typename T>
 void prod_y(SvdWork<T> &w, int m, int nc, const T *Mx, int64_t ldx, const T *Om, const int *kdyn, cudaStream_t st)
 {
-    // Y = M Omega (m x k), K = nc long
+    // Y = M Omega (m x k), K = nc long: fp32 on the tensor cores (three-part
+    // TF32 split, split-K partials summed in a fixed order) where the operands
+    // meet the TMA rules, else the cluster-reduced SIMT kernel
+    if constexpr (std::is_same<T, float>::value) {
+        if (w.tc) {
+            const int sp = launch_prod_tc(0, m, nc, Mx, ldx, Om, w.KM, w.KM, kdyn, w.Ypart, w.KM, (int64_t)m * w.KM,
+                                          16, w.err, st);
+            if (sp > 0) {
+                launch_reduce_partial<float>(w.Ypart, sp, m, w.KM, w.Y, w.KM, nullptr, kdyn, st);
+                return;
+            }
+        }
+    }
     if (!launch_ts_nn<T>(m, nc, Mx, ldx, Om, w.KM, w.Y, w.KM, nullptr, kdyn, nc, w.KM, nullptr, st))
         launch_gemm_nn_splitk<T>(m, nc, Mx, ldx, Om, w.KM, w.Y, w.KM, w.Ypart, kdyn, w.KM, st);
 }
@@ -623,7 +652,17 @@ template <typename T>
 void prod_z(SvdWork<T> &w, int m, int nc, const T *Mx, int64_t ldx, const T *Q, int64_t ldq, const int *kdyn,
             cudaStream_t st)
 {
-    // Z = M^T Q (nc x k), K = m long
+    // Z = M^T Q (nc x k), K = m long (tensor cores as for Y)
+    if constexpr (std::is_same<T, float>::value) {
+        if (w.tc && ldq == w.KM) {
+            const int sp = launch_prod_tc(1, nc, m, Mx, ldx, Q, ldq, w.KM, kdyn, w.Zpart, w.KM, (int64_t)nc * w.KM,
+                                          64, w.err, st);
+            if (sp > 0) {
+                launch_reduce_partial<float>(w.Zpart, sp, nc, w.KM, w.Z, w.KM, nullptr, kdyn, st);
+                return;
+            }
+        }
+    }
     if (!launch_ts_tn<T>(nc, m, Mx, ldx, Q, ldq, w.Z, w.KM, kdyn, w.KM, st)) {
         const int sp = launch_gemm_tn_partial<T>(m, nc, Mx, ldx, Q, ldq, w.Zpart, kdyn, w.KM, nc, st, nullptr);
         launch_reduce_partial<T>(w.Zpart, sp, nc, w.KM, w.Z, w.KM, nullptr, kdyn, st);
@@ -1093,10 +1132,8 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     w.stats = wf.stats = wsT<int>(h, "svd_stats", 4);
     CK(cudaMemsetAsync(w.stats, 0, sizeof(int) * 4, st));
     s.bf16 = o.precision == 1;
-    if (s.bf16) {
-        svd_work_bf16<T>(h, w, "it_", m, n);
-        CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
-    }
+    if (s.bf16) svd_work_bf16<T>(h, w, "it_", m, n);
+    CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
     if (std::is_same<T, float>::value && o.tc_pass) {
         s.tc_err = wsT<int>(h, "tc_err", 1);
         CK(cudaMemsetAsync(s.tc_err, 0, sizeof(int), st));
@@ -1366,6 +1403,7 @@ cpcp_status ialm_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, do
     double *partial = wsT<double>(h, "ia_partial", (size_t)std::max(nblk, 1024));
     double *sums = wsT<double>(h, "ia_sums", 4);
     SvdWork<T> w = svd_work<T>(h, "ia_svd_", m, n, kcap0);  // own tags: "ia_Y" is the multiplier
+    tc_err_clear(w.err, h->stream);
     // orthonormal-basis transfer (option): R C^{-1} with R^T R = C^T C
     const bool orth = H > 0 && o.transfer == 1;
     T *Cd = nullptr, *Ce = nullptr, *Vp = nullptr;
@@ -1504,6 +1542,7 @@ cpcp_status ialm_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, do
                              st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
+    tc_err_check(w.err, st);
     if (info) {
         cpcp_info inf;
         memset(&inf, 0, sizeof(inf));
@@ -1559,6 +1598,7 @@ cpcp_status fwt_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, con
     double *partial = wsT<double>(h, "fw_partial", (size_t)nb * 5), *amv = wsT<double>(h, "fw_amv", nb);
     int64_t *ami = wsT<int64_t>(h, "fw_ami", nb);
     SvdWork<T> w = svd_work<T>(h, "fw_svd_", m, n, kcap0);
+    tc_err_clear(w.err, h->stream);
     // orthonormal-basis transfer (option): the coarse LMO on G R C^{-1}, lifted by R C^{-1}
     const bool orth = H > 0 && o.transfer == 1;
     OrthTransfer<T> ot;
@@ -1685,6 +1725,7 @@ cpcp_status fwt_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, con
                              st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
+    tc_err_check(w.err, st);
     if (info) {
         cpcp_info inf;
         memset(&inf, 0, sizeof(inf));
@@ -1799,6 +1840,7 @@ cpcp_status step_impl(cpcp_context *h, int m, int n, const void *Dv, int64_t ldd
         throw CpcpError{CPCP_ERR_INVALID_ARG, "k must satisfy 1 <= k <= min(n_H, " +
                                                   std::to_string(kmax_small<T>()) + ")"};
     SvdWork<T> w = svd_work<T>(h, "st_", m, n, k);
+    tc_err_clear(w.err, h->stream);
     const int KM = w.KM;
     Ctrl c;
     memset(&c, 0, sizeof(c));
@@ -1893,6 +1935,7 @@ cpcp_status step_impl(cpcp_context *h, int m, int n, const void *Dv, int64_t ldd
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     if (tc_flag) throw CpcpError{CPCP_ERR_TIMEOUT, "a bounded wait of the tensor-core pass expired"};
+    tc_err_check(w.err, st);
     if (r_out) *r_out = out.r_new;
     return CPCP_OK;
 }
@@ -1906,6 +1949,7 @@ cpcp_status svd_impl(cpcp_context *h, int m, int n, const void *Mv, int64_t ldm,
         throw CpcpError{CPCP_ERR_INVALID_ARG, "k must satisfy 1 <= k <= min(n, " +
                                                   std::to_string(kmax_small<T>()) + ")"};
     SvdWork<T> w = svd_work<T>(h, "sv_", m, n, k);
+    tc_err_clear(w.err, h->stream);
     const int KM = w.KM;
     const bool bf16 = std::is_same<T, float>::value && h->opt.precision == 1;
     if (bf16) {
@@ -1935,11 +1979,7 @@ cpcp_status svd_impl(cpcp_context *h, int m, int n, const void *Mv, int64_t ldm,
     CK(cudaGetLastError());
     std::vector<double> sd(sh.begin(), sh.end());
     CK(cudaMemcpy(sigma, sd.data(), sizeof(double) * k, cudaMemcpyDefault));
-    if (bf16) {
-        int e = 0;
-        CK(cudaMemcpy(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (e) throw CpcpError{CPCP_ERR_TIMEOUT, "a bounded wait of the tensor-core kernel expired"};
-    }
+    tc_err_check(w.err, st);
     return CPCP_OK;
 }
 
@@ -2720,6 +2760,8 @@ cpcp_status cpcp_solve(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D
             throw CpcpError{CPCP_ERR_INVALID_ARG, "subspace_mode must be 0"};
         if (h->opt.early_test < -1 || h->opt.early_test > 1)
             throw CpcpError{CPCP_ERR_INVALID_ARG, "early_test must be -1, 0 or 1"};
+        if (h->opt.products_tc < -1 || h->opt.products_tc > 1)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "products_tc must be -1, 0 or 1"};
         if (h->opt.unroll > 0) {
             if (dt != CPCP_F32) throw CpcpError{CPCP_ERR_INVALID_ARG, "the unrolled program is fp32"};
             if (h->opt.transfer == 1)

@@ -3,7 +3,7 @@ the solver report (for profiling a solve under a profiler or by hand).
 
     python -m paper_2206_13369_gb300.run_solve --m 2000 --n 2000 --rank 50 \\
         --levels 3 --max-iter 200 [--fp64] [--power-iters 1] [--tol 1e-6]
-        [--precision 1] [--unroll K --rho R]
+        [--precision 1] [--products-tc 1] [--unroll K --rho R]
 
 The workload is workloads.planted_cpcp(m, n, rank, corruption, observed, seed),
 or with --config N one of the numbered workloads of workloads.config (3 is the
@@ -38,6 +38,8 @@ def main() -> int:
     ap.add_argument("--plain-launches", action="store_true", help="no CUDA graph replay of iterations")
     ap.add_argument("--config", type=int, default=0, help="use workloads.config(N) instead of planted_cpcp")
     ap.add_argument("--precision", type=int, default=0, help="1: BF16 tensor-core contractions, then fp32")
+    ap.add_argument("--products-tc", type=int, default=0,
+                    help="subspace products M Omega, M^T Q: 1 tensor cores, -1 SIMT, 0 by height")
     ap.add_argument("--transfer", type=int, default=0,
                     help="1: an orthonormal basis of the range of R on the coarse levels")
     ap.add_argument("--unroll", type=int, default=0, help="K > 0: the K-step differentiable program and its "
@@ -74,7 +76,7 @@ def main() -> int:
     Q = None if p["mask"] is None else torch.as_tensor(cpcp.pack_mask(p["mask"])).cuda()
     opts = dict(max_iter=args.max_iter, power_iters=args.power_iters, profile=int(args.profile),
                 pass_simt=int(args.pass_simt), plain_launches=int(args.plain_launches),
-                precision=args.precision, transfer=args.transfer)
+                precision=args.precision, transfer=args.transfer, products_tc=args.products_tc)
     if args.unroll > 0:
         opts.update(unroll=args.unroll, rho=args.rho)
     with cpcp.Handle(0, **opts) as h:

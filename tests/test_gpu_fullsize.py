@@ -71,19 +71,22 @@ def sampled_errors(p, L, S, name):
     return eL, eS, supp_ok, int(safe.sum())
 
 
-def test_cpcp2000_fp32_matches_oracle_optimum(cp):
+@pytest.mark.parametrize("ptc", [-1, 1])
+def test_cpcp2000_fp32_matches_oracle_optimum(cp, ptc):
     # solved to 7e-7, just above the fp32 path's residual floor on this workload
     # (6.5e-7 measured); the optimum moves about 2x the residual here, so the
-    # attainable error is about 1.3e-6: held to 2e-6
+    # attainable error is about 1.3e-6: held to 2e-6.  ptc: the subspace
+    # products on the SIMT (-1) or tensor (1) cores
     p = W.config(2)
     D = torch.as_tensor(p["D"], dtype=torch.float32).cuda()
     Q = torch.as_tensor(cp.pack_mask(p["mask"])).cuda()
-    with cp.Handle(0, max_iter=600) as h:
+    with cp.Handle(0, max_iter=600, products_tc=ptc) as h:
         L, S, info = h.solve(D, Q, p["lam"], p["mu"], levels=3, tol=7e-7)
     assert info["status"] in (0, 5) and info["relkkt"] <= 7.5e-7, info
     L, S = L.double().cpu().numpy(), S.double().cpu().numpy()
     eL, eS, supp_ok, nsafe = sampled_errors(p, L, S, "cpcp2000")
-    print(f"cpcp2000 fp32: sampled rel err L {eL:.3e} S {eS:.3e} relkkt {info['relkkt']:.3e} iters {info['iters']}")
+    print(f"cpcp2000 fp32 ptc={ptc}: sampled rel err L {eL:.3e} S {eS:.3e} relkkt {info['relkkt']:.3e} "
+          f"iters {info['iters']}")
     assert eL <= 2e-6 and eS <= 2e-6
     assert supp_ok and nsafe > 1400
     assert np.all(S[~p["mask"]] == 0)
@@ -104,21 +107,23 @@ def test_cpcp2000_bench_tolerance_error(cp):
     assert eL <= 3e-6 and eS <= 3e-6 and supp_ok
 
 
-@pytest.mark.parametrize("precision,transfer,tol,bar", [(1, 0, 1e-6, 1e-4), (1, 1, 1e-6, 1e-4), (0, 0, 4e-7, 2e-6)])
-def test_video_matches_oracle_optimum(cp, precision, transfer, tol, bar):
+@pytest.mark.parametrize("precision,transfer,tol,bar,ptc", [(1, 0, 1e-6, 1e-4, 0), (1, 1, 1e-6, 1e-4, 0),
+                                                            (0, 0, 4e-7, 2e-6, 0), (0, 0, 4e-7, 2e-6, -1)])
+def test_video_matches_oracle_optimum(cp, precision, transfer, tol, bar, ptc):
     # the mixed path (this workload's precision pattern) at the benchmark's tolerance,
     # within 1e-4; the fp32 path solved to 4e-7, near its residual floor of about
     # 3.5e-7, where this workload's optimum moves about 4x the residual (measured
-    # 1.4e-6), within 2e-6
+    # 1.4e-6), within 2e-6.  ptc 0: the default choice of product kernels (the
+    # tensor cores at this height), -1: SIMT
     p = W.config(3)
     D = torch.as_tensor(p["D"], dtype=torch.float32).cuda()
     Q = torch.as_tensor(cp.pack_mask(p["mask"])).cuda()
-    with cp.Handle(0, precision=precision, transfer=transfer, max_iter=1500) as h:
+    with cp.Handle(0, precision=precision, transfer=transfer, max_iter=1500, products_tc=ptc) as h:
         L, S, info = h.solve(D, Q, p["lam"], p["mu"], levels=4, tol=tol)
     assert info["status"] in (0, 5) and info["relkkt"] <= 1.25 * tol, info
     L, S = L.double().cpu().numpy(), S.double().cpu().numpy()
     eL, eS, supp_ok, _ = sampled_errors(p, L, S, "video")
-    print(f"video precision={precision} transfer={transfer}: sampled rel err L {eL:.3e} S {eS:.3e} "
+    print(f"video precision={precision} transfer={transfer} ptc={ptc}: sampled rel err L {eL:.3e} S {eS:.3e} "
           f"relkkt {info['relkkt']:.3e} iters {info['iters']}")
     assert eL <= bar and eS <= bar
     assert oracle.relkkt(p["D"], p["mask"], p["lam"], p["mu"], L, S) <= 2e-6

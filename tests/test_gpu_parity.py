@@ -81,16 +81,18 @@ def test_restrict_prolong_match_oracle(h, n, hv, dt):
 # subspace SVD
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("dt,fused", [(torch.float64, 0), (torch.float32, 0), (torch.float32, 1)])
-@pytest.mark.parametrize("shape", [(150, 60), (97, 33), (64, 64), (2000, 120), (3001, 17)])
-def test_svd_full_width_exact(cp, dt, fused, shape):
-    # fused = 1: fp32 CholeskyQR2 in one thread-block cluster launch; 0: six launches
+@pytest.mark.parametrize("dt,fused,ptc", [(torch.float64, 0, 0), (torch.float32, 0, -1), (torch.float32, 0, 1),
+                                           (torch.float32, 1, 1)])
+@pytest.mark.parametrize("shape", [(150, 60), (97, 33), (64, 64), (2000, 120), (3001, 17), (6000, 40)])
+def test_svd_full_width_exact(cp, dt, fused, ptc, shape):
+    # fused = 1: fp32 CholeskyQR2 in one thread-block cluster launch; 0: six launches.
+    # ptc: the products with M on the tensor cores (1) or the SIMT cores (-1)
     rng = np.random.default_rng(5)
     m, n = shape
     if dt == torch.float64 and n > 80:
         pytest.skip("fp64 subspace width is at most 80")
     A = rng.normal(size=(m, n)) @ np.diag(np.linspace(1, 0.05, n)) @ np.linalg.qr(rng.normal(size=(n, n)))[0]
-    with cp.Handle(0, cholqr_fused=fused) as h:
+    with cp.Handle(0, cholqr_fused=fused, products_tc=ptc) as h:
         U, s, V = h.svd(dev(A, dt), k=n, q=2)
     s_ref = np.linalg.svd(A, compute_uv=False)
     # fp32: backward error of the fp32 contractions, about sqrt(m) eps ||M||
