@@ -389,22 +389,63 @@ __global__ void __launch_bounds__(CQ_NT, 1) chol_q_kernel(const float *__restric
     }
     for (int c = tid; c < 4 * 64; c += CQ_NT) rowf[c] = 0.f;  // rowf and rowg
     __syncthreads();
+    // (eight entries per thread at a time, every load of a batch issued before
+    // the first is used: the partials sit in L2, and one round trip per entry
+    // was most of a small factorisation's time)
     double defect = 0.0;
-    for (int idx = tid; idx < k * k; idx += CQ_NT) {
-        const int x = idx / k, y = idx - (idx / k) * k;
-        if (x > y) continue;
-        const float dx = dsc[x], dy = dsc[y];
-        const float v = (dx > 0.f && dy > 0.f) ? chol_gram_entry(partial, splits, slice, kmax, x, y) / dx / dy : 0.f;
-        Gs[x * ldg + y] = v;
-        const float ev = v - (x == y ? 1.f : 0.f);
-        defect += (x == y ? 1.0 : 2.0) * (double)(ev * ev);
+    for (int base = 0; base < k * k; base += 8 * CQ_NT) {
+        float acc[8];
+        const float *src[8];
+        bool use[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int idx = base + u * CQ_NT + tid;
+            const int x = idx / k, y = idx - (idx / k) * k;
+            use[u] = idx < k * k && x <= y && dsc[x] > 0.f && dsc[y] > 0.f;
+            src[u] = partial + (use[u] ? (int64_t)x * kmax + y : 0);
+            acc[u] = 0.f;
+        }
+        int q = 0;
+        for (; q + 4 <= splits; q += 4) {
+            float v[8][4];
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+#pragma unroll
+                for (int t = 0; t < 4; t++) v[u][t] = use[u] ? src[u][(q + t) * slice] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; u++) acc[u] += (v[u][0] + v[u][1]) + (v[u][2] + v[u][3]);
+        }
+        for (; q < splits; q++)
+#pragma unroll
+            for (int u = 0; u < 8; u++) acc[u] += use[u] ? src[u][q * slice] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int idx = base + u * CQ_NT + tid;
+            const int x = idx / k, y = idx - (idx / k) * k;
+            if (idx >= k * k || x > y) continue;
+            const float v = use[u] ? acc[u] / dsc[x] / dsc[y] : 0.f;
+            Gs[x * ldg + y] = v;
+            const float ev = v - (x == y ? 1.f : 0.f);
+            defect += (x == y ? 1.0 : 2.0) * (double)(ev * ev);
+        }
     }
     defect = warp_sum(defect);
     if (lane == 0) red[warp] = defect;
     if (Rprev != nullptr)
-        for (int idx = tid; idx < k * k; idx += CQ_NT) {
-            const int i = idx / k, c = idx - (idx / k) * k;
-            Ps[i * ldg + c] = Rprev[(int64_t)i * ldr + c];
+        for (int base = 0; base < k * k; base += 8 * CQ_NT) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int idx = base + u * CQ_NT + tid;
+                const int i = idx / k, c = idx - (idx / k) * k;
+                v[u] = idx < k * k ? Rprev[(int64_t)i * ldr + c] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int idx = base + u * CQ_NT + tid;
+                const int i = idx / k, c = idx - (idx / k) * k;
+                if (idx < k * k) Ps[i * ldg + c] = v[u];
+            }
         }
     __syncthreads();
     if (tid == 0 && well_out != nullptr) {
@@ -421,11 +462,7 @@ __global__ void __launch_bounds__(CQ_NT, 1) chol_q_kernel(const float *__restric
         const float r0 = y < k ? S[0] : 0.f;
         rowf[y] = r0;
         rowg[y] = y > 0 ? r0 : 0.f;
-        if (y == 0) {
-            const bool dj = !(r0 > tol);
-            rinv[0] = dj ? 0.f : 1.f / r0;
-            piv[0] = dj ? 0.f : sqrtf(r0);
-        }
+        if (y == 0) rinv[0] = !(r0 > tol) ? 0.f : __frcp_rn(r0);
     }
     for (int j = 0; j < k; j++) {
         __syncthreads();
@@ -450,27 +487,36 @@ __global__ void __launch_bounds__(CQ_NT, 1) chol_q_kernel(const float *__restric
             for (int t = 0; t < 16; t++)
                 if (x0 + t <= xmax) S[t] = fmaf(-cf, g[t], S[t]);
         }
-        // publish row j + 1 (the owner of its diagonal: the pivot); S[jn - x0]
-        // by selects that the compiler cannot turn into an indexed
+        // publish row j + 1 (the owner of its diagonal: the pivot's reciprocal;
+        // the pivot itself is kept and its square root taken after the loop).
+        // S[jn - x0] by independent selects summed in a tree (exact: all but
+        // one are zero), in asm the compiler cannot turn into an indexed
         // (local-memory) load, which would take S out of registers
         const int jn = j + 1;
         if (jn < k && (jn >> 4) == q) {
-            float pub = 0.f;
+            float sel[16];
 #pragma unroll
             for (int t = 0; t < 16; t++)
-                asm("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %2, %3;\n\tselp.f32 %0, %1, %0, p;\n\t}"
-                    : "+f"(pub)
+                asm("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %2, %3;\n\tselp.f32 %0, %1, 0f00000000, p;\n\t}"
+                    : "=f"(sel[t])
                     : "f"(S[t]), "r"(x0 + t), "r"(jn));
-            if (y >= k) pub = 0.f;
+#pragma unroll
+            for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+                for (int t = 0; t < w; t++) sel[t] += sel[t + w];
+            const float pub = y >= k ? 0.f : sel[0];
             rowf[(b ^ 1) * 64 + y] = pub;
             rowg[(b ^ 1) * 64 + y] = y > jn ? pub : 0.f;
             if (y == jn) {
                 const bool dj = !(pub > tol);
-                rinv[b ^ 1] = dj ? 0.f : 1.f / pub;
-                piv[jn] = dj ? 0.f : sqrtf(pub);
+                rinv[b ^ 1] = dj ? 0.f : __frcp_rn(pub);
+                piv[jn] = dj ? 0.f : pub;
             }
         }
     }
+    if (q == 0 && y == 0) piv[0] = rinv[0] > 0.f ? S[0] : 0.f;
+    __syncthreads();
+    for (int c = tid; c < k; c += CQ_NT) piv[c] = sqrtf(piv[c]);
     // the columns back to shared memory (each thread its own quarter)
     if (y < k) {
 #pragma unroll
