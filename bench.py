@@ -180,7 +180,11 @@ def golden_error(name: str, L, S) -> dict | None:
 # (dram__bytes_read.sum + dram__bytes_write.sum); None where not captured for the
 # kernel as it stands
 TRAFFIC = {
-    "fused fine pass": (51.55e6, "profiles/pass_tc_cpcp2000.md"),
+    "fused fine pass": (50.8e6, "profiles/dram_cpcp2000.md"),
+    "products with M": (16.54e6, "profiles/dram_cpcp2000.md"),
+    "CholeskyQR2": (1.89e6, "profiles/dram_cpcp2000.md"),
+    "core Jacobi SVD": (0.081e6, "profiles/dram_cpcp2000.md"),
+    "factor products": (0.55e6, "profiles/dram_cpcp2000.md"),
 }
 FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
 
@@ -199,9 +203,10 @@ def kernel_families(prof: dict, m: int, n: int, peaks: dict) -> list:
          20 * m * n + 4 * m * math.ceil(n / 32)),
         ("coarse pass", "pass_kernel (step, with restriction)", ph["pass_coarse"], cnt["pass_coarse"], "hbm",
          16 * m * n + 4 * m * math.ceil(n / 32) + 4 * m * math.ceil(n / 2)),
-        ("products with M", "ts_gemm_kernel (M Omega, M^T Q)", det["products"], 2 * its, "hbm",
+        ("products with M", "ts_gemm_kernel (M Omega, M^T Q; prod_tc_kernel from 4096 rows)", det["products"],
+         2 * its, "hbm",
          4 * (m * n + n * k + m * k)),
-        ("CholeskyQR2", "chol_kernel with ts_gemm Gram and Q products", det["cholqr"], 2 * its, "alu",
+        ("CholeskyQR2", "chol_q_kernel with ts_gemm Gram and Q products", det["cholqr"], 2 * its, "alu",
          2 * (3 * m * k * k + k ** 3 / 3)),
         ("core Jacobi SVD", "jacobi_kernel", det["jacobi"], its, "alu", sweeps * (k * k / 2) * 12 * k),
         ("factor products", "ts_gemm_kernel (A = Q U, V = Q W) and fill_prolong", det["factors"], 3 * its, "hbm",
@@ -224,6 +229,18 @@ def kernel_families(prof: dict, m: int, n: int, peaks: dict) -> list:
                     "avg_launch_ms": avg, "work_per_launch": work, "bound": bound, "achieved": ach, "peak": peak,
                     "unit": unit, "frac": ach / peak, "peak_source": src,
                     "traffic": tr[0] if tr else None, "traffic_source": tr[1] if tr else None})
+    return out
+
+
+def per_level_ms(infos) -> dict:
+    """Device time of one iteration at each level (number of halvings), from
+    the phase events of the timed solves (pass and SVT phases, residual checks
+    excluded), averaged over the solves."""
+    out = {}
+    for lv in range(8):
+        it = sum(i["level_iters"][lv] for i in infos)
+        if it > 0:
+            out[str(lv)] = sum(i["level_ms"][lv] for i in infos) / it
     return out
 
 
@@ -393,7 +410,9 @@ def run_ours(args):
             "single_level": {"value": sl, "unit": "s", "iters": inf_sl[-1]["iters"], "err_vs_oracle": err_sl},
             "multilevel_over_single": ml / sl,
             "multilevel": {"iters": inf_ml[-1]["iters"], "level_iters": inf_ml[-1]["level_iters"][:3],
-                           "relkkt": inf_ml[-1]["relkkt"], "rank": inf_ml[-1]["rank"], "err_vs_oracle": err_ml},
+                           "relkkt": inf_ml[-1]["relkkt"], "rank": inf_ml[-1]["rank"], "err_vs_oracle": err_ml,
+                           "ms_per_iter_by_level": per_level_ms(inf_ml),
+                           "single_level_ms_per_iter": per_level_ms(inf_sl).get("0")},
             "clocks": clocks_info,
             "e2e": {"value": statistics.mean(e2e), "unit": "s",
                     "h2d_bytes_per_step": int(Dh.nbytes + Qhp.nbytes),
@@ -465,11 +484,12 @@ def extras(device, stream, flush) -> dict:
     vm = {}
     for name, prec, lv, tr in (("mixed_4lv", 1, 4, 0), ("fp32_4lv", 0, 4, 0), ("mixed_1lv", 1, 1, 0),
                                ("fp32_1lv", 0, 1, 0), ("mixed_4lv_orth", 1, 4, 1), ("fp32_4lv_orth", 0, 4, 1)):
-        with cpcp.Handle(device, stream=stream, precision=prec, transfer=tr) as hh:
+        with cpcp.Handle(device, stream=stream, precision=prec, transfer=tr, profile=1) as hh:
             hh.solve(D, Q, v["lam"], v["mu"], levels=lv, tol=TOL)
             t, (Lv, Sv, info) = _events_time(stream, lambda: hh.solve(D, Q, v["lam"], v["mu"], levels=lv, tol=TOL),
                                              3, flush)
         vm[name] = {"s": t, "iters": info["iters"], "level_iters": info["level_iters"][:lv], "bf16_iters": info["bf16_iters"],
+                    "ms_per_iter_by_level": per_level_ms([info]),
                     "relkkt": info["relkkt"], "err_vs_oracle": golden_error("video", Lv, Sv)}
         del Lv, Sv
     out["video_mixed"] = {"workload": "video-19200x400-r5-cpcp", "unit": "s", "tol": TOL, **vm}
@@ -521,12 +541,14 @@ def extras(device, stream, flush) -> dict:
     Q = torch.as_tensor(cpcp.pack_mask(c6["mask"])).cuda()
     hs = {}
     for name, lv, tr in (("3lv", 3, 0), ("1lv", 1, 0), ("3lv_orth", 3, 1)):
-        with cpcp.Handle(device, stream=stream, transfer=tr) as hh:
+        with cpcp.Handle(device, stream=stream, transfer=tr, profile=1) as hh:
             hh.solve(D, Q, c6["lam"], c6["mu"], levels=lv, tol=TOL)
-            t, (_, _, info) = _events_time(stream, lambda: hh.solve(D, Q, c6["lam"], c6["mu"], levels=lv, tol=TOL), 3,
-                                           flush)
+            t, (Lh6, Sh6, info) = _events_time(stream, lambda: hh.solve(D, Q, c6["lam"], c6["mu"], levels=lv, tol=TOL),
+                                               3, flush)
         hs[name] = {"s": t, "iters": info["iters"], "level_iters": info["level_iters"][:lv], "relkkt": info["relkkt"],
-                    "rank": info["rank"]}
+                    "rank": info["rank"], "ms_per_iter_by_level": per_level_ms([info]),
+                    "err_vs_oracle": golden_error("hyperspectral", Lh6, Sh6)}
+        del Lh6, Sh6
     out["hyperspectral"] = {"workload": "hyperspectral-65536x128-r8-cpcp", "unit": "s", "tol": TOL, **hs,
                             "multilevel_over_single": hs["3lv"]["s"] / hs["1lv"]["s"],
                             "multilevel_orth_over_single": hs["3lv_orth"]["s"] / hs["1lv"]["s"]}

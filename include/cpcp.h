@@ -195,6 +195,9 @@ typedef struct {
     int batch_threads;     /* cpcp_solve_batched: threads per CTA of the launch (256 or 512) */
     int batch_tile;        /* cpcp_solve_batched: output tiles of the CTA products wider than 32
                               columns, 0 = 64 x 64, 1 = 128 x 64 (the autotuner's choice, or 0) */
+    double level_ms[8];    /* cpcp_solve with profile: device time of the iterations at each
+                              number of halvings (their pass and SVT phases; residual checks
+                              excluded); divided by level_iters, the cost of one iteration there */
 } cpcp_info;
 
 /* One instance of cpcp_solve_batched (fp32, device pointers; conventions as

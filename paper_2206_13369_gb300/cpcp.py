@@ -47,7 +47,8 @@ class Info(C.Structure):
                 ("pqd_fro", C.c_double), ("seconds", C.c_double), ("phase_ms", C.c_double * 4),
                 ("phase_count", C.c_int * 4), ("launches", C.c_longlong), ("bf16_iters", C.c_int),
                 ("svt_detail_ms", C.c_double * 4), ("jacobi_calls", C.c_int), ("jacobi_sweeps", C.c_int),
-                ("chol_factors", C.c_int), ("batch_threads", C.c_int), ("batch_tile", C.c_int)]
+                ("chol_factors", C.c_int), ("batch_threads", C.c_int), ("batch_tile", C.c_int),
+                ("level_ms", C.c_double * 8)]
 
     PHASES = ("pass_coarse", "pass_fine", "svt", "check")
 
@@ -61,7 +62,7 @@ class Info(C.Structure):
                 "svt_detail_ms": dict(zip(("products", "cholqr", "jacobi", "factors"), list(self.svt_detail_ms))),
                 "jacobi_calls": self.jacobi_calls, "jacobi_sweeps": self.jacobi_sweeps,
                 "chol_factors": self.chol_factors, "batch_threads": self.batch_threads,
-                "batch_tile": self.batch_tile}
+                "batch_tile": self.batch_tile, "level_ms": list(self.level_ms)}
 
 
 _vp, _i64, _int, _dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double

@@ -71,7 +71,7 @@ struct BatchGraph {
 struct PhaseTimer {
     struct Pair {
         cudaEvent_t a, b;
-        int phase;
+        int phase, level;
     };
     // phases 0-3: CPCP_PHASE_*; with profile >= 2 also the SVT phase of the
     // iterations split into 4: products with M, 5: CholeskyQR, 6: core Jacobi SVD,
@@ -81,6 +81,9 @@ struct PhaseTimer {
     std::vector<Pair> pending;
     double ms[NPH] = {0, 0, 0, 0, 0, 0, 0, 0};
     int count[NPH] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // device time of the iterations (pass and SVT phases) by level
+    double lvl_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int level = 0;  // level of the intervals opened next
     bool on = false;
     bool detail = false;   // profile >= 2
     bool in_iter = false;  // inside an iteration's SVT phase (not a residual check)
@@ -104,7 +107,7 @@ struct PhaseTimer {
     int open(int phase)
     {
         if (!on) return -1;
-        Pair p{take(), take(), phase};
+        Pair p{take(), take(), phase, level};
         cudaEventRecord(p.a, st);
         pending.push_back(p);
         return (int)pending.size() - 1;
@@ -121,6 +124,7 @@ struct PhaseTimer {
             if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
                 ms[p.phase] += t;
                 count[p.phase]++;
+                if (p.phase <= CPCP_PHASE_SVT && p.level >= 0 && p.level < 8) lvl_ms[p.level] += t;
             }
             pool.push_back(p.a);
             pool.push_back(p.b);
@@ -134,6 +138,8 @@ struct PhaseTimer {
             ms[i] = 0;
             count[i] = 0;
         }
+        for (int i = 0; i < 8; i++) lvl_ms[i] = 0;
+        level = 0;
         on = enable;
         detail = enable && sub;
         in_iter = false;
@@ -1212,6 +1218,7 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
         const bool decide = (iter + 1) % o.check_every == 0;
         const bool early = o.early_test && level > 0 && iter == level_start;
         const bool want_g = (decide || early) && level > 0;
+        h->timer.level = level;
         if (use_graphs && !want_g && !s.bf16 && level < 8) {
             // the schedule update and the fused pass are launched directly (the
             // profile's events bracket the pass); the rest of the iteration is
@@ -1357,6 +1364,7 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
         inf.phase_count[i] = h->timer.count[i];
         inf.svt_detail_ms[i] = h->timer.ms[DETAIL_PROD_M + i];
     }
+    for (int i = 0; i < 8; i++) inf.level_ms[i] = h->timer.lvl_ms[i];
     if (info) *info = inf;
     return status;
 }

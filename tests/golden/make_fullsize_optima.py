@@ -1,6 +1,7 @@
 """Writes sampled entries of the fp64 oracle's optimum of eq. (cpcp) for the
-full-size CPCP workloads (the 2000 x 2000 rank-50 workload and the 19200 x 400
-video-shaped workload), for the full-size GPU parity tests.
+full-size CPCP workloads (the 2000 x 2000 rank-50 workload, the 19200 x 400
+video-shaped workload and the 65536 x 128 hyperspectral-shaped workload), for
+the full-size GPU parity tests and the benchmark's error columns.
 
 Only ``oracle/`` computes anything here (``oracle.fista``, single level, the
 plain full-SVD iteration; the optimum of the convex program does not depend on
@@ -13,7 +14,7 @@ entry: 1024 entries drawn uniformly (seeded) and 512 drawn from the support of
 the oracle's S.
 
 Run (takes tens of minutes on a few cores):
-    python tests/golden/make_fullsize_optima.py [cpcp2000] [video]
+    python tests/golden/make_fullsize_optima.py [cpcp2000] [video] [hyperspectral]
 """
 import os
 import sys
@@ -32,6 +33,7 @@ TOL = 1e-9
 WORKLOADS = {
     "cpcp2000": lambda: W.config(2),
     "video": lambda: W.config(3),
+    "hyperspectral": lambda: W.config(6),
 }
 
 

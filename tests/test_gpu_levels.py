@@ -85,3 +85,21 @@ def test_early_test_option_is_validated(cp):
         with pytest.raises(cp.CPCPError) as e:
             h.solve(D, None, 0.1, 1.0)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("profile", [1, 2])
+def test_level_times_add_up(cp, profile):
+    # the per-level device times of a profiled solve: positive exactly on the
+    # levels that ran iterations, and together the iterations' pass and SVT
+    # phase times (residual checks are not counted at any level)
+    v = W.video_cpcp(7, h=16, w=24, frames=64, rank=2, blocks=3, block=4, obs=0.8, levels=3)
+    Qb = torch.as_tensor(cp.pack_mask(v["mask"])).cuda()
+    with cp.Handle(0, transfer=1, profile=profile) as h:
+        _, _, info = h.solve(dev(v["D"], torch.float32), Qb, v["lam"], v["mu"], levels=3, tol=1e-6)
+    assert info["status"] == 0, info
+    lm, li = info["level_ms"], info["level_iters"]
+    for lv in range(8):
+        assert (lm[lv] > 0) == (li[lv] > 0), (lm, li)
+    ph = info["phase_ms"]
+    tot = ph["pass_coarse"] + ph["pass_fine"] + ph["svt"]
+    assert abs(sum(lm) - tot) <= 1e-9 * max(tot, 1.0) + 1e-6, (lm, ph)
