@@ -156,6 +156,17 @@ typedef struct {
                               arithmetic either way up to the summation order of the Gram
                               matrices.  Measured on GB300: 6% slower on the 2000 x 2000 workload
                               (k = 60), a few percent faster on the 19200 x 400 video shape */
+    int check_serial;      /* cpcp_solve: nonzero runs every fine residual check before the next
+                              iteration starts.  0 (default), with graph replay (plain_launches 0,
+                              profile < 2): a check on the fine level (fp32 contractions) runs on a
+                              second, low-priority stream from a copy of the checked iterate while
+                              the solve stream computes up to five further iterations (none of
+                              them a decision point; one where the last two checks' rate predicts
+                              that this check stops the solve); they count if the check lets the
+                              solve go on, and are dropped (the checked iterate restored) if it
+                              stops it.
+                              Same iterates, decisions and result either way; the overlap costs
+                              two more m x n buffers */
 } cpcp_options;
 
 /* Phases timed when cpcp_options.profile is set. */

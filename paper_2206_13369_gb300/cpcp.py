@@ -38,7 +38,8 @@ class Options(C.Structure):
                 ("batch_threads", C.c_int), ("batch_autotune", C.c_int), ("unroll", C.c_int),
                 ("ckpt_every", C.c_int), ("rho", C.c_double), ("subspace_mode", C.c_int),
                 ("pass_simt", C.c_int), ("plain_launches", C.c_int), ("transfer", C.c_int),
-                ("early_test", C.c_int), ("products_tc", C.c_int), ("cholqr_fused", C.c_int)]
+                ("early_test", C.c_int), ("products_tc", C.c_int), ("cholqr_fused", C.c_int),
+                ("check_serial", C.c_int)]
 
 
 class Info(C.Structure):

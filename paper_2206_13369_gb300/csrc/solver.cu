@@ -72,6 +72,7 @@ struct PhaseTimer {
     struct Pair {
         cudaEvent_t a, b;
         int phase, level;
+        bool spec;  // an iteration run while a residual check decides whether it counts
     };
     // phases 0-3: CPCP_PHASE_*; with profile >= 2 also the SVT phase of the
     // iterations split into 4: products with M, 5: CholeskyQR, 6: core Jacobi SVD,
@@ -83,7 +84,8 @@ struct PhaseTimer {
     int count[NPH] = {0, 0, 0, 0, 0, 0, 0, 0};
     // device time of the iterations (pass and SVT phases) by level
     double lvl_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int level = 0;  // level of the intervals opened next
+    int level = 0;      // level of the intervals opened next
+    bool spec = false;  // the intervals opened next belong to speculative iterations
     bool on = false;
     bool detail = false;   // profile >= 2
     bool in_iter = false;  // inside an iteration's SVT phase (not a residual check)
@@ -107,7 +109,7 @@ struct PhaseTimer {
     int open(int phase)
     {
         if (!on) return -1;
-        Pair p{take(), take(), phase, level};
+        Pair p{take(), take(), phase, level, spec};
         cudaEventRecord(p.a, st);
         pending.push_back(p);
         return (int)pending.size() - 1;
@@ -116,10 +118,17 @@ struct PhaseTimer {
     {
         if (idx >= 0) cudaEventRecord(pending[idx].b, st);
     }
-    // after a stream synchronisation: fold finished intervals into the totals
+    // after a stream synchronisation, with no interval open: fold the finished
+    // intervals into the totals; those of speculative iterations wait for
+    // keep_spec() or drop_spec()
     void harvest()
     {
+        std::vector<Pair> keep;
         for (auto &p : pending) {
+            if (p.spec) {
+                keep.push_back(p);
+                continue;
+            }
             float t = 0.f;
             if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
                 ms[p.phase] += t;
@@ -129,7 +138,27 @@ struct PhaseTimer {
             pool.push_back(p.a);
             pool.push_back(p.b);
         }
-        pending.clear();
+        pending.swap(keep);
+    }
+    // the speculative iterations count: their intervals are folded like others
+    void keep_spec()
+    {
+        for (auto &p : pending) p.spec = false;
+    }
+    // the speculative iterations are discarded (their stream has been
+    // synchronised): their intervals are dropped
+    void drop_spec()
+    {
+        std::vector<Pair> keep;
+        for (auto &p : pending) {
+            if (p.spec) {
+                pool.push_back(p.a);
+                pool.push_back(p.b);
+            } else {
+                keep.push_back(p);
+            }
+        }
+        pending.swap(keep);
     }
     void reset(bool enable, cudaStream_t s, bool sub = false)
     {
@@ -140,6 +169,8 @@ struct PhaseTimer {
         }
         for (int i = 0; i < 8; i++) lvl_ms[i] = 0;
         level = 0;
+        drop_spec();
+        spec = false;
         on = enable;
         detail = enable && sub;
         in_iter = false;
@@ -170,6 +201,12 @@ struct cpcp_context {
     // the two events that order it after and before the caller's stream
     cudaStream_t solve_stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // second private stream on which the fine residual check runs while the
+    // solve stream computes the next iterations, the event that orders it after
+    // the snapshot of the checked iterate, and pinned host memory for its results
+    cudaStream_t check_stream = nullptr;
+    cudaEvent_t ev_snap = nullptr;
+    void *check_host = nullptr;
     // transfer tables already uploaded to this handle's workspace, by
     // (operator, n, halvings, element size): built once, reused by every call
     struct TransferCache {
@@ -855,6 +892,11 @@ struct SolveState {
     T *Om, *Omf, *Ac, *Bc;
     Ctrl *ctrl, *cchk;
     double *partial, *sums;
+    // overlapped fine checks: the snapshot of the checked iterate (S, A, B and
+    // the control block) and the check's own M and partial sums
+    T *Ssnap = nullptr, *Asnap = nullptr, *Bsnap = nullptr, *Mc = nullptr;
+    Ctrl *csnap = nullptr;
+    double *partial_c = nullptr, *sums_c = nullptr;
     int partial_blocks;
     bool bf16;  // contractions of the iteration's SVD in BF16 (mixed precision, before refinement)
     int *tc_err = nullptr;  // set: the fine pass runs on the tensor cores (its bounded-wait error flag)
@@ -890,48 +932,83 @@ PassArgs<T> base_args(SolveState<T> &s)
     return a;
 }
 
-// Fine-level residual at (L_k, S_k) = (A[cur] B[cur]^T, S[cur]) for the
-// weight mu_c.  Returns rel-KKT (or +inf when the fine SVT width was
-// insufficient).
+// Where a fine residual check reads the checked iterate and writes its
+// scratch: the solve's live buffers (a check run in order), or a snapshot of
+// the iterate with scratch of its own (a check run on the second stream while
+// the next iterations are computed).  host: pinned memory for the results
+// (six sums, then the check's control block).
 template <typename T>
-double fine_check(cpcp_context *h, SolveState<T> &s, SvdWork<T> &wf, int cur, const Opts &o, double pqd,
-                  double mu_c, int *kf, double *s_part_out, int *rank_out)
+struct CheckSrc {
+    const T *S, *A, *B;
+    const Ctrl *it;  // the iteration's control block at the checked iterate (its rank rk)
+    T *M;
+    double *partial, *sums;
+    double *host;
+};
+
+double *check_host(cpcp_context *h)
+{
+    if (!h->check_host) CK(cudaMallocHost(&h->check_host, 64 + sizeof(Ctrl)));
+    return static_cast<double *>(h->check_host);
+}
+
+// Fine-level residual at (L_k, S_k) = (A B^T, S) of src for the weight mu_c:
+// the launches, on h->stream, ending with the copy of the results to
+// src.host.
+template <typename T>
+void check_launch(cpcp_context *h, SolveState<T> &s, SvdWork<T> &wf, const CheckSrc<T> &src, const Opts &o,
+                  double mu_c)
 {
     cudaStream_t st = h->stream;
     int tmr = h->timer.open(CPCP_PHASE_CHECK);
-    launch_ctrl_set_check(s.cchk, s.ctrl, mu_c, st);
+    launch_ctrl_set_check(s.cchk, src.it, mu_c, st);
     PassArgs<T> a = base_args(s);
     a.ctrl = s.cchk;
-    a.Sk = s.S[cur];
-    a.Ak = s.A[cur];
-    a.Bk = s.B[cur];
-    a.rk = &s.ctrl->rk;
+    a.M = src.M;
+    a.partial = src.partial;
+    a.Sk = src.S;
+    a.Ak = src.A;
+    a.Bk = src.B;
+    a.rk = &src.it->rk;
     int nb = launch_check_pass<T>(a, st);
-    launch_sum_partials(s.partial, nb, 3, s.sums, st);
+    launch_sum_partials(src.partial, nb, 3, src.sums, st);
     // fine SVT of M = L - tau G with width kf, warm-started from the last check
     launch_fill_random<T>(s.Omf, s.KM, s.n, s.cchk, 0, wf.sig, s.KM, 0xC4ECull, st);
     launch_ctrl_take_width(s.cchk, st);
-    subspace_svd<T>(h, wf, s.m, s.n, s.M, s.ldS, s.Omf, o.qc, &s.cchk->k, s.cchk, false, wf.Us, s.cchk);
+    subspace_svd<T>(h, wf, s.m, s.n, src.M, s.ldS, s.Omf, o.qc, &s.cchk->k, s.cchk, false, wf.Us, s.cchk);
     prod_nn_small<T>(s.m, wf.Qy, wf.KM, wf.Us, wf.KM, s.Ac, s.KM, &s.cchk->k, wf.KM, st);
     prod_nn_small<T>(s.n, wf.Qz, wf.KM, wf.Wt, wf.KM, s.Omf, s.KM, &s.cchk->k, wf.KM, st);
     launch_prolong<T>(s.n, s.Omf, s.KM, s.Bc, s.KM, s.tr[0], &s.cchk->r_new, s.KM, st);
     PassArgs<T> b = base_args(s);
     b.ctrl = s.cchk;
-    b.Ak = s.A[cur];
-    b.Bk = s.B[cur];
+    b.M = src.M;
+    b.partial = src.partial;
+    b.Ak = src.A;
+    b.Bk = src.B;
     b.Ap = s.Ac;
     b.Bp = s.Bc;
-    b.rk = &s.ctrl->rk;
+    b.rk = &src.it->rk;
     b.rp = &s.cchk->r_new;
     nb = launch_diff_pass<T>(b, st);
-    launch_sum_partials(s.partial, nb, 3, s.sums + 3, st);
-    double sums[6];
-    Ctrl cc;
+    launch_sum_partials(src.partial, nb, 3, src.sums + 3, st);
     h->timer.close(tmr);
-    CK(cudaMemcpyAsync(sums, s.sums, sizeof(sums), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&cc, s.cchk, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(src.host, src.sums, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(src.host + 8, s.cchk, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+}
+
+// The check's results once stream `st` (the one check_launch used) has run
+// them: rel-KKT (or +inf when the fine SVT width was insufficient), the next
+// check's width, the S part of the residual and the rank of the check's SVT.
+template <typename T>
+double check_finish(cpcp_context *h, SolveState<T> &s, const CheckSrc<T> &src, const Opts &o, double pqd, int *kf,
+                    double *s_part_out, int *rank_out, cudaStream_t st)
+{
     CK(cudaStreamSynchronize(st));
     h->timer.harvest();
+    double sums[6];
+    Ctrl cc;
+    memcpy(sums, src.host, sizeof(sums));
+    memcpy(&cc, src.host + 8, sizeof(Ctrl));
     *s_part_out = sums[0];
     int kcur = cc.k;
     int r = cc.r_new;
@@ -949,6 +1026,17 @@ double fine_check(cpcp_context *h, SolveState<T> &s, SvdWork<T> &wf, int cur, co
     if (saturated) return INFINITY;
     double tau = 0.5;
     return std::sqrt(std::max(sums[0] + sums[3], 0.0)) / tau / pqd;
+}
+
+// Fine-level residual at (L_k, S_k) = (A[cur] B[cur]^T, S[cur]), in order on
+// the solve's stream.
+template <typename T>
+double fine_check(cpcp_context *h, SolveState<T> &s, SvdWork<T> &wf, int cur, const Opts &o, double pqd,
+                  double mu_c, int *kf, double *s_part_out, int *rank_out)
+{
+    const CheckSrc<T> src{s.S[cur], s.A[cur], s.B[cur], s.ctrl, s.M, s.partial, s.sums, check_host(h)};
+    check_launch<T>(h, s, wf, src, o, mu_c);
+    return check_finish<T>(h, s, src, o, pqd, kf, s_part_out, rank_out, h->stream);
 }
 
 // One iteration.  With want_g on a coarse level the pass also restricts the
@@ -1133,6 +1221,23 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     s.partial_blocks = ((n + 63) / 64) * ((m + 63) / 64);
     s.partial = wsT<double>(h, "partial", (size_t)std::max(s.partial_blocks * 3, 512));
     s.sums = wsT<double>(h, "sums", 16);
+    const bool overlap = use_graphs && h->opt.check_serial == 0;
+    if (overlap) {
+        s.Ssnap = wsT<T>(h, "Ssnap", mn);
+        s.Asnap = wsT<T>(h, "Asnap", (size_t)m * s.KM);
+        s.Bsnap = wsT<T>(h, "Bsnap", (size_t)n * s.KM);
+        s.Mc = wsT<T>(h, "Mc", mn);
+        s.csnap = wsT<Ctrl>(h, "csnap", 1);
+        s.partial_c = wsT<double>(h, "partial_c", (size_t)std::max(s.partial_blocks * 3, 512));
+        s.sums_c = wsT<double>(h, "sums_c", 16);
+        if (!h->check_stream) {
+            // lowest priority: the iterations' latency chain goes first
+            int least = 0, greatest = 0;
+            CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+            CK(cudaStreamCreateWithPriority(&h->check_stream, cudaStreamNonBlocking, least));
+        }
+        if (!h->ev_snap) CK(cudaEventCreateWithFlags(&h->ev_snap, cudaEventDisableTiming));
+    }
     SvdWork<T> w = svd_work<T>(h, "it_", m, n, s.kcap0);
     SvdWork<T> wf = svd_work<T>(h, "ck_", m, n, s.kcap0);
     w.stats = wf.stats = wsT<int>(h, "svd_stats", 4);
@@ -1209,20 +1314,16 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     int cur = 0, iter = 0, checks = 0, kf = cc.k, rank = 0;
     int level_start = 0;  // iteration at which the current level began
     double rel = INFINITY, prev = INFINITY;
+    double prev2 = INFINITY;  // the check before prev (on the same level), for the overlap's guess
     cpcp_status status = CPCP_ERR_NOT_CONVERGED;
     IterGraphs graphs;
-    for (iter = 0; iter < o.max_iter;) {
-        // every check_every iterations: a level decision (coarse levels) and,
-        // once the weight is final, the fine residual check; with the early
-        // test also the coarse-gradient test at a coarse level's first iteration
-        const bool decide = (iter + 1) % o.check_every == 0;
-        const bool early = o.early_test && level > 0 && iter == level_start;
-        const bool want_g = (decide || early) && level > 0;
+    // one iteration at the current level and buffer parity: with graph replay
+    // the schedule update and the fused pass are launched directly (the
+    // profile's events bracket the pass) and the rest of the iteration is the
+    // graph
+    auto run_iteration = [&](bool want_g) {
         h->timer.level = level;
         if (use_graphs && !want_g && !s.bf16 && level < 8) {
-            // the schedule update and the fused pass are launched directly (the
-            // profile's events bracket the pass); the rest of the iteration is
-            // the graph
             one_iteration<T>(h, s, w, level, cur, o, false, 1);
             IterGraph &G = graphs.g[level][cur];
             if (G.exec == nullptr && G.seen) {
@@ -1257,6 +1358,15 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
             one_iteration<T>(h, s, w, level, cur, o, want_g);
         }
         cur ^= 1;
+    };
+    for (iter = 0; iter < o.max_iter;) {
+        // every check_every iterations: a level decision (coarse levels) and,
+        // once the weight is final, the fine residual check; with the early
+        // test also the coarse-gradient test at a coarse level's first iteration
+        const bool decide = (iter + 1) % o.check_every == 0;
+        const bool early = o.early_test && level > 0 && iter == level_start;
+        const bool want_g = (decide || early) && level > 0;
+        run_iteration(want_g);
         if (level < 8) inf.level_iters[level]++;
         if (s.bf16) inf.bf16_iters++;
         iter++;
@@ -1276,14 +1386,71 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
         }
         if (decide && !finer && at_final) {
             double spart;
-            rel = fine_check<T>(h, s, wf, cur, o, pqd, mu, &kf, &spart, &rank);
+            // on the fine level the check can only stop the solve or let it go
+            // on: it then runs on the check stream, from a snapshot of the
+            // iterate, while the solve stream computes the next iterations
+            // (none of them a decision point), which count only if it goes on
+            const bool ovl = overlap && level == 0 && !s.bf16;
+            int nspec = 0;
+            const int cur_k = cur;
+            if (ovl) {
+                // iterations computed meanwhile: five while the last two checks'
+                // rate says this one will not stop the solve, else one (the ones
+                // computed beside the stopping check are dropped, and the result
+                // waits for them).  The count changes no result.
+                const bool hist = std::isfinite(prev) && std::isfinite(prev2) && prev2 > 0.0;
+                const int want = (hist && prev * (prev / prev2) <= tol) ? 1 : 5;
+                nspec = std::min({want, o.check_every - 1, o.max_iter - iter});
+                CK(cudaMemcpyAsync(s.Ssnap, s.S[cur], sizeof(T) * (size_t)m * s.ldS, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(s.Asnap, s.A[cur], sizeof(T) * (size_t)m * s.KM, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(s.Bsnap, s.B[cur], sizeof(T) * (size_t)n * s.KM, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(s.csnap, s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToDevice, st));
+                CK(cudaEventRecord(h->ev_snap, st));
+                CK(cudaStreamWaitEvent(h->check_stream, h->ev_snap, 0));
+                const CheckSrc<T> src{s.Ssnap, s.Asnap, s.Bsnap, s.csnap, s.Mc, s.partial_c, s.sums_c, check_host(h)};
+                h->stream = h->check_stream;
+                h->timer.st = h->check_stream;
+                try {
+                    check_launch<T>(h, s, wf, src, o, mu);
+                } catch (...) {
+                    h->stream = st;
+                    h->timer.st = st;
+                    throw;
+                }
+                h->stream = st;
+                h->timer.st = st;
+                h->timer.spec = true;
+                for (int i = 0; i < nspec; i++) run_iteration(false);
+                h->timer.spec = false;
+                rel = check_finish<T>(h, s, src, o, pqd, &kf, &spart, &rank, h->check_stream);
+            } else {
+                rel = fine_check<T>(h, s, wf, cur, o, pqd, mu, &kf, &spart, &rank);
+            }
             if (h->opt.trace && checks < h->opt.trace_cap) h->opt.trace[checks] = rel;
             checks++;
             if (rel <= tol) {
                 status = CPCP_OK;
+                if (ovl) {
+                    // the checked iterate is the result: drop the iterations
+                    // computed meanwhile and put it back in its slot
+                    CK(cudaStreamSynchronize(st));
+                    h->timer.drop_spec();
+                    cur = cur_k;
+                    CK(cudaMemcpyAsync(s.S[cur], s.Ssnap, sizeof(T) * (size_t)m * s.ldS, cudaMemcpyDeviceToDevice,
+                                       st));
+                    CK(cudaMemcpyAsync(s.A[cur], s.Asnap, sizeof(T) * (size_t)m * s.KM, cudaMemcpyDeviceToDevice, st));
+                    CK(cudaMemcpyAsync(s.B[cur], s.Bsnap, sizeof(T) * (size_t)n * s.KM, cudaMemcpyDeviceToDevice, st));
+                    CK(cudaMemcpyAsync(s.ctrl, s.csnap, sizeof(Ctrl), cudaMemcpyDeviceToDevice, st));
+                }
                 break;
             }
+            if (ovl) {
+                h->timer.keep_spec();
+                inf.level_iters[0] += nspec;
+                iter += nspec;
+            }
             if (level > 0 && rel > o.ratio * prev) finer = true;
+            prev2 = prev;
             prev = rel;
             if (s.bf16 && rel <= o.refine_at) {
                 // mixed precision: fp32 contractions from here on, momentum restarts
@@ -1303,6 +1470,7 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
             level--;
             level_start = iter;
             prev = INFINITY;
+            prev2 = INFINITY;
             Ctrl cur_c;
             CK(cudaMemcpyAsync(&cur_c, s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
@@ -2704,6 +2872,12 @@ void cpcp_destroy(cpcp_handle h)
     }
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->check_stream) {
+        cudaStreamSynchronize(h->check_stream);
+        cudaStreamDestroy(h->check_stream);
+    }
+    if (h->ev_snap) cudaEventDestroy(h->ev_snap);
+    if (h->check_host) cudaFreeHost(h->check_host);
     for (auto &kv : h->bufs)
         if (kv.second.p) cudaFree(kv.second.p);
     delete h;

@@ -296,13 +296,15 @@ def test_iteration_cap_returns_not_converged(cp):
 
 def test_graph_replay_equals_plain_launches(cp, small_cpcp):
     # the iterations replayed from a captured CUDA graph run the same kernels
-    # on the same data as direct launches: bit-identical results
+    # on the same data as direct launches: bit-identical results, and the
+    # same launch count with the residual checks in order (overlapped checks
+    # also launch the iterations they drop: tests/test_gpu_check_overlap.py)
     p, _, _ = small_cpcp
     Qb = torch.as_tensor(cp.pack_mask(p["mask"])).cuda()
     D = dev(p["D"], torch.float32)
     out = []
     for plain in (0, 1):
-        with cp.Handle(0, plain_launches=plain) as hh:
+        with cp.Handle(0, plain_launches=plain, check_serial=1) as hh:
             L, S, info = hh.solve(D, Qb, p["lam"], p["mu"], levels=2, tol=1e-6)
         out.append((L, S, info))
     (L0, S0, i0), (L1, S1, i1) = out
