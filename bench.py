@@ -505,6 +505,19 @@ def extras(device, stream, flush) -> dict:
         hb.solve_batched(probs, tol=TOL)
         t, (Lb, Sb, infos, st) = _events_time(stream, lambda: hb.solve_batched(probs, tol=TOL), 3, flush)
     its = [f["iters"] for f in infos]
+    # the instance that sets the batch's time: its device time per iteration
+    # inside the batch (its own SM-cycle phase times) against the same instance
+    # solved alone with cpcp_solve
+    big = max(range(len(ps)), key=lambda i: sum(infos[i]["phase_ms"].values()))
+    qb = probs[big]
+    with cpcp.Handle(device, stream=stream) as h1:
+        h1.solve(qb["D"], qb["Q"], qb["lam"], qb["mu"], levels=qb["levels"], tol=TOL)
+        t1, (_, _, i1) = _events_time(stream, lambda: h1.solve(qb["D"], qb["Q"], qb["lam"], qb["mu"],
+                                                               levels=qb["levels"], tol=TOL), 3, flush)
+    slowest = {"instance": big, "shape": list(ps[big]["D"].shape), "levels": qb["levels"], "iters": its[big],
+               "ms_in_batch": sum(infos[big]["phase_ms"].values()),
+               "ms_per_iter_in_batch": sum(infos[big]["phase_ms"].values()) / max(its[big], 1),
+               "alone_ms": t1 * 1e3, "alone_iters": i1["iters"], "alone_ms_per_iter": t1 * 1e3 / max(i1["iters"], 1)}
     # error against the fp64 oracle's optimum for the three smallest instances
     import oracle
     errs = []
@@ -519,6 +532,7 @@ def extras(device, stream, flush) -> dict:
                       "elements": int(sum(q["D"].size for q in ps)), "gpu_launches": int(infos[0]["launches"]),
                       "autotuned": {"threads": infos[0]["batch_threads"],
                                     "wide_tile": ["64x64", "128x64"][infos[0]["batch_tile"]]},
+                      "slowest_instance": slowest,
                       "err_vs_oracle_smallest3": errs}
     del Lb, Sb
     del probs
