@@ -167,6 +167,36 @@ typedef struct {
                               stops it.
                               Same iterates, decisions and result either way; the overlap costs
                               two more m x n buffers */
+    int chol_form;         /* fp32 Cholesky factorisations of CholeskyQR (six-launch form): 0
+                              (default) = by 16-column block rows, each eliminated by one warp in
+                              registers (shuffles, no barrier inside the block) and applied to the
+                              trailing matrix by the whole CTA in one rank-16 update, R^{-1} by
+                              block back substitution; 1 = one elimination step per CTA barrier
+                              (column quarters per thread).  Same arithmetic up to rounding order.
+                              Other values: INVALID_ARG */
+    int svd_serial;        /* cpcp_solve, fp32 with power_iters = 1.  1: each iteration's subspace
+                              SVD runs in order on the solve stream.  0 (default) and 2: Z' = M^T Y
+                              starts on a second stream as soon as Y = M Omega exists, beside the
+                              CholeskyQR2 of Y (Gram matrix, Cholesky, and a second pass that is
+                              one launch, returning at once when the first pass found Y nearly
+                              orthogonal), and the solve stream forms Z = Z' R_Y^{-1} (equal to
+                              M^T Q_Y); with 0, Q_Y, Q_Z and the next start block are also formed
+                              on the second stream, beside the factorisation of Z and the core
+                              Jacobi SVD; with 2 they stay on the solve stream.  0 takes the two
+                              streams only where M^T Y leaves a quarter of the SMs free (always
+                              with SIMT products; with tensor-core products, sized to about one CTA
+                              per SM, only for short outputs), else the order of 1.  The rounding
+                              of Z differs from the in-order form by a factor of the equilibrated
+                              condition number of Y (near 1 once the subspace is warm-started).
+                              With profile = 2 everything runs in order.  Other values:
+                              INVALID_ARG */
+    int gram_form;         /* fp32 Gram matrices X^T X of the CholeskyQR passes: 0 (default) = for
+                              X of at least 4096 rows, by row ranges, each CTA staging 64 rows of
+                              the live columns at a time in
+                              shared memory and writing one partial slice (up to 16, summed in CTA
+                              order by the Cholesky kernel), shorter X as with 1; 1 = the tiled
+                              cluster-reduced kernel of the other tall products (64 x 64 output tiles
+                              whatever the live width).  Other values: INVALID_ARG */
 } cpcp_options;
 
 /* Phases timed when cpcp_options.profile is set. */

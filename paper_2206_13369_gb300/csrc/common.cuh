@@ -126,6 +126,10 @@ bool launch_pass_tc(const PassArgs<float> &p, int *err, cudaStream_t st);
 // rules) for launch_reduce_partial.  err: set when a bounded wait expired.
 int launch_prod_tc(int tn, int P, int K, const float *M, int64_t ldm, const float *B, int64_t ldb, int bcols_max,
                    const int *kdyn, float *part, int64_t ldc, int64_t slice, int max_splits, int *err, cudaStream_t st);
+// CTAs that launch_prod_tc runs for a P-row output with K-long contraction
+int prod_tc_ctas(int P, int K, int max_splits);
+// multiprocessors of the current device
+int gpu_sm_count();
 // per-block fp64 partial sums of squares of X (rows x cols); returns the block count
 template <typename T> int launch_sumsq(int rows, int cols, const T *X, int64_t ld, double *partial, cudaStream_t st);
 // check pass at (L_k, S_k) with weight mu_bar: writes M = L - tau G and
@@ -245,10 +249,11 @@ void launch_bidiag_left_solve(int nh, const T *V, int64_t ldv, const int *kdyn, 
 
 // small dense kernels (one CTA)
 // Cholesky pass of CholeskyQR: R = chol(X^T X) from row-split partial Gram
-// matrices; well_out / skip_in implement the skip of a second pass
+// matrices; well_out / skip_in implement the skip of a second pass.  form
+// (fp32): 0 = by 16-column block rows, 1 = one elimination step per barrier
 template <typename T>
 void launch_chol(const T *partialG, int splits, int kmax, const int *kdyn, T *R, T *Rinv, const T *Rprev, T *Rtot,
-                 int ldr, int *well_out, const int *skip_in, cudaStream_t st, int *stats = nullptr);
+                 int ldr, int *well_out, const int *skip_in, cudaStream_t st, int *stats = nullptr, int form = 0);
 // ctrl (optional): skip rotations that cannot change SVT_{ctrl->theta_L};
 // stats (optional): calls and sweeps are added to stats[0], stats[1];
 // Us, svt (optional): the SVT of launch_svt_small fused into the epilogue
@@ -260,6 +265,18 @@ void launch_chol(const T *partialG, int splits, int kmax, const int *kdyn, T *R,
 bool launch_cholqr2_cluster(int rows, const float *X, float *Q, float *Q1, int KM, const int *kdyn, float *G,
                             float *R1, float *R1i, float *R2, float *R2i, float *Rout, int *well, int *stats,
                             cudaStream_t st);
+// The second CholeskyQR pass of X (rows x k, ld KM) after a first pass that
+// left Rt = R1, Rti = R1^{-1} and the flag well (k_small.cu): nothing when
+// *well is set, else Rt <- R2 Rt, Rti <- Rti R2^{-1} with R2 the Cholesky
+// factor of the Gram matrix of X R1^{-1}.  Q1 (rows x KM), Gp (16 slices of
+// KM x KM), G, R2, R2i (KM x KM): workspace; ticket: a zeroed counter that
+// the launch leaves zeroed.  fp32.
+// X^T X of a tall block X (rows x k, ld KM, k = *kdyn) as partial slices by row
+// ranges (k_small.cu), loading only the live columns; returns the slice count
+int launch_gram_rows(int rows, const float *X, int KM, const int *kdyn, float *part, cudaStream_t st);
+void launch_cqr_pass2(int rows, const float *X, float *Q1, int KM, const int *kdyn, float *Rt, float *Rti,
+                      const int *well, float *Gp, float *G, float *R2, float *R2i, unsigned *ticket, int *stats,
+                      cudaStream_t st);
 template <typename T>
 void launch_jacobi(const T *Rz, int ldr, const int *kdyn, T *Ut, T *Wt, T *sig, int kmax, const Ctrl *ctrl,
                    cudaStream_t st, int *stats = nullptr, T *Us = nullptr, Ctrl *svt = nullptr);

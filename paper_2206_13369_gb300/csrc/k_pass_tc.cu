@@ -1016,6 +1016,19 @@ bool launch_pass_tc(const PassArgs<float> &p, int *err, cudaStream_t st)
 // columns used) the thin operand.  Writes `splits` partial slices of part
 // (slice floats apart, leading dimension ldc) and returns their number, or 0
 // (nothing launched) when an operand does not meet the TMA rules.
+int gpu_sm_count() { return sm_count(); }
+
+int prod_tc_ctas(int P, int K, int max_splits)
+{
+    // about one CTA per SM, at least 4 stages per CTA
+    const int tiles = (P + PP_M - 1) / PP_M;
+    const int total = (K + PP_K - 1) / PP_K;
+    int splits = std::max(1, std::min({sm_count() / tiles, max_splits, std::max(1, total / 4)}));
+    const int per = (total + splits - 1) / splits;
+    splits = (total + per - 1) / per;
+    return tiles * splits;
+}
+
 int launch_prod_tc(int tn, int P, int K, const float *M, int64_t ldm, const float *B, int64_t ldb, int bcols_max,
                    const int *kdyn, float *part, int64_t ldc, int64_t slice, int max_splits, int *err, cudaStream_t st)
 {
@@ -1037,10 +1050,8 @@ int launch_prod_tc(int tn, int P, int K, const float *M, int64_t ldm, const floa
     }
     const int tiles = (P + PP_M - 1) / PP_M;
     const int total = (K + PP_K - 1) / PP_K;
-    // about one CTA per SM, at least 4 stages per CTA
-    int splits = std::max(1, std::min({sm_count() / tiles, max_splits, std::max(1, total / 4)}));
+    const int splits = prod_tc_ctas(P, K, max_splits) / tiles;
     const int per = (total + splits - 1) / splits;
-    splits = (total + per - 1) / per;
     ProdArgs a;
     a.P = P;
     a.K = K;

@@ -561,6 +561,290 @@ __global__ void __launch_bounds__(CQ_NT, 1) chol_q_kernel(const float *__restric
 }
 
 // ---------------------------------------------------------------------------
+// The same factorisation in fp32 by 16-column block rows (k <= 128)
+// ---------------------------------------------------------------------------
+// Right-looking and blocked.  Block row J (rows c0 .. c0 + 15, c0 = 16 J) is
+// eliminated by one warp in registers: lane l holds columns c0 + l + 32 s
+// (s < SL) of those 16 rows, so a step j of the block takes the pivot from
+// lane j by a shuffle, scales the lane's own entries of row j into u_j
+// (U[j][y] = S[j][y] / p_j) and updates rows x > j of the block with the
+// entries S[j][c0 + x] of lanes x: no barrier inside the block.  The 16
+// finished rows (S and U) go to shared memory, and the whole CTA applies
+// them to the trailing upper triangle in one rank-16 update
+// (S[x][y] -= sum_j S[j][x] U[j][y], 4 x 4 register tiles), one barrier.
+// W = U^{-1} (unit upper triangular) follows by block back substitution: each
+// diagonal block inverted by its own warp, then the off-diagonal blocks block
+// row by block row from the bottom, W_IJ = -W_II sum_{I<L<=J} U_IL W_LJ.  A
+// pivot that is not positive (or below eps^2) drops its column: its U row
+// is e_j and it updates nothing, as in the unblocked forms.  Same outputs,
+// equilibration, pivot rule and well-conditioning test as chol_body; the
+// rounding order differs.
+constexpr int CB_NT = 256;
+
+__host__ __device__ inline int cb_ld(int kmax) { return (kmax + 4 + 3) / 4 * 4; }
+
+size_t chol_blk_smem(int kmax)
+{
+    const size_t ld = cb_ld(kmax);
+    // Gs, Us, Ws (kmax x ld each), the block-row scratch (16 x ld), scales, pivots
+    return (3 * (size_t)kmax * ld + 16 * ld + 2 * (size_t)kmax + 8) * sizeof(float) + 64;
+}
+
+// 1/p for a normal positive p: the hardware estimate and one Newton step
+__device__ __forceinline__ float rcp_nr(float p)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(p));
+    return fmaf(r, fmaf(-p, r, 1.f), r);
+}
+
+// block row J of S (rows c0 .. c0 + nr - 1 of the trailing upper triangle in
+// Gs) eliminated by one warp; its rows of S and U written back to Gs and Us,
+// the pivots to piv (0 = dropped)
+template <int SL>
+__device__ __forceinline__ void cb_block_row(float *Gs, float *Us, float *piv, int ld, int k, int c0, float tol)
+{
+    const int lane = threadIdx.x & 31;
+    float a[SL][16];
+#pragma unroll
+    for (int s = 0; s < SL; s++) {
+        const int y = c0 + lane + 32 * s;
+#pragma unroll
+        for (int x = 0; x < 16; x++) a[s][x] = (y < k && c0 + x <= y) ? Gs[(c0 + x) * ld + y] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+        if (c0 + j >= k) break;  // uniform over the warp
+        const float p = __shfl_sync(0xffffffffu, a[0][j], j);
+        const bool drop = !(p > tol);
+        const float inv = drop ? 0.f : rcp_nr(p);
+        float u[SL];
+#pragma unroll
+        for (int s = 0; s < SL; s++) {
+            u[s] = a[s][j] * inv;
+            const int y = c0 + lane + 32 * s;
+            if (y < k) {
+                Gs[(c0 + j) * ld + y] = a[s][j];
+                Us[(c0 + j) * ld + y] = y > c0 + j ? u[s] : (y == c0 + j ? 1.f : 0.f);
+            }
+        }
+        if (lane == 0) piv[c0 + j] = drop ? 0.f : p;
+        // rows x > j of the block: S[x][y] -= S[j][x] u_j[y] (positions below
+        // the diagonal of the block are never read)
+#pragma unroll
+        for (int x = j + 1; x < 16; x++) {
+            const float v = __shfl_sync(0xffffffffu, a[0][j], x);
+#pragma unroll
+            for (int s = 0; s < SL; s++) a[s][x] = fmaf(-v, u[s], a[s][x]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(CB_NT, 1) chol_blk_kernel(const float *__restrict__ partial, int splits, int kmax,
+                                                             const int *kdyn, float *__restrict__ R,
+                                                             float *__restrict__ Rinv, const float *__restrict__ Rprev,
+                                                             float *__restrict__ Rtot, int ldr, int *well_out,
+                                                             const int *skip_in, int *stats)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double red[CB_NT / 32];
+    const int k = *kdyn;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (skip_in != nullptr && *skip_in) {
+        for (int idx = tid; idx < k * k; idx += CB_NT) {
+            const int i = idx / k, c = idx % k;
+            R[(int64_t)i * ldr + c] = (i == c) ? 1.f : 0.f;
+            Rinv[(int64_t)i * ldr + c] = (i == c) ? 1.f : 0.f;
+            if (Rtot != nullptr) Rtot[(int64_t)i * ldr + c] = Rprev[(int64_t)i * ldr + c];
+        }
+        return;
+    }
+    if (stats != nullptr && tid == 0) atomicAdd(stats, 1);
+    const int ld = cb_ld(kmax);
+    float *Gs = reinterpret_cast<float *>(smraw);  // S (upper); later R
+    float *Us = Gs + (size_t)kmax * ld;            // U (unit upper); later R for Rtot
+    float *Ws = Us + (size_t)kmax * ld;            // W = U^{-1}; later Rprev
+    float *Ts = Ws + (size_t)kmax * ld;            // 16 x ld: sum_L U_IL W_LJ of one block row
+    float *dsc = Ts + 16 * ld;                     // column scales
+    float *piv = dsc + kmax;                       // pivots (0 = dropped); later their square roots
+    const int64_t slice = (int64_t)kmax * kmax;
+    const float tol = FLT_EPSILON * FLT_EPSILON;
+
+    // column scales, the equilibrated Gram matrix (upper) and its distance from I
+    for (int c = tid; c < k; c += CB_NT) {
+        const float g = chol_gram_entry(partial, splits, slice, kmax, c, c);
+        dsc[c] = (g > 0.f && isfinite(g)) ? sqrtf(g) : 0.f;
+    }
+    __syncthreads();
+    double defect = 0.0;
+    for (int base = 0; base < k * k; base += 8 * CB_NT) {
+        float acc[8];
+        const float *src[8];
+        bool use[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int idx = base + u * CB_NT + tid;
+            const int x = idx / k, y = idx - (idx / k) * k;
+            use[u] = idx < k * k && x <= y && dsc[x] > 0.f && dsc[y] > 0.f;
+            src[u] = partial + (use[u] ? (int64_t)x * kmax + y : 0);
+            acc[u] = 0.f;
+        }
+        int q = 0;
+        for (; q + 4 <= splits; q += 4) {
+            float v[8][4];
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+#pragma unroll
+                for (int t = 0; t < 4; t++) v[u][t] = use[u] ? src[u][(q + t) * slice] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; u++) acc[u] += (v[u][0] + v[u][1]) + (v[u][2] + v[u][3]);
+        }
+        for (; q < splits; q++)
+#pragma unroll
+            for (int u = 0; u < 8; u++) acc[u] += use[u] ? src[u][q * slice] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int idx = base + u * CB_NT + tid;
+            const int x = idx / k, y = idx - (idx / k) * k;
+            if (idx >= k * k || x > y) continue;
+            const float v = use[u] ? acc[u] / dsc[x] / dsc[y] : 0.f;
+            Gs[x * ld + y] = v;
+            const float ev = v - (x == y ? 1.f : 0.f);
+            defect += (x == y ? 1.0 : 2.0) * (double)(ev * ev);
+        }
+    }
+    defect = warp_sum(defect);
+    if (lane == 0) red[warp] = defect;
+    __syncthreads();
+    if (tid == 0 && well_out != nullptr) {
+        double tot = 0.0;
+        for (int q = 0; q < CB_NT / 32; q++) tot += red[q];
+        *well_out = tot <= 0.25 ? 1 : 0;
+    }
+
+    // elimination, block row by block row
+    const int nb = (k + 15) >> 4;
+    for (int J = 0; J < nb; J++) {
+        const int c0 = 16 * J;
+        if (warp == 0) {
+            if (k - c0 <= 64)
+                cb_block_row<2>(Gs, Us, piv, ld, k, c0, tol);
+            else
+                cb_block_row<4>(Gs, Us, piv, ld, k, c0, tol);
+        }
+        __syncthreads();
+        const int t0 = c0 + 16;
+        if (t0 >= k) break;
+        // trailing update of the upper triangle, 4 x 4 tiles (xb <= yb)
+        const int jn = 16;
+        const int nt4 = (k - t0 + 3) >> 2;
+        const int ntile = nt4 * (nt4 + 1) / 2;
+        for (int e = tid; e < ntile; e += CB_NT) {
+            int xb = 0, rem = e;
+            while (rem >= nt4 - xb) {
+                rem -= nt4 - xb;
+                xb++;
+            }
+            const int yb = xb + rem;
+            const int x = t0 + 4 * xb, y = t0 + 4 * yb;
+            float acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+                const float4 g = *reinterpret_cast<const float4 *>(Gs + (x + a) * ld + y);
+                acc[a][0] = g.x;
+                acc[a][1] = g.y;
+                acc[a][2] = g.z;
+                acc[a][3] = g.w;
+            }
+#pragma unroll 4
+            for (int j = 0; j < jn; j++) {
+                const float4 sx = *reinterpret_cast<const float4 *>(Gs + (c0 + j) * ld + x);
+                const float4 uy = *reinterpret_cast<const float4 *>(Us + (c0 + j) * ld + y);
+                const float sv[4] = {sx.x, sx.y, sx.z, sx.w}, uv[4] = {uy.x, uy.y, uy.z, uy.w};
+#pragma unroll
+                for (int a = 0; a < 4; a++)
+#pragma unroll
+                    for (int b = 0; b < 4; b++) acc[a][b] = fmaf(-sv[a], uv[b], acc[a][b]);
+            }
+#pragma unroll
+            for (int a = 0; a < 4; a++)
+                *reinterpret_cast<float4 *>(Gs + (x + a) * ld + y) =
+                    make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+        }
+        __syncthreads();
+    }
+
+    // W = U^{-1}: the diagonal blocks (warp J inverts block J, lane y its
+    // column), zero below them
+    for (int J = warp; J < nb; J += CB_NT / 32) {
+        const int c0 = 16 * J, nr = min(16, k - c0);
+        if (lane < nr) {
+            const int y = c0 + lane;
+            for (int i = lane + 1; i < nr; i++) Ws[(c0 + i) * ld + y] = 0.f;
+            Ws[y * ld + y] = 1.f;
+            for (int i = lane - 1; i >= 0; i--) {
+                float sacc = 0.f;
+                for (int c = i + 1; c <= lane; c++) sacc = fmaf(Us[(c0 + i) * ld + c0 + c], Ws[(c0 + c) * ld + y], sacc);
+                Ws[(c0 + i) * ld + y] = -sacc;
+            }
+        }
+    }
+    __syncthreads();
+    // off-diagonal blocks, block row I from the bottom: T = sum_{L > I} U_IL W_L,
+    // then W_I = -W_II T (columns beyond block I)
+    for (int I = nb - 2; I >= 0; I--) {
+        const int i0 = 16 * I, t0 = i0 + 16, nc = k - t0;
+        for (int e = tid; e < 16 * nc; e += CB_NT) {
+            const int i = e / nc, y = t0 + (e - (e / nc) * nc);
+            float sacc = 0.f;
+            for (int c = t0; c <= y; c++) sacc = fmaf(Us[(i0 + i) * ld + c], Ws[c * ld + y], sacc);
+            Ts[i * ld + y] = sacc;
+        }
+        __syncthreads();
+        for (int e = tid; e < 16 * nc; e += CB_NT) {
+            const int i = e / nc, y = t0 + (e - (e / nc) * nc);
+            float sacc = 0.f;
+            for (int c = i; c < 16; c++) sacc = fmaf(Ws[(i0 + i) * ld + i0 + c], Ts[c * ld + y], sacc);
+            Ws[(i0 + i) * ld + y] = -sacc;
+        }
+        __syncthreads();
+    }
+    for (int c = tid; c < k; c += CB_NT) piv[c] = sqrtf(piv[c]);
+    __syncthreads();
+
+    // undo the equilibration: R = P U D (row x of P U is S[x][x:] / P_x), R^{-1} = D^{-1} W P^{-1}
+    for (int idx = tid; idx < k * k; idx += CB_NT) {
+        const int x = idx / k, y = idx - (idx / k) * k;
+        const float px = piv[x], py = piv[y];
+        float rv = 0.f, ri = 0.f;
+        if (x < y) {
+            rv = px > 0.f ? Gs[x * ld + y] / px * dsc[y] : 0.f;
+            ri = (py > 0.f && dsc[x] > 0.f) ? Ws[x * ld + y] / py / dsc[x] : 0.f;
+        } else if (x == y) {
+            rv = px * dsc[x];
+            ri = (px > 0.f && dsc[x] > 0.f) ? 1.f / px / dsc[x] : 0.f;
+        }
+        R[(int64_t)x * ldr + y] = rv;
+        Rinv[(int64_t)x * ldr + y] = ri;
+        if (Rprev != nullptr && x <= y) Us[x * ld + y] = rv;
+    }
+    if (Rprev == nullptr) return;
+    __syncthreads();
+    for (int idx = tid; idx < k * k; idx += CB_NT) {
+        const int i = idx / k, c = idx - (idx / k) * k;
+        Ws[i * ld + c] = Rprev[(int64_t)i * ldr + c];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < k * k; idx += CB_NT) {
+        const int x = idx / k, y = idx - (idx / k) * k;
+        float sacc = 0.f;
+        if (x <= y)
+            for (int p = x; p <= y; p++) sacc = fmaf(Us[x * ld + p], Ws[p * ld + y], sacc);
+        Rtot[(int64_t)x * ldr + y] = sacc;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // CholeskyQR2 of a tall block in one thread-block cluster
 // ---------------------------------------------------------------------------
 // The two CholeskyQR passes (Gram, Cholesky, Q = X R^{-1}, twice) as one
@@ -789,6 +1073,110 @@ __global__ void __launch_bounds__(CQR_NT, 1)
     cluster.sync();
     cqr_stage<T>(R2i, KM, k, Gp);
     cqr_apply<T>(Q1, KM, r0, r1, k, Gp, Q, KM, ch);
+}
+
+// ---------------------------------------------------------------------------
+// Gram matrix of a tall block by row ranges, loading only the live columns
+// ---------------------------------------------------------------------------
+// CTA b takes a contiguous range of rows of X (rows x k, ld KM) and writes
+// X[r0:r1]^T X[r0:r1] (upper 4 x 4 tiles, zero below) as slice b of part (ld
+// KM, slices KM x KM apart), which the Cholesky kernels sum in CTA order.  The
+// rows come through shared memory 64 at a time, round4(k) columns each, so a
+// narrow block (k = 15 on a 128-wide workspace) costs what its live columns
+// cost.  fp32.
+template <typename T>
+__global__ void __launch_bounds__(CQR_NT) gram_rows_kernel(int rows, const T *__restrict__ X, int KM, const int *kdyn,
+                                                            T *part)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int k = *kdyn;
+    if (k < 1) return;
+    const int nb = (int)gridDim.x, b = (int)blockIdx.x;
+    const int rpc = (rows + nb - 1) / nb;
+    const int r0 = min(rows, b * rpc), r1 = min(rows, r0 + rpc);
+    const int k4 = (k + 3) / 4 * 4;
+    T *scratch = reinterpret_cast<T *>(smraw);  // 512 x 16
+    T *ch = scratch + CQR_NT * 16;              // CQR_CH x k4
+    T *Gs = ch + CQR_CH * k4;                   // k x k
+    cqr_gram<T>(X, KM, r0, r1, k, Gs, scratch, ch);
+    T *slice = part + (int64_t)b * KM * KM;
+    for (int e = threadIdx.x; e < k * k; e += CQR_NT) slice[(int64_t)(e / k) * KM + e % k] = Gs[e];
+}
+
+
+// ---------------------------------------------------------------------------
+// The second CholeskyQR pass in one launch that returns at once when skipped
+// ---------------------------------------------------------------------------
+// After a first pass over X (rows x k, ld KM) that left Rt = R1, Rti = R1^{-1}
+// (k x k, ld KM) and the well-conditioning flag.  When *well is set every CTA
+// returns at once: the steady state then costs one launch instead of the
+// three kernels of the multi-launch pass that each start only to find the
+// flag.  Otherwise CTA b forms its rows of Q1 = X R1^{-1} (into the workspace
+// Q1) and their Gram partial, written as slice b of Gp (ld KM); the last CTA
+// to finish (a ticket counter, which it resets) sums the slices in CTA order
+// into G, factorises it (chol_body: R2, R2^{-1}) and updates Rt <- R2 Rt and
+// Rti <- Rti R2^{-1} in place.  Q = X Rti is left to the caller.  fp32.
+template <typename T>
+__global__ void __launch_bounds__(CQR_NT, 1)
+    cqr_pass2_kernel(int rows, const T *__restrict__ X, T *Q1, int KM, const int *kdyn, T *Rt, T *Rti,
+                     const int *well, T *Gp, T *G, T *R2, T *R2i, unsigned *ticket, int *stats, int gp_off)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double red[CQR_NT / 32];
+    __shared__ int s_last;
+    if (*well) return;
+    const int k = *kdyn;
+    if (k < 1) return;
+    T *ws = reinterpret_cast<T *>(smraw);  // Cholesky workspace, or the Gram scratch (512 x 16) and a row chunk
+    T *ch = ws + CQR_NT * 16;
+    T *Bs = reinterpret_cast<T *>(smraw + gp_off);  // R1^{-1} staged, then this CTA's Gram partial
+    const int nb = (int)gridDim.x, b = (int)blockIdx.x, tid = threadIdx.x;
+    const int rpc = (rows + nb - 1) / nb;
+    const int r0 = min(rows, b * rpc), r1 = min(rows, r0 + rpc);
+
+    cqr_stage<T>(Rti, KM, k, Bs);
+    cqr_apply<T>(X, KM, r0, r1, k, Bs, Q1, KM, ch);
+    __syncthreads();  // Bs is reused and this CTA's rows of Q1 are read back
+    cqr_gram<T>(Q1, KM, r0, r1, k, Bs, ws, ch);
+    T *slice = Gp + (int64_t)b * KM * KM;
+    for (int e = tid; e < k * k; e += CQR_NT) slice[(int64_t)(e / k) * KM + e % k] = Bs[e];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(ticket, 1u) == (unsigned)(nb - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (tid == 0) {
+        *ticket = 0u;
+        if (stats != nullptr) atomicAdd(stats, 1);
+    }
+    // the slices summed in CTA order (L2-coherent loads: other CTAs wrote them)
+    for (int e = tid; e < k * k; e += CQR_NT) {
+        const int64_t off = (int64_t)(e / k) * KM + e % k;
+        T sacc = T(0);
+        for (int q = 0; q < nb; q++) sacc += __ldcg(Gp + (int64_t)q * KM * KM + off);
+        G[off] = sacc;
+    }
+    __threadfence();
+    __syncthreads();
+    cqr_chol<T>(G, KM, k, R2, R2i, Rt, Rt, nullptr, ws, red);
+    __threadfence();
+    __syncthreads();
+    // Rti <- Rti R2^{-1} (both upper triangular), staged in shared memory
+    T *A = ws, *Bm = Bs;
+    for (int e = tid; e < k * k; e += CQR_NT) {
+        const int64_t off = (int64_t)(e / k) * KM + e % k;
+        A[e] = __ldcg(Rti + off);
+        Bm[e] = __ldcg(R2i + off);
+    }
+    __syncthreads();
+    for (int e = tid; e < k * k; e += CQR_NT) {
+        const int x = e / k, y = e - (e / k) * k;
+        T sacc = T(0);
+        if (x <= y)
+            for (int p = x; p <= y; p++) sacc = fma(A[x * k + p], Bm[p * k + y], sacc);
+        Rti[(int64_t)x * KM + y] = sacc;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1169,9 +1557,12 @@ void ensure_small_attrs()
                          (int)chol_smem<T>(small_kmax<T>()));
     cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)jacobi_smem<T>(small_kmax<T>()));
-    if (std::is_same<T, float>::value)
+    if (std::is_same<T, float>::value) {
         cudaFuncSetAttribute(chol_q_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)chol_q_smem(small_kmax<float>()));
+        cudaFuncSetAttribute(chol_blk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)chol_blk_smem(small_kmax<float>()));
+    }
     done = true;
 }
 
@@ -1179,11 +1570,16 @@ void ensure_small_attrs()
 
 template <typename T>
 void launch_chol(const T *partialG, int splits, int kmax, const int *kdyn, T *R, T *Rinv, const T *Rprev, T *Rtot,
-                 int ldr, int *well_out, const int *skip_in, cudaStream_t st, int *stats)
+                 int ldr, int *well_out, const int *skip_in, cudaStream_t st, int *stats, int form)
 {
     ensure_small_attrs<T>();
     CPCP_COUNT_LAUNCH();
     if constexpr (std::is_same<T, float>::value) {
+        if (kmax <= small_kmax<float>() && form == 0) {
+            chol_blk_kernel<<<1, CB_NT, chol_blk_smem(kmax), st>>>(partialG, splits, kmax, kdyn, R, Rinv, Rprev, Rtot,
+                                                                  ldr, well_out, skip_in, stats);
+            return;
+        }
         if (kmax <= small_kmax<float>()) {
             chol_q_kernel<<<1, CQ_NT, chol_q_smem(kmax), st>>>(partialG, splits, kmax, kdyn, R, Rinv, Rprev, Rtot, ldr,
                                                               well_out, skip_in, stats);
@@ -1250,6 +1646,45 @@ bool launch_cholqr2_cluster(int rows, const float *X, float *Q, float *Q1, int K
     }
 }
 
+int launch_gram_rows(int rows, const float *X, int KM, const int *kdyn, float *part, cudaStream_t st)
+{
+    // up to 16 slices of at least 128 rows (the Cholesky kernels read every
+    // slice of every entry, so more slices cost more there than they save here)
+    const int nb = std::max(1, std::min(16, (rows + 127) / 128));
+    const size_t smem = (size_t)(CQR_NT * 16 + CQR_CH * KM + KM * KM) * sizeof(float);
+    static size_t attr = 0;
+    if (attr < smem) {
+        cudaFuncSetAttribute(gram_rows_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = smem;
+    }
+    CPCP_COUNT_LAUNCH();
+    gram_rows_kernel<float><<<nb, CQR_NT, smem, st>>>(rows, X, KM, kdyn, part);
+    return nb;
+}
+
+void launch_cqr_pass2(int rows, const float *X, float *Q1, int KM, const int *kdyn, float *Rt, float *Rti,
+                      const int *well, float *Gp, float *G, float *R2, float *R2i, unsigned *ticket, int *stats,
+                      cudaStream_t st)
+{
+    // the layout of the cluster kernel: Cholesky workspace (which also holds
+    // the Gram scratch and a row chunk), then a k x k staging area
+    const int kx = small_kmax<float>();
+    const size_t ws = std::max(chol_smem<float>(kx), (size_t)(CQR_NT * 16 + CQR_CH * kx) * sizeof(float));
+    const int gp_off = (int)((ws + 255) / 256 * 256);
+    const size_t smem = (size_t)gp_off + (size_t)kx * kx * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(cqr_pass2_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    // up to 16 CTAs of at least 128 rows each (the partial slices fit the
+    // workspace's 64)
+    const int nb = std::max(1, std::min(16, (rows + 127) / 128));
+    CPCP_COUNT_LAUNCH();
+    cqr_pass2_kernel<float><<<nb, CQR_NT, smem, st>>>(rows, X, Q1, KM, kdyn, Rt, Rti, well, Gp, G, R2, R2i, ticket,
+                                                      stats, gp_off);
+}
+
 template <typename T>
 void launch_jacobi(const T *Rz, int ldr, const int *kdyn, T *Ut, T *Wt, T *sig, int kmax, const Ctrl *ctrl,
                    cudaStream_t st, int *stats, T *Us, Ctrl *svt)
@@ -1298,7 +1733,7 @@ int small_kmax_f64() { return small_kmax<double>(); }
 
 #define INST(T)                                                                                                      \
     template void launch_chol<T>(const T *, int, int, const int *, T *, T *, const T *, T *, int, int *, const int *, \
-                                 cudaStream_t, int *);                                                               \
+                                 cudaStream_t, int *, int);                                                          \
     template void launch_jacobi<T>(const T *, int, const int *, T *, T *, T *, int, const Ctrl *, cudaStream_t,       \
                                    int *, T *, Ctrl *);                                                              \
     template void launch_svt_small<T>(const T *, const T *, int, Ctrl *, T *, double *, cudaStream_t);               \

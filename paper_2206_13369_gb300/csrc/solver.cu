@@ -207,6 +207,10 @@ struct cpcp_context {
     cudaStream_t check_stream = nullptr;
     cudaEvent_t ev_snap = nullptr;
     void *check_host = nullptr;
+    // second stream of an iteration's subspace SVD (the products off its
+    // critical path) and the events that fork and join it
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t ev_aux[8] = {};
     // transfer tables already uploaded to this handle's workspace, by
     // (operator, n, halvings, element size): built once, reused by every call
     struct TransferCache {
@@ -591,6 +595,10 @@ struct SvdWork {
     T *Y, *Q1, *Qy, *Z, *Qz;
     T *Gpart, *Zpart, *Ypart;
     T *R1, *R1i, *R2, *R2i, *Rz, *Ut, *Wt, *Us, *sig;
+    // the iteration's SVD with two streams: Z' = M^T Y, Rz^{-1}, the Gram
+    // matrix of the second CholeskyQR pass, and its zeroed ticket counter
+    T *Zp = nullptr, *Rzi = nullptr, *G2 = nullptr;
+    unsigned *ticket = nullptr;
     double *sig64;
     int *well;  // per orthogonalisation: 1 when the second CholeskyQR pass is skipped
     // mixed precision: BF16 copies of M (m x nc) and M^T, and of the thin
@@ -602,6 +610,8 @@ struct SvdWork {
     int *stats = nullptr;
     // fp32: the products with M on the tensor cores (options.products_tc)
     bool tc = false;
+    // fp32: Gram matrices by row ranges (options.gram_form 0)
+    bool gram_rows = false;
 };
 
 template <typename T>
@@ -631,10 +641,18 @@ SvdWork<T> svd_work(cpcp_context *h, const std::string &tag, int m, int ncols, i
     w.Us = wsT<T>(h, tag + "Us", KM * KM);
     w.sig = wsT<T>(h, tag + "sig", KM);
     w.sig64 = wsT<double>(h, tag + "sig64", KM);
+    if (std::is_same<T, float>::value) {
+        w.Zp = wsT<T>(h, tag + "Zp", (size_t)ncols * KM);
+        w.Rzi = wsT<T>(h, tag + "Rzi", KM * KM);
+        w.G2 = wsT<T>(h, tag + "G2", KM * KM);
+        w.ticket = wsT<unsigned>(h, tag + "ticket", 4);
+        CK(cudaMemsetAsync(w.ticket, 0, 4 * sizeof(unsigned), h->stream));
+    }
     // bounded-wait error flag of the tensor-core kernels (shared, cleared per solve)
     w.err = wsT<int>(h, "umma_err", 1);
     const int ptc = h->opt.products_tc;
     w.tc = std::is_same<T, float>::value && KM <= 128 && (ptc == 1 || (ptc == 0 && m >= 4096));
+    w.gram_rows = std::is_same<T, float>::value && KM <= 128 && h->opt.gram_form == 0;
     return w;
 }
 
@@ -693,28 +711,39 @@ void prod_y(SvdWork<T> &w, int m, int nc, const T *Mx, int64_t ldx, const T *Om,
 
 template <typename T>
 void prod_z(SvdWork<T> &w, int m, int nc, const T *Mx, int64_t ldx, const T *Q, int64_t ldq, const int *kdyn,
-            cudaStream_t st)
+            cudaStream_t st, T *out = nullptr)
 {
-    // Z = M^T Q (nc x k), K = m long (tensor cores as for Y)
+    // Z = M^T Q (nc x k), K = m long (tensor cores as for Y), into w.Z or out
+    T *Zo = out != nullptr ? out : w.Z;
     if constexpr (std::is_same<T, float>::value) {
         if (w.tc && ldq == w.KM) {
             const int sp = launch_prod_tc(1, nc, m, Mx, ldx, Q, ldq, w.KM, kdyn, w.Zpart, w.KM, (int64_t)nc * w.KM,
                                           64, w.err, st);
             if (sp > 0) {
-                launch_reduce_partial<float>(w.Zpart, sp, nc, w.KM, w.Z, w.KM, nullptr, kdyn, st);
+                launch_reduce_partial<float>(w.Zpart, sp, nc, w.KM, Zo, w.KM, nullptr, kdyn, st);
                 return;
             }
         }
     }
-    if (!launch_ts_tn<T>(nc, m, Mx, ldx, Q, ldq, w.Z, w.KM, kdyn, w.KM, st)) {
+    if (!launch_ts_tn<T>(nc, m, Mx, ldx, Q, ldq, Zo, w.KM, kdyn, w.KM, st)) {
         const int sp = launch_gemm_tn_partial<T>(m, nc, Mx, ldx, Q, ldq, w.Zpart, kdyn, w.KM, nc, st, nullptr);
-        launch_reduce_partial<T>(w.Zpart, sp, nc, w.KM, w.Z, w.KM, nullptr, kdyn, st);
+        launch_reduce_partial<T>(w.Zpart, sp, nc, w.KM, Zo, w.KM, nullptr, kdyn, st);
     }
 }
 
 template <typename T>
 int prod_gram(SvdWork<T> &w, int rows, const T *X, const int *kdyn, const int *skip, cudaStream_t st)
 {
+    // fp32 blocks of at least 4096 rows: by row ranges through shared memory,
+    // live columns only (gram_form 0), where X is 16-byte aligned; else the
+    // tiled cluster-reduced kernel.  (Measured: 19200 x 15 and 65536 x 18
+    // gain, e.g. 67.5 -> 62.8 ms per hyperspectral solve; 2000 x 60 loses
+    // 1.2 ms per solve, its Cholesky then summing 16 slices instead of 4.)
+    if constexpr (std::is_same<T, float>::value) {
+        if (skip == nullptr && w.gram_rows && rows >= 4096 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+            w.KM % 4 == 0)
+            return launch_gram_rows(rows, X, w.KM, kdyn, w.Gpart, st);
+    }
     const int g = launch_ts_gram<T>(rows, X, w.KM, w.Gpart, kdyn, w.KM, skip, st);
     if (g >= 0) return g;
     return launch_gemm_tn_partial<T>(rows, -1, X, w.KM, X, w.KM, w.Gpart, kdyn, w.KM, w.KM, st, skip);
@@ -750,13 +779,108 @@ void orth_impl(cpcp_context *h, SvdWork<T> &w, int rows, const T *X, T *Q, T *Ro
     }
     int sp = prod_gram<T>(w, rows, X, kdyn, nullptr, st);
     launch_chol<T>(w.Gpart, sp, KM, kdyn, w.R1, w.R1i, nullptr, nullptr, KM, well, nullptr, st,
-                   w.stats ? w.stats + 2 : nullptr);
+                   w.stats ? w.stats + 2 : nullptr, h->opt.chol_form);
     prod_nn_small<T>(rows, X, KM, w.R1i, KM, w.Q1, KM, kdyn, KM, st);
     // second pass; when skipped its factor is the identity and Q = Q1 exactly
     sp = prod_gram<T>(w, rows, w.Q1, kdyn, well, st);
     launch_chol<T>(w.Gpart, sp, KM, kdyn, w.R2, w.R2i, Rout ? w.R1 : nullptr, Rout, KM, nullptr, well, st,
-                   w.stats ? w.stats + 2 : nullptr);
+                   w.stats ? w.stats + 2 : nullptr, h->opt.chol_form);
     prod_nn_small<T>(rows, w.Q1, KM, w.R2i, KM, Q, KM, kdyn, KM, st, well);
+}
+
+// Second stream of an iteration's subspace SVD, created on first use; with
+// kernel-family timing (profile 2) everything stays in order on the solve
+// stream, so that each family's events bracket its own kernels only.
+cudaStream_t iter_aux(cpcp_context *h)
+{
+    if (h->timer.detail) return h->stream;
+    if (!h->aux_stream) {
+        CK(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
+        for (auto &e : h->ev_aux) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    return h->aux_stream;
+}
+
+// orders the work queued next on `to` after the work queued so far on `from`
+// (nothing on one stream); slot: which of the handle's events carries it
+void order_after(cpcp_context *h, cudaStream_t to, cudaStream_t from, int slot)
+{
+    if (to == from) return;
+    CK(cudaEventRecord(h->ev_aux[slot], from));
+    CK(cudaStreamWaitEvent(to, h->ev_aux[slot], 0));
+}
+
+// CholeskyQR2 of X (rows x k) as its triangular factors only: Rt = R (X = Q R)
+// and Rti = R^{-1}; Q = X Rti is left to the caller.  The second pass is one
+// launch that returns at once when the first found X nearly orthogonal after
+// equilibration.  fp32.
+void orth_factor_only(cpcp_context *h, SvdWork<float> &w, int rows, const float *X, float *Rt, float *Rti,
+                      const int *kdyn, int slot)
+{
+    cudaStream_t st = h->stream;
+    const int KM = w.KM;
+    int *well = w.well + slot;
+    int *stats = w.stats ? w.stats + 2 : nullptr;
+    const int sp = prod_gram<float>(w, rows, X, kdyn, nullptr, st);
+    launch_chol<float>(w.Gpart, sp, KM, kdyn, Rt, Rti, nullptr, nullptr, KM, well, nullptr, st, stats,
+                       h->opt.chol_form);
+    launch_cqr_pass2(rows, X, w.Q1, KM, kdyn, Rt, Rti, well, w.Gpart, w.G2, w.R2, w.R2i, w.ticket, stats, st);
+}
+
+// Whether the iteration's SVD runs on two streams by default: Z' = M^T Y
+// must leave room beside it.  On the tensor cores it is sized to about one CTA
+// per SM, and where that fills three quarters of the GPU or more the kernels
+// beside it push it into a second wave (measured on the 19200 x 400 video
+// shape: 31.2 against 27.8 ms per solve), so the SVD runs in order there.
+bool two_stream_fits(const SvdWork<float> &w, int nc, int m)
+{
+    if (!w.tc) return true;
+    return 4 * prod_tc_ctas(nc, m, 64) < 3 * gpu_sm_count();
+}
+
+// The subspace SVD of one iteration (one range pass, fp32) on two streams.
+// With Q_Y = Y R_Y^{-1} the CholeskyQR2 of Y = M Omega, Z = M^T Q_Y equals
+// (M^T Y) R_Y^{-1}, so Z' = M^T Y starts on the second stream as soon as Y
+// exists and runs beside the Gram matrix and the factorisations of Y; the
+// solve stream then needs only the k-wide product Z = Z' R_Y^{-1}.  Q_Y and
+// Q_Z = Z R_Z^{-1}, needed only for the new factors, are formed on the second
+// stream beside the factorisation of Z and the core Jacobi SVD.  Leaves the
+// same outputs as subspace_svd (Qy, Qz, Ut, Wt, sig, the fused SVT) with
+// Qy and Qz complete once the second stream has been joined (events 3, 6).
+// The rounding differs from forming Q_Y first by a factor of the condition
+// number of Y after column equilibration (near 1 in the warm-started steady
+// state: the second CholeskyQR pass is then skipped).
+void subspace_svd_iter(cpcp_context *h, SvdWork<float> &w, int m, int nc, const float *Mx, int64_t ldx,
+                       const float *Omega, const int *kdyn, const Ctrl *jac_ctrl, float *Us, Ctrl *svt)
+{
+    cudaStream_t st = h->stream, ax = iter_aux(h);
+    // svd_serial 2: only Z' on the second stream; the Q products in order
+    cudaStream_t aq = h->opt.svd_serial == 2 ? st : ax;
+    const int KM = w.KM;
+    int tp = h->timer.open_sub(DETAIL_PROD_M);
+    prod_y<float>(w, m, nc, Mx, ldx, Omega, kdyn, st);
+    h->timer.close(tp);
+    order_after(h, ax, st, 0);
+    prod_z<float>(w, m, nc, Mx, ldx, w.Y, KM, kdyn, ax, w.Zp);  // Z' = M^T Y
+    if (ax != st) CK(cudaEventRecord(h->ev_aux[1], ax));
+    int tq = h->timer.open_sub(DETAIL_CHOLQR);
+    orth_factor_only(h, w, m, w.Y, w.R1, w.R1i, kdyn, 0);
+    h->timer.close(tq);
+    order_after(h, aq, st, 2);
+    prod_nn_small<float>(m, w.Y, KM, w.R1i, KM, w.Qy, KM, kdyn, KM, aq);  // Q_Y
+    if (aq != st) CK(cudaEventRecord(h->ev_aux[3], aq));
+    if (ax != st) CK(cudaStreamWaitEvent(st, h->ev_aux[1], 0));
+    tp = h->timer.open_sub(DETAIL_PROD_M);
+    prod_nn_small<float>(nc, w.Zp, KM, w.R1i, KM, w.Z, KM, kdyn, KM, st);  // Z = Z' R_Y^{-1}
+    h->timer.close(tp);
+    tq = h->timer.open_sub(DETAIL_CHOLQR);
+    orth_factor_only(h, w, nc, w.Z, w.Rz, w.Rzi, kdyn, 1);
+    h->timer.close(tq);
+    order_after(h, aq, st, 4);
+    prod_nn_small<float>(nc, w.Z, KM, w.Rzi, KM, w.Qz, KM, kdyn, KM, aq);  // Q_Z
+    const int tj = h->timer.open_sub(DETAIL_JACOBI);
+    launch_jacobi<float>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st, w.stats, Us, svt);
+    h->timer.close(tj);
 }
 
 // The subspace SVD below with both contractions with M on the tensor cores:
@@ -1099,12 +1223,30 @@ void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, 
     if (part == 1) return;
     const int ts = part == 0 ? h->timer.open(CPCP_PHASE_SVT) : -1;
     h->timer.in_iter = true;
-    subspace_svd<T>(h, w, s.m, tr.nh, Mx, ldx, s.Om, o.q, &s.ctrl->k, s.ctrl, s.bf16, w.Us, s.ctrl);
+    bool two = false;
+    if constexpr (std::is_same<T, float>::value)
+        two = !s.bf16 && o.q == 1 && h->opt.svd_serial != 1 && w.KM <= kmax_small<float>() &&
+              (h->opt.svd_serial == 2 || two_stream_fits(w, tr.nh, s.m));
+    if constexpr (std::is_same<T, float>::value) {
+        if (two) subspace_svd_iter(h, w, s.m, tr.nh, Mx, ldx, s.Om, &s.ctrl->k, s.ctrl, w.Us, s.ctrl);
+    }
+    if (!two) subspace_svd<T>(h, w, s.m, tr.nh, Mx, ldx, s.Om, o.q, &s.ctrl->k, s.ctrl, s.bf16, w.Us, s.ctrl);
     const int tf = h->timer.open_sub(DETAIL_FACTORS);
     h->timer.in_iter = false;
-    // new factors into the "previous" slot (its old content was consumed above)
-    prod_nn_small<T>(s.m, w.Qy, w.KM, w.Us, w.KM, s.A[nxt], s.KM, &s.ctrl->k, w.KM, st);
-    prod_nn_small<T>(tr.nh, w.Qz, w.KM, w.Wt, w.KM, s.Om, s.KM, &s.ctrl->k, w.KM, st);
+    // new factors into the "previous" slot (its old content was consumed
+    // above); with the two-stream SVD, A = Q_Y U_s on the solve stream beside
+    // the next start block V = Q_Z W_t on the second one
+    if (two) {
+        cudaStream_t ax = h->opt.svd_serial == 2 ? st : iter_aux(h);
+        order_after(h, ax, st, 5);
+        if (ax != st) CK(cudaStreamWaitEvent(st, h->ev_aux[3], 0));
+        prod_nn_small<T>(s.m, w.Qy, w.KM, w.Us, w.KM, s.A[nxt], s.KM, &s.ctrl->k, w.KM, st);
+        prod_nn_small<T>(tr.nh, w.Qz, w.KM, w.Wt, w.KM, s.Om, s.KM, &s.ctrl->k, w.KM, ax);
+        order_after(h, st, ax, 6);
+    } else {
+        prod_nn_small<T>(s.m, w.Qy, w.KM, w.Us, w.KM, s.A[nxt], s.KM, &s.ctrl->k, w.KM, st);
+        prod_nn_small<T>(tr.nh, w.Qz, w.KM, w.Wt, w.KM, s.Om, s.KM, &s.ctrl->k, w.KM, st);
+    }
     if (s.orth && level > 0) {
         // B = R C^{-1} V; the next start block keeps V (random columns into Vp are unused)
         launch_bidiag_left_solve<T>(tr.nh, s.Om, s.KM, &s.ctrl->k, s.KM, s.ot[level].cd, s.ot[level].ce, s.Vp, s.KM,
@@ -1181,6 +1323,7 @@ cpcp_status solve_core(cpcp_context *h, int m, int n, const T *D, int64_t ldd, c
     cudaStream_t st = h->stream;
     const int H = levels - 1;
     h->timer.reset(h->opt.profile != 0, st, h->opt.profile >= 2);
+    if (std::is_same<T, float>::value) iter_aux(h);  // created before any stream capture
     const unsigned long long launches0 = g_kernel_launches;
     SolveState<T> s;
     s.m = m;
@@ -2877,6 +3020,12 @@ void cpcp_destroy(cpcp_handle h)
         cudaStreamDestroy(h->check_stream);
     }
     if (h->ev_snap) cudaEventDestroy(h->ev_snap);
+    if (h->aux_stream) {
+        cudaStreamSynchronize(h->aux_stream);
+        cudaStreamDestroy(h->aux_stream);
+    }
+    for (auto e : h->ev_aux)
+        if (e) cudaEventDestroy(e);
     if (h->check_host) cudaFreeHost(h->check_host);
     for (auto &kv : h->bufs)
         if (kv.second.p) cudaFree(kv.second.p);
@@ -2944,6 +3093,12 @@ cpcp_status cpcp_solve(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D
             throw CpcpError{CPCP_ERR_INVALID_ARG, "early_test must be -1, 0 or 1"};
         if (h->opt.products_tc < -1 || h->opt.products_tc > 1)
             throw CpcpError{CPCP_ERR_INVALID_ARG, "products_tc must be -1, 0 or 1"};
+        if (h->opt.chol_form < 0 || h->opt.chol_form > 1)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "chol_form must be 0 or 1"};
+        if (h->opt.svd_serial < 0 || h->opt.svd_serial > 2)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "svd_serial must be 0, 1 or 2"};
+        if (h->opt.gram_form < 0 || h->opt.gram_form > 1)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "gram_form must be 0 or 1"};
         if (h->opt.unroll > 0) {
             if (dt != CPCP_F32) throw CpcpError{CPCP_ERR_INVALID_ARG, "the unrolled program is fp32"};
             if (h->opt.transfer == 1)

@@ -45,6 +45,8 @@ def main() -> int:
     ap.add_argument("--unroll", type=int, default=0, help="K > 0: the K-step differentiable program and its "
                     "reverse sweep (loss ||L_K - L0||^2)")
     ap.add_argument("--rho", type=float, default=1100.0, help="continuation scale of the unrolled program")
+    ap.add_argument("--option", action="append", default=[], metavar="NAME=VALUE",
+                    help="any other cpcp_options field (integer or float), e.g. --option chol_form=1")
     ap.add_argument("--batched", type=int, default=0, help="N > 0: the first N instances of the 256-instance "
                     "workload in one cpcp_solve_batched call")
     args = ap.parse_args()
@@ -77,6 +79,9 @@ def main() -> int:
     opts = dict(max_iter=args.max_iter, power_iters=args.power_iters, profile=int(args.profile),
                 pass_simt=int(args.pass_simt), plain_launches=int(args.plain_launches),
                 precision=args.precision, transfer=args.transfer, products_tc=args.products_tc)
+    for kv in args.option:
+        name, val = kv.split("=", 1)
+        opts[name] = float(val) if any(c in val for c in ".e") else int(val)
     if args.unroll > 0:
         opts.update(unroll=args.unroll, rho=args.rho)
     with cpcp.Handle(0, **opts) as h:
