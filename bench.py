@@ -182,7 +182,6 @@ def golden_error(name: str, L, S) -> dict | None:
 TRAFFIC = {
     "fused fine pass": (50.8e6, "profiles/dram_cpcp2000.md"),
     "products with M": (16.54e6, "profiles/dram_cpcp2000.md"),
-    "CholeskyQR2": (1.89e6, "profiles/dram_cpcp2000.md"),
     "core Jacobi SVD": (0.081e6, "profiles/dram_cpcp2000.md"),
     "factor products": (0.55e6, "profiles/dram_cpcp2000.md"),
 }
@@ -203,10 +202,11 @@ def kernel_families(prof: dict, m: int, n: int, peaks: dict) -> list:
          20 * m * n + 4 * m * math.ceil(n / 32)),
         ("coarse pass", "pass_kernel (step, with restriction)", ph["pass_coarse"], cnt["pass_coarse"], "hbm",
          16 * m * n + 4 * m * math.ceil(n / 32) + 4 * m * math.ceil(n / 2)),
-        ("products with M", "ts_gemm_kernel (M Omega, M^T Q; prod_tc_kernel from 4096 rows)", det["products"],
+        ("products with M", "ts_gemm_kernel (M Omega, M^T Y; prod_tc_kernel from 4096 rows)", det["products"],
          2 * its, "hbm",
          4 * (m * n + n * k + m * k)),
-        ("CholeskyQR2", "chol_q_kernel with ts_gemm Gram and Q products", det["cholqr"], 2 * its, "alu",
+        ("CholeskyQR2", "chol_blk_kernel, cqr_pass2_kernel, the Gram matrices (ts_gemm_kernel; gram_rows_kernel "
+         "from 4096 rows), Z = Z' R^-1 and the Q products", det["cholqr"], 2 * its, "alu",
          2 * (3 * m * k * k + k ** 3 / 3)),
         ("core Jacobi SVD", "jacobi_kernel", det["jacobi"], its, "alu", sweeps * (k * k / 2) * 12 * k),
         ("factor products", "ts_gemm_kernel (A = Q U, V = Q W) and fill_prolong", det["factors"], 3 * its, "hbm",

@@ -197,6 +197,10 @@ typedef struct {
                               order by the Cholesky kernel), shorter X as with 1; 1 = the tiled
                               cluster-reduced kernel of the other tall products (64 x 64 output tiles
                               whatever the live width).  Other values: INVALID_ARG */
+    int jacobi_lanes;      /* lanes per column pair in the rounds of the core Jacobi SVD for widths
+                              k <= 64: 0 (default) or 16 = 16 lanes (the 32 pairs of a round over
+                              512 threads); 8 = 8 lanes (half the warps, a shorter shuffle tree).
+                              Wider k always take 8.  Other values: INVALID_ARG */
 } cpcp_options;
 
 /* Phases timed when cpcp_options.profile is set. */

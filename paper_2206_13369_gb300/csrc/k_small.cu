@@ -845,6 +845,140 @@ __global__ void __launch_bounds__(CB_NT, 1) chol_blk_kernel(const float *__restr
 }
 
 // ---------------------------------------------------------------------------
+// The same factorisation in fp32 with compact code (k <= 128)
+// ---------------------------------------------------------------------------
+// A one-CTA kernel runs most of its instructions once per launch, so each
+// launch fetches its whole code from L2 (the kernels above unroll their
+// register tiles into 167-665 KB of code, and a capture of the blocked one
+// stalls on instruction fetch more than on anything else).  This form keeps
+// S in shared memory and every loop rolled: the same right-looking
+// elimination as chol_body (G in the upper triangle, W^T in the strict lower
+// one, step j updating S[x][y] -= S[j][x] c_y / p_j for x > j and y <= j or
+// y >= x, c_y = 1 at y = j and S[j][y] otherwise), warp w taking rows
+// j + 1 + w, j + 1 + w + 16, ... and its lanes the columns, one barrier per
+// step.  Same outputs, equilibration, pivot rule and well-conditioning test.
+constexpr int CS_NT = 512;
+
+size_t chol_s_smem(int kmax)
+{
+    // S (kmax x (kmax + 1)), Rprev staged for Rtot (same), scales, pivots
+    return (size_t)(2 * kmax * (kmax + 1) + 2 * kmax + 8) * sizeof(float) + 64;
+}
+
+__global__ void __launch_bounds__(CS_NT, 1) chol_s_kernel(const float *__restrict__ partial, int splits, int kmax,
+                                                           const int *kdyn, float *__restrict__ R,
+                                                           float *__restrict__ Rinv, const float *__restrict__ Rprev,
+                                                           float *__restrict__ Rtot, int ldr, int *well_out,
+                                                           const int *skip_in, int *stats)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double red[CS_NT / 32];
+    const int k = *kdyn;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (skip_in != nullptr && *skip_in) {
+        for (int idx = tid; idx < k * k; idx += CS_NT) {
+            const int i = idx / k, c = idx % k;
+            R[(int64_t)i * ldr + c] = (i == c) ? 1.f : 0.f;
+            Rinv[(int64_t)i * ldr + c] = (i == c) ? 1.f : 0.f;
+            if (Rtot != nullptr) Rtot[(int64_t)i * ldr + c] = Rprev[(int64_t)i * ldr + c];
+        }
+        return;
+    }
+    if (stats != nullptr && tid == 0) atomicAdd(stats, 1);
+    const int ld = kmax + 1;
+    float *S = reinterpret_cast<float *>(smraw);
+    float *P = S + (size_t)kmax * ld;  // Rprev, then R for Rtot
+    float *dsc = P + (size_t)kmax * ld;
+    float *piv = dsc + kmax;
+    const int64_t slice = (int64_t)kmax * kmax;
+    const float tol = FLT_EPSILON * FLT_EPSILON;
+
+    for (int c = tid; c < k; c += CS_NT) {
+        const float g = chol_gram_entry(partial, splits, slice, kmax, c, c);
+        dsc[c] = (g > 0.f && isfinite(g)) ? sqrtf(g) : 0.f;
+    }
+    __syncthreads();
+    // the equilibrated Gram matrix (upper; W^T = 0 below) and its distance from I
+    double defect = 0.0;
+    for (int idx = tid; idx < k * k; idx += CS_NT) {
+        const int x = idx / k, y = idx - (idx / k) * k;
+        float v = 0.f;
+        if (x <= y && dsc[x] > 0.f && dsc[y] > 0.f) {
+            v = chol_gram_entry(partial, splits, slice, kmax, x, y) / dsc[x] / dsc[y];
+            const float ev = v - (x == y ? 1.f : 0.f);
+            defect += (x == y ? 1.0 : 2.0) * (double)(ev * ev);
+        }
+        S[x * ld + y] = v;
+        if (Rprev != nullptr) P[x * ld + y] = Rprev[(int64_t)x * ldr + y];
+    }
+    defect = warp_sum(defect);
+    if (lane == 0) red[warp] = defect;
+    __syncthreads();
+    if (tid == 0 && well_out != nullptr) {
+        double tot = 0.0;
+        for (int q = 0; q < CS_NT / 32; q++) tot += red[q];
+        *well_out = tot <= 0.25 ? 1 : 0;
+    }
+
+#pragma unroll 1
+    for (int j = 0; j < k; j++) {
+        const float p = S[j * ld + j];
+        const bool drop = !(p > tol);
+        if (tid == 0) piv[j] = drop ? 0.f : p;
+        if (!drop) {
+            const float inv = rcp_nr(p);
+#pragma unroll 1
+            for (int x = j + 1 + warp; x < k; x += CS_NT / 32) {
+                const float gx = S[j * ld + x] * inv;  // G[j][x] / p_j
+#pragma unroll 1
+                for (int y = lane; y < k; y += 32) {
+                    if (y > j && y < x) continue;
+                    const float cy = y == j ? 1.f : S[j * ld + y];
+                    S[x * ld + y] = fmaf(-gx, cy, S[x * ld + y]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int c = tid; c < k; c += CS_NT) piv[c] = sqrtf(piv[c]);
+    __syncthreads();
+
+    // undo the equilibration: R = P U D (row x of P U is S[x][x:] / P_x),
+    // R^{-1} = D^{-1} W P^{-1} with W[y][x] = S[x][y] below the diagonal
+    for (int idx = tid; idx < k * k; idx += CS_NT) {
+        const int x = idx / k, y = idx - (idx / k) * k;
+        const float px = piv[x], py = piv[y];
+        float rv = 0.f, ri = 0.f;
+        if (x < y) {
+            rv = px > 0.f ? S[x * ld + y] * rcp_nr(px) * dsc[y] : 0.f;
+            ri = (py > 0.f && dsc[x] > 0.f) ? S[y * ld + x] * rcp_nr(py) * rcp_nr(dsc[x]) : 0.f;
+        } else if (x == y) {
+            rv = px * dsc[x];
+            ri = (px > 0.f && dsc[x] > 0.f) ? rcp_nr(px * dsc[x]) : 0.f;
+        }
+        R[(int64_t)x * ldr + y] = rv;
+        Rinv[(int64_t)x * ldr + y] = ri;
+    }
+    if (Rprev == nullptr) return;
+    __syncthreads();
+    // R (upper) over the factorised S, for Rtot = R Rprev
+    for (int idx = tid; idx < k * k; idx += CS_NT) {
+        const int x = idx / k, y = idx - (idx / k) * k;
+        if (y < x) continue;
+        const float px = piv[x];
+        S[x * ld + y] = x == y ? px * dsc[x] : (px > 0.f ? S[x * ld + y] * rcp_nr(px) * dsc[y] : 0.f);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < k * k; idx += CS_NT) {
+        const int x = idx / k, y = idx - (idx / k) * k;
+        float sacc = 0.f;
+        if (x <= y)
+            for (int q = x; q <= y; q++) sacc = fmaf(S[x * ld + q], P[q * ld + y], sacc);
+        Rtot[(int64_t)x * ldr + y] = sacc;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // CholeskyQR2 of a tall block in one thread-block cluster
 // ---------------------------------------------------------------------------
 // The two CholeskyQR passes (Gram, Cholesky, Q = X R^{-1}, twice) as one
@@ -1393,7 +1527,7 @@ __device__ __forceinline__ void jacobi_body(const T *__restrict__ Rz, int ldr, i
 // stats (optional): stats[0] counts the calls, stats[1] their sweeps.
 // Us (optional, with svt): the SVT on the factors fused into the epilogue, as
 // svt_small_kernel computes it for svt->theta_L (same arithmetic).
-template <typename T>
+template <typename T, int NARROW = 0>
 __global__ void __launch_bounds__(JAC_NT) jacobi_kernel(const T *__restrict__ Rz, int ldr, const int *kdyn,
                                                         T *__restrict__ Ut, T *__restrict__ Wt, T *__restrict__ sig,
                                                         const Ctrl *ctrl, int *stats, T *__restrict__ Us,
@@ -1404,11 +1538,16 @@ __global__ void __launch_bounds__(JAC_NT) jacobi_kernel(const T *__restrict__ Rz
     __shared__ T amax;
     const int k = *kdyn;
     T *sm = reinterpret_cast<T *>(smraw);
-    // k <= 64: 16 lanes per column pair (32 pairs fill the 512 threads); else 8
-    if (k <= 64)
-        jacobi_body<T, 4, 16>(Rz, ldr, k, Ut, Wt, sig, ctrl, stats, Us, svt, sm, wmax, &amax);
-    else
+    // k <= 64: 16 lanes per column pair (32 pairs fill the 512 threads), or 8
+    // (NARROW: half the warps in the rounds, a shorter shuffle tree); else 8
+    if (k <= 64) {
+        if constexpr (NARROW)
+            jacobi_body<T, 8, 8>(Rz, ldr, k, Ut, Wt, sig, ctrl, stats, Us, svt, sm, wmax, &amax);
+        else
+            jacobi_body<T, 4, 16>(Rz, ldr, k, Ut, Wt, sig, ctrl, stats, Us, svt, sm, wmax, &amax);
+    } else {
         jacobi_body<T, 16, 8>(Rz, ldr, k, Ut, Wt, sig, ctrl, stats, Us, svt, sm, wmax, &amax);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1557,11 +1696,15 @@ void ensure_small_attrs()
                          (int)chol_smem<T>(small_kmax<T>()));
     cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)jacobi_smem<T>(small_kmax<T>()));
+    cudaFuncSetAttribute(jacobi_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)jacobi_smem<T>(small_kmax<T>()));
     if (std::is_same<T, float>::value) {
         cudaFuncSetAttribute(chol_q_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)chol_q_smem(small_kmax<float>()));
         cudaFuncSetAttribute(chol_blk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)chol_blk_smem(small_kmax<float>()));
+        cudaFuncSetAttribute(chol_s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)chol_s_smem(small_kmax<float>()));
     }
     done = true;
 }
@@ -1575,6 +1718,11 @@ void launch_chol(const T *partialG, int splits, int kmax, const int *kdyn, T *R,
     ensure_small_attrs<T>();
     CPCP_COUNT_LAUNCH();
     if constexpr (std::is_same<T, float>::value) {
+        if (kmax <= small_kmax<float>() && form == 2) {
+            chol_s_kernel<<<1, CS_NT, chol_s_smem(kmax), st>>>(partialG, splits, kmax, kdyn, R, Rinv, Rprev, Rtot,
+                                                              ldr, well_out, skip_in, stats);
+            return;
+        }
         if (kmax <= small_kmax<float>() && form == 0) {
             chol_blk_kernel<<<1, CB_NT, chol_blk_smem(kmax), st>>>(partialG, splits, kmax, kdyn, R, Rinv, Rprev, Rtot,
                                                                   ldr, well_out, skip_in, stats);
@@ -1687,11 +1835,15 @@ void launch_cqr_pass2(int rows, const float *X, float *Q1, int KM, const int *kd
 
 template <typename T>
 void launch_jacobi(const T *Rz, int ldr, const int *kdyn, T *Ut, T *Wt, T *sig, int kmax, const Ctrl *ctrl,
-                   cudaStream_t st, int *stats, T *Us, Ctrl *svt)
+                   cudaStream_t st, int *stats, T *Us, Ctrl *svt, int lanes)
 {
     ensure_small_attrs<T>();
     CPCP_COUNT_LAUNCH();
-    jacobi_kernel<T><<<1, JAC_NT, jacobi_smem<T>(kmax), st>>>(Rz, ldr, kdyn, Ut, Wt, sig, ctrl, stats, Us, svt);
+    if (lanes == 8)
+        jacobi_kernel<T, 1><<<1, JAC_NT, jacobi_smem<T>(kmax), st>>>(Rz, ldr, kdyn, Ut, Wt, sig, ctrl, stats, Us,
+                                                                     svt);
+    else
+        jacobi_kernel<T><<<1, JAC_NT, jacobi_smem<T>(kmax), st>>>(Rz, ldr, kdyn, Ut, Wt, sig, ctrl, stats, Us, svt);
 }
 
 template <typename T>
@@ -1735,7 +1887,7 @@ int small_kmax_f64() { return small_kmax<double>(); }
     template void launch_chol<T>(const T *, int, int, const int *, T *, T *, const T *, T *, int, int *, const int *, \
                                  cudaStream_t, int *, int);                                                          \
     template void launch_jacobi<T>(const T *, int, const int *, T *, T *, T *, int, const Ctrl *, cudaStream_t,       \
-                                   int *, T *, Ctrl *);                                                              \
+                                   int *, T *, Ctrl *, int);                                                         \
     template void launch_svt_small<T>(const T *, const T *, int, Ctrl *, T *, double *, cudaStream_t);               \
     template void launch_fill_random<T>(T *, int64_t, int, const Ctrl *, int, const T *, int, uint64_t, cudaStream_t); \
     template void launch_fill_prolong<T>(T *, int64_t, int, const Ctrl *, const T *, int, uint64_t, int, T *, int64_t, \

@@ -861,25 +861,33 @@ void subspace_svd_iter(cpcp_context *h, SvdWork<float> &w, int m, int nc, const 
     prod_y<float>(w, m, nc, Mx, ldx, Omega, kdyn, st);
     h->timer.close(tp);
     order_after(h, ax, st, 0);
+    // (the sub-interval timers only open with profile = 2, where ax is the solve stream)
+    tp = h->timer.open_sub(DETAIL_PROD_M);
     prod_z<float>(w, m, nc, Mx, ldx, w.Y, KM, kdyn, ax, w.Zp);  // Z' = M^T Y
+    h->timer.close(tp);
     if (ax != st) CK(cudaEventRecord(h->ev_aux[1], ax));
     int tq = h->timer.open_sub(DETAIL_CHOLQR);
     orth_factor_only(h, w, m, w.Y, w.R1, w.R1i, kdyn, 0);
     h->timer.close(tq);
     order_after(h, aq, st, 2);
+    tq = h->timer.open_sub(DETAIL_CHOLQR);
     prod_nn_small<float>(m, w.Y, KM, w.R1i, KM, w.Qy, KM, kdyn, KM, aq);  // Q_Y
+    h->timer.close(tq);
     if (aq != st) CK(cudaEventRecord(h->ev_aux[3], aq));
     if (ax != st) CK(cudaStreamWaitEvent(st, h->ev_aux[1], 0));
-    tp = h->timer.open_sub(DETAIL_PROD_M);
+    tq = h->timer.open_sub(DETAIL_CHOLQR);
     prod_nn_small<float>(nc, w.Zp, KM, w.R1i, KM, w.Z, KM, kdyn, KM, st);  // Z = Z' R_Y^{-1}
-    h->timer.close(tp);
+    h->timer.close(tq);
     tq = h->timer.open_sub(DETAIL_CHOLQR);
     orth_factor_only(h, w, nc, w.Z, w.Rz, w.Rzi, kdyn, 1);
     h->timer.close(tq);
     order_after(h, aq, st, 4);
+    tq = h->timer.open_sub(DETAIL_CHOLQR);
     prod_nn_small<float>(nc, w.Z, KM, w.Rzi, KM, w.Qz, KM, kdyn, KM, aq);  // Q_Z
+    h->timer.close(tq);
     const int tj = h->timer.open_sub(DETAIL_JACOBI);
-    launch_jacobi<float>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st, w.stats, Us, svt);
+    launch_jacobi<float>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st, w.stats, Us, svt,
+                     h->opt.jacobi_lanes == 8 ? 8 : 16);
     h->timer.close(tj);
 }
 
@@ -916,7 +924,8 @@ void subspace_svd_bf16(cpcp_context *h, SvdWork<float> &w, int m, int nc, const 
         Om = w.Qz;
     }
     const int tj = h->timer.open_sub(DETAIL_JACOBI);
-    launch_jacobi<float>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st, w.stats, Us, svt);
+    launch_jacobi<float>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st, w.stats, Us, svt,
+                     h->opt.jacobi_lanes == 8 ? 8 : 16);
     h->timer.close(tj);
 }
 
@@ -952,7 +961,8 @@ void subspace_svd(cpcp_context *h, SvdWork<T> &w, int m, int nc, const T *Mx, in
         Om = w.Qz;
     }
     const int tj = h->timer.open_sub(DETAIL_JACOBI);
-    launch_jacobi<T>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st, w.stats, Us, svt);
+    launch_jacobi<T>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st, w.stats, Us, svt,
+                     h->opt.jacobi_lanes == 8 ? 8 : 16);
     h->timer.close(tj);
 }
 
@@ -3093,12 +3103,14 @@ cpcp_status cpcp_solve(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D
             throw CpcpError{CPCP_ERR_INVALID_ARG, "early_test must be -1, 0 or 1"};
         if (h->opt.products_tc < -1 || h->opt.products_tc > 1)
             throw CpcpError{CPCP_ERR_INVALID_ARG, "products_tc must be -1, 0 or 1"};
-        if (h->opt.chol_form < 0 || h->opt.chol_form > 1)
-            throw CpcpError{CPCP_ERR_INVALID_ARG, "chol_form must be 0 or 1"};
+        if (h->opt.chol_form < 0 || h->opt.chol_form > 2)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "chol_form must be 0, 1 or 2"};
         if (h->opt.svd_serial < 0 || h->opt.svd_serial > 2)
             throw CpcpError{CPCP_ERR_INVALID_ARG, "svd_serial must be 0, 1 or 2"};
         if (h->opt.gram_form < 0 || h->opt.gram_form > 1)
             throw CpcpError{CPCP_ERR_INVALID_ARG, "gram_form must be 0 or 1"};
+        if (h->opt.jacobi_lanes != 0 && h->opt.jacobi_lanes != 8 && h->opt.jacobi_lanes != 16)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "jacobi_lanes must be 0, 8 or 16"};
         if (h->opt.unroll > 0) {
             if (dt != CPCP_F32) throw CpcpError{CPCP_ERR_INVALID_ARG, "the unrolled program is fp32"};
             if (h->opt.transfer == 1)
