@@ -167,12 +167,15 @@ typedef struct {
                               stops it.
                               Same iterates, decisions and result either way; the overlap costs
                               two more m x n buffers */
-    int chol_form;         /* fp32 Cholesky factorisations of CholeskyQR (six-launch form): 0
-                              (default) = by 16-column block rows, each eliminated by one warp in
+    int chol_form;         /* fp32 Cholesky factorisations of CholeskyQR: 0 (default) = for widths
+                              k > 32 by 16-column block rows, each eliminated by one warp in
                               registers (shuffles, no barrier inside the block) and applied to the
                               trailing matrix by the whole CTA in one rank-16 update, R^{-1} by
-                              block back substitution; 1 = one elimination step per CTA barrier
-                              (column quarters per thread).  Same arithmetic up to rounding order.
+                              block back substitution; for k <= 32 the form of 2; 1 = one
+                              elimination step per CTA barrier with column quarters per thread in
+                              registers; 2 = one elimination step per barrier over S in shared
+                              memory with rolled loops (small code: a one-CTA kernel fetches its
+                              code from L2 on every launch).  Same arithmetic up to rounding order.
                               Other values: INVALID_ARG */
     int svd_serial;        /* cpcp_solve, fp32 with power_iters = 1.  1: each iteration's subspace
                               SVD runs in order on the solve stream.  0 (default) and 2: Z' = M^T Y
@@ -199,8 +202,9 @@ typedef struct {
                               whatever the live width).  Other values: INVALID_ARG */
     int jacobi_lanes;      /* lanes per column pair in the rounds of the core Jacobi SVD for widths
                               k <= 64: 0 (default) or 16 = 16 lanes (the 32 pairs of a round over
-                              512 threads); 8 = 8 lanes (half the warps, a shorter shuffle tree).
-                              Wider k always take 8.  Other values: INVALID_ARG */
+                              512 threads); 8 = 8 lanes (half the warps, a shorter shuffle tree;
+                              measured 2-7% slower per solve).  Wider k always take 8.  Other
+                              values: INVALID_ARG */
 } cpcp_options;
 
 /* Phases timed when cpcp_options.profile is set. */

@@ -640,6 +640,14 @@ __device__ __forceinline__ void cb_block_row(float *Gs, float *Us, float *piv, i
     }
 }
 
+template <int NT>
+__device__ void chol_s_body(const float *__restrict__ partial, int splits, int kmax, int k, float *__restrict__ R,
+                            float *__restrict__ Rinv, const float *__restrict__ Rprev, float *__restrict__ Rtot,
+                            int ldr, int *well_out, unsigned char *smraw, double *red);
+
+// (widths k <= 32 take the compact unblocked form below, chol_s_body:
+// measured faster there, 27.7 -> 26.5 ms per video solve at k = 15, and
+// slower at k = 60, where the blocked form's four block rows win)
 __global__ void __launch_bounds__(CB_NT, 1) chol_blk_kernel(const float *__restrict__ partial, int splits, int kmax,
                                                              const int *kdyn, float *__restrict__ R,
                                                              float *__restrict__ Rinv, const float *__restrict__ Rprev,
@@ -660,6 +668,10 @@ __global__ void __launch_bounds__(CB_NT, 1) chol_blk_kernel(const float *__restr
         return;
     }
     if (stats != nullptr && tid == 0) atomicAdd(stats, 1);
+    if (k <= 32) {
+        chol_s_body<CB_NT>(partial, splits, kmax, k, R, Rinv, Rprev, Rtot, ldr, well_out, smraw, red);
+        return;
+    }
     const int ld = cb_ld(kmax);
     float *Gs = reinterpret_cast<float *>(smraw);  // S (upper); later R
     float *Us = Gs + (size_t)kmax * ld;            // U (unit upper); later R for Rtot
@@ -865,26 +877,12 @@ size_t chol_s_smem(int kmax)
     return (size_t)(2 * kmax * (kmax + 1) + 2 * kmax + 8) * sizeof(float) + 64;
 }
 
-__global__ void __launch_bounds__(CS_NT, 1) chol_s_kernel(const float *__restrict__ partial, int splits, int kmax,
-                                                           const int *kdyn, float *__restrict__ R,
-                                                           float *__restrict__ Rinv, const float *__restrict__ Rprev,
-                                                           float *__restrict__ Rtot, int ldr, int *well_out,
-                                                           const int *skip_in, int *stats)
+template <int NT>
+__device__ void chol_s_body(const float *__restrict__ partial, int splits, int kmax, int k, float *__restrict__ R,
+                            float *__restrict__ Rinv, const float *__restrict__ Rprev, float *__restrict__ Rtot,
+                            int ldr, int *well_out, unsigned char *smraw, double *red)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ double red[CS_NT / 32];
-    const int k = *kdyn;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (skip_in != nullptr && *skip_in) {
-        for (int idx = tid; idx < k * k; idx += CS_NT) {
-            const int i = idx / k, c = idx % k;
-            R[(int64_t)i * ldr + c] = (i == c) ? 1.f : 0.f;
-            Rinv[(int64_t)i * ldr + c] = (i == c) ? 1.f : 0.f;
-            if (Rtot != nullptr) Rtot[(int64_t)i * ldr + c] = Rprev[(int64_t)i * ldr + c];
-        }
-        return;
-    }
-    if (stats != nullptr && tid == 0) atomicAdd(stats, 1);
     const int ld = kmax + 1;
     float *S = reinterpret_cast<float *>(smraw);
     float *P = S + (size_t)kmax * ld;  // Rprev, then R for Rtot
@@ -893,14 +891,14 @@ __global__ void __launch_bounds__(CS_NT, 1) chol_s_kernel(const float *__restric
     const int64_t slice = (int64_t)kmax * kmax;
     const float tol = FLT_EPSILON * FLT_EPSILON;
 
-    for (int c = tid; c < k; c += CS_NT) {
+    for (int c = tid; c < k; c += NT) {
         const float g = chol_gram_entry(partial, splits, slice, kmax, c, c);
         dsc[c] = (g > 0.f && isfinite(g)) ? sqrtf(g) : 0.f;
     }
     __syncthreads();
     // the equilibrated Gram matrix (upper; W^T = 0 below) and its distance from I
     double defect = 0.0;
-    for (int idx = tid; idx < k * k; idx += CS_NT) {
+    for (int idx = tid; idx < k * k; idx += NT) {
         const int x = idx / k, y = idx - (idx / k) * k;
         float v = 0.f;
         if (x <= y && dsc[x] > 0.f && dsc[y] > 0.f) {
@@ -916,7 +914,7 @@ __global__ void __launch_bounds__(CS_NT, 1) chol_s_kernel(const float *__restric
     __syncthreads();
     if (tid == 0 && well_out != nullptr) {
         double tot = 0.0;
-        for (int q = 0; q < CS_NT / 32; q++) tot += red[q];
+        for (int q = 0; q < NT / 32; q++) tot += red[q];
         *well_out = tot <= 0.25 ? 1 : 0;
     }
 
@@ -928,7 +926,7 @@ __global__ void __launch_bounds__(CS_NT, 1) chol_s_kernel(const float *__restric
         if (!drop) {
             const float inv = rcp_nr(p);
 #pragma unroll 1
-            for (int x = j + 1 + warp; x < k; x += CS_NT / 32) {
+            for (int x = j + 1 + warp; x < k; x += NT / 32) {
                 const float gx = S[j * ld + x] * inv;  // G[j][x] / p_j
 #pragma unroll 1
                 for (int y = lane; y < k; y += 32) {
@@ -940,12 +938,12 @@ __global__ void __launch_bounds__(CS_NT, 1) chol_s_kernel(const float *__restric
         }
         __syncthreads();
     }
-    for (int c = tid; c < k; c += CS_NT) piv[c] = sqrtf(piv[c]);
+    for (int c = tid; c < k; c += NT) piv[c] = sqrtf(piv[c]);
     __syncthreads();
 
     // undo the equilibration: R = P U D (row x of P U is S[x][x:] / P_x),
     // R^{-1} = D^{-1} W P^{-1} with W[y][x] = S[x][y] below the diagonal
-    for (int idx = tid; idx < k * k; idx += CS_NT) {
+    for (int idx = tid; idx < k * k; idx += NT) {
         const int x = idx / k, y = idx - (idx / k) * k;
         const float px = piv[x], py = piv[y];
         float rv = 0.f, ri = 0.f;
@@ -962,20 +960,43 @@ __global__ void __launch_bounds__(CS_NT, 1) chol_s_kernel(const float *__restric
     if (Rprev == nullptr) return;
     __syncthreads();
     // R (upper) over the factorised S, for Rtot = R Rprev
-    for (int idx = tid; idx < k * k; idx += CS_NT) {
+    for (int idx = tid; idx < k * k; idx += NT) {
         const int x = idx / k, y = idx - (idx / k) * k;
         if (y < x) continue;
         const float px = piv[x];
         S[x * ld + y] = x == y ? px * dsc[x] : (px > 0.f ? S[x * ld + y] * rcp_nr(px) * dsc[y] : 0.f);
     }
     __syncthreads();
-    for (int idx = tid; idx < k * k; idx += CS_NT) {
+    for (int idx = tid; idx < k * k; idx += NT) {
         const int x = idx / k, y = idx - (idx / k) * k;
         float sacc = 0.f;
         if (x <= y)
             for (int q = x; q <= y; q++) sacc = fmaf(S[x * ld + q], P[q * ld + y], sacc);
         Rtot[(int64_t)x * ldr + y] = sacc;
     }
+}
+
+__global__ void __launch_bounds__(CS_NT, 1) chol_s_kernel(const float *__restrict__ partial, int splits, int kmax,
+                                                           const int *kdyn, float *__restrict__ R,
+                                                           float *__restrict__ Rinv, const float *__restrict__ Rprev,
+                                                           float *__restrict__ Rtot, int ldr, int *well_out,
+                                                           const int *skip_in, int *stats)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double red[CS_NT / 32];
+    const int k = *kdyn;
+    const int tid = threadIdx.x;
+    if (skip_in != nullptr && *skip_in) {
+        for (int idx = tid; idx < k * k; idx += CS_NT) {
+            const int i = idx / k, c = idx % k;
+            R[(int64_t)i * ldr + c] = (i == c) ? 1.f : 0.f;
+            Rinv[(int64_t)i * ldr + c] = (i == c) ? 1.f : 0.f;
+            if (Rtot != nullptr) Rtot[(int64_t)i * ldr + c] = Rprev[(int64_t)i * ldr + c];
+        }
+        return;
+    }
+    if (stats != nullptr && tid == 0) atomicAdd(stats, 1);
+    chol_s_body<CS_NT>(partial, splits, kmax, k, R, Rinv, Rprev, Rtot, ldr, well_out, smraw, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -1702,7 +1723,7 @@ void ensure_small_attrs()
         cudaFuncSetAttribute(chol_q_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)chol_q_smem(small_kmax<float>()));
         cudaFuncSetAttribute(chol_blk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)chol_blk_smem(small_kmax<float>()));
+                             (int)std::max(chol_blk_smem(small_kmax<float>()), chol_s_smem(small_kmax<float>())));
         cudaFuncSetAttribute(chol_s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)chol_s_smem(small_kmax<float>()));
     }
@@ -1724,7 +1745,8 @@ void launch_chol(const T *partialG, int splits, int kmax, const int *kdyn, T *R,
             return;
         }
         if (kmax <= small_kmax<float>() && form == 0) {
-            chol_blk_kernel<<<1, CB_NT, chol_blk_smem(kmax), st>>>(partialG, splits, kmax, kdyn, R, Rinv, Rprev, Rtot,
+            chol_blk_kernel<<<1, CB_NT, std::max(chol_blk_smem(kmax), chol_s_smem(kmax)), st>>>(
+                partialG, splits, kmax, kdyn, R, Rinv, Rprev, Rtot,
                                                                   ldr, well_out, skip_in, stats);
             return;
         }

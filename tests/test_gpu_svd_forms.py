@@ -1,6 +1,8 @@
 """GPU parity of the alternative forms of the iteration's subspace SVD (fp32):
-the Cholesky of CholeskyQR by 16-column block rows (chol_form 0) or one
-elimination step per barrier (1); the iteration's SVD on two streams with
+the Cholesky of CholeskyQR by 16-column block rows (chol_form 0; the
+compact unblocked form for widths up to 32) or one elimination step per
+barrier (1: registers, 2: shared memory); the core Jacobi rounds with 16 or 8
+lanes per column pair; the iteration's SVD on two streams with
 Z = (M^T Y) R_Y^{-1} (svd_serial 0 and 2) or in order with Z = M^T Q_Y (1);
 Gram matrices of tall blocks by row ranges (gram_form 0) or by 64 x 64 tiles
 (1).  Every form solves eq. (cpcp) to the fp64 oracle's optimum (FISTA with
@@ -40,11 +42,14 @@ def solve(cp, p, levels, tol, **opts):
     return L.double().cpu().numpy(), S.double().cpu().numpy(), info
 
 
-@pytest.fixture(scope="module")
-def small():
-    # 300 x 260 (SIMT products, tiled Gram matrices): ragged tiles, masked
-    p = W.planted_cpcp(300, 260, 8, 0.1, 0.8, seed=2024, levels=2)
-    L, S, _ = oracle.fista(p["D"], p["mask"], p["lam"], p["mu"], levels=1, tol=1e-11)
+@pytest.fixture(scope="module", params=[(8, 0.1, 0.8), (24, 0.05, 0.9)])
+def small(request):
+    # 300 x 260 (SIMT products, tiled Gram matrices): ragged tiles, masked;
+    # rank 8 gives a subspace width k = 18 (the compact Cholesky of form 0),
+    # rank 24 k = 34 (its blocked form)
+    rank, corr, obs = request.param
+    p = W.planted_cpcp(300, 260, rank, corr, obs, seed=2024, levels=2)
+    L, S, _ = oracle.fista(p["D"], p["mask"], p["lam"], p["mu"], levels=1, tol=1e-10 if rank > 8 else 1e-11)
     return p, L, S
 
 
@@ -58,7 +63,7 @@ def tall():
 
 
 @pytest.mark.parametrize("svd_serial", [0, 1, 2])
-@pytest.mark.parametrize("chol_form", [0, 1])
+@pytest.mark.parametrize("chol_form", [0, 1, 2])
 @pytest.mark.parametrize("levels", [1, 2])
 def test_forms_match_oracle_small(cp, small, svd_serial, chol_form, levels):
     p, Lr, Sr = small
@@ -76,7 +81,7 @@ def test_forms_tall_oracle_residual_and_agreement(cp, tall, levels):
     p = tall
     ref = None
     for opts in ({"svd_serial": 1, "chol_form": 1, "gram_form": 1}, {}, {"svd_serial": 2},
-                 {"chol_form": 1, "gram_form": 1}):
+                 {"chol_form": 1, "gram_form": 1}, {"chol_form": 2, "jacobi_lanes": 8}):
         L, S, info = solve(cp, p, levels, 1e-6, **opts)
         assert info["status"] == 0, (opts, info)
         r = oracle.relkkt(p["D"], p["mask"], p["lam"], p["mu"], L, S)
@@ -91,6 +96,6 @@ def test_forms_tall_oracle_residual_and_agreement(cp, tall, levels):
 
 def test_forms_reject_bad_values(cp):
     p = W.planted_cpcp(64, 48, 2, 0.1, 0.8, seed=1, levels=1)
-    for opts in ({"svd_serial": 3}, {"chol_form": 2}, {"gram_form": -1}):
+    for opts in ({"svd_serial": 3}, {"chol_form": 3}, {"gram_form": -1}, {"jacobi_lanes": 4}):
         with pytest.raises(cp.CPCPError):
             solve(cp, p, 1, 1e-6, **opts)
