@@ -182,7 +182,8 @@ def golden_error(name: str, L, S) -> dict | None:
 TRAFFIC = {
     "fused fine pass": (50.8e6, "profiles/dram_cpcp2000.md"),
     "products with M": (16.54e6, "profiles/dram_cpcp2000.md"),
-    "core Jacobi SVD": (0.081e6, "profiles/dram_cpcp2000.md"),
+    "CholeskyQR2": (1.31e6, "profiles/dram_cpcp2000.md"),
+    "core Jacobi SVD": (0.082e6, "profiles/dram_cpcp2000.md"),
     "factor products": (0.55e6, "profiles/dram_cpcp2000.md"),
 }
 FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
