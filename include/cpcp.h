@@ -205,6 +205,16 @@ typedef struct {
                               512 threads); 8 = 8 lanes (half the warps, a shorter shuffle tree;
                               measured 2-7% slower per solve).  Wider k always take 8.  Other
                               values: INVALID_ARG */
+    int jacobi_check;      /* core Jacobi SVD of the iterations' subspace steps (the residual checks
+                              keep 0): 0 (default) = sweeps until the
+                              largest rotated |x_p . x_q| / (|x_p| |x_q|) of a sweep is at most the
+                              stop level (1e-2 while the continuation weight falls, 1e-4 after); 1 =
+                              also, after a sweep that rotated more than that, measure every pair's
+                              off-orthogonality in one parallel pass and end when the largest is at
+                              most a tenth of the stop level, instead of running a sweep to confirm
+                              it (measured: 153 -> 151 sweeps and no time gained on the 2000 x 2000
+                              workload, whose second sweeps still rotate; -0.6% on the 4-level video
+                              solve).  Other values: INVALID_ARG */
 } cpcp_options;
 
 /* Phases timed when cpcp_options.profile is set. */

@@ -279,7 +279,8 @@ void launch_cqr_pass2(int rows, const float *X, float *Q1, int KM, const int *kd
                       cudaStream_t st);
 template <typename T>
 void launch_jacobi(const T *Rz, int ldr, const int *kdyn, T *Ut, T *Wt, T *sig, int kmax, const Ctrl *ctrl,
-                   cudaStream_t st, int *stats = nullptr, T *Us = nullptr, Ctrl *svt = nullptr, int lanes = 16);
+                   cudaStream_t st, int *stats = nullptr, T *Us = nullptr, Ctrl *svt = nullptr, int lanes = 16,
+                   int check = 0);
 template <typename T>
 void launch_svt_small(const T *Ut, const T *sig, int ldr, Ctrl *ctrl, T *Us, double *sig64, cudaStream_t st);
 // all_cols = 1: fill columns [0, ctrl->k); else columns [ctrl->k, ctrl->k_next)

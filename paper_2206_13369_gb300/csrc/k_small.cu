@@ -1348,7 +1348,8 @@ __host__ __device__ constexpr int jac_ld(int k) { return (k + 31) / 32 * 32 + 8;
 template <typename T, int EL, int TPP>
 __device__ __forceinline__ void jacobi_body(const T *__restrict__ Rz, int ldr, int k, T *__restrict__ Ut,
                                             T *__restrict__ Wt, T *__restrict__ sig, const Ctrl *ctrl, int *stats,
-                                            T *__restrict__ Us, Ctrl *svt, T *sm, T *wmax, T *amax_p)
+                                            T *__restrict__ Us, Ctrl *svt, T *sm, T *wmax, T *amax_p,
+                                            int check = 0)
 {
     // columns 8 banks apart (ld = 8 mod 32): with 8 lanes per pair the four
     // pairs a warp serves read 32 distinct banks
@@ -1494,6 +1495,31 @@ __device__ __forceinline__ void jacobi_body(const T *__restrict__ Rz, int ldr, i
         const int done = !(gmax > stop);
         __syncthreads();
         if (done) break;
+        if (check) {
+            // every pair's off-orthogonality after this sweep, in one pass
+            // (warp w rows p = w, w + 16, ..., lanes the partners q > p),
+            // with the rotation's own skip rules; below stop / 10 the call
+            // ends instead of running a sweep to confirm it
+            T cmax = T(0);
+            for (int p = warp; p < k; p += JAC_NT / 32) {
+                const T a = sv[p];
+                if (!(a > small)) continue;
+                for (int q = p + 1 + lane; q < k; q += 32) {
+                    const T b = sv[q];
+                    if (!(b > small) || a + b <= th2) continue;
+                    T g = T(0);
+                    for (int i = 0; i < k; i++) g = fma(X[p * ld + i], X[q * ld + i], g);
+                    cmax = max(cmax, fabs(g) * rsqrt_of(a) * rsqrt_of(b));
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+            if (lane == 0) wmax[warp] = cmax;
+            __syncthreads();
+            T call = T(0);
+            for (int w = 0; w < JAC_NT / 32; w++) call = max(call, wmax[w]);
+            __syncthreads();
+            if (!(call > T(0.1) * stop)) break;
+        }
     }
     if (stats != nullptr && tid == 0) {
         atomicAdd(stats, 1);
@@ -1552,7 +1578,7 @@ template <typename T, int NARROW = 0>
 __global__ void __launch_bounds__(JAC_NT) jacobi_kernel(const T *__restrict__ Rz, int ldr, const int *kdyn,
                                                         T *__restrict__ Ut, T *__restrict__ Wt, T *__restrict__ sig,
                                                         const Ctrl *ctrl, int *stats, T *__restrict__ Us,
-                                                        Ctrl *svt)
+                                                        Ctrl *svt, int check)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ T wmax[JAC_NT / 32];  // per-warp largest |g|/sqrt(ab) rotated in the sweep
@@ -1563,11 +1589,11 @@ __global__ void __launch_bounds__(JAC_NT) jacobi_kernel(const T *__restrict__ Rz
     // (NARROW: half the warps in the rounds, a shorter shuffle tree); else 8
     if (k <= 64) {
         if constexpr (NARROW)
-            jacobi_body<T, 8, 8>(Rz, ldr, k, Ut, Wt, sig, ctrl, stats, Us, svt, sm, wmax, &amax);
+            jacobi_body<T, 8, 8>(Rz, ldr, k, Ut, Wt, sig, ctrl, stats, Us, svt, sm, wmax, &amax, check);
         else
-            jacobi_body<T, 4, 16>(Rz, ldr, k, Ut, Wt, sig, ctrl, stats, Us, svt, sm, wmax, &amax);
+            jacobi_body<T, 4, 16>(Rz, ldr, k, Ut, Wt, sig, ctrl, stats, Us, svt, sm, wmax, &amax, check);
     } else {
-        jacobi_body<T, 16, 8>(Rz, ldr, k, Ut, Wt, sig, ctrl, stats, Us, svt, sm, wmax, &amax);
+        jacobi_body<T, 16, 8>(Rz, ldr, k, Ut, Wt, sig, ctrl, stats, Us, svt, sm, wmax, &amax, check);
     }
 }
 
@@ -1857,15 +1883,16 @@ void launch_cqr_pass2(int rows, const float *X, float *Q1, int KM, const int *kd
 
 template <typename T>
 void launch_jacobi(const T *Rz, int ldr, const int *kdyn, T *Ut, T *Wt, T *sig, int kmax, const Ctrl *ctrl,
-                   cudaStream_t st, int *stats, T *Us, Ctrl *svt, int lanes)
+                   cudaStream_t st, int *stats, T *Us, Ctrl *svt, int lanes, int check)
 {
     ensure_small_attrs<T>();
     CPCP_COUNT_LAUNCH();
     if (lanes == 8)
         jacobi_kernel<T, 1><<<1, JAC_NT, jacobi_smem<T>(kmax), st>>>(Rz, ldr, kdyn, Ut, Wt, sig, ctrl, stats, Us,
-                                                                     svt);
+                                                                     svt, check);
     else
-        jacobi_kernel<T><<<1, JAC_NT, jacobi_smem<T>(kmax), st>>>(Rz, ldr, kdyn, Ut, Wt, sig, ctrl, stats, Us, svt);
+        jacobi_kernel<T><<<1, JAC_NT, jacobi_smem<T>(kmax), st>>>(Rz, ldr, kdyn, Ut, Wt, sig, ctrl, stats, Us, svt,
+                                                                  check);
 }
 
 template <typename T>
@@ -1909,7 +1936,7 @@ int small_kmax_f64() { return small_kmax<double>(); }
     template void launch_chol<T>(const T *, int, int, const int *, T *, T *, const T *, T *, int, int *, const int *, \
                                  cudaStream_t, int *, int);                                                          \
     template void launch_jacobi<T>(const T *, int, const int *, T *, T *, T *, int, const Ctrl *, cudaStream_t,       \
-                                   int *, T *, Ctrl *, int);                                                         \
+                                   int *, T *, Ctrl *, int, int);                                                    \
     template void launch_svt_small<T>(const T *, const T *, int, Ctrl *, T *, double *, cudaStream_t);               \
     template void launch_fill_random<T>(T *, int64_t, int, const Ctrl *, int, const T *, int, uint64_t, cudaStream_t); \
     template void launch_fill_prolong<T>(T *, int64_t, int, const Ctrl *, const T *, int, uint64_t, int, T *, int64_t, \

@@ -887,7 +887,8 @@ void subspace_svd_iter(cpcp_context *h, SvdWork<float> &w, int m, int nc, const 
     h->timer.close(tq);
     const int tj = h->timer.open_sub(DETAIL_JACOBI);
     launch_jacobi<float>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st, w.stats, Us, svt,
-                     h->opt.jacobi_lanes == 8 ? 8 : 16);
+                     h->opt.jacobi_lanes == 8 ? 8 : 16,
+                     h->timer.in_iter ? h->opt.jacobi_check : 0);
     h->timer.close(tj);
 }
 
@@ -925,7 +926,8 @@ void subspace_svd_bf16(cpcp_context *h, SvdWork<float> &w, int m, int nc, const 
     }
     const int tj = h->timer.open_sub(DETAIL_JACOBI);
     launch_jacobi<float>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st, w.stats, Us, svt,
-                     h->opt.jacobi_lanes == 8 ? 8 : 16);
+                     h->opt.jacobi_lanes == 8 ? 8 : 16,
+                     h->timer.in_iter ? h->opt.jacobi_check : 0);
     h->timer.close(tj);
 }
 
@@ -962,7 +964,8 @@ void subspace_svd(cpcp_context *h, SvdWork<T> &w, int m, int nc, const T *Mx, in
     }
     const int tj = h->timer.open_sub(DETAIL_JACOBI);
     launch_jacobi<T>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st, w.stats, Us, svt,
-                     h->opt.jacobi_lanes == 8 ? 8 : 16);
+                     h->opt.jacobi_lanes == 8 ? 8 : 16,
+                     h->timer.in_iter ? h->opt.jacobi_check : 0);
     h->timer.close(tj);
 }
 
@@ -3111,6 +3114,8 @@ cpcp_status cpcp_solve(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D
             throw CpcpError{CPCP_ERR_INVALID_ARG, "gram_form must be 0 or 1"};
         if (h->opt.jacobi_lanes != 0 && h->opt.jacobi_lanes != 8 && h->opt.jacobi_lanes != 16)
             throw CpcpError{CPCP_ERR_INVALID_ARG, "jacobi_lanes must be 0, 8 or 16"};
+        if (h->opt.jacobi_check < 0 || h->opt.jacobi_check > 1)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "jacobi_check must be 0 or 1"};
         if (h->opt.unroll > 0) {
             if (dt != CPCP_F32) throw CpcpError{CPCP_ERR_INVALID_ARG, "the unrolled program is fp32"};
             if (h->opt.transfer == 1)
