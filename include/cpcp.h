@@ -215,6 +215,15 @@ typedef struct {
                               it (measured: 153 -> 151 sweeps and no time gained on the 2000 x 2000
                               workload, whose second sweeps still rotate; -0.6% on the 4-level video
                               solve).  Other values: INVALID_ARG */
+    int pdl_off;           /* cpcp_solve iterations in the two-stream subspace step (svd_serial):
+                              0 (default) = programmatic dependent launch of the solve stream's
+                              chain of small kernels (Gram matrices, Cholesky, second CholeskyQR
+                              pass, Jacobi, schedule end): each starts while its predecessor runs
+                              and waits for its results on the device, which hides a launch latency
+                              per kernel (measured 25.0 -> 24.4 ms on the 2000 x 2000 workload,
+                              results bit-identical); not while profiling, and not in the in-order
+                              form (where it made the 4-level video solve 4% slower).  1 = ordinary
+                              stream order.  Other values: INVALID_ARG */
 } cpcp_options;
 
 /* Phases timed when cpcp_options.profile is set. */

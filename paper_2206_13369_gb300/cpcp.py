@@ -40,7 +40,8 @@ class Options(C.Structure):
                 ("pass_simt", C.c_int), ("plain_launches", C.c_int), ("transfer", C.c_int),
                 ("early_test", C.c_int), ("products_tc", C.c_int), ("cholqr_fused", C.c_int),
                 ("check_serial", C.c_int), ("chol_form", C.c_int), ("svd_serial", C.c_int),
-                ("gram_form", C.c_int), ("jacobi_lanes", C.c_int), ("jacobi_check", C.c_int)]
+                ("gram_form", C.c_int), ("jacobi_lanes", C.c_int), ("jacobi_check", C.c_int),
+                ("pdl_off", C.c_int)]
 
 
 class Info(C.Structure):

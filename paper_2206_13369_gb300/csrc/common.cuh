@@ -15,6 +15,41 @@ namespace cpcp {
 extern unsigned long long g_kernel_launches;
 #define CPCP_COUNT_LAUNCH() (++::cpcp::g_kernel_launches)
 
+// Programmatic dependent launch of the iteration's chain of small kernels:
+// while g_pdl is set (by the solver, around launches that follow a kernel of
+// the same stream), the launchers below ask for programmatic stream
+// serialisation, so the next kernel starts while its predecessor runs and
+// waits at pdl_enter() for the predecessor's completion and memory.  Every
+// kernel such a launcher starts calls pdl_enter() before it reads anything
+// (it does nothing for a kernel launched without the attribute).
+extern thread_local int g_pdl;
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+struct PdlScope {
+    int prev;
+    explicit PdlScope(bool on) : prev(g_pdl) { g_pdl = on ? 1 : 0; }
+    ~PdlScope() { g_pdl = prev; }
+};
+// kernel launch with the programmatic-serialisation attribute when g_pdl is set
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = g_pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Device-resident scalars of one solve.  The per-iteration schedule (momentum
 // weight, continuation weight, thresholds, ranks, subspace width) lives here
 // so that an iteration needs no host round trip and can be graph-captured.

@@ -654,6 +654,7 @@ __global__ void __launch_bounds__(CB_NT, 1) chol_blk_kernel(const float *__restr
                                                              float *__restrict__ Rtot, int ldr, int *well_out,
                                                              const int *skip_in, int *stats)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ double red[CB_NT / 32];
     const int k = *kdyn;
@@ -1243,6 +1244,7 @@ template <typename T>
 __global__ void __launch_bounds__(CQR_NT) gram_rows_kernel(int rows, const T *__restrict__ X, int KM, const int *kdyn,
                                                             T *part)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smraw[];
     const int k = *kdyn;
     if (k < 1) return;
@@ -1279,6 +1281,7 @@ __global__ void __launch_bounds__(CQR_NT, 1)
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ double red[CQR_NT / 32];
     __shared__ int s_last;
+    pdl_enter();
     if (*well) return;
     const int k = *kdyn;
     if (k < 1) return;
@@ -1580,6 +1583,7 @@ __global__ void __launch_bounds__(JAC_NT) jacobi_kernel(const T *__restrict__ Rz
                                                         const Ctrl *ctrl, int *stats, T *__restrict__ Us,
                                                         Ctrl *svt, int check)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ T wmax[JAC_NT / 32];  // per-warp largest |g|/sqrt(ab) rotated in the sweep
     __shared__ T amax;
@@ -1705,6 +1709,7 @@ __global__ void ctrl_set_check_kernel(Ctrl *chk, const Ctrl *it, double mu_c)
 
 __global__ void ctrl_end_kernel(Ctrl *c)
 {
+    pdl_enter();
     c->t = c->t_next;
     c->rp = c->rk;
     c->rk = c->r_new;
@@ -1771,9 +1776,8 @@ void launch_chol(const T *partialG, int splits, int kmax, const int *kdyn, T *R,
             return;
         }
         if (kmax <= small_kmax<float>() && form == 0) {
-            chol_blk_kernel<<<1, CB_NT, std::max(chol_blk_smem(kmax), chol_s_smem(kmax)), st>>>(
-                partialG, splits, kmax, kdyn, R, Rinv, Rprev, Rtot,
-                                                                  ldr, well_out, skip_in, stats);
+            launch_pdl(chol_blk_kernel, dim3(1), dim3(CB_NT), std::max(chol_blk_smem(kmax), chol_s_smem(kmax)), st,
+                       partialG, splits, kmax, kdyn, R, Rinv, Rprev, Rtot, ldr, well_out, skip_in, stats);
             return;
         }
         if (kmax <= small_kmax<float>()) {
@@ -1854,7 +1858,7 @@ int launch_gram_rows(int rows, const float *X, int KM, const int *kdyn, float *p
         attr = smem;
     }
     CPCP_COUNT_LAUNCH();
-    gram_rows_kernel<float><<<nb, CQR_NT, smem, st>>>(rows, X, KM, kdyn, part);
+    launch_pdl(gram_rows_kernel<float>, dim3(nb), dim3(CQR_NT), smem, st, rows, X, KM, kdyn, part);
     return nb;
 }
 
@@ -1877,8 +1881,8 @@ void launch_cqr_pass2(int rows, const float *X, float *Q1, int KM, const int *kd
     // workspace's 64)
     const int nb = std::max(1, std::min(16, (rows + 127) / 128));
     CPCP_COUNT_LAUNCH();
-    cqr_pass2_kernel<float><<<nb, CQR_NT, smem, st>>>(rows, X, Q1, KM, kdyn, Rt, Rti, well, Gp, G, R2, R2i, ticket,
-                                                      stats, gp_off);
+    launch_pdl(cqr_pass2_kernel<float>, dim3(nb), dim3(CQR_NT), smem, st, rows, X, Q1, KM, kdyn, Rt, Rti, well, Gp,
+               G, R2, R2i, ticket, stats, gp_off);
 }
 
 template <typename T>
@@ -1888,11 +1892,11 @@ void launch_jacobi(const T *Rz, int ldr, const int *kdyn, T *Ut, T *Wt, T *sig, 
     ensure_small_attrs<T>();
     CPCP_COUNT_LAUNCH();
     if (lanes == 8)
-        jacobi_kernel<T, 1><<<1, JAC_NT, jacobi_smem<T>(kmax), st>>>(Rz, ldr, kdyn, Ut, Wt, sig, ctrl, stats, Us,
-                                                                     svt, check);
+        launch_pdl(jacobi_kernel<T, 1>, dim3(1), dim3(JAC_NT), jacobi_smem<T>(kmax), st, Rz, ldr, kdyn, Ut, Wt, sig,
+                   ctrl, stats, Us, svt, check);
     else
-        jacobi_kernel<T><<<1, JAC_NT, jacobi_smem<T>(kmax), st>>>(Rz, ldr, kdyn, Ut, Wt, sig, ctrl, stats, Us, svt,
-                                                                  check);
+        launch_pdl(jacobi_kernel<T, 0>, dim3(1), dim3(JAC_NT), jacobi_smem<T>(kmax), st, Rz, ldr, kdyn, Ut, Wt, sig,
+                   ctrl, stats, Us, svt, check);
 }
 
 template <typename T>
@@ -1921,7 +1925,11 @@ void launch_fill_prolong(T *Omega, int64_t ldo, int rows_o, const Ctrl *ctrl, co
 }
 
 void launch_ctrl_begin(Ctrl *c, cudaStream_t st) { CPCP_COUNT_LAUNCH(); ctrl_begin_kernel<<<1, 1, 0, st>>>(c); }
-void launch_ctrl_end(Ctrl *c, cudaStream_t st) { CPCP_COUNT_LAUNCH(); ctrl_end_kernel<<<1, 1, 0, st>>>(c); }
+void launch_ctrl_end(Ctrl *c, cudaStream_t st)
+{
+    CPCP_COUNT_LAUNCH();
+    launch_pdl(ctrl_end_kernel, dim3(1), dim3(1), 0, st, c);
+}
 void launch_ctrl_take_width(Ctrl *c, cudaStream_t st) { CPCP_COUNT_LAUNCH(); ctrl_take_width_kernel<<<1, 1, 0, st>>>(c); }
 void launch_ctrl_set_check(Ctrl *chk, const Ctrl *it, double mu_c, cudaStream_t st)
 {

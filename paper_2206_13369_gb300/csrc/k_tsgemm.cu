@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(TS_NT)
                    T *__restrict__ C, int64_t ldc, int64_t slice, const int *kdynR, const int *kdynK,
                    const int *kdynN, int Nstat, int ks, const int *skip)
 {
+    pdl_enter();
     using Cfg = TsCfg<T>;
     constexpr int TK = Cfg::TK, V = Cfg::V;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -300,13 +301,15 @@ void ts_launch(int rows, int K, const T *A, int64_t lda, const T *B, int64_t ldb
     cfg.blockDim = dim3(TS_NT);
     cfg.dynamicSmemBytes = ts_smem<T>();
     cfg.stream = st;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = (unsigned)cl;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = g_pdl ? 2 : 1;
     CPCP_COUNT_LAUNCH();
     cudaError_t e = cudaLaunchKernelEx(&cfg, ts_gemm_kernel<T, TN>, rows, K, A, lda, B, ldb, C, ldc, slice, kdynR,
                                        kdynK, kdynN, kmaxN, ks, skip);

@@ -33,6 +33,7 @@
 using namespace cpcp;
 
 unsigned long long cpcp::g_kernel_launches = 0;
+thread_local int cpcp::g_pdl = 0;
 
 namespace {
 
@@ -866,8 +867,14 @@ void subspace_svd_iter(cpcp_context *h, SvdWork<float> &w, int m, int nc, const 
     prod_z<float>(w, m, nc, Mx, ldx, w.Y, KM, kdyn, ax, w.Zp);  // Z' = M^T Y
     h->timer.close(tp);
     if (ax != st) CK(cudaEventRecord(h->ev_aux[1], ax));
+    // programmatic dependent launch where a kernel follows a kernel of the
+    // solve stream (not after a cross-stream wait; not while profiling)
+    const bool pdl = h->opt.pdl_off == 0 && !h->timer.on;
     int tq = h->timer.open_sub(DETAIL_CHOLQR);
-    orth_factor_only(h, w, m, w.Y, w.R1, w.R1i, kdyn, 0);
+    {
+        PdlScope ps(pdl);
+        orth_factor_only(h, w, m, w.Y, w.R1, w.R1i, kdyn, 0);
+    }
     h->timer.close(tq);
     order_after(h, aq, st, 2);
     tq = h->timer.open_sub(DETAIL_CHOLQR);
@@ -879,16 +886,21 @@ void subspace_svd_iter(cpcp_context *h, SvdWork<float> &w, int m, int nc, const 
     prod_nn_small<float>(nc, w.Zp, KM, w.R1i, KM, w.Z, KM, kdyn, KM, st);  // Z = Z' R_Y^{-1}
     h->timer.close(tq);
     tq = h->timer.open_sub(DETAIL_CHOLQR);
-    orth_factor_only(h, w, nc, w.Z, w.Rz, w.Rzi, kdyn, 1);
+    {
+        PdlScope ps(pdl);
+        orth_factor_only(h, w, nc, w.Z, w.Rz, w.Rzi, kdyn, 1);
+    }
     h->timer.close(tq);
     order_after(h, aq, st, 4);
     tq = h->timer.open_sub(DETAIL_CHOLQR);
     prod_nn_small<float>(nc, w.Z, KM, w.Rzi, KM, w.Qz, KM, kdyn, KM, aq);  // Q_Z
     h->timer.close(tq);
     const int tj = h->timer.open_sub(DETAIL_JACOBI);
-    launch_jacobi<float>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st, w.stats, Us, svt,
-                     h->opt.jacobi_lanes == 8 ? 8 : 16,
-                     h->timer.in_iter ? h->opt.jacobi_check : 0);
+    {
+        PdlScope ps(pdl && aq != st);  // (with Q_Z in order, the Jacobi follows it)
+        launch_jacobi<float>(w.Rz, KM, kdyn, w.Ut, w.Wt, w.sig, w.kcap, jac_ctrl, st, w.stats, Us, svt,
+                             h->opt.jacobi_lanes == 8 ? 8 : 16, h->timer.in_iter ? h->opt.jacobi_check : 0);
+    }
     h->timer.close(tj);
 }
 
@@ -1243,6 +1255,9 @@ void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, 
     if constexpr (std::is_same<T, float>::value) {
         if (two) subspace_svd_iter(h, w, s.m, tr.nh, Mx, ldx, s.Om, &s.ctrl->k, s.ctrl, w.Us, s.ctrl);
     }
+    // (programmatic dependent launch stays with the two-stream form: in the
+    // in-order form it made the 4-level video solve 3.6 ms slower, 93.2 ->
+    // 96.8 ms, its waiting CTAs holding SMs that the other streams' kernels use)
     if (!two) subspace_svd<T>(h, w, s.m, tr.nh, Mx, ldx, s.Om, o.q, &s.ctrl->k, s.ctrl, s.bf16, w.Us, s.ctrl);
     const int tf = h->timer.open_sub(DETAIL_FACTORS);
     h->timer.in_iter = false;
@@ -1271,7 +1286,10 @@ void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, 
     }
     h->timer.close(tf);
     h->timer.close(ts);
-    launch_ctrl_end(s.ctrl, st);
+    {
+        PdlScope ps(two && h->opt.pdl_off == 0 && !h->timer.on);
+        launch_ctrl_end(s.ctrl, st);
+    }
 }
 
 // Runs the solve on the handle's private stream: ordered after the work the
@@ -3116,6 +3134,8 @@ cpcp_status cpcp_solve(cpcp_handle h, int m, int n, cpcp_dtype dt, const void *D
             throw CpcpError{CPCP_ERR_INVALID_ARG, "jacobi_lanes must be 0, 8 or 16"};
         if (h->opt.jacobi_check < 0 || h->opt.jacobi_check > 1)
             throw CpcpError{CPCP_ERR_INVALID_ARG, "jacobi_check must be 0 or 1"};
+        if (h->opt.pdl_off < 0 || h->opt.pdl_off > 1)
+            throw CpcpError{CPCP_ERR_INVALID_ARG, "pdl_off must be 0 or 1"};
         if (h->opt.unroll > 0) {
             if (dt != CPCP_F32) throw CpcpError{CPCP_ERR_INVALID_ARG, "the unrolled program is fp32"};
             if (h->opt.transfer == 1)

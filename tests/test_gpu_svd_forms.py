@@ -96,6 +96,19 @@ def test_forms_tall_oracle_residual_and_agreement(cp, tall, levels):
 
 def test_forms_reject_bad_values(cp):
     p = W.planted_cpcp(64, 48, 2, 0.1, 0.8, seed=1, levels=1)
-    for opts in ({"svd_serial": 3}, {"chol_form": 3}, {"gram_form": -1}, {"jacobi_lanes": 4}):
+    for opts in ({"svd_serial": 3}, {"chol_form": 3}, {"gram_form": -1}, {"jacobi_lanes": 4}, {"pdl_off": 2},
+                 {"jacobi_check": 2}):
         with pytest.raises(cp.CPCPError):
             solve(cp, p, 1, 1e-6, **opts)
+
+
+@pytest.mark.parametrize("svd_serial", [0, 1])
+def test_pdl_results_bit_identical(cp, tall, svd_serial):
+    # programmatic dependent launch changes only when kernels start, never
+    # what they compute: the results match the in-order launches bit for bit
+    p = tall
+    L0, S0, i0 = solve(cp, p, 2, 1e-6, svd_serial=svd_serial, pdl_off=1)
+    L1, S1, i1 = solve(cp, p, 2, 1e-6, svd_serial=svd_serial)
+    assert i0["status"] == 0 and i1["status"] == 0
+    assert i0["iters"] == i1["iters"]
+    assert np.array_equal(L0, L1) and np.array_equal(S0, S1)
