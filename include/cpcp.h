@@ -221,7 +221,7 @@ typedef struct {
                               pass, Jacobi, schedule end): each starts while its predecessor runs
                               and waits for its results on the device, which hides a launch latency
                               per kernel (measured 25.0 -> 24.4 ms on the 2000 x 2000 workload,
-                              results bit-identical); not while profiling, and not in the in-order
+                              results bit-identical); not with profile = 2, and not in the in-order
                               form (where it made the 4-level video solve 4% slower).  1 = ordinary
                               stream order.  Other values: INVALID_ARG */
 } cpcp_options;

@@ -868,8 +868,9 @@ void subspace_svd_iter(cpcp_context *h, SvdWork<float> &w, int m, int nc, const 
     h->timer.close(tp);
     if (ax != st) CK(cudaEventRecord(h->ev_aux[1], ax));
     // programmatic dependent launch where a kernel follows a kernel of the
-    // solve stream (not after a cross-stream wait; not while profiling)
-    const bool pdl = h->opt.pdl_off == 0 && !h->timer.on;
+    // solve stream (not after a cross-stream wait; not while kernel families
+    // are timed, whose events bracket single kernels)
+    const bool pdl = h->opt.pdl_off == 0 && !h->timer.detail;
     int tq = h->timer.open_sub(DETAIL_CHOLQR);
     {
         PdlScope ps(pdl);
@@ -1287,7 +1288,7 @@ void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, 
     h->timer.close(tf);
     h->timer.close(ts);
     {
-        PdlScope ps(two && h->opt.pdl_off == 0 && !h->timer.on);
+        PdlScope ps(two && h->opt.pdl_off == 0 && !h->timer.detail);
         launch_ctrl_end(s.ctrl, st);
     }
 }
