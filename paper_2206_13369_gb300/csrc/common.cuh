@@ -160,9 +160,11 @@ bool launch_pass_tc(const PassArgs<float> &p, int *err, cudaStream_t st);
 // partial slices (returned count, 0 = not launched: an operand breaks the TMA
 // rules) for launch_reduce_partial.  err: set when a bounded wait expired.
 int launch_prod_tc(int tn, int P, int K, const float *M, int64_t ldm, const float *B, int64_t ldb, int bcols_max,
-                   const int *kdyn, float *part, int64_t ldc, int64_t slice, int max_splits, int *err, cudaStream_t st);
+                   const int *kdyn, float *part, int64_t ldc, int64_t slice, int max_splits, int *err, cudaStream_t st,
+                   int max_ctas = 0);
 // CTAs that launch_prod_tc runs for a P-row output with K-long contraction
-int prod_tc_ctas(int P, int K, int max_splits);
+// (max_ctas > 0: at most that many instead of about one per SM)
+int prod_tc_ctas(int P, int K, int max_splits, int max_ctas = 0);
 // multiprocessors of the current device
 int gpu_sm_count();
 // per-block fp64 partial sums of squares of X (rows x cols); returns the block count

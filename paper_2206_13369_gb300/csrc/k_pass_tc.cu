@@ -1018,19 +1018,21 @@ bool launch_pass_tc(const PassArgs<float> &p, int *err, cudaStream_t st)
 // (nothing launched) when an operand does not meet the TMA rules.
 int gpu_sm_count() { return sm_count(); }
 
-int prod_tc_ctas(int P, int K, int max_splits)
+int prod_tc_ctas(int P, int K, int max_splits, int max_ctas)
 {
-    // about one CTA per SM, at least 4 stages per CTA
+    // about one CTA per SM (or max_ctas), at least 4 stages per CTA
     const int tiles = (P + PP_M - 1) / PP_M;
     const int total = (K + PP_K - 1) / PP_K;
-    int splits = std::max(1, std::min({sm_count() / tiles, max_splits, std::max(1, total / 4)}));
+    const int budget = max_ctas > 0 ? std::min(max_ctas, sm_count()) : sm_count();
+    int splits = std::max(1, std::min({budget / tiles, max_splits, std::max(1, total / 4)}));
     const int per = (total + splits - 1) / splits;
     splits = (total + per - 1) / per;
     return tiles * splits;
 }
 
 int launch_prod_tc(int tn, int P, int K, const float *M, int64_t ldm, const float *B, int64_t ldb, int bcols_max,
-                   const int *kdyn, float *part, int64_t ldc, int64_t slice, int max_splits, int *err, cudaStream_t st)
+                   const int *kdyn, float *part, int64_t ldc, int64_t slice, int max_splits, int *err, cudaStream_t st,
+                   int max_ctas)
 {
     if (P < 1 || K < 1 || bcols_max < 1 || bcols_max > PP_NB) return 0;
     ProdMaps maps;
@@ -1050,7 +1052,7 @@ int launch_prod_tc(int tn, int P, int K, const float *M, int64_t ldm, const floa
     }
     const int tiles = (P + PP_M - 1) / PP_M;
     const int total = (K + PP_K - 1) / PP_K;
-    const int splits = prod_tc_ctas(P, K, max_splits) / tiles;
+    const int splits = prod_tc_ctas(P, K, max_splits, max_ctas) / tiles;
     const int per = (total + splits - 1) / splits;
     ProdArgs a;
     a.P = P;

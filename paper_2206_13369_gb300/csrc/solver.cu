@@ -712,14 +712,15 @@ void prod_y(SvdWork<T> &w, int m, int nc, const T *Mx, int64_t ldx, const T *Om,
 
 template <typename T>
 void prod_z(SvdWork<T> &w, int m, int nc, const T *Mx, int64_t ldx, const T *Q, int64_t ldq, const int *kdyn,
-            cudaStream_t st, T *out = nullptr)
+            cudaStream_t st, T *out = nullptr, int max_ctas = 0)
 {
-    // Z = M^T Q (nc x k), K = m long (tensor cores as for Y), into w.Z or out
+    // Z = M^T Q (nc x k), K = m long (tensor cores as for Y), into w.Z or out;
+    // max_ctas > 0 caps the tensor-core grid (a product beside other kernels)
     T *Zo = out != nullptr ? out : w.Z;
     if constexpr (std::is_same<T, float>::value) {
         if (w.tc && ldq == w.KM) {
             const int sp = launch_prod_tc(1, nc, m, Mx, ldx, Q, ldq, w.KM, kdyn, w.Zpart, w.KM, (int64_t)nc * w.KM,
-                                          64, w.err, st);
+                                          64, w.err, st, max_ctas);
             if (sp > 0) {
                 launch_reduce_partial<float>(w.Zpart, sp, nc, w.KM, Zo, w.KM, nullptr, kdyn, st);
                 return;
@@ -839,6 +840,15 @@ bool two_stream_fits(const SvdWork<float> &w, int nc, int m)
     return 4 * prod_tc_ctas(nc, m, 64) < 3 * gpu_sm_count();
 }
 
+// the CTA budget of Z' on the tensor cores beside the other stream's chain:
+// where its usual grid would fill three quarters of the SMs or more, three
+// quarters of them, so that the chain's kernels find free SMs
+int zp_ctas(const SvdWork<float> &w, int nc, int m)
+{
+    if (!w.tc || two_stream_fits(w, nc, m)) return 0;
+    return 3 * gpu_sm_count() / 4 - 1;
+}
+
 // The subspace SVD of one iteration (one range pass, fp32) on two streams.
 // With Q_Y = Y R_Y^{-1} the CholeskyQR2 of Y = M Omega, Z = M^T Q_Y equals
 // (M^T Y) R_Y^{-1}, so Z' = M^T Y starts on the second stream as soon as Y
@@ -864,7 +874,7 @@ void subspace_svd_iter(cpcp_context *h, SvdWork<float> &w, int m, int nc, const 
     order_after(h, ax, st, 0);
     // (the sub-interval timers only open with profile = 2, where ax is the solve stream)
     tp = h->timer.open_sub(DETAIL_PROD_M);
-    prod_z<float>(w, m, nc, Mx, ldx, w.Y, KM, kdyn, ax, w.Zp);  // Z' = M^T Y
+    prod_z<float>(w, m, nc, Mx, ldx, w.Y, KM, kdyn, ax, w.Zp, ax != st ? zp_ctas(w, nc, m) : 0);  // Z' = M^T Y
     h->timer.close(tp);
     if (ax != st) CK(cudaEventRecord(h->ev_aux[1], ax));
     // programmatic dependent launch where a kernel follows a kernel of the
@@ -1251,8 +1261,7 @@ void one_iteration(cpcp_context *h, SolveState<T> &s, SvdWork<T> &w, int level, 
     h->timer.in_iter = true;
     bool two = false;
     if constexpr (std::is_same<T, float>::value)
-        two = !s.bf16 && o.q == 1 && h->opt.svd_serial != 1 && w.KM <= kmax_small<float>() &&
-              (h->opt.svd_serial == 2 || two_stream_fits(w, tr.nh, s.m));
+        two = !s.bf16 && o.q == 1 && h->opt.svd_serial != 1 && w.KM <= kmax_small<float>();
     if constexpr (std::is_same<T, float>::value) {
         if (two) subspace_svd_iter(h, w, s.m, tr.nh, Mx, ldx, s.Om, &s.ctrl->k, s.ctrl, w.Us, s.ctrl);
     }
