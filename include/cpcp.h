@@ -185,10 +185,10 @@ typedef struct {
                               orthogonal), and the solve stream forms Z = Z' R_Y^{-1} (equal to
                               M^T Q_Y); with 0, Q_Y, Q_Z and the next start block are also formed
                               on the second stream, beside the factorisation of Z and the core
-                              Jacobi SVD; with 2 they stay on the solve stream.  0 takes the two
-                              streams only where M^T Y leaves a quarter of the SMs free (always
-                              with SIMT products; with tensor-core products, sized to about one CTA
-                              per SM, only for short outputs), else the order of 1.  The rounding
+                              Jacobi SVD; with 2 they stay on the solve stream.  Where M^T Y on the
+                              tensor cores (sized to about one CTA per SM) would fill three quarters
+                              of the SMs or more, it runs on three quarters of them beside the other
+                              chain.  The rounding
                               of Z differs from the in-order form by a factor of the equilibrated
                               condition number of Y (near 1 once the subspace is warm-started).
                               With profile = 2 everything runs in order.  Other values:

@@ -829,11 +829,12 @@ void orth_factor_only(cpcp_context *h, SvdWork<float> &w, int rows, const float 
     launch_cqr_pass2(rows, X, w.Q1, KM, kdyn, Rt, Rti, well, w.Gpart, w.G2, w.R2, w.R2i, w.ticket, stats, st);
 }
 
-// Whether the iteration's SVD runs on two streams by default: Z' = M^T Y
-// must leave room beside it.  On the tensor cores it is sized to about one CTA
-// per SM, and where that fills three quarters of the GPU or more the kernels
-// beside it push it into a second wave (measured on the 19200 x 400 video
-// shape: 31.2 against 27.8 ms per solve), so the SVD runs in order there.
+// Whether Z' = M^T Y leaves room beside it on its usual grid.  On the tensor
+// cores it is sized to about one CTA per SM, and where that fills three
+// quarters of the GPU or more the kernels beside it push it into a second
+// wave (measured on the 19200 x 400 video shape: 31.2 against 27.8 ms per
+// solve with the SVD in order); its grid is then capped (zp_ctas), which
+// measured 22.6 against 26.5 ms.
 bool two_stream_fits(const SvdWork<float> &w, int nc, int m)
 {
     if (!w.tc) return true;
