@@ -264,6 +264,23 @@ def batched_cpcp(count: int, seed: int, m_range=(64, 1024), n_range=(64, 512),
     return out
 
 
+def batched_instance(seed: int, index: int, **ranges) -> dict:
+    """Instance `index` of batched_cpcp(count, seed, **ranges) (count > index),
+    built alone: the size draws of the instances before it are replayed, their
+    matrices are not."""
+    keys = ("m_range", "n_range", "rank_range", "rho_range", "obs_range")
+    defaults = dict(zip(keys, ((64, 1024), (64, 512), (2, 20), (0.05, 0.20), (0.5, 1.0))))
+    rg = {k: ranges.get(k, defaults[k]) for k in keys}
+    rng = np.random.default_rng(seed)
+    for i in range(index + 1):
+        m = int(rng.integers(rg["m_range"][0], rg["m_range"][1] + 1))
+        n = int(rng.integers(rg["n_range"][0], rg["n_range"][1] + 1))
+        r = int(rng.integers(rg["rank_range"][0], rg["rank_range"][1] + 1))
+        rho = float(rng.uniform(*rg["rho_range"]))
+        obs = float(rng.uniform(*rg["obs_range"]))
+    return planted_cpcp(m, n, r, rho, obs, seed + 1 + index, levels=_batched_levels(m, n, r))
+
+
 CONFIG_NAMES = {
     1: "pcp-200x200-r10-fp64",
     2: "cpcp-2000x2000-r50-fp32-3lv",

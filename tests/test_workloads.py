@@ -30,3 +30,13 @@ def test_hyperspectral_recipe():
 
 def test_config_names_cover_configs():
     assert set(W.CONFIG_NAMES) == {1, 2, 3, 4, 5, 6}
+
+
+def test_batched_instance_matches_the_batch():
+    # one instance built alone equals the same instance of the whole batch
+    batch = W.batched_cpcp(6, 4000)
+    for i in (0, 5):
+        q = W.batched_instance(4000, i)
+        assert q["D"].shape == batch[i]["D"].shape and q["levels"] == batch[i]["levels"]
+        assert np.array_equal(q["D"], batch[i]["D"]) and np.array_equal(q["mask"], batch[i]["mask"])
+        assert q["lam"] == batch[i]["lam"] and q["mu"] == batch[i]["mu"]
